@@ -1,0 +1,865 @@
+/*
+ * b3d_oracle.c - plain FP64 CPU oracle for the Bayes3D render-and-score path
+ * (Gothoskar et al., "Bayes3D: fast learning and inference in structured generative
+ * models of 3D objects and scenes", arXiv 2312.08715).
+ *
+ * TEST INFRASTRUCTURE. Only the tests, the package smoke check and the benchmark's CPU
+ * baseline leg load this library. It shares no code, header, table or constant with the
+ * CUDA library; the CUDA path never links or calls it.
+ *
+ * Every function is the plain definition, written for a reader to check against the
+ * paper by eye: no blocking, no culling, no incremental tricks. Where the paper is silent
+ * the reading used is stated at the function. FP64 throughout.
+ *
+ * Conventions
+ *   - Poses are row-major 4x4 cam_from_obj: p_cam = R p_obj + t, R = P[0..2,0..2],
+ *     t = (P[3], P[7], P[11]). OpenCV camera axes: x right, y down, z forward.
+ *   - Pixel (u, v) is column u, row v; its ray passes through the pixel centre:
+ *     r(u,v) = ((u + 1/2 - cx)/fx, (v + 1/2 - cy)/fy, 1). Depth is camera z.
+ *   - A scene is a list of objects; object o owns faces f_off[o]..f_off[o+1]-1 and
+ *     vertices v_off[o]..v_off[o+1]-1 (face indices are local to the object). The global
+ *     triangle id of face f of object o is f_off[o] + f.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int32_t width, height;
+    double fx, fy, cx, cy, near_z, far_z;
+} orc_camera;
+
+typedef struct {
+    int32_t kind;        /* 0: inlier ball of radius r; 1: isotropic 3D Gaussian, sd sigma */
+    double radius;       /* r (kind 0) or sigma (kind 1), metres */
+    double p_outlier;
+    int32_t half_window; /* w: window (2w+1)^2 pixels */
+    double volume;       /* V of Eq. 1; <= 0 selects the camera frustum volume */
+    double norm;         /* normaliser replacing 1/|y| of Eq. 1; <= 0 selects (2w+1)^2 */
+    int32_t miss_mode;   /* 0: a pixel with no triangle renders at far; 1: it has no point */
+} orc_lik;
+
+typedef struct {
+    int32_t n_obj;
+    const int64_t *v_off;  /* [n_obj + 1] */
+    const int64_t *f_off;  /* [n_obj + 1] */
+    const double *verts;   /* [v_off[n_obj], 3] object frame */
+    const int32_t *faces;  /* [f_off[n_obj], 3] object-local vertex indices */
+    const double *poses;   /* [n_obj, 16] cam_from_obj */
+} orc_scene;
+
+typedef struct {
+    int32_t n_per_axis;
+    double step;
+    int32_t rot_kind;    /* 0 Fibonacci-sphere set, 1 perturbation set */
+    int32_t n_rot;
+    double rot_max;
+} orc_stage;
+
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+#define ORC_ENOMEM (-2)
+
+static const double ORC_PI = 3.14159265358979323846;
+
+/* ------------------------------------------------------------------------------------ */
+/* Camera geometry                                                                        */
+/* ------------------------------------------------------------------------------------ */
+
+static void pixel_ray(const orc_camera *cam, int u, int v, double r[3]) {
+    r[0] = ((double)u + 0.5 - cam->cx) / cam->fx;
+    r[1] = ((double)v + 0.5 - cam->cy) / cam->fy;
+    r[2] = 1.0;
+}
+
+/* V of Eq. 1, "the volume of the visible scene". Reading: the camera frustum between the
+ * near and far planes. A slice at depth z spans (W z / fx) x (H z / fy), so
+ * V = (W H / (fx fy)) * (far^3 - near^3) / 3. */
+double orc_frustum_volume(const orc_camera *cam) {
+    double a = (double)cam->width * (double)cam->height / (cam->fx * cam->fy);
+    return a * (cam->far_z * cam->far_z * cam->far_z - cam->near_z * cam->near_z * cam->near_z) / 3.0;
+}
+
+static void apply_pose(const double *P, const double *p, double out[3]) {
+    for (int i = 0; i < 3; ++i)
+        out[i] = P[4 * i + 0] * p[0] + P[4 * i + 1] * p[1] + P[4 * i + 2] * p[2] + P[4 * i + 3];
+}
+
+static void cross3(const double a[3], const double b[3], double o[3]) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* ------------------------------------------------------------------------------------ */
+/* Depth renderer (Alg. 1, DepthRenderer; the depth buffer of Sec. III-A (iii))           */
+/* ------------------------------------------------------------------------------------ */
+/*
+ * Standard z-buffer over every triangle of every scene object.
+ * Readings:
+ *   - coverage: the pixel centre is inside the screen-space triangle or on its boundary
+ *     (all three edge functions, oriented by the sign of the triangle's signed area, are
+ *     >= 0). Triangles with zero screen area cover nothing.
+ *   - depth: camera z of the intersection of the pixel-centre ray with the triangle's
+ *     plane, z = (n . a) / (n . r).
+ *   - a triangle with any vertex at z < near is dropped; a fragment with z > far is dropped.
+ *   - the nearest fragment wins; equal depths go to the smaller global triangle id.
+ *   - a pixel with no fragment has depth = far and triangle id -1.
+ *
+ * Ambiguity flags (optional, flags != NULL), used to make FP32-vs-FP64 parity well posed:
+ *   bit 0: the triangle id at this pixel could change under a perturbation of the edge
+ *          tests by edge_tol_px pixels or of depths by z_tol_rel (relative);
+ *   bit 1: additionally, the depth at this pixel could change by more than z_tol_rel.
+ * These are computed by a second pass over the triangles; they do not alter the image.
+ */
+typedef struct {
+    double a[3], b[3], c[3];     /* camera-frame vertices */
+    double su[3], sv[3];         /* screen coordinates */
+    double area;                 /* signed screen area x2 */
+    double n[3];                 /* (b - a) x (c - a) */
+} tri_cam;
+
+static int setup_tri(const orc_camera *cam, const double *P, const double *verts, const int32_t *f, tri_cam *t) {
+    apply_pose(P, verts + 3 * (int64_t)f[0], t->a);
+    apply_pose(P, verts + 3 * (int64_t)f[1], t->b);
+    apply_pose(P, verts + 3 * (int64_t)f[2], t->c);
+    const double *p[3] = {t->a, t->b, t->c};
+    for (int k = 0; k < 3; ++k) {
+        if (!(p[k][2] >= cam->near_z)) return 0;
+        t->su[k] = cam->fx * p[k][0] / p[k][2] + cam->cx;
+        t->sv[k] = cam->fy * p[k][1] / p[k][2] + cam->cy;
+    }
+    t->area = (t->su[1] - t->su[0]) * (t->sv[2] - t->sv[0]) - (t->sv[1] - t->sv[0]) * (t->su[2] - t->su[0]);
+    if (t->area == 0.0) return 0;
+    double e1[3] = {t->b[0] - t->a[0], t->b[1] - t->a[1], t->b[2] - t->a[2]};
+    double e2[3] = {t->c[0] - t->a[0], t->c[1] - t->a[1], t->c[2] - t->a[2]};
+    cross3(e1, e2, t->n);
+    return 1;
+}
+
+/* Smallest signed distance (pixels) from the pixel centre to the three edges, positive
+ * inside. Covered iff >= 0. */
+static double coverage_margin(const tri_cam *t, double pu, double pv) {
+    double s = t->area > 0 ? 1.0 : -1.0;
+    double m = INFINITY;
+    for (int k = 0; k < 3; ++k) {
+        int k1 = (k + 1) % 3;
+        double du = t->su[k1] - t->su[k], dv = t->sv[k1] - t->sv[k];
+        double e = du * (pv - t->sv[k]) - dv * (pu - t->su[k]);
+        double d = s * e / sqrt(du * du + dv * dv);
+        if (d < m) m = d;
+    }
+    return m;
+}
+
+static double plane_depth(const tri_cam *t, const double r[3]) {
+    double nr = dot3(t->n, r);
+    if (nr == 0.0) return INFINITY;
+    return dot3(t->n, t->a) / nr;
+}
+
+static const double *object_pose(const orc_scene *sc, int o, int32_t slot, const double *slot_pose) {
+    if (o == slot && slot_pose) return slot_pose;
+    return sc->poses + 16 * (int64_t)o;
+}
+
+static void pixel_range(double lo, double hi, double tol, int n, int *a, int *b) {
+    double fa = ceil(lo - 0.5 - tol), fb = floor(hi - 0.5 + tol);
+    if (fa < 0) fa = 0;
+    if (fb > n - 1) fb = n - 1;
+    if (!(fa <= fb)) { *a = 1; *b = 0; return; }
+    *a = (int)fa;
+    *b = (int)fb;
+}
+
+int orc_render(const orc_camera *cam, const orc_scene *sc, int32_t slot, const double *slot_pose,
+               double edge_tol_px, double z_tol_rel, double *depth, int32_t *triid, uint8_t *flags) {
+    if (!cam || !sc || !depth || !triid || cam->width <= 0 || cam->height <= 0) return ORC_EINVAL;
+    const int W = cam->width, H = cam->height;
+    const int64_t P = (int64_t)W * H;
+    double *best_z = malloc(sizeof(double) * P), *second_z = malloc(sizeof(double) * P);
+    double *best_m = malloc(sizeof(double) * P);
+    if (!best_z || !second_z || !best_m) { free(best_z); free(second_z); free(best_m); return ORC_ENOMEM; }
+    for (int64_t i = 0; i < P; ++i) { best_z[i] = INFINITY; second_z[i] = INFINITY; best_m[i] = 0; triid[i] = -1; }
+    const double tol = flags ? edge_tol_px : 0.0;
+
+    for (int pass = 0; pass < (flags ? 2 : 1); ++pass) {
+        if (pass == 1)
+            for (int64_t i = 0; i < P; ++i) flags[i] = 0;
+        for (int o = 0; o < sc->n_obj; ++o) {
+            const double *Po = object_pose(sc, o, slot, slot_pose);
+            const double *verts = sc->verts + 3 * sc->v_off[o];
+            for (int64_t f = sc->f_off[o]; f < sc->f_off[o + 1]; ++f) {
+                tri_cam t;
+                if (!setup_tri(cam, Po, verts, sc->faces + 3 * f, &t)) continue;
+                double umin = fmin(t.su[0], fmin(t.su[1], t.su[2])), umax = fmax(t.su[0], fmax(t.su[1], t.su[2]));
+                double vmin = fmin(t.sv[0], fmin(t.sv[1], t.sv[2])), vmax = fmax(t.sv[0], fmax(t.sv[1], t.sv[2]));
+                int x0, x1, y0, y1;
+                pixel_range(umin, umax, tol, W, &x0, &x1);
+                pixel_range(vmin, vmax, tol, H, &y0, &y1);
+                const int32_t gid = (int32_t)f;
+                for (int y = y0; y <= y1; ++y)
+                    for (int x = x0; x <= x1; ++x) {
+                        double r[3];
+                        pixel_ray(cam, x, y, r);
+                        double m = coverage_margin(&t, x + 0.5, y + 0.5);
+                        double z = plane_depth(&t, r);
+                        if (!(z <= cam->far_z)) continue;
+                        const int64_t i = (int64_t)y * W + x;
+                        if (pass == 0) {
+                            if (m < 0) continue;
+                            if (z < best_z[i] || (z == best_z[i] && gid < triid[i])) {
+                                second_z[i] = best_z[i];
+                                best_z[i] = z;
+                                triid[i] = gid;
+                                best_m[i] = m;
+                            } else if (z < second_z[i]) {
+                                second_z[i] = z;
+                            }
+                        } else {
+                            /* a triangle other than the winner whose coverage is marginal and
+                             * that is not behind the winner could take the pixel */
+                            if (gid == triid[i] || fabs(m) >= tol) continue;
+                            double zb = triid[i] >= 0 ? best_z[i] : cam->far_z;
+                            if (z <= zb * (1.0 + z_tol_rel)) {
+                                flags[i] |= 1;
+                                if (fabs(z - zb) > z_tol_rel * zb) flags[i] |= 2;
+                            }
+                        }
+                    }
+            }
+        }
+    }
+    for (int64_t i = 0; i < P; ++i) {
+        if (triid[i] >= 0) {
+            depth[i] = best_z[i];
+            if (flags) {
+                /* the winner itself barely covers the pixel: the next candidate takes over */
+                if (best_m[i] < tol) {
+                    double alt = isinf(second_z[i]) ? cam->far_z : second_z[i];
+                    flags[i] |= 1;
+                    if (fabs(alt - best_z[i]) > z_tol_rel * best_z[i]) flags[i] |= 2;
+                }
+                /* near-equal depths: the id decided by the depth test could swap */
+                if (second_z[i] - best_z[i] <= z_tol_rel * best_z[i]) flags[i] |= 1;
+            }
+        } else {
+            depth[i] = cam->far_z;
+        }
+    }
+    free(best_z); free(second_z); free(best_m);
+    return ORC_OK;
+}
+
+/* Depth with visibility held fixed: pixel i keeps triangle triid[i] (rendered with the
+ * scene's poses except slot at slot_pose); its depth is the intersection of the pixel ray
+ * with that triangle's plane, whether or not the centre is still inside the triangle.
+ * Used to check the fixed-visibility gradient by central differences. */
+int orc_render_fixed(const orc_camera *cam, const orc_scene *sc, int32_t slot, const double *slot_pose,
+                     const int32_t *triid, double *depth) {
+    if (!cam || !sc || !triid || !depth) return ORC_EINVAL;
+    const int W = cam->width, H = cam->height;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const int64_t i = (int64_t)y * W + x;
+            int32_t g = triid[i];
+            if (g < 0) { depth[i] = cam->far_z; continue; }
+            int o = 0;
+            while (o + 1 < sc->n_obj && g >= sc->f_off[o + 1]) ++o;
+            const double *Po = object_pose(sc, o, slot, slot_pose);
+            const double *verts = sc->verts + 3 * sc->v_off[o];
+            const int32_t *f = sc->faces + 3 * (int64_t)g;
+            double a[3], b[3], c[3], e1[3], e2[3], n[3], r[3];
+            apply_pose(Po, verts + 3 * (int64_t)f[0], a);
+            apply_pose(Po, verts + 3 * (int64_t)f[1], b);
+            apply_pose(Po, verts + 3 * (int64_t)f[2], c);
+            for (int k = 0; k < 3; ++k) { e1[k] = b[k] - a[k]; e2[k] = c[k] - a[k]; }
+            cross3(e1, e2, n);
+            pixel_ray(cam, x, y, r);
+            depth[i] = dot3(n, a) / dot3(n, r);
+        }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Windowed robust likelihood (Eq. 1 with the window truncation of Sec. III-B)            */
+/* ------------------------------------------------------------------------------------ */
+/*
+ * For every observed pixel i with finite depth > 0, with observed point
+ * qt_i = depth_obs[i] * r_i and rendered points q_j = depth_ren[j] * r_j over the
+ * (2w+1)^2 pixels j around i that lie inside the image:
+ *   kind 0:  n_i = #{ j : |qt_i - q_j|^2 <= r^2 },
+ *            l_i = log( p_out / V + (1 - p_out) * n_i / (K * (4/3) pi r^3) )
+ *   kind 1:  S_i = sum_j (2 pi s^2)^(-3/2) exp(-|qt_i - q_j|^2 / (2 s^2)),
+ *            l_i = log( p_out / V + (1 - p_out) * S_i / K )
+ * Readings: the inlier kernel of Eq. 1 is the uniform density of a ball of radius r
+ * (kind 0) or an isotropic Gaussian with per-coordinate standard deviation s (kind 1);
+ * the normaliser 1/|y| becomes 1/K with K = (2w+1)^2 (window slots outside the image count
+ * in K and contribute nothing); the prefactor sigma/sigma_max of Eq. 1 is left out (a
+ * constant for fixed noise parameters); rendered pixels without a triangle sit at the far
+ * plane (miss_mode 0) or carry no point (miss_mode 1). Pixels not scored get NaN.
+ *
+ * Outputs (each optional): ell[H*W], count[H*W] (kind 0 n_i), ssum[H*W] (kind 1 S_i).
+ * *n_border counts window pairs with |d^2 - r^2| <= border_tol * r^2 (kind 0).
+ */
+static void lik_constants(const orc_camera *cam, const orc_lik *lk, double *V, double *K) {
+    int w = lk->half_window;
+    *V = lk->volume > 0 ? lk->volume : orc_frustum_volume(cam);
+    *K = lk->norm > 0 ? lk->norm : (double)((2 * w + 1) * (2 * w + 1));
+}
+
+int orc_pixel_loglik(const orc_camera *cam, const orc_lik *lk, const double *depth_ren, const int32_t *triid_ren,
+                     const double *depth_obs, double border_tol, double *ell, int32_t *count, double *ssum,
+                     int64_t *n_border) {
+    if (!cam || !lk || !depth_ren || !depth_obs || lk->half_window < 0 || !(lk->radius > 0)) return ORC_EINVAL;
+    if (lk->miss_mode == 1 && !triid_ren) return ORC_EINVAL;
+    const int W = cam->width, H = cam->height, w = lk->half_window;
+    double V, K;
+    lik_constants(cam, lk, &V, &K);
+    const double r = lk->radius, r2 = r * r;
+    const double ball = 4.0 / 3.0 * ORC_PI * r * r * r;
+    const double gnorm = pow(2.0 * ORC_PI * r2, -1.5);
+    int64_t nb = 0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const int64_t i = (int64_t)y * W + x;
+            double d_obs = depth_obs[i];
+            if (!(d_obs > 0) || !isfinite(d_obs)) {
+                if (ell) ell[i] = NAN;
+                if (count) count[i] = 0;
+                if (ssum) ssum[i] = 0;
+                continue;
+            }
+            double ri[3], qt[3];
+            pixel_ray(cam, x, y, ri);
+            for (int k = 0; k < 3; ++k) qt[k] = d_obs * ri[k];
+            int n = 0;
+            double S = 0.0;
+            for (int dy = -w; dy <= w; ++dy)
+                for (int dx = -w; dx <= w; ++dx) {
+                    int xj = x + dx, yj = y + dy;
+                    if (xj < 0 || xj >= W || yj < 0 || yj >= H) continue;
+                    const int64_t j = (int64_t)yj * W + xj;
+                    if (lk->miss_mode == 1 && triid_ren[j] < 0) continue;
+                    double rj[3], q[3];
+                    pixel_ray(cam, xj, yj, rj);
+                    for (int k = 0; k < 3; ++k) q[k] = depth_ren[j] * rj[k];
+                    double d2 = (qt[0] - q[0]) * (qt[0] - q[0]) + (qt[1] - q[1]) * (qt[1] - q[1]) +
+                                (qt[2] - q[2]) * (qt[2] - q[2]);
+                    if (lk->kind == 0) {
+                        if (d2 <= r2) ++n;
+                        if (fabs(d2 - r2) <= border_tol * r2) ++nb;
+                    } else {
+                        S += gnorm * exp(-d2 / (2.0 * r2));
+                    }
+                }
+            double li = lk->kind == 0 ? log(lk->p_outlier / V + (1.0 - lk->p_outlier) * n / (K * ball))
+                                      : log(lk->p_outlier / V + (1.0 - lk->p_outlier) * S / K);
+            if (ell) ell[i] = li;
+            if (count) count[i] = n;
+            if (ssum) ssum[i] = S;
+        }
+    if (n_border) *n_border = nb;
+    return ORC_OK;
+}
+
+/* l_i as a function of the inlier count n (kind 0). */
+static double ell_of_count(const orc_camera *cam, const orc_lik *lk, int n) {
+    double V, K;
+    lik_constants(cam, lk, &V, &K);
+    const double r = lk->radius, ball = 4.0 / 3.0 * ORC_PI * r * r * r;
+    return log(lk->p_outlier / V + (1.0 - lk->p_outlier) * n / (K * ball));
+}
+
+/* Largest change of one observed pixel's l_i that moving ONE rendered point of its window
+ * can cause: a count step 0 <-> 1 (kind 0, the largest step since l is concave in n) or
+ * one Gaussian term between 0 and its peak (kind 1). */
+static double pixel_jump(const orc_camera *cam, const orc_lik *lk) {
+    double V, K;
+    lik_constants(cam, lk, &V, &K);
+    const double r = lk->radius;
+    double top = lk->kind == 0 ? (1.0 - lk->p_outlier) / (K * (4.0 / 3.0 * ORC_PI * r * r * r))
+                               : (1.0 - lk->p_outlier) * pow(2.0 * ORC_PI * r * r, -1.5) / K;
+    return log(lk->p_outlier / V + top) - log(lk->p_outlier / V);
+}
+
+/* Largest change of l_i when k of its window pairs may each flip in or out of the ball,
+ * from the current count n (kind 0). */
+static double count_flip_bound(const orc_camera *cam, const orc_lik *lk, int n, int k) {
+    const int w = lk->half_window, slots = (2 * w + 1) * (2 * w + 1);
+    int hi = n + k > slots ? slots : n + k, lo = n - k < 0 ? 0 : n - k;
+    double l = ell_of_count(cam, lk, n);
+    return fmax(ell_of_count(cam, lk, hi) - l, l - ell_of_count(cam, lk, lo));
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Per-hypothesis log-likelihood: render the scene with object `slot` at each pose, then */
+/* sum l_i over the scored pixels (the product over i of Eq. 1, in logs).                */
+/* ------------------------------------------------------------------------------------ */
+/*
+ * Outputs per hypothesis h (each optional except ll):
+ *   ll[h]     = sum_i l_i
+ *   scale[h]  = sum_i |l_i|                (the tolerance scale)
+ *   bound[h]  = largest |change of ll| that FP32-resolution decisions could cause: for
+ *               every depth-ambiguous rendered pixel (flag bit 1), one point's jump for
+ *               each observed pixel whose window contains it; plus, for kind 0, the change
+ *               of l_i when its borderline pairs (|d^2 - r^2| <= border_tol r^2) flip.
+ *   n_flag[h] = number of depth-ambiguous rendered pixels; n_border[h] = borderline pairs.
+ */
+int orc_score(const orc_camera *cam, const orc_scene *sc, int32_t slot, int64_t n_hyp, const double *poses,
+              const orc_lik *lk, const double *depth_obs, double edge_tol_px, double z_tol_rel, double border_tol,
+              double *ll, double *scale, double *bound, int32_t *n_flag, int32_t *n_border, int32_t n_threads) {
+    if (!cam || !sc || !lk || !depth_obs || !ll || n_hyp < 0 || (n_hyp > 0 && !poses)) return ORC_EINVAL;
+    if (slot < 0 || slot >= sc->n_obj) return ORC_EINVAL;
+    const int W = cam->width, H = cam->height, w = lk->half_window;
+    const int64_t P = (int64_t)W * H;
+    const int want_flags = (bound || n_flag || n_border) ? 1 : 0;
+    const double jump = pixel_jump(cam, lk);
+    int err = ORC_OK;
+#ifdef _OPENMP
+    if (n_threads <= 0) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
+#endif
+    for (int64_t h = 0; h < n_hyp; ++h) {
+        double *depth = malloc(sizeof(double) * P), *ell = malloc(sizeof(double) * P);
+        int32_t *tid = malloc(sizeof(int32_t) * P), *cnt = malloc(sizeof(int32_t) * P);
+        uint8_t *fl = want_flags ? malloc(P) : NULL;
+        if (!depth || !ell || !tid || !cnt || (want_flags && !fl)) {
+            err = ORC_ENOMEM;
+        } else {
+            orc_render(cam, sc, slot, poses + 16 * h, edge_tol_px, z_tol_rel, depth, tid, fl);
+            int64_t nb = 0;
+            orc_pixel_loglik(cam, lk, depth, tid, depth_obs, border_tol, ell, cnt, NULL, &nb);
+            double s = 0, a = 0, bd = 0;
+            int32_t nf = 0;
+            for (int64_t i = 0; i < P; ++i) {
+                if (isnan(ell[i])) continue;
+                s += ell[i];
+                a += fabs(ell[i]);
+            }
+            if (want_flags) {
+                for (int y = 0; y < H; ++y)
+                    for (int x = 0; x < W; ++x) {
+                        if (!(fl[(int64_t)y * W + x] & 2)) continue;
+                        ++nf;
+                        for (int dy = -w; dy <= w; ++dy)
+                            for (int dx = -w; dx <= w; ++dx) {
+                                int xi = x + dx, yi = y + dy;
+                                if (xi < 0 || xi >= W || yi < 0 || yi >= H) continue;
+                                if (!isnan(ell[(int64_t)yi * W + xi])) bd += jump;
+                            }
+                    }
+                if (lk->kind == 0 && nb > 0) {
+                    /* recount borderline pairs per observed pixel to size their steps */
+                    const double r2 = lk->radius * lk->radius;
+                    for (int y = 0; y < H; ++y)
+                        for (int x = 0; x < W; ++x) {
+                            const int64_t i = (int64_t)y * W + x;
+                            if (isnan(ell[i])) continue;
+                            double ri[3];
+                            pixel_ray(cam, x, y, ri);
+                            int k_b = 0;
+                            for (int dy = -w; dy <= w; ++dy)
+                                for (int dx = -w; dx <= w; ++dx) {
+                                    int xj = x + dx, yj = y + dy;
+                                    if (xj < 0 || xj >= W || yj < 0 || yj >= H) continue;
+                                    const int64_t j = (int64_t)yj * W + xj;
+                                    if (lk->miss_mode == 1 && tid[j] < 0) continue;
+                                    double rj[3];
+                                    pixel_ray(cam, xj, yj, rj);
+                                    double d2 = 0;
+                                    for (int k = 0; k < 3; ++k) {
+                                        double d = depth_obs[i] * ri[k] - depth[j] * rj[k];
+                                        d2 += d * d;
+                                    }
+                                    if (fabs(d2 - r2) <= border_tol * r2) ++k_b;
+                                }
+                            if (k_b > 0) bd += count_flip_bound(cam, lk, cnt[i], k_b);
+                        }
+                }
+            }
+            ll[h] = s;
+            if (scale) scale[h] = a;
+            if (bound) bound[h] = bd;
+            if (n_flag) n_flag[h] = nf;
+            if (n_border) n_border[h] = (int32_t)nb;
+        }
+        free(depth); free(ell); free(tid); free(cnt); free(fl);
+    }
+    return err;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Log-sum-exp normalisation (the categorical over C2F cells, Sec. III-B)                 */
+/* ------------------------------------------------------------------------------------ */
+/* m = max ll; Z = m + log sum_h exp(ll_h - m); logp_h = ll_h - Z. Entries equal to -inf
+ * get logp = -inf. Returns EINVAL for n <= 0 or if every entry is -inf or NaN. */
+int orc_lse(int64_t n, const double *ll, double *z_out, double *logp) {
+    if (n <= 0 || !ll || !z_out) return ORC_EINVAL;
+    double m = -INFINITY;
+    for (int64_t h = 0; h < n; ++h)
+        if (ll[h] > m) m = ll[h];
+    if (!isfinite(m)) return ORC_EINVAL;
+    double s = 0;
+    for (int64_t h = 0; h < n; ++h) s += exp(ll[h] - m);
+    double Z = m + log(s);
+    *z_out = Z;
+    if (logp)
+        for (int64_t h = 0; h < n; ++h) logp[h] = ll[h] - Z;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Counter-based uniforms: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11)              */
+/* ------------------------------------------------------------------------------------ */
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo) {
+    __uint128_t p = (__uint128_t)a * (__uint128_t)b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t hi0, lo0, hi1, lo1;
+        mulhilo64(0xD2E7470EE14C6C93ULL, x0, &hi0, &lo0);
+        mulhilo64(0xCA5A826395121157ULL, x2, &hi1, &lo1);
+        uint64_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += 0x9E3779B97F4A7C15ULL;
+        k1 += 0xBB67AE8584CAA73BULL;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* 24-bit uniform in [0, 1): exactly representable in FP32 and FP64 alike. */
+double orc_uniform24(uint64_t x) { return (double)(x >> 40) * (1.0 / 16777216.0); }
+
+/* Uniform number `lane` (0..3) of block (m, stage, stream) under seed. */
+static double draw_uniform(uint64_t seed, int64_t m, int32_t stage, int32_t stream, int lane) {
+    uint64_t ctr[4] = {(uint64_t)m, (uint64_t)(uint32_t)stage, (uint64_t)(uint32_t)stream, 0};
+    uint64_t key[2] = {seed, 0};
+    uint64_t out[4];
+    orc_philox4x64(ctr, key, out);
+    return orc_uniform24(out[lane]);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Categorical resampling by inverse CDF (sample the next region "with probability        */
+/* proportional to its score", Sec. III-B)                                               */
+/* ------------------------------------------------------------------------------------ */
+/* Weights w_h = exp(ll_h - max ll), S = sum w_h, CDF_k = sum_{h<=k} w_h. Draw m uses
+ * u_m = uniform24(philox(ctr = (m, stage, 0, 0), key = (seed, 0)).x0) and picks
+ * idx_m = min{ k : CDF_k > u_m S }. logq_m = ll[idx_m] - Z. margin_m = distance of u_m S
+ * to the nearer end of the chosen interval, divided by S (small = decision fragile). */
+int orc_resample(int64_t n, const double *ll, int32_t m, uint64_t seed, int32_t stage, int32_t *idx,
+                 double *logq, double *margin) {
+    if (n <= 0 || m < 0 || !ll || (m > 0 && !idx)) return ORC_EINVAL;
+    double Z;
+    if (orc_lse(n, ll, &Z, NULL) != ORC_OK) return ORC_EINVAL;
+    double mx = -INFINITY;
+    for (int64_t h = 0; h < n; ++h)
+        if (ll[h] > mx) mx = ll[h];
+    double *cdf = malloc(sizeof(double) * n);
+    if (!cdf) return ORC_ENOMEM;
+    double s = 0;
+    for (int64_t h = 0; h < n; ++h) { s += exp(ll[h] - mx); cdf[h] = s; }
+    for (int32_t k = 0; k < m; ++k) {
+        double t = draw_uniform(seed, k, stage, 0, 0) * s;
+        int64_t lo = 0, hi = n - 1;
+        while (lo < hi) { /* first index with cdf > t */
+            int64_t mid = lo + (hi - lo) / 2;
+            if (cdf[mid] > t) hi = mid; else lo = mid + 1;
+        }
+        idx[k] = (int32_t)lo;
+        if (logq) logq[k] = ll[lo] - Z;
+        if (margin) {
+            double left = lo > 0 ? cdf[lo - 1] : 0.0;
+            margin[k] = fmin(t - left, cdf[lo] - t) / s;
+        }
+    }
+    free(cdf);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Coarse-to-fine hypothesis grids (the partitions Pi_t of Sec. III-B)                   */
+/* ------------------------------------------------------------------------------------ */
+static void rot_axis_angle(const double axis[3], double angle, double *R) {
+    double n = sqrt(dot3(axis, axis));
+    double k[3] = {axis[0] / n, axis[1] / n, axis[2] / n};
+    double c = cos(angle), s = sin(angle), C = 1.0 - c;
+    R[0] = c + k[0] * k[0] * C;        R[1] = k[0] * k[1] * C - k[2] * s; R[2] = k[0] * k[2] * C + k[1] * s;
+    R[3] = k[1] * k[0] * C + k[2] * s; R[4] = c + k[1] * k[1] * C;        R[5] = k[1] * k[2] * C - k[0] * s;
+    R[6] = k[2] * k[0] * C - k[1] * s; R[7] = k[2] * k[1] * C + k[0] * s; R[8] = c + k[2] * k[2] * C;
+}
+
+/* Rotation sets (reading; the paper gives no scheme):
+ *   kind 0, Fibonacci sphere: d_k = (sqrt(1-z^2) cos(2 pi k / phi), sqrt(1-z^2) sin(2 pi k / phi), z),
+ *           z = 1 - (2k+1)/n, phi the golden ratio; R_k is the minimal-arc rotation taking
+ *           +z to d_k (pi about x for the antipode, identity for +z itself).
+ *   kind 1, perturbation: R_k = Exp(theta_k d_k) with d_k as above and
+ *           theta_k = rot_max (2 frac((k + 1/2) / phi) - 1).
+ * Output R[n, 9] row-major. */
+int orc_rotation_set(int32_t kind, int32_t n, double rot_max, double *R) {
+    if (n <= 0 || !R || (kind != 0 && kind != 1)) return ORC_EINVAL;
+    const double phi = (1.0 + sqrt(5.0)) / 2.0;
+    for (int k = 0; k < n; ++k) {
+        double z = 1.0 - (2.0 * k + 1.0) / n;
+        double rho = sqrt(fmax(0.0, 1.0 - z * z));
+        double ang = 2.0 * ORC_PI * k / phi;
+        double d[3] = {rho * cos(ang), rho * sin(ang), z};
+        double *Rk = R + 9 * k;
+        if (kind == 0) {
+            double ez[3] = {0, 0, 1}, ax[3];
+            cross3(ez, d, ax);
+            double sn = sqrt(dot3(ax, ax));
+            if (sn == 0.0) {
+                if (z > 0) { double I[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}; memcpy(Rk, I, sizeof I); }
+                else { double X[3] = {1, 0, 0}; rot_axis_angle(X, ORC_PI, Rk); }
+            } else {
+                rot_axis_angle(ax, atan2(sn, z), Rk);
+            }
+        } else {
+            double fr = (k + 0.5) / phi;
+            fr -= floor(fr);
+            double theta = rot_max * (2.0 * fr - 1.0);
+            if (theta == 0.0) { double I[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}; memcpy(Rk, I, sizeof I); }
+            else rot_axis_angle(d, theta, Rk);
+        }
+    }
+    return ORC_OK;
+}
+
+/* Grid offset of index i on an axis of n points with spacing step: odd n is centred
+ * ((i - (n-1)/2) step); even n puts the centre at i = n/2 ((i - n/2) step). */
+static double grid_offset(int i, int n, double step) {
+    return (n % 2 ? (i - (n - 1) / 2) : (i - n / 2)) * step;
+}
+
+/* Hypothesis h = ((ir * n + ix) * n + iy) * n + iz of one stage:
+ *   R_h = R_c R_ir        (rotation sets act in the object frame)
+ *   t_h = t_c + G (o_ix, o_iy, o_iz)   (G: grid frame rotation, cam_from_grid)
+ * Output poses[n^3 * n_rot, 16]. */
+int orc_expand(const double *centre, const double *G, int32_t n, double step, const double *rotset,
+               int32_t n_rot, double *poses) {
+    if (!centre || !G || !rotset || !poses || n <= 0 || n_rot <= 0) return ORC_EINVAL;
+    int64_t h = 0;
+    for (int ir = 0; ir < n_rot; ++ir)
+        for (int ix = 0; ix < n; ++ix)
+            for (int iy = 0; iy < n; ++iy)
+                for (int iz = 0; iz < n; ++iz, ++h) {
+                    const double *Rk = rotset + 9 * ir;
+                    double *P = poses + 16 * h;
+                    double o[3] = {grid_offset(ix, n, step), grid_offset(iy, n, step), grid_offset(iz, n, step)};
+                    for (int a = 0; a < 3; ++a) {
+                        for (int b = 0; b < 3; ++b)
+                            P[4 * a + b] = centre[4 * a + 0] * Rk[0 * 3 + b] + centre[4 * a + 1] * Rk[1 * 3 + b] +
+                                           centre[4 * a + 2] * Rk[2 * 3 + b];
+                        P[4 * a + 3] = centre[4 * a + 3] + G[3 * a + 0] * o[0] + G[3 * a + 1] * o[1] + G[3 * a + 2] * o[2];
+                    }
+                    P[12] = 0; P[13] = 0; P[14] = 0; P[15] = 1;
+                }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Coarse-to-fine enumeration (Sec. III-B), one object                                    */
+/* ------------------------------------------------------------------------------------ */
+/*
+ * For stage t = 0..T-1: expand the stage grid around centre_t, score every hypothesis
+ * (scoring strategy: one point per cell, its centre, weight 1), draw M cells by
+ * orc_resample(seed, stage t), and take as centre_{t+1} the drawn cell with the highest
+ * ll (ties to the smaller hypothesis index). After the last stage each particle is its
+ * drawn cell's pose with a uniform translation jitter inside the cell:
+ * t += G ((u0 - 1/2) s, (u1 - 1/2) s, (u2 - 1/2) s), u from philox(ctr = (m, T, 1, 0)).
+ *   logw_m = ll_T(idx_m)  (score of the drawn cell)
+ *   logq_m = ll_T(idx_m) - Z_T - 3 log(s_T)  (categorical x uniform-in-cell density)
+ * Optional diagnostics: centres[T,16], zs[T], idx_all[T, M].
+ */
+int orc_enumerate_c2f(const orc_camera *cam, const orc_scene *sc, int32_t slot, const double *centre0,
+                      const double *G, const orc_lik *lk, const double *depth_obs, int32_t n_stages,
+                      const orc_stage *stages, int32_t m, uint64_t seed, double *particles, double *logw,
+                      double *logq, double *centres, double *zs, int32_t *idx_all, int32_t n_threads) {
+    if (!cam || !sc || !centre0 || !G || !lk || !depth_obs || n_stages <= 0 || !stages || m <= 0 || !particles)
+        return ORC_EINVAL;
+    double centre[16];
+    memcpy(centre, centre0, sizeof centre);
+    int err = ORC_OK;
+    int32_t *idx = malloc(sizeof(int32_t) * m);
+    double *poses = NULL, *ll = NULL, *rot = NULL;
+    for (int t = 0; t < n_stages && err == ORC_OK; ++t) {
+        const orc_stage *st = &stages[t];
+        int64_t nh = (int64_t)st->n_per_axis * st->n_per_axis * st->n_per_axis * st->n_rot;
+        free(poses); free(ll); free(rot);
+        poses = malloc(sizeof(double) * 16 * nh);
+        ll = malloc(sizeof(double) * nh);
+        rot = malloc(sizeof(double) * 9 * st->n_rot);
+        if (!poses || !ll || !rot || !idx) { err = ORC_ENOMEM; break; }
+        if (centres) memcpy(centres + 16 * t, centre, sizeof centre);
+        if ((err = orc_rotation_set(st->rot_kind, st->n_rot, st->rot_max, rot)) != ORC_OK) break;
+        if ((err = orc_expand(centre, G, st->n_per_axis, st->step, rot, st->n_rot, poses)) != ORC_OK) break;
+        if ((err = orc_score(cam, sc, slot, nh, poses, lk, depth_obs, 0, 0, 0, ll, NULL, NULL, NULL, NULL,
+                             n_threads)) != ORC_OK) break;
+        double Z;
+        orc_lse(nh, ll, &Z, NULL);
+        if (zs) zs[t] = Z;
+        if ((err = orc_resample(nh, ll, m, seed, t, idx, NULL, NULL)) != ORC_OK) break;
+        if (idx_all) memcpy(idx_all + (int64_t)t * m, idx, sizeof(int32_t) * m);
+        int32_t best = idx[0];
+        for (int k = 1; k < m; ++k)
+            if (ll[idx[k]] > ll[best] || (ll[idx[k]] == ll[best] && idx[k] < best)) best = idx[k];
+        if (t + 1 < n_stages) {
+            memcpy(centre, poses + 16 * (int64_t)best, sizeof centre);
+        } else {
+            const double s = st->step;
+            for (int k = 0; k < m; ++k) {
+                double *out = particles + 16 * (int64_t)k;
+                memcpy(out, poses + 16 * (int64_t)idx[k], sizeof(double) * 16);
+                double u[3];
+                for (int l = 0; l < 3; ++l) u[l] = (draw_uniform(seed, k, n_stages, 1, l) - 0.5) * s;
+                for (int a = 0; a < 3; ++a) out[4 * a + 3] += G[3 * a + 0] * u[0] + G[3 * a + 1] * u[1] + G[3 * a + 2] * u[2];
+                if (logw) logw[k] = ll[idx[k]];
+                if (logq) logq[k] = ll[idx[k]] - Z - 3.0 * log(s);
+            }
+        }
+    }
+    free(idx); free(poses); free(ll); free(rot);
+    return err;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Gradient of the Gaussian-window log-likelihood (kind 1)                                */
+/* ------------------------------------------------------------------------------------ */
+/*
+ * With a = p_out / V, b = (1 - p_out) / K, N_ij = (2 pi s^2)^(-3/2) exp(-d_ij^2 / (2 s^2)),
+ * S_i = sum_j N_ij, p_i = a + b S_i, LL = sum_i log p_i:
+ *   dLL/ds     = sum_i (b / p_i) sum_j N_ij (d_ij^2 / s^3 - 3 / s)
+ *   dLL/dp_out = sum_i (1/V - S_i / K) / p_i
+ *   dLL/dxi    = sum_j g_j dz_j/dxi,  g_j = sum_{i : j in win(i)} (b / p_i) N_ij (qt_i - q_j).r_j / s^2
+ * Pose derivative (reading; the paper is silent): left perturbation in the camera frame,
+ * T(xi) = Exp([v, w]^) T at xi = 0, visibility held fixed, and the rendered point sliding
+ * along its pixel ray on the fixed triangle's plane (n . (z r - a) = 0):
+ *   dz_j/dv = n / (n . r_j),   dz_j/dw = (q_j x n) / (n . r_j)
+ * Only pixels whose triangle belongs to object `slot` move; misses and other objects don't.
+ * Output dpose[n_hyp, 6] ordered (v, w).
+ */
+int orc_score_grad(const orc_camera *cam, const orc_scene *sc, int32_t slot, int64_t n_hyp, const double *poses,
+                   const orc_lik *lk, const double *depth_obs, double *ll, double *dpose, double *dsigma,
+                   double *dpout, int32_t n_threads) {
+    if (!cam || !sc || !lk || lk->kind != 1 || !depth_obs || !ll || (n_hyp > 0 && !poses)) return ORC_EINVAL;
+    if (slot < 0 || slot >= sc->n_obj || !(lk->radius > 0)) return ORC_EINVAL;
+    const int W = cam->width, H = cam->height, w = lk->half_window;
+    const int64_t P = (int64_t)W * H;
+    double V, K;
+    lik_constants(cam, lk, &V, &K);
+    const double s = lk->radius, s2 = s * s;
+    const double gnorm = pow(2.0 * ORC_PI * s2, -1.5);
+    const double a = lk->p_outlier / V, b = (1.0 - lk->p_outlier) / K;
+    int err = ORC_OK;
+#ifdef _OPENMP
+    if (n_threads <= 0) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
+#endif
+    for (int64_t h = 0; h < n_hyp; ++h) {
+        double *depth = malloc(sizeof(double) * P), *inv_p = malloc(sizeof(double) * P);
+        int32_t *tid = malloc(sizeof(int32_t) * P);
+        if (!depth || !inv_p || !tid) { err = ORC_ENOMEM; free(depth); free(inv_p); free(tid); continue; }
+        const double *Ph = poses + 16 * h;
+        orc_render(cam, sc, slot, Ph, 0, 0, depth, tid, NULL);
+        double L = 0, gs = 0, gp = 0, gx[6] = {0, 0, 0, 0, 0, 0};
+        /* pass 1: p_i, and the sigma / p_out terms */
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const int64_t i = (int64_t)y * W + x;
+                inv_p[i] = 0;
+                double d_obs = depth_obs[i];
+                if (!(d_obs > 0) || !isfinite(d_obs)) continue;
+                double ri[3];
+                pixel_ray(cam, x, y, ri);
+                double S = 0, dS = 0;
+                for (int dy = -w; dy <= w; ++dy)
+                    for (int dx = -w; dx <= w; ++dx) {
+                        int xj = x + dx, yj = y + dy;
+                        if (xj < 0 || xj >= W || yj < 0 || yj >= H) continue;
+                        const int64_t j = (int64_t)yj * W + xj;
+                        if (lk->miss_mode == 1 && tid[j] < 0) continue;
+                        double rj[3], d2 = 0;
+                        pixel_ray(cam, xj, yj, rj);
+                        for (int k = 0; k < 3; ++k) {
+                            double d = d_obs * ri[k] - depth[j] * rj[k];
+                            d2 += d * d;
+                        }
+                        double N = gnorm * exp(-d2 / (2.0 * s2));
+                        S += N;
+                        dS += N * (d2 / (s2 * s) - 3.0 / s);
+                    }
+                double p = a + b * S;
+                L += log(p);
+                gs += b * dS / p;
+                gp += (1.0 / V - S / K) / p;
+                inv_p[i] = 1.0 / p;
+            }
+        /* pass 2: pose gradient through the slot object's rendered points */
+        const int64_t f0 = sc->f_off[slot], f1 = sc->f_off[slot + 1];
+        const double *verts = sc->verts + 3 * sc->v_off[slot];
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const int64_t j = (int64_t)y * W + x;
+                if (tid[j] < f0 || tid[j] >= f1) continue;
+                double rj[3], qj[3];
+                pixel_ray(cam, x, y, rj);
+                for (int k = 0; k < 3; ++k) qj[k] = depth[j] * rj[k];
+                double g = 0;
+                for (int dy = -w; dy <= w; ++dy)
+                    for (int dx = -w; dx <= w; ++dx) {
+                        int xi = x + dx, yi = y + dy;
+                        if (xi < 0 || xi >= W || yi < 0 || yi >= H) continue;
+                        const int64_t i = (int64_t)yi * W + xi;
+                        if (inv_p[i] == 0) continue;
+                        double ri[3], diff[3], d2 = 0;
+                        pixel_ray(cam, xi, yi, ri);
+                        for (int k = 0; k < 3; ++k) {
+                            diff[k] = depth_obs[i] * ri[k] - qj[k];
+                            d2 += diff[k] * diff[k];
+                        }
+                        double N = gnorm * exp(-d2 / (2.0 * s2));
+                        g += b * inv_p[i] * N * dot3(diff, rj) / s2;
+                    }
+                const int32_t *f = sc->faces + 3 * (int64_t)tid[j];
+                double A[3], B[3], C[3], e1[3], e2[3], n[3], qxn[3];
+                apply_pose(Ph, verts + 3 * (int64_t)f[0], A);
+                apply_pose(Ph, verts + 3 * (int64_t)f[1], B);
+                apply_pose(Ph, verts + 3 * (int64_t)f[2], C);
+                for (int k = 0; k < 3; ++k) { e1[k] = B[k] - A[k]; e2[k] = C[k] - A[k]; }
+                cross3(e1, e2, n);
+                double nr = dot3(n, rj);
+                cross3(qj, n, qxn);
+                for (int k = 0; k < 3; ++k) {
+                    gx[k] += g * n[k] / nr;
+                    gx[3 + k] += g * qxn[k] / nr;
+                }
+            }
+        ll[h] = L;
+        if (dpose) for (int k = 0; k < 6; ++k) dpose[6 * h + k] = gx[k];
+        if (dsigma) dsigma[h] = gs;
+        if (dpout) dpout[h] = gp;
+        free(depth); free(inv_p); free(tid);
+    }
+    return err;
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

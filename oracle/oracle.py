@@ -1,0 +1,244 @@
+"""Python wrapper of the FP64 CPU oracle (``b3d_oracle.c``).
+
+TEST INFRASTRUCTURE. Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` may import this module. The product library never imports it, and it
+shares no code with the CUDA path: it takes plain numpy arrays (float64) and the seeded
+inputs of ``paper_2312_08715_gb300.synth``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "b3d_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liborc.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP when available). Returns the library path."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Camera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_double), ("fy", C.c_double),
+                ("cx", C.c_double), ("cy", C.c_double), ("near_z", C.c_double), ("far_z", C.c_double)]
+
+
+class _Lik(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("radius", C.c_double), ("p_outlier", C.c_double),
+                ("half_window", C.c_int32), ("volume", C.c_double), ("norm", C.c_double),
+                ("miss_mode", C.c_int32)]
+
+
+class _Scene(C.Structure):
+    _fields_ = [("n_obj", C.c_int32), ("v_off", C.c_void_p), ("f_off", C.c_void_p),
+                ("verts", C.c_void_p), ("faces", C.c_void_p), ("poses", C.c_void_p)]
+
+
+class _Stage(C.Structure):
+    _fields_ = [("n_per_axis", C.c_int32), ("step", C.c_double), ("rot_kind", C.c_int32),
+                ("n_rot", C.c_int32), ("rot_max", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _lib.orc_frustum_volume.restype = C.c_double
+        _lib.orc_uniform24.restype = C.c_double
+        _lib.orc_uniform24.argtypes = [C.c_uint64]
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def camera(cam) -> _Camera:
+    return _Camera(int(cam.width), int(cam.height), float(cam.fx), float(cam.fy), float(cam.cx),
+                   float(cam.cy), float(cam.near), float(cam.far))
+
+
+def lik(kind=0, radius=0.005, p_outlier=0.01, half_window=1, volume=0.0, norm=0.0, miss_mode=0) -> _Lik:
+    return _Lik(int(kind), float(radius), float(p_outlier), int(half_window), float(volume), float(norm),
+                int(miss_mode))
+
+
+class SceneArrays:
+    """Flattened scene for the oracle: keeps the numpy buffers alive with the struct."""
+
+    def __init__(self, scene, poses=None):
+        meshes = scene.meshes
+        self.cam = camera(scene.camera)
+        self.v_off = np.cumsum([0] + [m.verts.shape[0] for m in meshes]).astype(np.int64)
+        self.f_off = np.cumsum([0] + [m.faces.shape[0] for m in meshes]).astype(np.int64)
+        self.verts = _f64(np.concatenate([m.verts for m in meshes]))
+        self.faces = np.ascontiguousarray(np.concatenate([m.faces for m in meshes]), dtype=np.int32)
+        self.poses = _f64((scene.poses if poses is None else poses).reshape(-1, 16))
+        self.st = _Scene(len(meshes), _p(self.v_off), _p(self.f_off), _p(self.verts), _p(self.faces),
+                         _p(self.poses))
+        self.H, self.W = int(scene.camera.height), int(scene.camera.width)
+
+
+def frustum_volume(cam) -> float:
+    return float(lib().orc_frustum_volume(C.byref(camera(cam))))
+
+
+def render(scene, slot=-1, slot_pose=None, edge_tol=0.0, z_tol=0.0, want_flags=False, arrays=None):
+    sa = arrays or SceneArrays(scene)
+    depth = np.empty((sa.H, sa.W), np.float64)
+    triid = np.empty((sa.H, sa.W), np.int32)
+    flags = np.empty((sa.H, sa.W), np.uint8) if want_flags else None
+    sp = _f64(slot_pose).reshape(16) if slot_pose is not None else None
+    rc = lib().orc_render(C.byref(sa.cam), C.byref(sa.st), C.c_int32(slot), _p(sp), C.c_double(edge_tol),
+                          C.c_double(z_tol), _p(depth), _p(triid), _p(flags))
+    assert rc == 0, rc
+    return (depth, triid, flags) if want_flags else (depth, triid)
+
+
+def render_fixed(scene, slot, slot_pose, triid, arrays=None):
+    sa = arrays or SceneArrays(scene)
+    depth = np.empty((sa.H, sa.W), np.float64)
+    tid = np.ascontiguousarray(triid, dtype=np.int32)
+    rc = lib().orc_render_fixed(C.byref(sa.cam), C.byref(sa.st), C.c_int32(slot), _p(_f64(slot_pose).reshape(16)),
+                                _p(tid), _p(depth))
+    assert rc == 0, rc
+    return depth
+
+
+def pixel_loglik(cam, lk: dict, depth_ren, triid_ren, depth_obs, border_tol=0.0):
+    c = camera(cam)
+    H, W = int(cam.height), int(cam.width)
+    ell = np.empty((H, W), np.float64)
+    cnt = np.empty((H, W), np.int32)
+    ss = np.empty((H, W), np.float64)
+    nb = C.c_int64(0)
+    dr = _f64(depth_ren)
+    tr = np.ascontiguousarray(triid_ren, dtype=np.int32) if triid_ren is not None else None
+    do = _f64(depth_obs)
+    rc = lib().orc_pixel_loglik(C.byref(c), C.byref(lik(**lk)), _p(dr), _p(tr), _p(do), C.c_double(border_tol),
+                                _p(ell), _p(cnt), _p(ss), C.byref(nb))
+    assert rc == 0, rc
+    return ell, cnt, ss, int(nb.value)
+
+
+def score(scene, slot, poses, lk: dict, depth_obs, edge_tol=1e-4, z_tol=1e-5, border_tol=1e-3, n_threads=0,
+          flags=True, arrays=None):
+    """Per-hypothesis ll, with (when flags) scale, ambiguity bound, #flagged px, #borderline."""
+    sa = arrays or SceneArrays(scene)
+    P = _f64(poses).reshape(-1, 16)
+    n = P.shape[0]
+    ll = np.empty(n, np.float64)
+    out = dict(ll=ll)
+    scale = bound = nf = nb = None
+    if flags:
+        scale, bound = np.empty(n), np.empty(n)
+        nf, nb = np.empty(n, np.int32), np.empty(n, np.int32)
+        out.update(scale=scale, bound=bound, n_flag=nf, n_border=nb)
+    rc = lib().orc_score(C.byref(sa.cam), C.byref(sa.st), C.c_int32(slot), C.c_int64(n), _p(P), C.byref(lik(**lk)),
+                         _p(_f64(depth_obs)), C.c_double(edge_tol), C.c_double(z_tol), C.c_double(border_tol),
+                         _p(ll), _p(scale), _p(bound), _p(nf), _p(nb), C.c_int32(n_threads))
+    assert rc == 0, rc
+    return out
+
+
+def lse(ll):
+    ll = _f64(ll)
+    z = C.c_double(0)
+    logp = np.empty_like(ll)
+    rc = lib().orc_lse(C.c_int64(ll.size), _p(ll), C.byref(z), _p(logp))
+    assert rc == 0, rc
+    return float(z.value), logp
+
+
+def philox(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.empty(4, np.uint64)
+    lib().orc_philox4x64(_p(c), _p(k), _p(out))
+    return out
+
+
+def uniform24(x) -> float:
+    return float(lib().orc_uniform24(C.c_uint64(int(x))))
+
+
+def resample(ll, m, seed, stage):
+    ll = _f64(ll)
+    idx = np.empty(m, np.int32)
+    logq = np.empty(m, np.float64)
+    margin = np.empty(m, np.float64)
+    rc = lib().orc_resample(C.c_int64(ll.size), _p(ll), C.c_int32(m), C.c_uint64(seed), C.c_int32(stage),
+                            _p(idx), _p(logq), _p(margin))
+    assert rc == 0, rc
+    return idx, logq, margin
+
+
+def rotation_set(kind, n, rot_max=0.0):
+    R = np.empty((n, 3, 3), np.float64)
+    rc = lib().orc_rotation_set(C.c_int32(kind), C.c_int32(n), C.c_double(rot_max), _p(R))
+    assert rc == 0, rc
+    return R
+
+
+def expand(centre, G, n, step, rotset):
+    rotset = _f64(rotset).reshape(-1, 9)
+    nh = n ** 3 * rotset.shape[0]
+    poses = np.empty((nh, 4, 4), np.float64)
+    rc = lib().orc_expand(_p(_f64(centre).reshape(16)), _p(_f64(G).reshape(9)), C.c_int32(n), C.c_double(step),
+                          _p(rotset), C.c_int32(rotset.shape[0]), _p(poses))
+    assert rc == 0, rc
+    return poses
+
+
+def enumerate_c2f(scene, slot, centre, G, lk: dict, depth_obs, stages, m, seed, n_threads=0, arrays=None):
+    sa = arrays or SceneArrays(scene)
+    T = len(stages)
+    st = (_Stage * T)(*[_Stage(s.n_per_axis, s.step, s.rot_kind, s.n_rot, s.rot_max) for s in stages])
+    particles = np.empty((m, 4, 4))
+    logw, logq = np.empty(m), np.empty(m)
+    centres, zs = np.empty((T, 4, 4)), np.empty(T)
+    idx = np.empty((T, m), np.int32)
+    rc = lib().orc_enumerate_c2f(C.byref(sa.cam), C.byref(sa.st), C.c_int32(slot), _p(_f64(centre).reshape(16)),
+                                 _p(_f64(G).reshape(9)), C.byref(lik(**lk)), _p(_f64(depth_obs)), C.c_int32(T), st,
+                                 C.c_int32(m), C.c_uint64(seed), _p(particles), _p(logw), _p(logq), _p(centres),
+                                 _p(zs), _p(idx), C.c_int32(n_threads))
+    assert rc == 0, rc
+    return dict(particles=particles, logw=logw, logq=logq, centres=centres, z=zs, idx=idx)
+
+
+def score_grad(scene, slot, poses, lk: dict, depth_obs, n_threads=0, arrays=None):
+    sa = arrays or SceneArrays(scene)
+    P = _f64(poses).reshape(-1, 16)
+    n = P.shape[0]
+    ll, dpose, ds, dp = np.empty(n), np.empty((n, 6)), np.empty(n), np.empty(n)
+    rc = lib().orc_score_grad(C.byref(sa.cam), C.byref(sa.st), C.c_int32(slot), C.c_int64(n), _p(P),
+                              C.byref(lik(**lk)), _p(_f64(depth_obs)), _p(ll), _p(dpose), _p(ds), _p(dp),
+                              C.c_int32(n_threads))
+    assert rc == 0, rc
+    return dict(ll=ll, dpose=dpose, dsigma=ds, dpout=dp)
+
+
+def max_threads() -> int:
+    return int(lib().orc_max_threads())
