@@ -1,0 +1,440 @@
+#!/usr/bin/env python
+"""Benchmark of the render-and-score hot path: a coarse-to-fine multi-object parse.
+
+One step = parse one synthetic tabletop scene (160x120 camera, table, box occluder, five
+voxel objects of 2k-8k voxels at 5 mm): for each object in turn, the already-placed objects
+are fixed at their inferred poses and the object's pose is enumerated coarse-to-fine
+around a tracking prior: 3 stages x 9^3 translations x 200 rotations = 145,800 hypotheses
+per stage, each rendered and scored under the windowed inlier-ball likelihood (r = 5 mm,
+p_out = 0.01, 3x3 window), log-sum-exp normalised and resampled to 100 particles. That is
+5 x 3 x 145,800 = 2,187,000 hypotheses per step, all on the device.
+
+Prints one JSON line (rank 0). With --impl reference the CPU oracle is timed instead on a
+bounded sample of the same workload (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2312_08715_gb300 import synth  # noqa: E402
+
+METRIC = "pose hypotheses rendered+scored/sec on 1 GB300 (% HBM roofline); p99 frame latency"
+UNIT = "hyp/s"
+N_OBJECTS = 5
+M_PARTICLES = 100
+FIRST_SLOT = 2  # 0 = table, 1 = occluder
+
+# FP32 operations per unit of counted work, from the kernel source (an FMA counts 2):
+#   vertex: 3x3 rotation + translation (9 FMA), 1/z, two projections (FMA + MUL each)
+#   triangle: signed area (edge function: 4 SUB, MUL, FMA) + screen bbox (6 MIN/MAX, 4 SUB)
+#   pixel test: three edge functions (3 x 7) + three sign tests
+#   fragment: 1/z interpolation (2 FMA + MUL) + division + far test
+#   composite pixel: key min + depth decode; scored pixel: ray row, lookup/log, delta, sum
+#   window pair: ray column (SUB, SUB, MUL), offsets (2 FMA + SUB), |d|^2 (2 FMA + MUL), test
+FLOPS_PER_UNIT = np.array([0.0, 25.0, 17.0, 24.0, 7.0, 2.0, 12.0, 14.0])
+UNIT_NAMES = ["hypotheses", "vertices", "triangles", "pixel_tests", "fragments", "composited_px",
+              "scored_px", "window_pairs"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b3d", choices=["b3d", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU work of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--trial", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload(trial):
+    return synth.tabletop_workload(trial, n_objects=N_OBJECTS)
+
+
+def config_dict(wl, extra=None):
+    c = dict(workload="coarse-to-fine tabletop parse: 160x120, 5 voxel objects (2k-8k voxels, 5 mm) + box "
+                      "occluder + table, 3 stages x 9^3 translations x 200 rotations per object, 100 particles",
+             hyps_per_step=N_OBJECTS * sum(s.n_per_axis ** 3 * s.n_rot for s in wl.stages),
+             image=[wl.scene.camera.width, wl.scene.camera.height], likelihood="inlier ball r=5mm, p_out=0.01, 3x3",
+             precision="fp32 kernels", l2="flushed between timed steps (256 MiB write)")
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------------------------------------
+# clocks
+# ------------------------------------------------------------------------------------------
+_CLOCK_Q = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+            "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+            "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, uuid_hint=None):
+        self.uuid_hint = uuid_hint
+        self.proc = None
+        self.path = os.path.join("/tmp", f"b3d_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={_CLOCK_Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 10:
+                continue
+            if self.uuid_hint and self.uuid_hint not in f[1]:
+                continue
+            rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------
+# the GPU path
+# ------------------------------------------------------------------------------------------
+class Parse:
+    """One multi-object coarse-to-fine parse through the C ABI (the timed step)."""
+
+    def __init__(self, ctx, wl, torch):
+        self.ctx, self.wl, self.torch = ctx, wl, torch
+        sc = wl.scene
+        self.ids = [ctx.load_mesh(m, closed=m.faces.shape[0] > 2) for m in sc.meshes]
+        # known objects (table, occluder) at their true poses; objects at their tracking priors
+        self.host_poses = np.array(sc.poses, np.float32)
+        pri = wl.extra["priors"]
+        for s in wl.extra["object_slots"]:
+            self.host_poses[s] = pri[s]
+        dev = ctx.device
+        self.particles = torch.empty((N_OBJECTS, M_PARTICLES, 4, 4), dtype=torch.float32, device=dev)
+        self.logw = torch.empty((N_OBJECTS, M_PARTICLES), dtype=torch.float32, device=dev)
+        self.logq = torch.empty((N_OBJECTS, M_PARTICLES), dtype=torch.float32, device=dev)
+        self.priors = pri
+
+    def run(self, obs_dev, seed=0):
+        from paper_2312_08715_gb300 import b3d
+        ctx, wl = self.ctx, self.wl
+        for k in range(N_OBJECTS):
+            slot = FIRST_SLOT + k
+            b3d.b3d_set_scene(ctx.h, b3d.intrinsics(wl.scene.camera), self.ids[:slot + 1],
+                              self.host_poses[:slot + 1], obs_dev, ctx.stream)
+            for j in range(k):
+                b3d.b3d_set_object_pose_dev(ctx.h, FIRST_SLOT + j, self.particles[j, 0], ctx.stream)
+            ctx.enumerate_c2f(slot, self.priors[slot], wl.stages, wl.lik, M_PARTICLES, seed + 7919 * k,
+                              wl.grid_frame, out=(self.particles[k], self.logw[k], self.logq[k]))
+
+
+def gpu_observation(ctx, wl, torch):
+    """Render the scene at its hidden poses on the GPU, then corrupt it with the seeded
+    noise draws (host)."""
+    sc = wl.scene
+    ids = [ctx.load_mesh(m, closed=m.faces.shape[0] > 2) for m in sc.meshes]
+    zeros = torch.zeros((sc.camera.height, sc.camera.width), dtype=torch.float32, device=ctx.device)
+    ctx.set_scene(sc.camera, ids, sc.poses, zeros)
+    depth, _ = ctx.render(FIRST_SLOT, sc.poses[FIRST_SLOT][None], want_tid=False)
+    ctx.sync()
+    return synth.corrupt_depth(depth[0].cpu().numpy(), sc.camera.far, wl.draws)
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2312_08715_gb300 import b3d
+    b3d.load()
+
+    wl = workload(args.trial + rank)  # each rank parses its own independent scene
+    setup_ctx = b3d.Context(dev.index)
+    obs_np = gpu_observation(setup_ctx, wl, torch)
+    setup_ctx.close()
+
+    ctx = b3d.Context(dev.index)
+    parse = Parse(ctx, wl, torch)
+    obs_dev = torch.as_tensor(obs_np, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # calibration (untimed): work counted by the kernels for one step
+    b3d.b3d_set_instrumentation(ctx.h, b3d.B3D_INSTR_WORK)
+    parse.run(obs_dev, seed=args.trial)
+    ctx.sync()
+    work = b3d.b3d_work_counters(ctx.h).astype(np.float64)
+    b3d.b3d_set_instrumentation(ctx.h, 0)
+
+    for w in range(args.warmup):
+        parse.run(obs_dev, seed=args.trial + 100 + w)
+    ctx.sync()
+
+    # timed region: barrier + synchronize on both sides; per-step CUDA events; L2 flushed
+    # before every step outside the events; per-kernel events recorded by the library.
+    b3d.b3d_set_instrumentation(ctx.h, b3d.B3D_INSTR_TIMING)
+    for k in range(b3d.B3D_K_COUNT):
+        b3d.b3d_kernel_time(ctx.h, k)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = ctx.launches()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(uuid) as clk:
+        t_wall = time.perf_counter()
+        for s in range(args.steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            parse.run(obs_dev, seed=args.trial + 1000 + s)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall
+    ctx.sync()
+    gpu_launches = ctx.launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    ktimes = {k: b3d.b3d_kernel_time(ctx.h, k) for k in range(b3d.B3D_K_COUNT)}
+    b3d.b3d_set_instrumentation(ctx.h, 0)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    hyps_step = N_OBJECTS * sum(s.n_per_axis ** 3 * s.n_rot for s in wl.stages)
+    value = hyps_step * args.steps * world / (total_ms / 1e3)
+    px = wl.scene.camera.width * wl.scene.camera.height
+
+    # roofline of the dominant kernel (the fused render+score kernel)
+    score_ms, score_n = ktimes[b3d.B3D_K_SCORE]
+    launches_per_step = N_OBJECTS * len(wl.stages)
+    flop_per_launch = float(work @ FLOPS_PER_UNIT) / launches_per_step
+    avg_launch_s = score_ms / max(score_n, 1) / 1e3
+    peak_alu = 152 * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x max SM clock
+    achieved = flop_per_launch / avg_launch_s / 1e12
+    traffic = _committed_traffic()
+    hyps_per_launch = hyps_step / launches_per_step
+    hbm_bytes_launch = (8.0 * px + 4.0) * hyps_per_launch
+    peaks = _measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        e2e = run_e2e(args, ctx, parse, obs_np, flush, dev, torch, hyps_step)
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(wl, {"parallelism": f"replicas x{world} (independent scenes)"}),
+        "px_hyps_per_s": value * px,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
+                     "frac": achieved / peak_alu, "traffic": traffic,
+                     "kernel": "k_fused<score, grid> (render + windowed likelihood)",
+                     "avg_launch_ms": avg_launch_s * 1e3, "launches": score_n,
+                     "flop_per_launch": flop_per_launch, "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "work_per_step": {n: float(v) for n, v in zip(UNIT_NAMES, work)}},
+        "hbm_equivalent": {"bytes_per_launch": hbm_bytes_launch,
+                           "achieved_gbs": hbm_bytes_launch / avg_launch_s / 1e9, "peak_gbs": hbm_peak,
+                           "frac": hbm_bytes_launch / avg_launch_s / 1e9 / hbm_peak,
+                           "note": "materialised render-then-score traffic (8 B per pixel-hypothesis + 4 B per "
+                                   "hypothesis) over the fused kernel's time, of measured HBM copy bandwidth"},
+        "kernel_ms_per_step": {name: ktimes[k][0] / args.steps for k, name in enumerate(
+            ["score", "render", "score_depth", "resample", "select", "grad", "scene"])},
+        "gpu_launches": int(gpu_launches),
+        "clocks": clk.summary(),
+        "wall_s_timed": t_wall,
+    }
+    if e2e:
+        result["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args, wl, seconds=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(args, ctx, parse, obs_np, flush, dev, torch, hyps_step):
+    """End to end through the public API: every step copies its observation from pinned host
+    memory to the device and reads the particles, weights and proposal densities back."""
+    host_obs = torch.as_tensor(obs_np).pin_memory()
+    dev_obs = torch.empty_like(host_obs, device=dev)
+    outs = [parse.particles, parse.logw, parse.logq]
+    host_out = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+    stream = torch.cuda.current_stream(dev)
+    times = []
+    for s in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        dev_obs.copy_(host_obs, non_blocking=True)
+        parse.run(dev_obs, seed=args.trial + 5000 + s)
+        for h, o in zip(host_out, outs):
+            h.copy_(o, non_blocking=True)
+        stream.synchronize()
+        times.append(time.perf_counter() - t0)
+    h2d = host_obs.numel() * 4
+    d2h = sum(o.numel() * 4 for o in outs)
+    return {"value": hyps_step * len(times) / sum(times), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * sum(times) / len(times),
+            "p50_ms": 1e3 * float(np.percentile(times, 50)), "p99_ms": 1e3 * float(np.percentile(times, 99))}
+
+
+def _measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_render.cu", "b3d_device.cuh", "b3d_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2312_08715_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _committed_traffic():
+    """DRAM bytes per launch of the fused score kernel from the committed ncu summary, if
+    it was taken from the current kernel source (else null)."""
+    p = os.path.join(ROOT, "profiles", "fused_score_tabletop.json")
+    try:
+        d = json.load(open(p))
+        if d.get("source_hash") == _kernel_source_hash():
+            return d.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle: baseline leg and reference arm
+# ------------------------------------------------------------------------------------------
+def _oracle_sample_inputs(wl):
+    """First enumeration of the parse: object slot 2 in a scene of table + occluder + it,
+    stage-1 grid around its tracking prior; observation rendered by the oracle."""
+    from oracle import oracle as O
+    sc = wl.scene
+    full = O.render(sc)[0]
+    obs = synth.corrupt_depth(full, sc.camera.far, wl.draws)
+    sub = synth.Scene(sc.camera, sc.meshes[:FIRST_SLOT + 1], sc.poses[:FIRST_SLOT + 1].copy())
+    st = wl.stages[0]
+    rot = O.rotation_set(st.rot_kind, st.n_rot, st.rot_max)
+    centre = wl.extra["priors"][FIRST_SLOT]
+    poses = O.expand(centre, wl.grid_frame, st.n_per_axis, st.step, rot)
+    return O, sub, obs, poses
+
+
+def cpu_baseline(args, wl, seconds=12.0, label="oracle"):
+    O, sub, obs, poses = _oracle_sample_inputs(wl)
+    arrays = O.SceneArrays(sub)
+    rng = np.random.default_rng(17)
+    cores = O.max_threads()
+    probe = poses[rng.choice(len(poses), 2 * cores, replace=False)]
+    t0 = time.perf_counter()
+    O.score(sub, FIRST_SLOT, probe, wl.lik, obs, flags=False, arrays=arrays)
+    per = (time.perf_counter() - t0) / len(probe)
+    n = int(min(len(poses), max(2 * cores, seconds / max(per, 1e-6))))
+    sample = poses[rng.choice(len(poses), n, replace=False)]
+    t0 = time.perf_counter()
+    O.score(sub, FIRST_SLOT, sample, wl.lik, obs, flags=False, arrays=arrays)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} random hypotheses of the first stage of the first object (of 145,800; table + "
+                      f"occluder + object, 160x120), FP64, OpenMP over hypotheses, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl = workload(args.trial)
+    O, sub, obs, poses = _oracle_sample_inputs(wl)
+    arrays = O.SceneArrays(sub)
+    cores = O.max_threads()
+    rng = np.random.default_rng(23)
+    probe = poses[rng.choice(len(poses), 2 * cores, replace=False)]
+    t0 = time.perf_counter()
+    O.score(sub, FIRST_SLOT, probe, wl.lik, obs, flags=False, arrays=arrays)
+    per = (time.perf_counter() - t0) / len(probe)
+    n_step = int(max(2 * cores, min(len(poses), 8.0 / max(per, 1e-6))))
+    times = []
+    for s in range(args.warmup + args.steps):
+        sample = poses[rng.choice(len(poses), n_step, replace=False)]
+        t0 = time.perf_counter()
+        O.score(sub, FIRST_SLOT, sample, wl.lik, obs, flags=False, arrays=arrays)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = n_step * len(times) / sum(times)
+    sample = (f"{n_step} random first-stage hypotheses per step (of 145,800), FP64 oracle, OpenMP over "
+              f"{cores} host threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(wl, {"parallelism": "host cores"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.warmup < 3 and args.impl == "b3d":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

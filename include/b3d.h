@@ -1,0 +1,254 @@
+/*
+ * b3d.h - C ABI of libb3d, a GB300 (sm_103a) implementation of the render-and-score hot
+ * path of Bayes3D's coarse-to-fine sequential Monte Carlo inference (Gothoskar et al.,
+ * arXiv 2312.08715): many 6-DoF pose hypotheses of voxel-mesh objects are rasterised into
+ * depth images, scored against an observed depth image under the paper's windowed
+ * outlier-mixture likelihood (Eq. 1 with the window truncation of Sec. III-B), reduced to
+ * one log-likelihood per hypothesis, normalised by log-sum-exp and resampled to seed the
+ * next, finer pose grid (the coarse-to-fine proposal of Sec. III-B).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns a b3d_status: B3D_OK (0) or a negative error. No exception or
+ *     longjmp crosses the ABI. b3d_last_error() describes the last failure on a context.
+ *   - Argument errors are detected on the host, before any work is queued. Device-side
+ *     failures (a kernel's own bounds or timeout checks) set a flag in the context that
+ *     b3d_sync() reports as B3D_EDEVICE.
+ *   - Pointers named *_dev are caller-owned device memory on the context's device, 16-byte
+ *     aligned, with the size each call states; the library neither frees nor retains them
+ *     past the call (work queued on the stream reads/writes them asynchronously, so keep
+ *     them alive until the stream reaches that point). Host pointers are read during the
+ *     call only.
+ *   - Meshes, the scene and all internal scratch are owned by the context and freed by
+ *     b3d_destroy(). The context's device allocations count against hbm_budget_bytes.
+ *   - All device work is asynchronous on the caller's stream (a cudaStream_t passed as
+ *     b3d_stream; NULL is the legacy default stream). A context is not thread-safe: use
+ *     one context per host thread, or serialise calls.
+ *   - Poses are row-major 4x4 float32 cam_from_obj matrices (p_cam = R p_obj + t,
+ *     t = (P[3], P[7], P[11]), bottom row 0 0 0 1). OpenCV camera axes: x right, y down,
+ *     z forward. Pixel (u, v) is column u, row v; its ray passes through the pixel centre,
+ *     ((u + 1/2 - cx)/fx, (v + 1/2 - cy)/fy, 1). Depth is camera z.
+ *   - Images are row-major [H, W] float32; batches of images are [n, H, W].
+ */
+#ifndef B3D_H
+#define B3D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t b3d_status;
+#define B3D_OK 0
+#define B3D_EINVAL (-1)    /* invalid argument (message in b3d_last_error) */
+#define B3D_ENOMEM (-2)    /* a device or host allocation failed */
+#define B3D_EBUDGET (-3)   /* the allocation would exceed the context's HBM budget */
+#define B3D_ECUDA (-4)     /* a CUDA runtime call failed */
+#define B3D_ETIMEOUT (-5)  /* a bounded wait expired */
+#define B3D_ENOTFOUND (-6) /* unknown mesh id or object slot */
+#define B3D_EDEVICE (-7)   /* a kernel raised the context's device error flag */
+
+#define B3D_MAX_STAGES 8
+#define B3D_MAX_HALF_WINDOW 7
+
+/* load_mesh flags */
+#define B3D_MESH_CLOSED 1  /* closed, outward-oriented (counter-clockwise seen from outside)
+                              solid, e.g. a voxel mesh: back faces and coincident internal
+                              face pairs can never be the nearest surface, so the library
+                              skips them (triangle ids reported stay the original ones) */
+
+typedef struct b3d_ctx b3d_ctx;
+typedef void *b3d_stream; /* cudaStream_t */
+
+/* Pinhole camera: image size, focal lengths and principal point in pixels, near/far planes
+ * in metres. A triangle with a vertex closer than near_z is not drawn; fragments beyond
+ * far_z are dropped; a pixel without a fragment renders at far_z. */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy, near_z, far_z;
+} b3d_intrinsics;
+
+/* Likelihood of Eq. 1, truncated to a (2w+1)^2 pixel window (Sec. III-B):
+ *   l_i = log( p_out / V + (1 - p_out) / K * sum_{j in win(i)} k(qt_i, q_j) )
+ * over observed pixels i with finite depth > 0 (qt_i its point), rendered points q_j.
+ *   kind 0 ("plain"): k = 1{|qt - q|^2 <= r^2} / ((4/3) pi r^3)   (inlier ball)
+ *   kind 1 ("smooth"): k = (2 pi s^2)^(-3/2) exp(-|qt - q|^2 / (2 s^2))
+ * radius is r (kind 0) or s (kind 1), metres. volume <= 0 selects V = the camera frustum
+ * between near and far, (W H / (fx fy)) (far^3 - near^3) / 3; norm <= 0 selects
+ * K = (2w+1)^2 (window slots outside the image count in K and contribute 0).
+ * miss_mode 0: a rendered pixel without a triangle is a point on the far plane;
+ * miss_mode 1: it carries no point. 0 <= half_window <= B3D_MAX_HALF_WINDOW,
+ * 0 < p_outlier < 1, radius > 0. */
+typedef struct {
+    int32_t kind;
+    float radius;
+    float p_outlier;
+    int32_t half_window;
+    float volume;
+    float norm;
+    int32_t miss_mode;
+} b3d_lik_params;
+
+/* One coarse-to-fine stage (a partition Pi_t of Sec. III-B): an n^3 translation grid of
+ * spacing step (odd n centred, even n with the centre at index n/2) times a rotation set
+ * of n_rot rotations, hypothesis h = ((ir * n + ix) * n + iy) * n + iz with
+ *   R_h = R_centre R_ir,  t_h = t_centre + G (o_ix, o_iy, o_iz).
+ * rot_kind 0: Fibonacci-sphere set, R_k the minimal-arc rotation taking +z to
+ *   d_k = (sqrt(1-z^2) cos(2 pi k / phi), sqrt(1-z^2) sin(2 pi k / phi), z),
+ *   z = 1 - (2k+1)/n_rot, phi the golden ratio;
+ * rot_kind 1: perturbation set, R_k = Exp(theta_k d_k), theta_k = rot_max (2 frac((k+1/2)/phi) - 1). */
+typedef struct {
+    int32_t n_per_axis;
+    float step;
+    int32_t rot_kind;
+    int32_t n_rot;
+    float rot_max;
+} b3d_stage;
+
+/* A coarse-to-fine schedule: stages, particles drawn per stage, the seed of the
+ * counter-based generator, and G, the rotation (row-major 3x3, cam_from_grid) whose
+ * columns are the translation grid's axes in the camera frame. */
+typedef struct {
+    int32_t n_stages;
+    b3d_stage stage[B3D_MAX_STAGES];
+    int32_t n_particles;
+    uint64_t seed;
+    float grid_frame[9];
+} b3d_c2f_schedule;
+
+/* Create a context on CUDA device `device`. Allocations made on its behalf may total at
+ * most hbm_budget_bytes (0 = no limit). *out receives the context, or NULL on error. */
+b3d_status b3d_create(b3d_ctx **out, int32_t device, uint64_t hbm_budget_bytes);
+
+/* Free the context and everything it owns. Waits for the device to finish its work. */
+b3d_status b3d_destroy(b3d_ctx *ctx);
+
+/* Message of the last failed call on ctx (never NULL; "" after success). With ctx NULL,
+ * the message of the last failed b3d_create on this thread. Valid until the next call. */
+const char *b3d_last_error(b3d_ctx *ctx);
+
+/* Number of kernels the library launched on this context so far (a running count). */
+int64_t b3d_launch_count(b3d_ctx *ctx);
+
+/* Load an object model (the paper's voxel object model, Sec. III: voxels placed on the
+ * points of a fused cloud; here any triangle mesh). verts: host [n_v, 3] float32 object
+ * frame; faces: host [n_f, 3] int32 vertex indices in [0, n_v). flags: B3D_MESH_CLOSED or 0.
+ * Triangle ids reported by the renderer are face indices of this array (offset per scene
+ * object, see b3d_set_scene). *mesh_id receives a context-local id. n_f >= 1. */
+b3d_status b3d_load_mesh(b3d_ctx *ctx, const float *verts, int64_t n_v, const int32_t *faces, int64_t n_f,
+                         int32_t flags, int32_t *mesh_id);
+
+/* Set the scene (the scene graph of Alg. 1, flattened): n_obj objects, object k is mesh
+ * mesh_ids[k] at host pose poses[16 k .. 16 k + 15]; camera intrinsics; and the observed
+ * depth image obs_depth_dev [H, W] (copied to an observed point cloud on the device; the
+ * caller's buffer is no longer needed once the stream has passed this call). Pixels with
+ * depth <= 0 or not finite are not scored. The global triangle id of face f of object k is
+ * f + (sum of the face counts of objects 0..k-1). */
+b3d_status b3d_set_scene(b3d_ctx *ctx, const b3d_intrinsics *intr, int32_t n_obj, const int32_t *mesh_ids,
+                         const float *poses, const float *obs_depth_dev, b3d_stream stream);
+
+/* Replace the observed depth image of the current scene (same size). */
+b3d_status b3d_set_observation(b3d_ctx *ctx, const float *obs_depth_dev, b3d_stream stream);
+
+/* Set the pose of scene object `obj` from device memory pose_dev [16] (no host round
+ * trip; used to fix an object at a pose found on the device). */
+b3d_status b3d_set_object_pose_dev(b3d_ctx *ctx, int32_t obj, const float *pose_dev, b3d_stream stream);
+
+/* Render n_hyp hypotheses (the depth renderer of Alg. 1, DepthRenderer): the scene with
+ * object obj_slot at poses_dev [n_hyp, 16] and every other object at its scene pose.
+ * Writes depth_dev [n_hyp, H, W] (far_z where nothing is drawn) and, unless NULL,
+ * triid_dev [n_hyp, H, W] (global triangle id, -1 where nothing is drawn). Nearest
+ * fragment wins; equal depths go to the smaller triangle id. */
+b3d_status b3d_render_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const float *poses_dev, float *depth_dev,
+                            int32_t *triid_dev, b3d_stream stream);
+
+/* Render and score n_hyp hypotheses in one pass (render, Eq. 1 likelihood per observed
+ * pixel, sum over pixels): loglik_dev [n_hyp] receives sum_i l_i for the scene with
+ * object obj_slot at poses_dev [n_hyp, 16]. The rendered images never leave the chip. */
+b3d_status b3d_score_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const float *poses_dev,
+                           const b3d_lik_params *lik, float *loglik_dev, b3d_stream stream);
+
+/* Score materialised depth images: depth_dev [n_hyp, H, W] (e.g. from b3d_render_batch)
+ * against the scene's observation; triid_dev [n_hyp, H, W] is needed only for
+ * miss_mode 1 (pixels with id -1 carry no point), else may be NULL. loglik_dev [n_hyp]. */
+b3d_status b3d_score_depth_batch(b3d_ctx *ctx, int64_t n_hyp, const float *depth_dev, const int32_t *triid_dev,
+                                 const b3d_lik_params *lik, float *loglik_dev, b3d_stream stream);
+
+/* Expand one coarse-to-fine stage around centre_pose (host [16]) with grid frame G (host
+ * [9], row-major cam_from_grid): poses_dev [n^3 * n_rot, 16] in hypothesis order (see
+ * b3d_stage). */
+b3d_status b3d_expand_hypotheses(b3d_ctx *ctx, const float *centre_pose, const float *grid_frame,
+                                 const b3d_stage *stage, float *poses_dev, b3d_stream stream);
+
+/* Log-sum-exp normalisation and categorical resampling (Sec. III-B: the next region is
+ * sampled with probability proportional to its score). For loglik_dev [n] (n >= 1):
+ * logz_dev [1] = log sum_h exp(ll_h); for draw k < m, u_k = the top 24 bits of the first
+ * word of Philox4x64-10 (Salmon et al., SC'11) at counter (k, stage, 0, 0) and key
+ * (seed, 0), divided by 2^24; idx_dev[k] = min{ h : sum_{g<=h} exp(ll_g) > u_k sum_g exp(ll_g) }
+ * and logq_dev[k] = ll[idx_k] - logz. m may be 0 (idx/logq then unused). */
+b3d_status b3d_lse_resample(b3d_ctx *ctx, int64_t n, const float *loglik_dev, int32_t m, uint64_t seed,
+                            int32_t stage, float *logz_dev, int32_t *idx_dev, float *logq_dev, b3d_stream stream);
+
+/* Coarse-to-fine enumeration of object obj_slot's pose (Sec. III-B). Stage t expands
+ * its grid around centre_t (centre_0 = centre_pose, host [16]), scores every hypothesis
+ * with lik (scoring strategy: the cell centre, weight 1), draws n_particles cells by
+ * b3d_lse_resample(seed, stage t), and takes as centre_{t+1} the drawn cell with the
+ * highest score (ties to the smaller index). After the last stage, particle k is its
+ * drawn cell's pose moved uniformly within the cell, t += G ((u0-1/2) s, (u1-1/2) s,
+ * (u2-1/2) s) with (u0, u1, u2) the top-24-bit uniforms of words 0..2 of Philox at
+ * counter (k, n_stages, 1, 0), key (seed, 0):
+ *   particles_dev [M, 16], logw_dev [M] = the drawn cell's score,
+ *   logq_dev [M] = score - logZ_last - 3 log(s_last)   (proposal density q).
+ * Every step runs on the device; the call can be captured into a CUDA graph once it has
+ * run once with the same sizes (scratch is sized on first use). */
+b3d_status b3d_enumerate_c2f(b3d_ctx *ctx, int32_t obj_slot, const float *centre_pose,
+                             const b3d_c2f_schedule *schedule, const b3d_lik_params *lik, float *particles_dev,
+                             float *logw_dev, float *logq_dev, b3d_stream stream);
+
+/* Forward and backward of the smooth (kind 1) likelihood for n_hyp poses: loglik_dev [n],
+ * dpose_dev [n, 6] = d loglik / d xi at xi = 0 for the left perturbation
+ * T(xi) = Exp([v, w]^) T in the camera frame, ordered (v, w), with visibility held fixed
+ * and each rendered point sliding along its pixel ray on its triangle's plane;
+ * dsigma_dev [n] and dpout_dev [n] = d loglik / d s and d loglik / d p_outlier. Any of the
+ * gradient outputs may be NULL. The forward is recomputed; nothing per pixel is stored. */
+b3d_status b3d_score_grad(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const float *poses_dev,
+                          const b3d_lik_params *lik, float *loglik_dev, float *dpose_dev, float *dsigma_dev,
+                          float *dpout_dev, b3d_stream stream);
+
+/* Instrumentation (off by default; used by the benchmark).
+ * flags bit 0 (B3D_INSTR_TIMING): bracket every kernel launch of the library with CUDA
+ *   events recorded on the launching stream; b3d_kernel_time() reports the device time.
+ * flags bit 1 (B3D_INSTR_WORK): the render/score kernels count the work they do
+ *   (b3d_work_counters); counting slows them, so never enable it for a timed run. */
+#define B3D_INSTR_TIMING 1
+#define B3D_INSTR_WORK 2
+b3d_status b3d_set_instrumentation(b3d_ctx *ctx, int32_t flags);
+
+/* Kernel classes for b3d_kernel_time. */
+#define B3D_K_SCORE 0       /* fused render + score (b3d_score_batch, b3d_enumerate_c2f) */
+#define B3D_K_RENDER 1      /* b3d_render_batch */
+#define B3D_K_SCORE_DEPTH 2 /* b3d_score_depth_batch */
+#define B3D_K_RESAMPLE 3    /* log-sum-exp + resampling */
+#define B3D_K_SELECT 4      /* coarse-to-fine centre selection / particles */
+#define B3D_K_GRAD 5        /* b3d_score_grad */
+#define B3D_K_SCENE 6       /* scene set-up: observed points, background render and tables, grids */
+#define B3D_K_COUNT 7
+
+/* Device time (milliseconds) and number of launches of one kernel class recorded since the
+ * previous call for that class (waits for the recorded events; then resets the class). */
+b3d_status b3d_kernel_time(b3d_ctx *ctx, int32_t kernel_class, double *total_ms, int64_t *launches);
+
+/* Work counted by the render/score kernels since the previous call (then cleared; waits
+ * for the device): out[8] = hypotheses, vertices transformed, triangles processed,
+ * pixel-centre coverage tests, fragments written, z-buffer pixels composited, observed
+ * pixels scored, window pairs evaluated. */
+b3d_status b3d_work_counters(b3d_ctx *ctx, int64_t *out);
+
+/* Wait for the stream, then report (and clear) the context's device error flag. */
+b3d_status b3d_sync(b3d_ctx *ctx, b3d_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* B3D_H */

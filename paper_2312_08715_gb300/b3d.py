@@ -1,0 +1,442 @@
+"""Python binding of libb3d: the C ABI of include/b3d.h, name for name, over ctypes.
+
+Argument marshalling only: every step of the path runs in the library's kernels. Device
+buffers are passed as integer addresses (for torch tensors, ``t.data_ptr()``) and streams as
+integer ``cudaStream_t`` handles (``torch.cuda.current_stream().cuda_stream``); host arrays
+are numpy arrays. The module refuses to load without the compiled library: there is no
+fallback path.
+
+On top of the raw functions, ``Context`` is a thin convenience wrapper used by the tests
+and the benchmark (still marshalling only), and ``ScoreSmooth`` is the
+``torch.autograd.Function`` over ``b3d_score_grad``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+B3D_OK = 0
+B3D_EINVAL = -1
+B3D_ENOMEM = -2
+B3D_EBUDGET = -3
+B3D_ECUDA = -4
+B3D_ETIMEOUT = -5
+B3D_ENOTFOUND = -6
+B3D_EDEVICE = -7
+B3D_MAX_STAGES = 8
+B3D_MAX_HALF_WINDOW = 7
+B3D_MESH_CLOSED = 1
+B3D_INSTR_TIMING = 1
+B3D_INSTR_WORK = 2
+B3D_K_SCORE, B3D_K_RENDER, B3D_K_SCORE_DEPTH, B3D_K_RESAMPLE, B3D_K_SELECT, B3D_K_GRAD, B3D_K_SCENE = range(7)
+B3D_K_COUNT = 7
+
+_STATUS = {0: "B3D_OK", -1: "B3D_EINVAL", -2: "B3D_ENOMEM", -3: "B3D_EBUDGET", -4: "B3D_ECUDA",
+           -5: "B3D_ETIMEOUT", -6: "B3D_ENOTFOUND", -7: "B3D_EDEVICE"}
+
+
+class b3d_intrinsics(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("near_z", C.c_float), ("far_z", C.c_float)]
+
+
+class b3d_lik_params(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("radius", C.c_float), ("p_outlier", C.c_float), ("half_window", C.c_int32),
+                ("volume", C.c_float), ("norm", C.c_float), ("miss_mode", C.c_int32)]
+
+
+class b3d_stage(C.Structure):
+    _fields_ = [("n_per_axis", C.c_int32), ("step", C.c_float), ("rot_kind", C.c_int32), ("n_rot", C.c_int32),
+                ("rot_max", C.c_float)]
+
+
+class b3d_c2f_schedule(C.Structure):
+    _fields_ = [("n_stages", C.c_int32), ("stage", b3d_stage * B3D_MAX_STAGES), ("n_particles", C.c_int32),
+                ("seed", C.c_uint64), ("grid_frame", C.c_float * 9)]
+
+
+_P = C.c_void_p
+_SIGNATURES = {
+    "b3d_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int32, C.c_uint64]),
+    "b3d_destroy": (C.c_int32, [_P]),
+    "b3d_last_error": (C.c_char_p, [_P]),
+    "b3d_launch_count": (C.c_int64, [_P]),
+    "b3d_load_mesh": (C.c_int32, [_P, _P, C.c_int64, _P, C.c_int64, C.c_int32, C.POINTER(C.c_int32)]),
+    "b3d_set_scene": (C.c_int32, [_P, C.POINTER(b3d_intrinsics), C.c_int32, _P, _P, _P, _P]),
+    "b3d_set_observation": (C.c_int32, [_P, _P, _P]),
+    "b3d_set_object_pose_dev": (C.c_int32, [_P, C.c_int32, _P, _P]),
+    "b3d_render_batch": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, _P, _P, _P]),
+    "b3d_score_batch": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_lik_params), _P, _P]),
+    "b3d_score_depth_batch": (C.c_int32, [_P, C.c_int64, _P, _P, C.POINTER(b3d_lik_params), _P, _P]),
+    "b3d_expand_hypotheses": (C.c_int32, [_P, _P, _P, C.POINTER(b3d_stage), _P, _P]),
+    "b3d_lse_resample": (C.c_int32, [_P, C.c_int64, _P, C.c_int32, C.c_uint64, C.c_int32, _P, _P, _P, _P]),
+    "b3d_enumerate_c2f": (C.c_int32, [_P, C.c_int32, _P, C.POINTER(b3d_c2f_schedule), C.POINTER(b3d_lik_params),
+                                      _P, _P, _P, _P]),
+    "b3d_score_grad": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_lik_params), _P, _P, _P, _P, _P]),
+    "b3d_set_instrumentation": (C.c_int32, [_P, C.c_int32]),
+    "b3d_kernel_time": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "b3d_work_counters": (C.c_int32, [_P, _P]),
+    "b3d_sync": (C.c_int32, [_P, _P]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libb3d.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"libb3d is not built ({_build.LIB} missing); run paper_2312_08715_gb300.build.build()")
+    lib = C.CDLL(_build.LIB)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class B3DError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def _addr(x):
+    """Address of a device/host buffer: torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ------------------------------------------------------------------------------------------
+# the C ABI, name for name
+# ------------------------------------------------------------------------------------------
+
+def b3d_create(device: int = 0, hbm_budget_bytes: int = 0):
+    lib = load()
+    out = C.c_void_p()
+    st = lib.b3d_create(C.byref(out), device, hbm_budget_bytes)
+    if st != B3D_OK:
+        raise B3DError(st, lib.b3d_last_error(None).decode())
+    return out.value
+
+
+def b3d_destroy(ctx):
+    return load().b3d_destroy(ctx)
+
+
+def b3d_last_error(ctx) -> str:
+    return load().b3d_last_error(ctx).decode()
+
+
+def b3d_launch_count(ctx) -> int:
+    return int(load().b3d_launch_count(ctx))
+
+
+def _check(ctx, st):
+    if st != B3D_OK:
+        raise B3DError(st, b3d_last_error(ctx))
+    return st
+
+
+def b3d_load_mesh(ctx, verts, faces, flags=B3D_MESH_CLOSED) -> int:
+    v = np.ascontiguousarray(verts, dtype=np.float32).reshape(-1, 3)
+    f = np.ascontiguousarray(faces, dtype=np.int32).reshape(-1, 3)
+    mid = C.c_int32(-1)
+    _check(ctx, load().b3d_load_mesh(ctx, v.ctypes.data, v.shape[0], f.ctypes.data, f.shape[0], flags, C.byref(mid)))
+    return int(mid.value)
+
+
+def intrinsics(cam) -> b3d_intrinsics:
+    return b3d_intrinsics(int(cam.width), int(cam.height), float(cam.fx), float(cam.fy), float(cam.cx),
+                          float(cam.cy), float(cam.near), float(cam.far))
+
+
+def lik_params(kind=0, radius=0.005, p_outlier=0.01, half_window=1, volume=0.0, norm=0.0, miss_mode=0):
+    return b3d_lik_params(int(kind), float(radius), float(p_outlier), int(half_window), float(volume), float(norm),
+                          int(miss_mode))
+
+
+def stage_params(s) -> b3d_stage:
+    return b3d_stage(int(s.n_per_axis), float(s.step), int(s.rot_kind), int(s.n_rot), float(s.rot_max))
+
+
+def schedule(stages, n_particles, seed, grid_frame) -> b3d_c2f_schedule:
+    sch = b3d_c2f_schedule()
+    sch.n_stages = len(stages)
+    for k, s in enumerate(stages):
+        sch.stage[k] = stage_params(s)
+    sch.n_particles = int(n_particles)
+    sch.seed = int(seed)
+    g = np.asarray(grid_frame, dtype=np.float32).reshape(9)
+    for k in range(9):
+        sch.grid_frame[k] = float(g[k])
+    return sch
+
+
+def b3d_set_scene(ctx, intr: b3d_intrinsics, mesh_ids, poses, obs_depth_dev, stream=None):
+    ids = np.ascontiguousarray(mesh_ids, dtype=np.int32)
+    P = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 16)
+    return _check(ctx, load().b3d_set_scene(ctx, C.byref(intr), ids.size, ids.ctypes.data, P.ctypes.data,
+                                            _addr(obs_depth_dev), _stream(stream)))
+
+
+def b3d_set_observation(ctx, obs_depth_dev, stream=None):
+    return _check(ctx, load().b3d_set_observation(ctx, _addr(obs_depth_dev), _stream(stream)))
+
+
+def b3d_set_object_pose_dev(ctx, obj, pose_dev, stream=None):
+    return _check(ctx, load().b3d_set_object_pose_dev(ctx, obj, _addr(pose_dev), _stream(stream)))
+
+
+def b3d_render_batch(ctx, obj_slot, n_hyp, poses_dev, depth_dev, triid_dev=None, stream=None):
+    return _check(ctx, load().b3d_render_batch(ctx, obj_slot, n_hyp, _addr(poses_dev), _addr(depth_dev),
+                                               _addr(triid_dev), _stream(stream)))
+
+
+def b3d_score_batch(ctx, obj_slot, n_hyp, poses_dev, lik: b3d_lik_params, loglik_dev, stream=None):
+    return _check(ctx, load().b3d_score_batch(ctx, obj_slot, n_hyp, _addr(poses_dev), C.byref(lik),
+                                              _addr(loglik_dev), _stream(stream)))
+
+
+def b3d_score_depth_batch(ctx, n_hyp, depth_dev, triid_dev, lik: b3d_lik_params, loglik_dev, stream=None):
+    return _check(ctx, load().b3d_score_depth_batch(ctx, n_hyp, _addr(depth_dev), _addr(triid_dev), C.byref(lik),
+                                                    _addr(loglik_dev), _stream(stream)))
+
+
+def b3d_expand_hypotheses(ctx, centre_pose, grid_frame, stage: b3d_stage, poses_dev, stream=None):
+    c = np.ascontiguousarray(centre_pose, dtype=np.float32).reshape(16)
+    g = np.ascontiguousarray(grid_frame, dtype=np.float32).reshape(9)
+    return _check(ctx, load().b3d_expand_hypotheses(ctx, c.ctypes.data, g.ctypes.data, C.byref(stage),
+                                                    _addr(poses_dev), _stream(stream)))
+
+
+def b3d_lse_resample(ctx, n, loglik_dev, m, seed, stage, logz_dev, idx_dev, logq_dev, stream=None):
+    return _check(ctx, load().b3d_lse_resample(ctx, n, _addr(loglik_dev), m, seed, stage, _addr(logz_dev),
+                                               _addr(idx_dev), _addr(logq_dev), _stream(stream)))
+
+
+def b3d_enumerate_c2f(ctx, obj_slot, centre_pose, sch: b3d_c2f_schedule, lik: b3d_lik_params, particles_dev,
+                      logw_dev, logq_dev, stream=None):
+    c = np.ascontiguousarray(centre_pose, dtype=np.float32).reshape(16)
+    return _check(ctx, load().b3d_enumerate_c2f(ctx, obj_slot, c.ctypes.data, C.byref(sch), C.byref(lik),
+                                                _addr(particles_dev), _addr(logw_dev), _addr(logq_dev),
+                                                _stream(stream)))
+
+
+def b3d_score_grad(ctx, obj_slot, n_hyp, poses_dev, lik: b3d_lik_params, loglik_dev, dpose_dev=None,
+                   dsigma_dev=None, dpout_dev=None, stream=None):
+    return _check(ctx, load().b3d_score_grad(ctx, obj_slot, n_hyp, _addr(poses_dev), C.byref(lik), _addr(loglik_dev),
+                                             _addr(dpose_dev), _addr(dsigma_dev), _addr(dpout_dev),
+                                             _stream(stream)))
+
+
+def b3d_set_instrumentation(ctx, flags):
+    return _check(ctx, load().b3d_set_instrumentation(ctx, flags))
+
+
+def b3d_kernel_time(ctx, kernel_class):
+    ms, n = C.c_double(0), C.c_int64(0)
+    _check(ctx, load().b3d_kernel_time(ctx, kernel_class, C.byref(ms), C.byref(n)))
+    return float(ms.value), int(n.value)
+
+
+def b3d_work_counters(ctx):
+    out = np.zeros(8, np.int64)
+    _check(ctx, load().b3d_work_counters(ctx, out.ctypes.data))
+    return out
+
+
+def b3d_sync(ctx, stream=None):
+    return _check(ctx, load().b3d_sync(ctx, _stream(stream)))
+
+
+# ------------------------------------------------------------------------------------------
+# thin convenience layer (torch tensors for device memory and streams)
+# ------------------------------------------------------------------------------------------
+
+class Context:
+    """Owns a b3d context; methods allocate outputs with torch and call the C ABI."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.h = b3d_create(device, hbm_budget_bytes)
+        self.cam = None
+        self.n_obj = 0
+
+    def close(self):
+        if self.h:
+            b3d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def stream(self):
+        return self.torch.cuda.current_stream(self.device)
+
+    def launches(self) -> int:
+        return b3d_launch_count(self.h)
+
+    def load_mesh(self, mesh, closed=True) -> int:
+        return b3d_load_mesh(self.h, mesh.verts, mesh.faces, B3D_MESH_CLOSED if closed else 0)
+
+    def set_scene(self, cam, mesh_ids, poses, obs_depth):
+        obs = self._dev(obs_depth, self.torch.float32)
+        b3d_set_scene(self.h, intrinsics(cam), mesh_ids, poses, obs, self.stream)
+        self.cam = cam
+        self.n_obj = len(mesh_ids)
+        self._obs = obs  # keep alive until the stream has consumed it
+
+    def set_observation(self, obs_depth):
+        obs = self._dev(obs_depth, self.torch.float32)
+        b3d_set_observation(self.h, obs, self.stream)
+        self._obs = obs
+
+    def _dev(self, x, dtype):
+        t = self.torch
+        if isinstance(x, t.Tensor):
+            return x.to(device=self.device, dtype=dtype).contiguous()
+        return t.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=self.device)
+
+    def render(self, slot, poses, want_tid=True):
+        P = self._dev(poses, self.torch.float32).reshape(-1, 16)
+        n = P.shape[0]
+        H, W = self.cam.height, self.cam.width
+        depth = self.torch.empty((n, H, W), dtype=self.torch.float32, device=self.device)
+        tid = self.torch.empty((n, H, W), dtype=self.torch.int32, device=self.device) if want_tid else None
+        b3d_render_batch(self.h, slot, n, P, depth, tid, self.stream)
+        return depth, tid
+
+    def score(self, slot, poses, lik: dict, out=None):
+        P = self._dev(poses, self.torch.float32).reshape(-1, 16)
+        n = P.shape[0]
+        ll = out if out is not None else self.torch.empty(n, dtype=self.torch.float32, device=self.device)
+        b3d_score_batch(self.h, slot, n, P, lik_params(**lik), ll, self.stream)
+        return ll
+
+    def score_depth(self, depth, lik: dict, tid=None):
+        n = depth.shape[0]
+        ll = self.torch.empty(n, dtype=self.torch.float32, device=self.device)
+        b3d_score_depth_batch(self.h, n, depth, tid, lik_params(**lik), ll, self.stream)
+        return ll
+
+    def expand(self, centre, grid_frame, stage):
+        n = stage.n_per_axis ** 3 * stage.n_rot
+        poses = self.torch.empty((n, 4, 4), dtype=self.torch.float32, device=self.device)
+        b3d_expand_hypotheses(self.h, centre, grid_frame, stage_params(stage), poses, self.stream)
+        return poses
+
+    def lse_resample(self, ll, m, seed, stage):
+        t = self.torch
+        logz = t.empty(1, dtype=t.float32, device=self.device)
+        idx = t.empty(max(m, 1), dtype=t.int32, device=self.device)
+        logq = t.empty(max(m, 1), dtype=t.float32, device=self.device)
+        b3d_lse_resample(self.h, ll.numel(), ll, m, seed, stage, logz, idx, logq, self.stream)
+        return logz, idx[:m], logq[:m]
+
+    def enumerate_c2f(self, slot, centre, stages, lik: dict, n_particles, seed, grid_frame, out=None):
+        t = self.torch
+        if out is None:
+            out = (t.empty((n_particles, 4, 4), dtype=t.float32, device=self.device),
+                   t.empty(n_particles, dtype=t.float32, device=self.device),
+                   t.empty(n_particles, dtype=t.float32, device=self.device))
+        particles, logw, logq = out
+        b3d_enumerate_c2f(self.h, slot, centre, schedule(stages, n_particles, seed, grid_frame), lik_params(**lik),
+                          particles, logw, logq, self.stream)
+        return particles, logw, logq
+
+    def score_grad(self, slot, poses, lik: dict):
+        t = self.torch
+        P = self._dev(poses, t.float32).reshape(-1, 16)
+        n = P.shape[0]
+        ll = t.empty(n, dtype=t.float32, device=self.device)
+        dpose = t.empty((n, 6), dtype=t.float32, device=self.device)
+        ds = t.empty(n, dtype=t.float32, device=self.device)
+        dp = t.empty(n, dtype=t.float32, device=self.device)
+        b3d_score_grad(self.h, slot, n, P, lik_params(**lik), ll, dpose, ds, dp, self.stream)
+        return ll, dpose, ds, dp
+
+    def set_object_pose_dev(self, obj, pose_dev):
+        b3d_set_object_pose_dev(self.h, obj, pose_dev, self.stream)
+
+    def sync(self):
+        b3d_sync(self.h, self.stream)
+
+
+def _se3_exp(xi):
+    """Exp of twists xi [n, 6] = (v, w) as 4x4 matrices (Rodrigues with the SE(3) V matrix)."""
+    import torch
+    v, w = xi[:, :3], xi[:, 3:]
+    th = torch.linalg.norm(w, dim=1, keepdim=True).clamp_min(1e-12)
+    k = w / th
+    K = torch.zeros(xi.shape[0], 3, 3, dtype=xi.dtype, device=xi.device)
+    K[:, 0, 1], K[:, 0, 2], K[:, 1, 0] = -k[:, 2], k[:, 1], k[:, 2]
+    K[:, 1, 2], K[:, 2, 0], K[:, 2, 1] = -k[:, 0], -k[:, 1], k[:, 0]
+    s, c = torch.sin(th)[..., None], torch.cos(th)[..., None]
+    I = torch.eye(3, dtype=xi.dtype, device=xi.device).expand_as(K)
+    R = I + s * K + (1 - c) * (K @ K)
+    V = I + ((1 - c) / th[..., None]) * K + ((th[..., None] - s) / th[..., None]) * (K @ K)
+    T = torch.zeros(xi.shape[0], 4, 4, dtype=xi.dtype, device=xi.device)
+    T[:, :3, :3] = R
+    T[:, :3, 3] = (V @ v[..., None])[..., 0]
+    T[:, 3, 3] = 1
+    return T
+
+
+def make_score_smooth():
+    """Build the autograd.Function over b3d_score_grad (imports torch lazily)."""
+    import torch
+
+    class ScoreSmooth(torch.autograd.Function):
+        """loglik = score of poses Exp(xi^) T0 under the smooth likelihood with noise
+        (sigma, p_out); gradients w.r.t. xi (exact at xi = 0: re-base T0 after each step),
+        sigma and p_out from the library's backward kernel."""
+
+        @staticmethod
+        def forward(fctx, xi, sigma, p_out, b3d_ctx, slot, T0, half_window):
+            poses = (_se3_exp(xi.detach()) @ T0).contiguous()
+            lik = dict(kind=1, radius=float(sigma), p_outlier=float(p_out), half_window=int(half_window))
+            ll, dpose, ds, dp = b3d_ctx.score_grad(slot, poses, lik)
+            fctx.save_for_backward(dpose, ds, dp)
+            return ll
+
+        @staticmethod
+        def backward(fctx, g):
+            dpose, ds, dp = fctx.saved_tensors
+            return (g[:, None] * dpose, (g * ds).sum().reshape(()), (g * dp).sum().reshape(()), None, None, None, None)
+
+    return ScoreSmooth

@@ -1,0 +1,997 @@
+// b3d_api.cu - host runtime behind the C ABI of include/b3d.h: the context (device
+// allocations under an HBM budget, error reporting, launch counting), mesh preparation
+// (vertex welding, culling of coincident internal faces of closed meshes, spatial chunking
+// for shared-memory staging), scene state (observed point cloud, background z-buffer of
+// the fixed objects and its likelihood tables, cached per object slot and likelihood), and
+// the dispatch of every entry point onto the caller's stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "b3d.h"
+#include "b3d_internal.h"
+
+using namespace b3d;
+
+namespace {
+
+struct MeshRec {
+    int64_t n_faces = 0;  // original face count (triangle ids are 0..n_faces-1)
+    int32_t flags = 0;
+    float4 *verts = nullptr;
+    int4 *tris = nullptr;
+    int4 *chunks = nullptr;
+    int *face_map = nullptr;
+    int n_chunks = 0, n_tris = 0, n_verts = 0;
+    float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+};
+
+struct LikKey {
+    int kind, w, miss_mode;
+    float radius, p_out, volume, norm;
+    bool operator==(const LikKey &o) const {
+        return kind == o.kind && w == o.w && miss_mode == o.miss_mode && radius == o.radius && p_out == o.p_out &&
+               volume == o.volume && norm == o.norm;
+    }
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct b3d_ctx {
+    int device = 0;
+    uint64_t budget = 0, used = 0;
+    std::string err;
+    int64_t launches = 0;
+    std::map<void *, size_t> allocs;
+    std::vector<MeshRec> meshes;
+
+    // scene
+    bool has_scene = false;
+    Cam cam{};
+    std::vector<int32_t> obj_mesh;
+    std::vector<int64_t> tri_base;
+    float *d_poses = nullptr;
+    int pose_cap = 0;
+    float4 *d_obs = nullptr;
+    unsigned long long *d_bg = nullptr;
+    float *d_ell_bg = nullptr, *d_gs_bg = nullptr, *d_gp_bg = nullptr;
+    double *d_sums = nullptr;
+    int64_t px_cap = 0;
+    int bg_slot = -1;
+    bool bg_dirty = true;
+    bool bg_lik_valid = false, bg_grad_valid = false;
+    LikKey bg_key{};
+
+    int *d_err = nullptr;
+
+    // coarse-to-fine and resampling scratch
+    float *d_ll = nullptr;
+    int64_t ll_cap = 0;
+    float2 *d_part = nullptr;
+    unsigned *d_counter = nullptr;
+    float *d_logz = nullptr;
+    int *d_idx = nullptr;
+    float *d_logq_tmp = nullptr;
+    int idx_cap = 0;
+    float *d_centre = nullptr;  // [3][16]: two ping-pong centres and one expand scratch
+    std::map<std::tuple<int, int, float>, float *> rot_cache;
+
+    // instrumentation
+    int instr = 0;
+    unsigned long long *d_stats = nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[B3D_K_COUNT];
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+b3d_status fail(b3d_ctx *ctx, b3d_status st, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+b3d_status cuda_fail(b3d_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, B3D_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+b3d_status check_launch(b3d_ctx *ctx, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    return B3D_OK;
+}
+
+cudaEvent_t take_event(b3d_ctx *ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets the launches made during its lifetime with events on stream s (when timing).
+struct Timed {
+    b3d_ctx *ctx;
+    int cls;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    Timed(b3d_ctx *c, int k, cudaStream_t st) : ctx(c), cls(k), s(st) {
+        if (ctx->instr & B3D_INSTR_TIMING) {
+            a = take_event(ctx);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~Timed() {
+        if (a) {
+            cudaEvent_t b = take_event(ctx);
+            cudaEventRecord(b, s);
+            ctx->pending[cls].push_back({a, b});
+        }
+    }
+};
+
+template <class T>
+b3d_status dalloc(b3d_ctx *ctx, T **p, size_t count, const char *what) {
+    *p = nullptr;
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    if (ctx->budget && ctx->used + bytes > ctx->budget)
+        return fail(ctx, B3D_EBUDGET, std::string(what) + ": allocation of " + std::to_string(bytes) +
+                                          " bytes exceeds the HBM budget (" + std::to_string(ctx->used) + " of " +
+                                          std::to_string(ctx->budget) + " used)");
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, B3D_ENOMEM, std::string(what) + ": cudaMalloc failed: " + cudaGetErrorString(e));
+    }
+    ctx->allocs[q] = bytes;
+    ctx->used += bytes;
+    *p = static_cast<T *>(q);
+    return B3D_OK;
+}
+
+template <class T>
+void dfree(b3d_ctx *ctx, T *&p) {
+    if (!p) return;
+    auto it = ctx->allocs.find((void *)p);
+    if (it != ctx->allocs.end()) {
+        ctx->used -= it->second;
+        ctx->allocs.erase(it);
+    }
+    cudaFree((void *)p);
+    p = nullptr;
+}
+
+bool finite_all(const float *p, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// Build the device-side likelihood constants from the public parameters.
+b3d_status make_lik(b3d_ctx *ctx, const b3d_lik_params *lp, Lik *L) {
+    if (!lp) return fail(ctx, B3D_EINVAL, "lik is NULL");
+    if (lp->kind != 0 && lp->kind != 1) return fail(ctx, B3D_EINVAL, "lik.kind must be 0 (ball) or 1 (Gaussian)");
+    if (!(lp->radius > 0.f) || !std::isfinite(lp->radius)) return fail(ctx, B3D_EINVAL, "lik.radius must be > 0");
+    if (!(lp->p_outlier > 0.f && lp->p_outlier < 1.f)) return fail(ctx, B3D_EINVAL, "lik.p_outlier must be in (0,1)");
+    if (lp->half_window < 0 || lp->half_window > B3D_MAX_HALF_WINDOW)
+        return fail(ctx, B3D_EINVAL, "lik.half_window must be in [0, " + std::to_string(B3D_MAX_HALF_WINDOW) + "]");
+    if (lp->miss_mode != 0 && lp->miss_mode != 1) return fail(ctx, B3D_EINVAL, "lik.miss_mode must be 0 or 1");
+    if (!std::isfinite(lp->volume) || !std::isfinite(lp->norm)) return fail(ctx, B3D_EINVAL, "lik.volume/norm not finite");
+    const Cam &c = ctx->cam;
+    const int w = lp->half_window;
+    const double V = lp->volume > 0 ? (double)lp->volume
+                                    : (double)c.W * c.H / ((double)c.fx * c.fy) *
+                                          ((double)c.far_z * c.far_z * c.far_z - (double)c.near_z * c.near_z * c.near_z) / 3.0;
+    const double K = lp->norm > 0 ? (double)lp->norm : (double)((2 * w + 1) * (2 * w + 1));
+    const double r = lp->radius, p = lp->p_outlier, pi = 3.14159265358979323846;
+    memset(L, 0, sizeof(Lik));
+    L->kind = lp->kind;
+    L->w = w;
+    L->miss_mode = lp->miss_mode;
+    L->n_lut = (2 * w + 1) * (2 * w + 1) + 1;
+    L->r2 = (float)(r * r);
+    L->inv2s2 = (float)(1.0 / (2.0 * r * r));
+    L->a = (float)(p / V);
+    const double gnorm = pow(2.0 * pi * r * r, -1.5);
+    L->bg = (float)((1.0 - p) / K * gnorm);
+    const double ball = 4.0 / 3.0 * pi * r * r * r;
+    for (int n = 0; n < L->n_lut; ++n) L->lut[n] = (float)log(p / V + (1.0 - p) * n / (K * ball));
+    L->s = (float)r;
+    L->inv_s2 = (float)(1.0 / (r * r));
+    L->b = (float)((1.0 - p) / K);
+    L->inv_V = (float)(1.0 / V);
+    L->inv_K = (float)(1.0 / K);
+    L->gnorm = (float)gnorm;
+    return B3D_OK;
+}
+
+LikKey key_of(const b3d_lik_params *lp) {
+    return LikKey{lp->kind, lp->half_window, lp->miss_mode, lp->radius, lp->p_outlier, lp->volume, lp->norm};
+}
+
+MeshView view_of(const MeshRec &m) {
+    MeshView v{};
+    v.verts = m.verts;
+    v.tris = m.tris;
+    v.chunks = m.chunks;
+    v.face_map = m.face_map;
+    v.n_chunks = m.n_chunks;
+    v.n_tris = m.n_tris;
+    for (int k = 0; k < 3; ++k) { v.lo[k] = m.lo[k]; v.hi[k] = m.hi[k]; }
+    v.cull_back = (m.flags & B3D_MESH_CLOSED) ? 1 : 0;
+    return v;
+}
+
+b3d_status check_slot(b3d_ctx *ctx, int32_t slot) {
+    if (!ctx->has_scene) return fail(ctx, B3D_EINVAL, "no scene: call b3d_set_scene first");
+    if (slot < 0 || slot >= (int32_t)ctx->obj_mesh.size())
+        return fail(ctx, B3D_ENOTFOUND, "object slot " + std::to_string(slot) + " is not in the scene");
+    return B3D_OK;
+}
+
+// Background z-buffer of every scene object except `slot` (slot = -1: all objects).
+b3d_status ensure_bg(b3d_ctx *ctx, int32_t slot, cudaStream_t s) {
+    if (!ctx->bg_dirty && ctx->bg_slot == slot) return B3D_OK;
+    const int64_t npx = (int64_t)ctx->cam.W * ctx->cam.H;
+    Timed tm(ctx, B3D_K_SCENE, s);
+    launch_bg_clear(ctx->d_bg, npx, s);
+    ++ctx->launches;
+    for (size_t o = 0; o < ctx->obj_mesh.size(); ++o) {
+        if ((int32_t)o == slot) continue;
+        const MeshRec &m = ctx->meshes[ctx->obj_mesh[o]];
+        if (m.n_tris <= 0) continue;
+        launch_bg_raster(ctx->cam, view_of(m), ctx->d_poses + 16 * o, (int)ctx->tri_base[o], ctx->d_bg, s);
+        ++ctx->launches;
+    }
+    ctx->bg_slot = slot;
+    ctx->bg_dirty = false;
+    ctx->bg_lik_valid = false;
+    ctx->bg_grad_valid = false;
+    return check_launch(ctx, "background render");
+}
+
+SceneView scene_view(b3d_ctx *ctx, int32_t slot) {
+    SceneView sv{};
+    sv.cam = ctx->cam;
+    sv.obs = ctx->d_obs;
+    sv.bg = ctx->d_bg;
+    sv.ell_bg = ctx->d_ell_bg;
+    sv.ll_bg = ctx->d_sums;
+    sv.gs_bg = ctx->d_gs_bg;
+    sv.gp_bg = ctx->d_gp_bg;
+    sv.sums_bg = ctx->d_sums;
+    if (slot >= 0) {
+        sv.mesh = view_of(ctx->meshes[ctx->obj_mesh[slot]]);
+        sv.tri_base = (int)ctx->tri_base[slot];
+    }
+    sv.err = ctx->d_err;
+    sv.stats = (ctx->instr & B3D_INSTR_WORK) ? ctx->d_stats : nullptr;
+    return sv;
+}
+
+b3d_status ensure_bg_lik(b3d_ctx *ctx, int32_t slot, const b3d_lik_params *lp, const Lik &L, bool grad,
+                         cudaStream_t s) {
+    const LikKey k = key_of(lp);
+    if (ctx->bg_lik_valid && ctx->bg_key == k && (!grad || ctx->bg_grad_valid)) return B3D_OK;
+    SceneView sv = scene_view(ctx, slot);
+    const int64_t npx = (int64_t)ctx->cam.W * ctx->cam.H;
+    Timed tm(ctx, B3D_K_SCENE, s);
+    launch_bg_tables(sv, L, ctx->d_ell_bg, grad ? ctx->d_gs_bg : nullptr, grad ? ctx->d_gp_bg : nullptr, s);
+    launch_bg_sums(ctx->d_ell_bg, grad ? ctx->d_gs_bg : nullptr, grad ? ctx->d_gp_bg : nullptr, npx, ctx->d_sums, s);
+    ctx->launches += 2;
+    ctx->bg_key = k;
+    ctx->bg_lik_valid = true;
+    ctx->bg_grad_valid = grad;
+    return check_launch(ctx, "background likelihood tables");
+}
+
+b3d_status ensure_scratch(b3d_ctx *ctx, int64_t n_ll, int m) {
+    b3d_status st;
+    if (n_ll > ctx->ll_cap) {
+        dfree(ctx, ctx->d_ll);
+        if ((st = dalloc(ctx, &ctx->d_ll, (size_t)n_ll, "score buffer")) != B3D_OK) { ctx->ll_cap = 0; return st; }
+        ctx->ll_cap = n_ll;
+    }
+    if (!ctx->d_part) {
+        if ((st = dalloc(ctx, &ctx->d_part, 1024, "resampling partials")) != B3D_OK) return st;
+        if ((st = dalloc(ctx, &ctx->d_counter, 1, "resampling counter")) != B3D_OK) return st;
+        cudaMemset(ctx->d_counter, 0, sizeof(unsigned));
+        if ((st = dalloc(ctx, &ctx->d_logz, B3D_MAX_STAGES, "log normalisers")) != B3D_OK) return st;
+        if ((st = dalloc(ctx, &ctx->d_centre, 3 * 16, "grid centres")) != B3D_OK) return st;
+    }
+    if (m > ctx->idx_cap) {
+        dfree(ctx, ctx->d_idx);
+        dfree(ctx, ctx->d_logq_tmp);
+        if ((st = dalloc(ctx, &ctx->d_idx, (size_t)m, "draw indices")) != B3D_OK) { ctx->idx_cap = 0; return st; }
+        if ((st = dalloc(ctx, &ctx->d_logq_tmp, (size_t)m, "draw log-probabilities")) != B3D_OK) { ctx->idx_cap = 0; return st; }
+        ctx->idx_cap = m;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch set-up");
+    return B3D_OK;
+}
+
+b3d_status rotation_table(b3d_ctx *ctx, const b3d_stage &st, float **out, cudaStream_t s) {
+    const float rm = st.rot_kind == 0 ? 0.f : st.rot_max;
+    auto key = std::make_tuple(st.rot_kind, st.n_rot, rm);
+    auto it = ctx->rot_cache.find(key);
+    if (it != ctx->rot_cache.end()) { *out = it->second; return B3D_OK; }
+    float *p = nullptr;
+    b3d_status r = dalloc(ctx, &p, (size_t)9 * st.n_rot, "rotation set");
+    if (r != B3D_OK) return r;
+    {
+        Timed tm(ctx, B3D_K_SCENE, s);
+        launch_rotation_set(st.rot_kind, st.n_rot, (double)rm, p, s);
+    }
+    ++ctx->launches;
+    ctx->rot_cache[key] = p;
+    *out = p;
+    return check_launch(ctx, "rotation set");
+}
+
+b3d_status check_stage(b3d_ctx *ctx, const b3d_stage &st, int64_t *n_out) {
+    if (st.n_per_axis < 1 || st.n_per_axis > 1024) return fail(ctx, B3D_EINVAL, "stage.n_per_axis must be in [1, 1024]");
+    if (st.n_rot < 1) return fail(ctx, B3D_EINVAL, "stage.n_rot must be >= 1");
+    if (st.rot_kind != 0 && st.rot_kind != 1) return fail(ctx, B3D_EINVAL, "stage.rot_kind must be 0 or 1");
+    if (!(st.step > 0.f) || !std::isfinite(st.step)) return fail(ctx, B3D_EINVAL, "stage.step must be > 0");
+    if (!std::isfinite(st.rot_max)) return fail(ctx, B3D_EINVAL, "stage.rot_max must be finite");
+    const int64_t n = (int64_t)st.n_per_axis * st.n_per_axis * st.n_per_axis * st.n_rot;
+    if (n > INT32_MAX) return fail(ctx, B3D_EINVAL, "stage has more than 2^31-1 hypotheses");
+    *n_out = n;
+    return B3D_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+
+}  // namespace
+
+// ==========================================================================================
+// C ABI
+// ==========================================================================================
+extern "C" {
+
+b3d_status b3d_create(b3d_ctx **out, int32_t device, uint64_t hbm_budget_bytes) {
+    if (!out) { g_create_error = "out is NULL"; return B3D_EINVAL; }
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        g_create_error = "no CUDA device " + std::to_string(device) + " (" + std::to_string(n) + " visible" +
+                         (e != cudaSuccess ? std::string(", ") + cudaGetErrorString(e) : std::string()) + ")";
+        return B3D_EINVAL;
+    }
+    b3d_ctx *ctx = new (std::nothrow) b3d_ctx();
+    if (!ctx) { g_create_error = "host allocation failed"; return B3D_ENOMEM; }
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    DeviceGuard g(device);
+    b3d_status st = dalloc(ctx, &ctx->d_err, 1, "error flag");
+    if (st != B3D_OK) {
+        g_create_error = ctx->err;
+        delete ctx;
+        return st;
+    }
+    cudaMemset(ctx->d_err, 0, sizeof(int));
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        g_create_error = std::string("device set-up: ") + cudaGetErrorString(e);
+        cudaFree(ctx->d_err);
+        delete ctx;
+        return B3D_ECUDA;
+    }
+    g_create_error.clear();
+    *out = ctx;
+    return B3D_OK;
+}
+
+b3d_status b3d_destroy(b3d_ctx *ctx) {
+    if (!ctx) return B3D_EINVAL;
+    {
+        DeviceGuard g(ctx->device);
+        cudaDeviceSynchronize();
+        for (auto &kv : ctx->allocs) cudaFree(kv.first);
+        for (auto &v : ctx->pending)
+            for (auto &ab : v) { cudaEventDestroy(ab.first); cudaEventDestroy(ab.second); }
+        for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    }
+    delete ctx;
+    return B3D_OK;
+}
+
+const char *b3d_last_error(b3d_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+int64_t b3d_launch_count(b3d_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+b3d_status b3d_load_mesh(b3d_ctx *ctx, const float *verts, int64_t n_v, const int32_t *faces, int64_t n_f, int32_t flags,
+                         int32_t *mesh_id) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    if (!verts || !faces || !mesh_id) return fail(ctx, B3D_EINVAL, "verts, faces and mesh_id must be non-NULL");
+    if (n_v < 1 || n_f < 1) return fail(ctx, B3D_EINVAL, "a mesh needs n_v >= 1 and n_f >= 1");
+    if (n_f > (int64_t)1 << 30) return fail(ctx, B3D_EINVAL, "too many faces");
+    if (flags & ~B3D_MESH_CLOSED) return fail(ctx, B3D_EINVAL, "unknown mesh flags");
+    if (!finite_all(verts, 3 * n_v)) return fail(ctx, B3D_EINVAL, "vertex coordinates must be finite");
+    for (int64_t i = 0; i < 3 * n_f; ++i)
+        if (faces[i] < 0 || faces[i] >= n_v) return fail(ctx, B3D_EINVAL, "face " + std::to_string(i / 3) + " indexes a missing vertex");
+
+    // 1. weld vertices with bitwise-equal coordinates (-0 == +0)
+    struct K3 {
+        uint32_t a, b, c;
+        bool operator==(const K3 &o) const { return a == o.a && b == o.b && c == o.c; }
+    };
+    struct H3 {
+        size_t operator()(const K3 &k) const {
+            uint64_t h = k.a * 0x9E3779B97F4A7C15ULL;
+            h ^= (uint64_t)k.b * 0xC2B2AE3D27D4EB4FULL + (h << 6) + (h >> 2);
+            h ^= (uint64_t)k.c * 0x165667B19E3779F9ULL + (h << 6) + (h >> 2);
+            return (size_t)h;
+        }
+    };
+    auto bits = [](float x) {
+        if (x == 0.f) x = 0.f;
+        uint32_t u;
+        memcpy(&u, &x, 4);
+        return u;
+    };
+    std::unordered_map<K3, int32_t, H3> weld;
+    weld.reserve((size_t)n_v * 2);
+    std::vector<int32_t> remap((size_t)n_v);
+    std::vector<float> wv;
+    for (int64_t i = 0; i < n_v; ++i) {
+        K3 k{bits(verts[3 * i]), bits(verts[3 * i + 1]), bits(verts[3 * i + 2])};
+        auto it = weld.find(k);
+        if (it == weld.end()) {
+            const int32_t id = (int32_t)(wv.size() / 3);
+            weld.emplace(k, id);
+            wv.push_back(verts[3 * i]); wv.push_back(verts[3 * i + 1]); wv.push_back(verts[3 * i + 2]);
+            remap[i] = id;
+        } else {
+            remap[i] = it->second;
+        }
+    }
+    // 2. triangles on welded vertices; drop degenerate ones (they cover nothing)
+    struct Tri { int32_t a, b, c, f; };
+    std::vector<Tri> tris;
+    tris.reserve((size_t)n_f);
+    for (int64_t f = 0; f < n_f; ++f) {
+        Tri t{remap[faces[3 * f]], remap[faces[3 * f + 1]], remap[faces[3 * f + 2]], (int32_t)f};
+        if (t.a == t.b || t.b == t.c || t.a == t.c) continue;
+        tris.push_back(t);
+    }
+    // 3. closed meshes: coincident triangles of opposite orientation are internal faces
+    if (flags & B3D_MESH_CLOSED) {
+        struct KT {
+            int32_t a, b, c;
+            bool operator==(const KT &o) const { return a == o.a && b == o.b && c == o.c; }
+        };
+        struct HT {
+            size_t operator()(const KT &k) const {
+                return (size_t)((uint64_t)k.a * 0x9E3779B97F4A7C15ULL ^ (uint64_t)k.b * 0xC2B2AE3D27D4EB4FULL ^
+                                (uint64_t)k.c * 0x165667B19E3779F9ULL);
+            }
+        };
+        std::unordered_map<KT, std::vector<int32_t>, HT> groups;
+        groups.reserve(tris.size() * 2);
+        auto parity = [](const Tri &t) {  // +1 if (a,b,c) is an even permutation of its sorted order
+            int v[3] = {t.a, t.b, t.c}, inv = 0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = i + 1; j < 3; ++j) inv += v[i] > v[j];
+            return (inv & 1) ? -1 : 1;
+        };
+        for (size_t i = 0; i < tris.size(); ++i) {
+            int v[3] = {tris[i].a, tris[i].b, tris[i].c};
+            std::sort(v, v + 3);
+            groups[KT{v[0], v[1], v[2]}].push_back((int32_t)i);
+        }
+        std::vector<char> drop(tris.size(), 0);
+        for (auto &kv : groups) {
+            auto &g = kv.second;
+            if (g.size() < 2) continue;
+            std::vector<int32_t> pos, neg;
+            for (int32_t i : g) (parity(tris[i]) > 0 ? pos : neg).push_back(i);
+            const size_t k = std::min(pos.size(), neg.size());
+            for (size_t j = 0; j < k; ++j) { drop[pos[j]] = 1; drop[neg[j]] = 1; }
+        }
+        std::vector<Tri> kept;
+        kept.reserve(tris.size());
+        for (size_t i = 0; i < tris.size(); ++i)
+            if (!drop[i]) kept.push_back(tris[i]);
+        tris.swap(kept);
+    }
+    // 4. spatial order (Morton code of the centroid) so chunks stay compact
+    MeshRec rec;
+    rec.n_faces = n_f;
+    rec.flags = flags;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (const Tri &t : tris)
+        for (int32_t v : {t.a, t.b, t.c})
+            for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], wv[3 * v + k]); hi[k] = std::max(hi[k], wv[3 * v + k]); }
+    if (tris.empty())
+        for (int k = 0; k < 3; ++k) { lo[k] = 0; hi[k] = 0; }
+    for (int k = 0; k < 3; ++k) { rec.lo[k] = lo[k]; rec.hi[k] = hi[k]; }
+    auto spread = [](uint32_t x) {  // 10 bits -> every third bit
+        x &= 0x3ff;
+        x = (x | (x << 16)) & 0x30000ff;
+        x = (x | (x << 8)) & 0x300f00f;
+        x = (x | (x << 4)) & 0x30c30c3;
+        x = (x | (x << 2)) & 0x9249249;
+        return x;
+    };
+    std::vector<std::pair<uint32_t, int32_t>> order(tris.size());
+    for (size_t i = 0; i < tris.size(); ++i) {
+        uint32_t q[3];
+        for (int k = 0; k < 3; ++k) {
+            const float cen = (wv[3 * tris[i].a + k] + wv[3 * tris[i].b + k] + wv[3 * tris[i].c + k]) / 3.f;
+            const float ext = hi[k] - lo[k];
+            q[k] = ext > 0 ? (uint32_t)std::min(1023.f, std::max(0.f, (cen - lo[k]) / ext * 1023.f)) : 0u;
+        }
+        order[i] = {spread(q[0]) | (spread(q[1]) << 1) | (spread(q[2]) << 2), (int32_t)i};
+    }
+    std::sort(order.begin(), order.end());
+    // 5. chunks of at most kChunkV distinct vertices
+    std::vector<float4> cverts;
+    std::vector<int4> ctris, chunks;
+    std::vector<int32_t> local(wv.size() / 3, -1);
+    std::vector<int32_t> touched;
+    int v_begin = 0, t_begin = 0;
+    auto close_chunk = [&]() {
+        chunks.push_back(make_int4(v_begin, (int)cverts.size(), t_begin, (int)ctris.size()));
+        for (int32_t v : touched) local[v] = -1;
+        touched.clear();
+        v_begin = (int)cverts.size();
+        t_begin = (int)ctris.size();
+    };
+    for (auto &o : order) {
+        const Tri &t = tris[o.second];
+        int fresh = 0;
+        for (int32_t v : {t.a, t.b, t.c}) fresh += local[v] < 0;
+        if ((int)cverts.size() - v_begin + fresh > kChunkV) close_chunk();
+        int li[3], k = 0;
+        for (int32_t v : {t.a, t.b, t.c}) {
+            if (local[v] < 0) {
+                local[v] = (int32_t)cverts.size() - v_begin;
+                touched.push_back(v);
+                cverts.push_back(make_float4(wv[3 * v], wv[3 * v + 1], wv[3 * v + 2], 0.f));
+            }
+            li[k++] = local[v];
+        }
+        ctris.push_back(make_int4(li[0], li[1], li[2], t.f));
+    }
+    if (!ctris.empty()) close_chunk();
+    std::vector<int> fmap((size_t)n_f, -1);
+    for (size_t t = 0; t < ctris.size(); ++t) fmap[ctris[t].w] = (int)t;
+    rec.n_tris = (int)ctris.size();
+    rec.n_verts = (int)cverts.size();
+    rec.n_chunks = (int)chunks.size();
+
+    DeviceGuard g(ctx->device);
+    b3d_status st;
+    if ((st = dalloc(ctx, &rec.verts, cverts.size(), "mesh vertices")) != B3D_OK) return st;
+    if ((st = dalloc(ctx, &rec.tris, ctris.size(), "mesh triangles")) != B3D_OK) { dfree(ctx, rec.verts); return st; }
+    if ((st = dalloc(ctx, &rec.chunks, chunks.size(), "mesh chunks")) != B3D_OK) {
+        dfree(ctx, rec.verts); dfree(ctx, rec.tris); return st;
+    }
+    if ((st = dalloc(ctx, &rec.face_map, fmap.size(), "mesh face map")) != B3D_OK) {
+        dfree(ctx, rec.verts); dfree(ctx, rec.tris); dfree(ctx, rec.chunks); return st;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!cverts.empty()) e = cudaMemcpy(rec.verts, cverts.data(), cverts.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !ctris.empty())
+        e = cudaMemcpy(rec.tris, ctris.data(), ctris.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !chunks.empty())
+        e = cudaMemcpy(rec.chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(rec.face_map, fmap.data(), fmap.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        dfree(ctx, rec.verts); dfree(ctx, rec.tris); dfree(ctx, rec.chunks); dfree(ctx, rec.face_map);
+        return cuda_fail(ctx, e, "mesh upload");
+    }
+    ctx->meshes.push_back(rec);
+    *mesh_id = (int32_t)ctx->meshes.size() - 1;
+    return B3D_OK;
+}
+
+b3d_status b3d_set_scene(b3d_ctx *ctx, const b3d_intrinsics *intr, int32_t n_obj, const int32_t *mesh_ids,
+                         const float *poses, const float *obs_depth_dev, b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    if (!intr || !obs_depth_dev) return fail(ctx, B3D_EINVAL, "intrinsics and obs_depth_dev must be non-NULL");
+    if (n_obj < 1 || !mesh_ids || !poses) return fail(ctx, B3D_EINVAL, "a scene needs n_obj >= 1, mesh_ids and poses");
+    if (intr->width < 1 || intr->height < 1 || (int64_t)intr->width * intr->height > ((int64_t)1 << 26))
+        return fail(ctx, B3D_EINVAL, "image size must be >= 1x1 and at most 2^26 pixels");
+    const float vals[6] = {intr->fx, intr->fy, intr->cx, intr->cy, intr->near_z, intr->far_z};
+    if (!finite_all(vals, 6) || !(intr->fx > 0) || !(intr->fy > 0) || !(intr->near_z > 0) || !(intr->far_z > intr->near_z))
+        return fail(ctx, B3D_EINVAL, "intrinsics need fx, fy > 0 and 0 < near_z < far_z, all finite");
+    for (int32_t k = 0; k < n_obj; ++k)
+        if (mesh_ids[k] < 0 || mesh_ids[k] >= (int32_t)ctx->meshes.size())
+            return fail(ctx, B3D_ENOTFOUND, "scene object " + std::to_string(k) + " names an unknown mesh");
+    if (!finite_all(poses, 16 * (int64_t)n_obj)) return fail(ctx, B3D_EINVAL, "poses must be finite");
+    int64_t total_faces = 0;
+    for (int32_t k = 0; k < n_obj; ++k) total_faces += ctx->meshes[mesh_ids[k]].n_faces;
+    if (total_faces >= INT32_MAX) return fail(ctx, B3D_EINVAL, "scene has more than 2^31-1 triangles");
+    if (!aligned16(obs_depth_dev) && ((uintptr_t)obs_depth_dev & 3u))
+        return fail(ctx, B3D_EINVAL, "obs_depth_dev must be 4-byte aligned");
+
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t npx = (int64_t)intr->width * intr->height;
+    b3d_status st;
+    if (npx > ctx->px_cap) {
+        dfree(ctx, ctx->d_obs); dfree(ctx, ctx->d_bg); dfree(ctx, ctx->d_ell_bg); dfree(ctx, ctx->d_gs_bg); dfree(ctx, ctx->d_gp_bg);
+        ctx->px_cap = 0;
+        if ((st = dalloc(ctx, &ctx->d_obs, (size_t)npx, "observed points")) != B3D_OK) return st;
+        if ((st = dalloc(ctx, &ctx->d_bg, (size_t)npx, "background z-buffer")) != B3D_OK) return st;
+        if ((st = dalloc(ctx, &ctx->d_ell_bg, (size_t)npx, "background likelihood")) != B3D_OK) return st;
+        if ((st = dalloc(ctx, &ctx->d_gs_bg, (size_t)npx, "background sigma gradient")) != B3D_OK) return st;
+        if ((st = dalloc(ctx, &ctx->d_gp_bg, (size_t)npx, "background p_out gradient")) != B3D_OK) return st;
+        ctx->px_cap = npx;
+    }
+    if (!ctx->d_sums && (st = dalloc(ctx, &ctx->d_sums, 3, "background sums")) != B3D_OK) return st;
+    if (n_obj > ctx->pose_cap) {
+        dfree(ctx, ctx->d_poses);
+        ctx->pose_cap = 0;
+        if ((st = dalloc(ctx, &ctx->d_poses, (size_t)16 * n_obj, "scene poses")) != B3D_OK) return st;
+        ctx->pose_cap = n_obj;
+    }
+    cudaError_t e = cudaMemcpyAsync(ctx->d_poses, poses, sizeof(float) * 16 * n_obj, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "scene poses upload");
+    Cam c{};
+    c.W = intr->width; c.H = intr->height;
+    c.fx = intr->fx; c.fy = intr->fy; c.cx = intr->cx; c.cy = intr->cy;
+    c.near_z = intr->near_z; c.far_z = intr->far_z;
+    c.inv_fx = 1.0f / intr->fx; c.inv_fy = 1.0f / intr->fy;
+    ctx->cam = c;
+    ctx->obj_mesh.assign(mesh_ids, mesh_ids + n_obj);
+    ctx->tri_base.assign(n_obj, 0);
+    for (int32_t k = 1; k < n_obj; ++k) ctx->tri_base[k] = ctx->tri_base[k - 1] + ctx->meshes[mesh_ids[k - 1]].n_faces;
+    {
+        Timed tm(ctx, B3D_K_SCENE, s);
+        launch_obs_points(c, obs_depth_dev, ctx->d_obs, s);
+    }
+    ++ctx->launches;
+    ctx->has_scene = true;
+    ctx->bg_dirty = true;
+    ctx->bg_lik_valid = ctx->bg_grad_valid = false;
+    return check_launch(ctx, "set_scene");
+}
+
+b3d_status b3d_set_observation(b3d_ctx *ctx, const float *obs_depth_dev, b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    if (!ctx->has_scene) return fail(ctx, B3D_EINVAL, "no scene: call b3d_set_scene first");
+    if (!obs_depth_dev) return fail(ctx, B3D_EINVAL, "obs_depth_dev is NULL");
+    DeviceGuard g(ctx->device);
+    {
+        Timed tm(ctx, B3D_K_SCENE, (cudaStream_t)stream);
+        launch_obs_points(ctx->cam, obs_depth_dev, ctx->d_obs, (cudaStream_t)stream);
+    }
+    ++ctx->launches;
+    ctx->bg_lik_valid = ctx->bg_grad_valid = false;
+    return check_launch(ctx, "set_observation");
+}
+
+b3d_status b3d_set_object_pose_dev(b3d_ctx *ctx, int32_t obj, const float *pose_dev, b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    b3d_status st = check_slot(ctx, obj);
+    if (st != B3D_OK) return st;
+    if (!pose_dev) return fail(ctx, B3D_EINVAL, "pose_dev is NULL");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaMemcpyAsync(ctx->d_poses + 16 * obj, pose_dev, 16 * sizeof(float), cudaMemcpyDeviceToDevice,
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set_object_pose_dev");
+    ctx->bg_dirty = true;
+    return B3D_OK;
+}
+
+b3d_status b3d_render_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const float *poses_dev, float *depth_dev,
+                            int32_t *triid_dev, b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    b3d_status st = check_slot(ctx, obj_slot);
+    if (st != B3D_OK) return st;
+    if (n_hyp < 0) return fail(ctx, B3D_EINVAL, "n_hyp must be >= 0");
+    if (n_hyp == 0) return B3D_OK;
+    if (!poses_dev || !depth_dev) return fail(ctx, B3D_EINVAL, "poses_dev and depth_dev must be non-NULL");
+    if (!aligned16(poses_dev)) return fail(ctx, B3D_EINVAL, "poses_dev must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ensure_bg(ctx, obj_slot, s)) != B3D_OK) return st;
+    {
+        Timed tm(ctx, B3D_K_RENDER, s);
+        launch_render_list(scene_view(ctx, obj_slot), PoseList{poses_dev}, n_hyp, depth_dev, triid_dev, 0, s);
+    }
+    ++ctx->launches;
+    return check_launch(ctx, "render_batch");
+}
+
+b3d_status b3d_score_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const float *poses_dev,
+                           const b3d_lik_params *lik, float *loglik_dev, b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    b3d_status st = check_slot(ctx, obj_slot);
+    if (st != B3D_OK) return st;
+    Lik L;
+    if ((st = make_lik(ctx, lik, &L)) != B3D_OK) return st;
+    if (n_hyp < 0) return fail(ctx, B3D_EINVAL, "n_hyp must be >= 0");
+    if (n_hyp == 0) return B3D_OK;
+    if (!poses_dev || !loglik_dev) return fail(ctx, B3D_EINVAL, "poses_dev and loglik_dev must be non-NULL");
+    if (!aligned16(poses_dev)) return fail(ctx, B3D_EINVAL, "poses_dev must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ensure_bg(ctx, obj_slot, s)) != B3D_OK) return st;
+    if ((st = ensure_bg_lik(ctx, obj_slot, lik, L, false, s)) != B3D_OK) return st;
+    {
+        Timed tm(ctx, B3D_K_SCORE, s);
+        launch_score_list(scene_view(ctx, obj_slot), L, PoseList{poses_dev}, n_hyp, loglik_dev, 0, s);
+    }
+    ++ctx->launches;
+    return check_launch(ctx, "score_batch");
+}
+
+b3d_status b3d_score_depth_batch(b3d_ctx *ctx, int64_t n_hyp, const float *depth_dev, const int32_t *triid_dev,
+                                 const b3d_lik_params *lik, float *loglik_dev, b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    if (!ctx->has_scene) return fail(ctx, B3D_EINVAL, "no scene: call b3d_set_scene first");
+    Lik L;
+    b3d_status st = make_lik(ctx, lik, &L);
+    if (st != B3D_OK) return st;
+    if (n_hyp < 0) return fail(ctx, B3D_EINVAL, "n_hyp must be >= 0");
+    if (n_hyp == 0) return B3D_OK;
+    if (!depth_dev || !loglik_dev) return fail(ctx, B3D_EINVAL, "depth_dev and loglik_dev must be non-NULL");
+    if (lik->miss_mode == 1 && !triid_dev) return fail(ctx, B3D_EINVAL, "miss_mode 1 needs triid_dev");
+    if ((int64_t)ctx->cam.W * (2 * lik->half_window + 1) > 2 * kRegionPx)
+        return fail(ctx, B3D_EINVAL, "image too wide for this window in score_depth_batch (W (2w+1) must be <= 8192)");
+    DeviceGuard g(ctx->device);
+    {
+        Timed tm(ctx, B3D_K_SCORE_DEPTH, (cudaStream_t)stream);
+        launch_score_depth(scene_view(ctx, -1), L, depth_dev, triid_dev, n_hyp, loglik_dev, 0, (cudaStream_t)stream);
+    }
+    ++ctx->launches;
+    return check_launch(ctx, "score_depth_batch");
+}
+
+b3d_status b3d_expand_hypotheses(b3d_ctx *ctx, const float *centre_pose, const float *grid_frame,
+                                 const b3d_stage *stage, float *poses_dev, b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    if (!centre_pose || !grid_frame || !stage || !poses_dev)
+        return fail(ctx, B3D_EINVAL, "centre_pose, grid_frame, stage and poses_dev must be non-NULL");
+    if (!finite_all(centre_pose, 16) || !finite_all(grid_frame, 9)) return fail(ctx, B3D_EINVAL, "non-finite pose or grid frame");
+    int64_t n;
+    b3d_status st = check_stage(ctx, *stage, &n);
+    if (st != B3D_OK) return st;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ensure_scratch(ctx, 0, 0)) != B3D_OK) return st;
+    float *rot = nullptr;
+    if ((st = rotation_table(ctx, *stage, &rot, s)) != B3D_OK) return st;
+    float *centre = ctx->d_centre + 32;
+    Timed tm(ctx, B3D_K_SCENE, s);
+    launch_set16(centre, centre_pose, s);
+    PoseGrid P{};
+    P.centre = centre;
+    P.rot = rot;
+    for (int k = 0; k < 9; ++k) P.G[k] = grid_frame[k];
+    P.n = stage->n_per_axis;
+    P.n_rot = stage->n_rot;
+    P.step = stage->step;
+    launch_expand(P, n, poses_dev, s);
+    ctx->launches += 2;
+    return check_launch(ctx, "expand_hypotheses");
+}
+
+b3d_status b3d_lse_resample(b3d_ctx *ctx, int64_t n, const float *loglik_dev, int32_t m, uint64_t seed, int32_t stage,
+                            float *logz_dev, int32_t *idx_dev, float *logq_dev, b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    if (n < 1 || n > INT32_MAX) return fail(ctx, B3D_EINVAL, "n must be in [1, 2^31-1]");
+    if (m < 0) return fail(ctx, B3D_EINVAL, "m must be >= 0");
+    if (!loglik_dev || !logz_dev) return fail(ctx, B3D_EINVAL, "loglik_dev and logz_dev must be non-NULL");
+    if (m > 0 && (!idx_dev || !logq_dev)) return fail(ctx, B3D_EINVAL, "idx_dev and logq_dev must be non-NULL when m > 0");
+    DeviceGuard g(ctx->device);
+    b3d_status st = ensure_scratch(ctx, 0, 0);
+    if (st != B3D_OK) return st;
+    {
+        Timed tm(ctx, B3D_K_RESAMPLE, (cudaStream_t)stream);
+        launch_lse_resample(loglik_dev, n, m, seed, stage, ctx->d_part, ctx->d_counter, logz_dev, idx_dev, logq_dev,
+                            ctx->d_err, (cudaStream_t)stream);
+    }
+    ++ctx->launches;
+    return check_launch(ctx, "lse_resample");
+}
+
+b3d_status b3d_enumerate_c2f(b3d_ctx *ctx, int32_t obj_slot, const float *centre_pose, const b3d_c2f_schedule *sch,
+                             const b3d_lik_params *lik, float *particles_dev, float *logw_dev, float *logq_dev,
+                             b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    b3d_status st = check_slot(ctx, obj_slot);
+    if (st != B3D_OK) return st;
+    Lik L;
+    if ((st = make_lik(ctx, lik, &L)) != B3D_OK) return st;
+    if (!centre_pose || !sch || !particles_dev || !logw_dev || !logq_dev)
+        return fail(ctx, B3D_EINVAL, "centre_pose, schedule and the three outputs must be non-NULL");
+    if (!finite_all(centre_pose, 16) || !finite_all(sch->grid_frame, 9)) return fail(ctx, B3D_EINVAL, "non-finite centre or grid frame");
+    if (sch->n_stages < 1 || sch->n_stages > B3D_MAX_STAGES) return fail(ctx, B3D_EINVAL, "n_stages must be in [1, 8]");
+    if (sch->n_particles < 1 || sch->n_particles > (1 << 20)) return fail(ctx, B3D_EINVAL, "n_particles must be in [1, 2^20]");
+    int64_t n_max = 0, n_t[B3D_MAX_STAGES];
+    for (int t = 0; t < sch->n_stages; ++t) {
+        if ((st = check_stage(ctx, sch->stage[t], &n_t[t])) != B3D_OK) return st;
+        n_max = std::max(n_max, n_t[t]);
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ensure_scratch(ctx, n_max, sch->n_particles)) != B3D_OK) return st;
+    float *rot[B3D_MAX_STAGES];
+    for (int t = 0; t < sch->n_stages; ++t)
+        if ((st = rotation_table(ctx, sch->stage[t], &rot[t], s)) != B3D_OK) return st;
+    if ((st = ensure_bg(ctx, obj_slot, s)) != B3D_OK) return st;
+    if ((st = ensure_bg_lik(ctx, obj_slot, lik, L, false, s)) != B3D_OK) return st;
+    const SceneView sv = scene_view(ctx, obj_slot);
+    {
+        Timed tm(ctx, B3D_K_SCENE, s);
+        launch_set16(ctx->d_centre, centre_pose, s);
+    }
+    ++ctx->launches;
+    for (int t = 0; t < sch->n_stages; ++t) {
+        PoseGrid P{};
+        P.centre = ctx->d_centre + 16 * (t & 1);
+        P.rot = rot[t];
+        for (int k = 0; k < 9; ++k) P.G[k] = sch->grid_frame[k];
+        P.n = sch->stage[t].n_per_axis;
+        P.n_rot = sch->stage[t].n_rot;
+        P.step = sch->stage[t].step;
+        {
+            Timed tm(ctx, B3D_K_SCORE, s);
+            launch_score_grid(sv, L, P, n_t[t], ctx->d_ll, 0, s);
+        }
+        {
+            Timed tm(ctx, B3D_K_RESAMPLE, s);
+            launch_lse_resample(ctx->d_ll, n_t[t], sch->n_particles, sch->seed, t, ctx->d_part, ctx->d_counter,
+                                ctx->d_logz + t, ctx->d_idx, ctx->d_logq_tmp, ctx->d_err, s);
+        }
+        const int last = t == sch->n_stages - 1;
+        {
+            Timed tm(ctx, B3D_K_SELECT, s);
+            launch_c2f_select(ctx->d_ll, ctx->d_idx, sch->n_particles, P, ctx->d_logz + t, last, sch->seed,
+                              sch->n_stages, ctx->d_centre + 16 * ((t + 1) & 1), particles_dev, logw_dev, logq_dev, s);
+        }
+        ctx->launches += 3;
+    }
+    return check_launch(ctx, "enumerate_c2f");
+}
+
+b3d_status b3d_score_grad(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const float *poses_dev,
+                          const b3d_lik_params *lik, float *loglik_dev, float *dpose_dev, float *dsigma_dev,
+                          float *dpout_dev, b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    b3d_status st = check_slot(ctx, obj_slot);
+    if (st != B3D_OK) return st;
+    Lik L;
+    if ((st = make_lik(ctx, lik, &L)) != B3D_OK) return st;
+    if (lik->kind != 1) return fail(ctx, B3D_EINVAL, "score_grad needs the smooth likelihood (kind 1)");
+    if (n_hyp < 0) return fail(ctx, B3D_EINVAL, "n_hyp must be >= 0");
+    if (n_hyp == 0) return B3D_OK;
+    if (!poses_dev || !loglik_dev) return fail(ctx, B3D_EINVAL, "poses_dev and loglik_dev must be non-NULL");
+    if (!aligned16(poses_dev)) return fail(ctx, B3D_EINVAL, "poses_dev must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ensure_bg(ctx, obj_slot, s)) != B3D_OK) return st;
+    if ((st = ensure_bg_lik(ctx, obj_slot, lik, L, true, s)) != B3D_OK) return st;
+    {
+        Timed tm(ctx, B3D_K_GRAD, s);
+        launch_grad_list(scene_view(ctx, obj_slot), L, PoseList{poses_dev}, n_hyp, loglik_dev, dpose_dev, dsigma_dev,
+                         dpout_dev, 0, s);
+    }
+    ++ctx->launches;
+    return check_launch(ctx, "score_grad");
+}
+
+b3d_status b3d_set_instrumentation(b3d_ctx *ctx, int32_t flags) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    if (flags & ~(B3D_INSTR_TIMING | B3D_INSTR_WORK)) return fail(ctx, B3D_EINVAL, "unknown instrumentation flags");
+    DeviceGuard g(ctx->device);
+    if ((flags & B3D_INSTR_WORK) && !ctx->d_stats) {
+        b3d_status st = dalloc(ctx, &ctx->d_stats, kNumStats, "work counters");
+        if (st != B3D_OK) return st;
+        cudaError_t e = cudaMemset(ctx->d_stats, 0, kNumStats * sizeof(unsigned long long));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "work counters");
+    }
+    ctx->instr = flags;
+    return B3D_OK;
+}
+
+b3d_status b3d_kernel_time(b3d_ctx *ctx, int32_t kernel_class, double *total_ms, int64_t *launches) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    if (kernel_class < 0 || kernel_class >= B3D_K_COUNT || !total_ms || !launches)
+        return fail(ctx, B3D_EINVAL, "kernel_class out of range or NULL output");
+    DeviceGuard g(ctx->device);
+    double ms = 0;
+    int64_t n = 0;
+    for (auto &ab : ctx->pending[kernel_class]) {
+        cudaError_t e = cudaEventSynchronize(ab.second);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel timing");
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ab.first, ab.second);
+        ms += t;
+        ++n;
+        ctx->event_pool.push_back(ab.first);
+        ctx->event_pool.push_back(ab.second);
+    }
+    ctx->pending[kernel_class].clear();
+    *total_ms = ms;
+    *launches = n;
+    return B3D_OK;
+}
+
+b3d_status b3d_work_counters(b3d_ctx *ctx, int64_t *out) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    if (!out) return fail(ctx, B3D_EINVAL, "out is NULL");
+    if (!ctx->d_stats) {
+        for (int k = 0; k < kNumStats; ++k) out[k] = 0;
+        return B3D_OK;
+    }
+    DeviceGuard g(ctx->device);
+    unsigned long long h[kNumStats];
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h, ctx->d_stats, sizeof h, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_stats, 0, sizeof h);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "work counters");
+    for (int k = 0; k < kNumStats; ++k) out[k] = (int64_t)h[k];
+    return B3D_OK;
+}
+
+b3d_status b3d_sync(b3d_ctx *ctx, b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    int flag = 0;
+    e = cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "error flag read");
+    if (flag) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        std::string what;
+        if (flag & 1) what += " bounds check failed;";
+        if (flag & 2) what += " bounded wait expired;";
+        if (flag & 4) what += " resampling over all -inf scores;";
+        return fail(ctx, B3D_EDEVICE, "device error flag " + std::to_string(flag) + ":" + what);
+    }
+    return B3D_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+// b3d_internal.h - device-side data layout and kernel launchers of libb3d (not part of
+// the public ABI; include/b3d.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace b3d {
+
+constexpr int kThreads = 256;          // threads per CTA of the render/score kernels
+constexpr int kChunkV = 2048;          // vertices per mesh chunk staged in shared memory
+constexpr int kRegionPx = 4096;        // z-buffer pixels per screen tile in shared memory
+constexpr int kMaxHalfWindow = 7;
+constexpr int kMaxLut = (2 * kMaxHalfWindow + 1) * (2 * kMaxHalfWindow + 1) + 1;
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr int kNumStats = 8;  // work counters of the fused kernel (see k_fused)
+
+struct Cam {
+    int W, H;
+    float fx, fy, cx, cy, near_z, far_z;
+    float inv_fx, inv_fy;
+};
+
+// One object's render data. A mesh is split into chunks of at most kChunkV vertices; a
+// chunk owns a contiguous run of triangles whose vertex indices are local to the chunk.
+struct MeshView {
+    const float4 *verts;   // concatenated chunk vertex lists, object frame (w unused)
+    const int4 *tris;      // (i0, i1, i2, original face index)
+    const int4 *chunks;    // (v_begin, v_end, t_begin, t_end)
+    const int *face_map;   // [n_faces] original face index -> position in tris, -1 if culled
+    int n_chunks;
+    int n_tris;
+    float lo[3], hi[3];    // object-frame bounding box of the vertices
+    int cull_back;         // closed outward mesh: faces turned away are skipped
+};
+
+// Windowed likelihood constants (Eq. 1 with the window of Sec. III-B).
+struct Lik {
+    int kind;        // 0 inlier ball, 1 Gaussian
+    int w;           // half window
+    int miss_mode;   // 0 miss = far-plane point, 1 miss = no point
+    int n_lut;       // (2w+1)^2 + 1
+    float r2;        // kind 0: r^2
+    float inv2s2;    // kind 1: 1 / (2 s^2)
+    float a;         // p_out / V
+    float bg;        // kind 1: (1 - p_out) / K * (2 pi s^2)^(-3/2)
+    float lut[kMaxLut];  // kind 0: l(n) = log(a + (1 - p_out) n / (K (4/3) pi r^3))
+    // gradient constants (kind 1)
+    float s;         // sigma
+    float inv_s2;    // 1 / s^2
+    float b;         // (1 - p_out) / K
+    float inv_V;     // 1 / V
+    float inv_K;     // 1 / K
+    float gnorm;     // (2 pi s^2)^(-3/2)
+};
+
+// The scene as the fused kernels see it, for one hypothesised object (the slot).
+struct SceneView {
+    Cam cam;
+    const float4 *obs;                 // [H*W] observed points (x, y, z, 1) or (0,0,0,0) if not scored
+    const unsigned long long *bg;      // [H*W] (depth bits << 32 | triangle id) of the fixed objects
+    const float *ell_bg;               // [H*W] l_i of the fixed objects alone (0 where not scored)
+    const double *ll_bg;               // [1]   sum of ell_bg
+    const float *gs_bg;                // [H*W] d l_i / d sigma, fixed objects alone (gradient only)
+    const float *gp_bg;                // [H*W] d l_i / d p_out, fixed objects alone (gradient only)
+    const double *sums_bg;             // [3]   sums of ell_bg, gs_bg, gp_bg (gradient only)
+    MeshView mesh;                     // the slot object
+    int tri_base;                      // global triangle id of the slot object's face 0
+    int *err;                          // device error flag
+    unsigned long long *stats;         // [kNumStats] work counters, or NULL (no counting)
+};
+
+// Hypothesis poses as 12 floats: R row-major (9) then t (3).
+struct PoseList {
+    const float *p;  // [n, 16]
+};
+
+struct PoseGrid {
+    const float *centre;  // device [16] cam_from_obj of the grid centre
+    const float *rot;     // device [n_rot, 9]
+    float G[9];           // cam_from_grid rotation
+    int n;                // points per axis
+    int n_rot;
+    float step;
+};
+
+// ---- launchers (k_render.cu) -------------------------------------------------------------
+void launch_obs_points(const Cam &cam, const float *depth, float4 *obs, cudaStream_t s);
+void launch_bg_clear(unsigned long long *bg, int64_t n, cudaStream_t s);
+void launch_bg_raster(const Cam &cam, const MeshView &m, const float *pose16_dev, int tri_base,
+                      unsigned long long *bg, cudaStream_t s);
+void launch_bg_tables(const SceneView &sv, const Lik &L, float *ell_bg, float *gs_bg, float *gp_bg,
+                      cudaStream_t s);
+void launch_bg_sums(const float *a, const float *b, const float *c, int64_t n, double *out, cudaStream_t s);
+int launch_score_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, int grid, cudaStream_t s);
+int launch_score_grid(const SceneView &sv, const Lik &L, PoseGrid P, int64_t n, float *ll, int grid, cudaStream_t s);
+int launch_render_list(const SceneView &sv, PoseList P, int64_t n, float *depth, int *tid, int grid, cudaStream_t s);
+void launch_score_depth(const SceneView &sv, const Lik &L, const float *depth, const int *tid, int64_t n,
+                        float *ll, int grid, cudaStream_t s);
+int launch_grad_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, float *dpose,
+                     float *dsigma, float *dpout, int grid, cudaStream_t s);
+int fused_smem_bytes();
+
+// ---- launchers (k_c2f.cu) ----------------------------------------------------------------
+void launch_set16(float *dst, const float *src16_host_values, cudaStream_t s);
+void launch_rotation_set(int kind, int n, double rot_max, float *out, cudaStream_t s);
+void launch_expand(PoseGrid P, int64_t n, float *poses, cudaStream_t s);
+int lse_blocks(int64_t n);
+void launch_lse_resample(const float *ll, int64_t n, int m, uint64_t seed, int stage, float2 *part,
+                         unsigned *counter, float *logz, int *idx, float *logq, int *err, cudaStream_t s);
+void launch_c2f_select(const float *ll, const int *idx, int m, PoseGrid P, const float *logz, int last,
+                       uint64_t seed, int n_stages, float *centre_next, float *particles, float *logw,
+                       float *logq, cudaStream_t s);
+void launch_copy16(const float *src, float *dst, cudaStream_t s);
+
+}  // namespace b3d

@@ -1,0 +1,393 @@
+// k_render.cu - rasterisation and windowed-likelihood kernels of libb3d.
+//
+// The fused kernel renders one pose hypothesis per CTA iteration into a shared-memory
+// z-buffer of packed (depth bits << 32 | triangle id) keys (64-bit atomicMin: nearest
+// fragment wins, equal depths go to the smaller id), composites it with the fixed objects'
+// background keys, converts keys to rendered depths, and scores every observed pixel whose
+// (2w+1)^2 window can see the object (the windowed Eq. 1 likelihood of Sec. III-B). Pixels
+// whose window cannot see the object keep their background term, which is precomputed once
+// per scene, so a hypothesis costs work in proportion to its screen footprint:
+//   LL_h = sum_i l_i(h) = LL_bg + sum_{i in footprint + w} (l_i(h) - l_i(bg)),
+// an exact identity (the terms outside the dilated footprint are equal, bit for bit, since
+// they are computed by the same device function from the same inputs).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "b3d_device.cuh"
+#include "b3d_internal.h"
+
+namespace b3d {
+
+// ------------------------------------------------------------------------------------------
+// fused render (+ score) kernel
+// ------------------------------------------------------------------------------------------
+// MODE 0: score; MODE 1: render (write depth / triangle id of the whole image).
+// STATS: count the work done (hypotheses, vertices, triangles, pixel tests, fragments,
+// composited pixels, scored pixels, window pairs) into S.stats for the roofline accounting.
+template <int MODE, class PS, bool STATS>
+__global__ void __launch_bounds__(kThreads) k_fused(SceneView S, Lik L, PS P, int64_t n_hyp, float *out_ll,
+                                                    float *out_depth, int *out_tid) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long *zb = reinterpret_cast<unsigned long long *>(smem_raw);
+    float4 *sv = reinterpret_cast<float4 *>(smem_raw + kRegionPx * sizeof(unsigned long long));
+    float *zd = reinterpret_cast<float *>(sv);  // rendered depths, alias of sv after rasterising
+    __shared__ float s_lut[kMaxLut];
+    __shared__ float s_pose[12];
+    __shared__ int s_bb[5];
+    __shared__ float s_red[kThreads / 32];
+
+    const Cam &c = S.cam;
+    const MeshView &m = S.mesh;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (MODE == 0)
+        for (int i = tid; i < L.n_lut; i += nt) s_lut[i] = L.lut[i];
+    const int w = MODE == 0 ? L.w : 0;
+    const int64_t npx = (int64_t)c.W * c.H;
+    unsigned long long cnt[kNumStats] = {0, 0, 0, 0, 0, 0, 0, 0};
+
+    for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
+        __syncthreads();
+        if (STATS && tid == 0) ++cnt[0];
+        if (tid == 0) {
+            pose12(P, h, s_pose);
+            s_bb[4] = object_bbox(m, s_pose, c, s_bb) ? 1 : 0;
+        }
+        __syncthreads();
+        float pose[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) pose[k] = s_pose[k];
+        const bool has_bb = s_bb[4] != 0;
+        const int bx0 = s_bb[0], bx1 = s_bb[1], by0 = s_bb[2], by1 = s_bb[3];
+
+        int sx0, sx1, sy0, sy1;
+        if (MODE == 0) {
+            if (has_bb) {
+                sx0 = max(bx0 - w, 0); sx1 = min(bx1 + w, c.W - 1);
+                sy0 = max(by0 - w, 0); sy1 = min(by1 + w, c.H - 1);
+            } else {
+                sx0 = 0; sx1 = -1; sy0 = 0; sy1 = -1;
+            }
+        } else {
+            sx0 = 0; sx1 = c.W - 1; sy0 = 0; sy1 = c.H - 1;
+        }
+        float acc = 0.f;
+        const int sw = sx1 - sx0 + 1;
+        if (sw > 0 && sy1 >= sy0) {
+            const int tw = MODE == 0 ? min(sw, 64) : min(sw, kRegionPx);
+            const int th = max(1, kRegionPx / (tw + 2 * w) - 2 * w);
+            for (int ty0 = sy0; ty0 <= sy1; ty0 += th) {
+                for (int tx0 = sx0; tx0 <= sx1; tx0 += tw) {
+                    const int tx1 = min(tx0 + tw - 1, sx1), ty1 = min(ty0 + th - 1, sy1);
+                    const int zx0 = max(tx0 - w, 0), zx1 = min(tx1 + w, c.W - 1);
+                    const int zy0 = max(ty0 - w, 0), zy1 = min(ty1 + w, c.H - 1);
+                    const int zw = zx1 - zx0 + 1, zh = zy1 - zy0 + 1;
+                    const int rx0 = max(zx0, bx0), rx1 = min(zx1, bx1), ry0 = max(zy0, by0), ry1 = min(zy1, by1);
+                    const bool need = has_bb && rx0 <= rx1 && ry0 <= ry1;
+                    if (need) {
+                        for (int i = tid; i < zw * zh; i += nt) zb[i] = kEmptyKey;
+                        for (int ch = 0; ch < m.n_chunks; ++ch) {
+                            const int4 cr = m.chunks[ch];
+                            __syncthreads();
+                            for (int v = tid; v < cr.y - cr.x; v += nt) sv[v] = project(pose, m.verts[cr.x + v], c);
+                            if (STATS) cnt[1] += (cr.y - cr.x - tid + nt - 1 > 0) ? (cr.y - cr.x - tid + nt - 1) / nt : 0;
+                            __syncthreads();
+                            for (int t = cr.z + tid; t < cr.w; t += nt) {
+                                const int4 tr = m.tris[t];
+                                if (STATS) ++cnt[2];
+                                raster_tri(sv[tr.x], sv[tr.y], sv[tr.z], (unsigned)(S.tri_base + tr.w), m.cull_back,
+                                           rx0, rx1, ry0, ry1, c.far_z, [&](int x, int y, unsigned long long key) {
+                                               if (STATS) ++cnt[4];
+                                               atomicMin(&zb[(y - zy0) * zw + (x - zx0)], key);
+                                           }, STATS ? &cnt[3] : nullptr);
+                            }
+                        }
+                        __syncthreads();
+                    }
+                    if (STATS) cnt[5] += (zw * zh - tid + nt - 1 > 0) ? (zw * zh - tid + nt - 1) / nt : 0;
+                    if (MODE == 0) {
+                        for (int i = tid; i < zw * zh; i += nt) {
+                            const int gx = zx0 + i % zw, gy = zy0 + i / zw;
+                            unsigned long long key = S.bg[(int64_t)gy * c.W + gx];
+                            if (need) key = min(key, zb[i]);
+                            zd[i] = key_depth(key, L.miss_mode, c.far_z);
+                        }
+                        __syncthreads();
+                        const int tww = tx1 - tx0 + 1, n_t = tww * (ty1 - ty0 + 1);
+                        for (int k = tid; k < n_t; k += nt) {
+                            const int x = tx0 + k % tww, y = ty0 + k / tww;
+                            const int64_t gi = (int64_t)y * c.W + x;
+                            const float4 q = S.obs[gi];
+                            if (q.w == 0.f) continue;
+                            if (STATS) {
+                                ++cnt[6];
+                                cnt[7] += (unsigned long long)((min(y + w, c.H - 1) - max(y - w, 0) + 1) *
+                                                               (min(x + w, c.W - 1) - max(x - w, 0) + 1));
+                            }
+                            const float l = pixel_ell(L, s_lut, c, q, x, y,
+                                                      [&](int xj, int yj) { return zd[(yj - zy0) * zw + (xj - zx0)]; });
+                            acc += l - S.ell_bg[gi];
+                        }
+                    } else {
+                        for (int i = tid; i < zw * zh; i += nt) {
+                            const int gx = zx0 + i % zw, gy = zy0 + i / zw;
+                            const int64_t gi = (int64_t)gy * c.W + gx;
+                            unsigned long long key = S.bg[gi];
+                            if (need) key = min(key, zb[i]);
+                            out_depth[h * npx + gi] = key_depth(key, 0, c.far_z);
+                            if (out_tid) out_tid[h * npx + gi] = key == kEmptyKey ? -1 : (int)(unsigned)(key & 0xffffffffu);
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+        }
+        if (MODE == 0) {
+            const float tot = block_sum(acc, s_red);
+            if (tid == 0) out_ll[h] = (float)(*S.ll_bg + (double)tot);
+        }
+    }
+    if (STATS)
+        for (int k = 0; k < kNumStats; ++k)
+            if (cnt[k]) atomicAdd(&S.stats[k], cnt[k]);
+}
+
+// ------------------------------------------------------------------------------------------
+// scene set-up kernels
+// ------------------------------------------------------------------------------------------
+
+__global__ void k_obs_points(Cam c, const float *depth, float4 *obs) {
+    const int64_t n = (int64_t)c.W * c.H;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = depth[i];
+        const int x = (int)(i % c.W), y = (int)(i / c.W);
+        if (d > 0.f && isfinite(d)) {
+            const float rx = ((float)x + 0.5f - c.cx) * c.inv_fx, ry = ((float)y + 0.5f - c.cy) * c.inv_fy;
+            obs[i] = make_float4(d * rx, d * ry, d, 1.f);
+        } else {
+            obs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+__global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+// Background render of one fixed object: one warp per triangle, lanes split its pixels.
+__global__ void k_bg_raster(Cam c, MeshView m, const float *pose16, int tri_base, unsigned long long *bg) {
+    float P[12];
+    const float *p = pose16;
+    P[0] = p[0]; P[1] = p[1]; P[2] = p[2]; P[3] = p[4]; P[4] = p[5]; P[5] = p[6];
+    P[6] = p[8]; P[7] = p[9]; P[8] = p[10]; P[9] = p[3]; P[10] = p[7]; P[11] = p[11];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int ch = 0; ch < m.n_chunks; ++ch) {
+        const int4 cr = m.chunks[ch];
+        for (int64_t t = cr.z + warp; t < cr.w; t += n_warps) {
+            const int4 tr = m.tris[t];
+            const float4 A = project(P, m.verts[cr.x + tr.x], c);
+            const float4 B = project(P, m.verts[cr.x + tr.y], c);
+            const float4 C = project(P, m.verts[cr.x + tr.z], c);
+            if (A.z < 0.f || B.z < 0.f || C.z < 0.f) continue;
+            const float umin = fminf(A.x, fminf(B.x, C.x)), umax = fmaxf(A.x, fmaxf(B.x, C.x));
+            const float vmin = fminf(A.y, fminf(B.y, C.y)), vmax = fmaxf(A.y, fmaxf(B.y, C.y));
+            const int x0 = (int)ceilf(fmaxf(umin - 0.5f, 0.f)), x1 = (int)floorf(fminf(umax - 0.5f, (float)(c.W - 1)));
+            const int y0 = (int)ceilf(fmaxf(vmin - 0.5f, 0.f)), y1 = (int)floorf(fminf(vmax - 0.5f, (float)(c.H - 1)));
+            if (x0 > x1 || y0 > y1) continue;
+            const int bw = x1 - x0 + 1;
+            const int64_t nb = (int64_t)bw * (y1 - y0 + 1);
+            for (int64_t k = lane; k < nb; k += 32) {
+                const int x = x0 + (int)(k % bw), y = y0 + (int)(k / bw);
+                raster_tri(A, B, C, (unsigned)(tri_base + tr.w), m.cull_back, x, x, y, y, c.far_z,
+                           [&](int xx, int yy, unsigned long long key) { atomicMin(&bg[(int64_t)yy * c.W + xx], key); },
+                           nullptr);
+            }
+        }
+    }
+}
+
+// Per-pixel background terms: l_i of the fixed objects alone and, when requested, the
+// sigma / p_out derivatives of l_i (kind 1).
+__global__ void k_bg_tables(SceneView S, Lik L, float *ell_bg, float *gs_bg, float *gp_bg) {
+    __shared__ float s_lut[kMaxLut];
+    for (int i = threadIdx.x; i < L.n_lut; i += blockDim.x) s_lut[i] = L.lut[i];
+    __syncthreads();
+    const Cam &c = S.cam;
+    const int64_t n = (int64_t)c.W * c.H;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 q = S.obs[i];
+        const int x = (int)(i % c.W), y = (int)(i / c.W);
+        float l = 0.f, gs = 0.f, gp = 0.f;
+        if (q.w != 0.f) {
+            auto fetch = [&](int xj, int yj) { return key_depth(S.bg[(int64_t)yj * c.W + xj], L.miss_mode, c.far_z); };
+            l = pixel_ell(L, s_lut, c, q, x, y, fetch);
+            if (gs_bg) {
+                float Si, dSi, bp;
+                pixel_terms(L, c, q, x, y, fetch, Si, dSi);
+                pixel_noise_grads(L, Si, dSi, gs, gp, bp);
+            }
+        }
+        ell_bg[i] = l;
+        if (gs_bg) { gs_bg[i] = gs; gp_bg[i] = gp; }
+    }
+}
+
+// Sums of up to three arrays in double precision, fixed order (one block).
+__global__ void k_sums(const float *a, const float *b, const float *c, int64_t n, double *out) {
+    __shared__ double red[3][1024 / 32];
+    double s[3] = {0, 0, 0};
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        s[0] += a[i];
+        if (b) s[1] += b[i];
+        if (c) s[2] += c[i];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < 3; ++k) {
+        double v = s[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double v = 0;
+        for (int k = 0; k < nw; ++k) v += red[threadIdx.x][k];
+        out[threadIdx.x] = v;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// two-pass scoring of materialised depth images [n, H, W]
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_score_depth(SceneView S, Lik L, const float *depth, const int *tid_in,
+                                                          int64_t n_hyp, float *out_ll) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *zd = reinterpret_cast<float *>(smem_raw);
+    __shared__ float s_lut[kMaxLut];
+    __shared__ float s_red[kThreads / 32];
+    const Cam &c = S.cam;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < L.n_lut; i += nt) s_lut[i] = L.lut[i];
+    const int w = L.w;
+    const int64_t npx = (int64_t)c.W * c.H;
+    const int rows = max(1, (2 * kRegionPx) / c.W - 2 * w);  // 32 KB of float depths per tile
+    for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
+        const float *img = depth + h * npx;
+        const int *tim = tid_in ? tid_in + h * npx : nullptr;
+        float acc = 0.f;
+        for (int ty0 = 0; ty0 < c.H; ty0 += rows) {
+            const int ty1 = min(ty0 + rows - 1, c.H - 1);
+            const int zy0 = max(ty0 - w, 0), zy1 = min(ty1 + w, c.H - 1);
+            const int nz = (zy1 - zy0 + 1) * c.W;
+            __syncthreads();
+            for (int i = tid; i < nz; i += nt) {
+                const int64_t gi = (int64_t)zy0 * c.W + i;
+                float d = img[gi];
+                if (L.miss_mode == 1 && tim[gi] < 0) d = -1.f;
+                zd[i] = d;
+            }
+            __syncthreads();
+            const int n_t = (ty1 - ty0 + 1) * c.W;
+            for (int k = tid; k < n_t; k += nt) {
+                const int x = k % c.W, y = ty0 + k / c.W;
+                const float4 q = S.obs[(int64_t)y * c.W + x];
+                if (q.w == 0.f) continue;
+                acc += pixel_ell(L, s_lut, c, q, x, y, [&](int xj, int yj) { return zd[(yj - zy0) * c.W + xj]; });
+            }
+        }
+        const float tot = block_sum(acc, s_red);
+        if (tid == 0) out_ll[h] = tot;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------------
+
+int fused_smem_bytes() { return kRegionPx * (int)sizeof(unsigned long long) + kChunkV * (int)sizeof(float4); }
+
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <class K>
+static int persistent_grid(K kernel, int smem, int64_t n, int grid) {
+    if (grid > 0) return (int)std::min<int64_t>(grid, std::max<int64_t>(n, 1));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+    if (per_sm <= 0) per_sm = 1;
+    return (int)std::min<int64_t>((int64_t)per_sm * sm_count(), std::max<int64_t>(n, 1));
+}
+
+template <int MODE, class PS>
+static int launch_fused(const SceneView &sv, const Lik &L, PS P, int64_t n, float *ll, float *depth, int *tid,
+                        int grid, cudaStream_t s) {
+    if (n <= 0) return 0;
+    const int smem = fused_smem_bytes();
+    auto kern = sv.stats ? k_fused<MODE, PS, true> : k_fused<MODE, PS, false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int g = persistent_grid(kern, smem, n, grid);
+    kern<<<g, kThreads, smem, s>>>(sv, L, P, n, ll, depth, tid);
+    return g;
+}
+
+int launch_score_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, int grid, cudaStream_t s) {
+    return launch_fused<0>(sv, L, P, n, ll, nullptr, nullptr, grid, s);
+}
+
+int launch_score_grid(const SceneView &sv, const Lik &L, PoseGrid P, int64_t n, float *ll, int grid, cudaStream_t s) {
+    return launch_fused<0>(sv, L, P, n, ll, nullptr, nullptr, grid, s);
+}
+
+int launch_render_list(const SceneView &sv, PoseList P, int64_t n, float *depth, int *tid, int grid, cudaStream_t s) {
+    Lik L{};
+    L.w = 0;
+    return launch_fused<1>(sv, L, P, n, nullptr, depth, tid, grid, s);
+}
+
+void launch_score_depth(const SceneView &sv, const Lik &L, const float *depth, const int *tid, int64_t n, float *ll,
+                        int grid, cudaStream_t s) {
+    if (n <= 0) return;
+    const int smem = 2 * kRegionPx * (int)sizeof(float);
+    const int g = persistent_grid(k_score_depth, smem, n, grid);
+    k_score_depth<<<g, kThreads, smem, s>>>(sv, L, depth, tid, n, ll);
+}
+
+void launch_obs_points(const Cam &cam, const float *depth, float4 *obs, cudaStream_t s) {
+    const int64_t n = (int64_t)cam.W * cam.H;
+    k_obs_points<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(cam, depth, obs);
+}
+
+void launch_bg_clear(unsigned long long *bg, int64_t n, cudaStream_t s) {
+    k_fill_u64<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(bg, n, kEmptyKey);
+}
+
+void launch_bg_raster(const Cam &cam, const MeshView &m, const float *pose16_dev, int tri_base,
+                      unsigned long long *bg, cudaStream_t s) {
+    if (m.n_tris <= 0) return;
+    const int warps_per_block = 8;
+    const int blocks = (int)std::min<int64_t>((m.n_tris + warps_per_block - 1) / warps_per_block, 8 * sm_count());
+    k_bg_raster<<<blocks, 32 * warps_per_block, 0, s>>>(cam, m, pose16_dev, tri_base, bg);
+}
+
+void launch_bg_tables(const SceneView &sv, const Lik &L, float *ell_bg, float *gs_bg, float *gp_bg, cudaStream_t s) {
+    const int64_t n = (int64_t)sv.cam.W * sv.cam.H;
+    k_bg_tables<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(sv, L, ell_bg, gs_bg, gp_bg);
+}
+
+void launch_bg_sums(const float *a, const float *b, const float *c, int64_t n, double *out, cudaStream_t s) {
+    k_sums<<<1, 1024, 0, s>>>(a, b, c, n, out);
+}
+
+}  // namespace b3d

@@ -1,0 +1,95 @@
+"""The C ABI library loads on the host and exports every entry point include/b3d.h
+declares; the binding defines the same names; struct layouts agree with the header.
+No compute call here needs a GPU."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "b3d.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:b3d_status|const char \*|int64_t)\s*(b3d_\w+)\s*\(", txt, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2312_08715_gb300 import b3d
+    return b3d.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ["b3d_load_mesh", "b3d_set_scene", "b3d_render_batch", "b3d_score_batch", "b3d_enumerate_c2f",
+                 "b3d_score_grad", "b3d_lse_resample", "b3d_sync", "b3d_last_error"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2312_08715_gb300 import b3d
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert hasattr(b3d, name), f"binding lacks {name}"
+
+
+def test_null_context_is_rejected_without_device_work(lib):
+    assert lib.b3d_destroy(None) == -1
+    assert lib.b3d_sync(None, None) == -1
+    assert lib.b3d_score_batch(None, 0, 1, None, None, None, None) == -1
+    assert lib.b3d_launch_count(None) == 0
+
+
+def test_create_fails_cleanly_without_a_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2312_08715_gb300 import b3d
+    with pytest.raises(b3d.B3DError) as e:
+        b3d.b3d_create(0)
+    assert e.value.status == b3d.B3D_EINVAL
+    assert "device" in b3d.b3d_last_error(None)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    from paper_2312_08715_gb300 import b3d
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "b3d.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\\n", sizeof(b3d_intrinsics), sizeof(b3d_lik_params), sizeof(b3d_stage), sizeof(b3d_c2f_schedule));
+  printf("%zu %zu %zu %zu\\n", offsetof(b3d_c2f_schedule, stage), offsetof(b3d_c2f_schedule, n_particles),
+         offsetof(b3d_c2f_schedule, seed), offsetof(b3d_c2f_schedule, grid_frame));
+  printf("%zu %zu\\n", offsetof(b3d_lik_params, volume), offsetof(b3d_lik_params, miss_mode));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", f"-I{os.path.join(ROOT, 'include')}", str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    got = [int(x) for x in out]
+    want = [C.sizeof(b3d.b3d_intrinsics), C.sizeof(b3d.b3d_lik_params), C.sizeof(b3d.b3d_stage),
+            C.sizeof(b3d.b3d_c2f_schedule),
+            b3d.b3d_c2f_schedule.stage.offset, b3d.b3d_c2f_schedule.n_particles.offset,
+            b3d.b3d_c2f_schedule.seed.offset, b3d.b3d_c2f_schedule.grid_frame.offset,
+            b3d.b3d_lik_params.volume.offset, b3d.b3d_lik_params.miss_mode.offset]
+    assert got == want
+
+
+def test_oracle_and_product_share_no_code():
+    """The CUDA sources include nothing from oracle/ and the oracle nothing from the package."""
+    csrc = os.path.join(ROOT, "paper_2312_08715_gb300", "csrc")
+    for f in os.listdir(csrc):
+        txt = open(os.path.join(csrc, f)).read()
+        assert "oracle" not in txt.lower() or f.endswith(".md"), f
+    for f in ("b3d.py", "build.py", "synth.py", "__init__.py"):
+        txt = open(os.path.join(ROOT, "paper_2312_08715_gb300", f)).read()
+        assert "import oracle" not in txt and "from oracle" not in txt, f
+    otxt = open(os.path.join(ROOT, "oracle", "b3d_oracle.c")).read()
+    assert "b3d.h" not in otxt and "b3d_internal" not in otxt

@@ -1,0 +1,344 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 CPU oracle on
+identical seeded inputs. Tolerances (from the FP32 arithmetic of the kernels):
+  - triangle-id maps identical except at pixels the oracle flags as edge/depth ties
+    (coverage within 1e-4 px of an edge, depths within 1e-5 relative), and at no more than
+    1e-4 of all pixels;
+  - depth within 1e-5 relative where the triangle ids agree;
+  - log-likelihood within 1e-4 * sum_i |l_i| plus the oracle's bound on what FP32-resolution
+    decisions (flagged pixels, inlier-ball borderline pairs) can change;
+  - the argmax hypothesis identical unless the oracle's top-two gap is inside that tolerance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2312_08715_gb300 import synth
+from _scenes import gpu_context, jitter_poses, ll_tolerance, observed
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _check_render(orc, scene, slot, poses, depth, tid, max_frac=1e-4):
+    n_mis = n_px = 0
+    for k, P in enumerate(poses):
+        od, ot, of = orc.render(scene, slot=slot, slot_pose=P, edge_tol=1e-4, z_tol=1e-5, want_flags=True)
+        mis = ot != tid[k]
+        assert not (mis & ((of & 1) == 0)).any(), f"pose {k}: {int((mis & ((of & 1) == 0)).sum())} unflagged id mismatches"
+        agree = ~mis
+        rel = np.abs(depth[k][agree] - od[agree]) / od[agree]
+        assert rel.max() <= 1e-5, f"pose {k}: depth rel err {rel.max()}"
+        n_mis += int(mis.sum())
+        n_px += mis.size
+    assert n_mis <= max(1, max_frac * n_px), f"{n_mis} of {n_px} pixels differ"
+    return n_mis
+
+
+def _check_ll(got, ref, what):
+    tol = ll_tolerance(ref)
+    err = np.abs(got.astype(np.float64) - ref["ll"])
+    bad = np.nonzero(err > tol)[0]
+    assert bad.size == 0, f"{what}: {bad.size} hypotheses outside tolerance, e.g. {bad[:5]} err {err[bad[:5]]} tol {tol[bad[:5]]}"
+    unflagged = ref["bound"] == 0
+    assert unflagged.mean() > 0.5, f"{what}: too many flagged hypotheses ({1 - unflagged.mean():.2f})"
+    return err
+
+
+def _check_argmax(got, ref):
+    o = ref["ll"]
+    top = np.argsort(o)[::-1]
+    gap = o[top[0]] - o[top[1]] if o.size > 1 else np.inf
+    if gap > ll_tolerance(ref)[top[0]] * 2:
+        assert int(np.argmax(got)) == int(top[0])
+
+
+# ---------------------------------------------------------------------------------------
+# rendering
+# ---------------------------------------------------------------------------------------
+
+def test_render_single_object(orc, single_object):
+    wl = single_object
+    sc = wl.scene
+    poses = jitter_poses(np.random.default_rng(11), wl.hidden, 32)
+    ctx = gpu_context(sc, observed(orc, wl))
+    d, t = ctx.render(0, poses)
+    ctx.sync()
+    _check_render(orc, sc, 0, poses, _np(d), _np(t))
+
+
+def test_render_tabletop_composite(orc, tabletop):
+    wl = tabletop
+    sc = wl.scene
+    poses = jitter_poses(np.random.default_rng(12), wl.hidden, 6, trans=0.05, rot_deg=30)
+    ctx = gpu_context(sc, observed(orc, wl))
+    d, t = ctx.render(wl.slot, poses)
+    ctx.sync()
+    _check_render(orc, sc, wl.slot, poses, _np(d), _np(t))
+    # every other object is present in the composite
+    ids = _np(t)[0]
+    f_off = np.cumsum([0] + [m.n_faces for m in sc.meshes])
+    for o in range(len(sc.meshes)):
+        if o != wl.slot:
+            assert ((ids >= f_off[o]) & (ids < f_off[o + 1])).any() or o == 1
+
+
+def test_render_large_footprint_and_ragged_image(orc):
+    """An object close to the camera covers several screen tiles; a ragged 37x29 image."""
+    rng = np.random.default_rng(13)
+    cells = np.array(np.unravel_index(rng.permutation(512)[:300], (8, 8, 8))).T
+    mesh = synth.voxel_mesh(cells, 0.02, origin=(-0.08, -0.08, -0.08))
+    for cam, z in [(synth.Camera(160, 120, 150.0, 150.0, 80.0, 60.0, 0.01, 2.0), 0.22),
+                   (synth.Camera(37, 29, 30.0, 31.0, 17.3, 15.1, 0.01, 2.0), 0.35)]:
+        R = synth.random_rotation(rng)
+        pose = synth.rigid(R, [0.01, -0.02, z]).astype(np.float32)
+        sc = synth.Scene(cam, [mesh], pose[None].copy())
+        obs = orc.render(sc)[0].astype(np.float32)
+        ctx = gpu_context(sc, obs)
+        poses = jitter_poses(rng, pose, 4, trans=0.01, rot_deg=5)
+        d, t = ctx.render(0, poses)
+        ctx.sync()
+        _check_render(orc, sc, 0, poses, _np(d), _np(t), max_frac=5e-4)
+        lik = dict(kind=0, radius=0.005, p_outlier=0.01, half_window=2)
+        ll = _np(ctx.score(0, poses, lik))
+        ctx.sync()
+        _check_ll(ll, orc.score(sc, 0, poses, lik, obs), "large footprint")
+
+
+def test_near_plane_and_out_of_view(orc, single_object):
+    wl = single_object
+    sc = wl.scene
+    obs = observed(orc, wl)
+    P = [wl.hidden.copy() for _ in range(4)]
+    P[1][:3, 3] = [0.0, 0.0, 0.03]    # straddles the near plane (0.01 m)
+    P[2][:3, 3] = [5.0, 0.0, 0.5]     # far outside the view
+    P[3][:3, 3] = [0.0, 0.0, -0.5]    # behind the camera
+    poses = np.stack(P).astype(np.float32)
+    ctx = gpu_context(sc, obs)
+    d, t = ctx.render(0, poses)
+    ll = ctx.score(0, poses, wl.lik)
+    ctx.sync()
+    _check_render(orc, sc, 0, poses, _np(d), _np(t))
+    ref = orc.score(sc, 0, poses, wl.lik, obs)
+    _check_ll(_np(ll), ref, "near/out of view")
+
+
+# ---------------------------------------------------------------------------------------
+# scoring
+# ---------------------------------------------------------------------------------------
+
+def test_score_single_object_full_grid(orc, single_object):
+    """1,000 hypotheses: 10^3 translation grid (1 cm) around the hidden pose."""
+    wl = single_object
+    sc = wl.scene
+    obs = observed(orc, wl)
+    poses = orc.expand(wl.hidden, np.eye(3), 10, 0.01, np.eye(3)[None]).astype(np.float32)
+    ref = orc.score(sc, 0, poses, wl.lik, obs)
+    ctx = gpu_context(sc, obs)
+    ll = _np(ctx.score(0, poses, wl.lik))
+    ctx.sync()
+    _check_ll(ll, ref, "plain 64x48")
+    _check_argmax(ll, ref)
+    assert int(np.argmax(ll)) == 555
+    # permuting the hypotheses permutes the scores bit for bit
+    perm = np.random.default_rng(1).permutation(1000)
+    ll2 = _np(ctx.score(0, poses[perm], wl.lik))
+    ctx.sync()
+    np.testing.assert_array_equal(ll[perm], ll2)
+
+
+@pytest.mark.parametrize("w,miss_mode", [(2, 0), (1, 1)])
+def test_score_smooth_and_miss_modes(orc, single_object, w, miss_mode):
+    wl = single_object
+    sc = wl.scene
+    obs = observed(orc, wl)
+    poses = orc.expand(wl.hidden, np.eye(3), 5, 0.004, orc.rotation_set(1, 4, 0.1)).astype(np.float32)
+    for lik in (dict(kind=1, radius=0.003, p_outlier=0.01, half_window=w, miss_mode=miss_mode),
+                dict(kind=0, radius=0.005, p_outlier=0.05, half_window=w, miss_mode=miss_mode)):
+        ref = orc.score(sc, 0, poses, lik, obs)
+        ctx = gpu_context(sc, obs)
+        ll = _np(ctx.score(0, poses, lik))
+        ctx.sync()
+        _check_ll(ll, ref, f"lik {lik}")
+        _check_argmax(ll, ref)
+
+
+def test_two_pass_matches_fused(orc, single_object):
+    """Render to HBM then score the materialised images == the fused path == the oracle."""
+    wl = single_object
+    sc = wl.scene
+    obs = observed(orc, wl)
+    poses = orc.expand(wl.hidden, np.eye(3), 4, 0.01, np.eye(3)[None]).astype(np.float32)
+    ref = orc.score(sc, 0, poses, wl.lik, obs)
+    ctx = gpu_context(sc, obs)
+    d, t = ctx.render(0, poses)
+    ll2 = _np(ctx.score_depth(d, wl.lik, t))
+    ll1 = _np(ctx.score(0, poses, wl.lik))
+    lk_b = dict(wl.lik, miss_mode=1)
+    ll3 = _np(ctx.score_depth(d, lk_b, t))
+    ctx.sync()
+    _check_ll(ll1, ref, "fused")
+    _check_ll(ll2, ref, "two-pass")
+    _check_ll(ll3, orc.score(sc, 0, poses, lk_b, obs), "two-pass miss_mode 1")
+
+
+def test_tabletop_first_stage_full_size_sampled(orc, tabletop):
+    """Full first-stage grid (9^3 x 200 = 145,800 hypotheses) in one launch, 40 sampled
+    hypotheses checked against the oracle one by one; the grid poses against the oracle's."""
+    wl = tabletop
+    sc = wl.scene
+    obs = observed(orc, wl)
+    st = wl.stages[0]
+    ctx = gpu_context(sc, obs)
+    poses_gpu = ctx.expand(wl.centre, wl.grid_frame, st)
+    ll = ctx.score(wl.slot, poses_gpu, wl.lik)
+    ctx.sync()
+    ll = _np(ll)
+    assert ll.shape == (145800,) and np.isfinite(ll).all()
+    rot = orc.rotation_set(st.rot_kind, st.n_rot, st.rot_max)
+    P_orc = orc.expand(wl.centre, wl.grid_frame, st.n_per_axis, st.step, rot)
+    np.testing.assert_allclose(_np(poses_gpu), P_orc, atol=2e-6)
+    rng = np.random.default_rng(7)
+    sample = np.concatenate([rng.choice(145800, 39, replace=False), [int(np.argmax(ll))]])
+    ref = orc.score(sc, wl.slot, P_orc[sample], wl.lik, obs)
+    _check_ll(ll[sample], ref, "tabletop stage 1 sample")
+
+
+# ---------------------------------------------------------------------------------------
+# log-sum-exp + resampling
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 7, 2048, 2049, 145800, 1_000_003])
+def test_lse_resample(orc, n):
+    rng = np.random.default_rng(n)
+    ll = synth.random_ll(rng, n)
+    m = 100
+    from paper_2312_08715_gb300 import b3d
+    ctx = b3d.Context(0)
+    t = torch.as_tensor(ll, device="cuda")
+    for stage in (0, 3):
+        logz, idx, logq = ctx.lse_resample(t, m, seed=1234, stage=stage)
+        ctx.sync()
+        Z, _ = orc.lse(ll.astype(np.float64))
+        assert abs(float(_np(logz)[0]) - Z) <= 1e-5 * max(1.0, abs(Z)) + 1e-4
+        oi, oq, om = orc.resample(ll.astype(np.float64), m, 1234, stage)
+        gi = _np(idx)
+        solid = om > 1e-5
+        np.testing.assert_array_equal(gi[solid], oi[solid])
+        assert (gi >= 0).all() and (gi < n).all()
+        np.testing.assert_allclose(_np(logq)[solid], oq[solid], atol=1e-4 * max(1.0, abs(Z)))
+    ctx.close()
+
+
+def test_lse_resample_degenerate(orc):
+    from paper_2312_08715_gb300 import b3d
+    ctx = b3d.Context(0)
+    ll = np.full(5000, -1e4, np.float32)
+    ll[4321] = 0.0
+    logz, idx, logq = ctx.lse_resample(torch.as_tensor(ll, device="cuda"), 64, seed=5, stage=1)
+    ctx.sync()
+    assert (_np(idx) == 4321).all()
+    assert abs(float(_np(logz)[0])) < 1e-6
+    ll = np.full(3000, 2.5, np.float32)
+    logz, idx, _ = ctx.lse_resample(torch.as_tensor(ll, device="cuda"), 1000, seed=6, stage=0)
+    ctx.sync()
+    assert float(_np(logz)[0]) == pytest.approx(2.5 + math.log(3000), abs=1e-4)
+    oi, _, om = orc.resample(ll.astype(np.float64), 1000, 6, 0)
+    np.testing.assert_array_equal(_np(idx)[om > 1e-5], oi[om > 1e-5])
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------------------
+# coarse-to-fine enumeration
+# ---------------------------------------------------------------------------------------
+
+def test_enumerate_c2f_matches_oracle(orc, single_object):
+    wl = single_object
+    sc = wl.scene
+    obs = observed(orc, wl)
+    centre = wl.hidden.astype(np.float64).copy()
+    centre[:3, 3] += [0.012, -0.007, 0.02]
+    stages = [synth.StageSpec(7, 0.01, 1, 3, math.radians(3)), synth.StageSpec(5, 0.003, 1, 2, math.radians(1))]
+    M = 16
+    ref = orc.enumerate_c2f(sc, 0, centre, np.eye(3), wl.lik, obs, stages, M, seed=9)
+    ctx = gpu_context(sc, obs)
+    parts, logw, logq = ctx.enumerate_c2f(0, centre.astype(np.float32), stages, wl.lik, M, 9, np.eye(3))
+    ctx.sync()
+    np.testing.assert_allclose(_np(parts), ref["particles"], atol=2e-6)
+    scale = np.abs(ref["logw"]).max()
+    np.testing.assert_allclose(_np(logw), ref["logw"], atol=1e-4 * scale * 4)
+    np.testing.assert_allclose(_np(logq), ref["logq"], atol=1e-4 * scale * 4)
+
+
+def test_enumerate_c2f_tabletop_tracks_hidden_pose(orc, tabletop):
+    """Three stages of 145,800 hypotheses around a tracking prior (<= 2 cm, <= 5 deg off)
+    end within a few millimetres of the hidden pose (a sanity check of the whole path)."""
+    wl = tabletop
+    sc = wl.scene
+    obs = observed(orc, wl)
+    ctx = gpu_context(sc, obs)
+    parts, logw, logq = ctx.enumerate_c2f(wl.slot, wl.centre, wl.stages, wl.lik, 100, 3, wl.grid_frame)
+    ctx.sync()
+    p = _np(parts)
+    best = p[int(np.argmax(_np(logw)))]
+    assert np.linalg.norm(best[:3, 3] - wl.hidden[:3, 3]) < 0.006
+    assert np.isfinite(_np(logq)).all()
+
+
+# ---------------------------------------------------------------------------------------
+# gradient
+# ---------------------------------------------------------------------------------------
+
+def test_score_grad_matches_oracle(orc, single_object):
+    wl = single_object
+    sc = wl.scene
+    obs = observed(orc, wl)
+    lik = dict(kind=1, radius=0.003, p_outlier=0.01, half_window=2)
+    poses = jitter_poses(np.random.default_rng(21), wl.hidden, 8, trans=0.006, rot_deg=4)
+    ref = orc.score_grad(sc, 0, poses, lik, obs)
+    ctx = gpu_context(sc, obs)
+    ll, dpose, ds, dp = (_np(x) for x in ctx.score_grad(0, poses, lik))
+    ctx.sync()
+    sref = orc.score(sc, 0, poses, lik, obs)
+    _check_ll(ll, sref, "score_grad forward")
+    for k in range(len(poses)):
+        if sref["bound"][k] > 0:
+            continue  # a flagged pixel may change visibility between FP32 and FP64
+        g, gr = dpose[k], ref["dpose"][k]
+        assert np.linalg.norm(g - gr) <= 1e-3 * np.linalg.norm(gr), (k, g, gr)
+        assert ds[k] == pytest.approx(ref["dsigma"][k], rel=1e-3)
+        assert dp[k] == pytest.approx(ref["dpout"][k], rel=1e-3)
+
+
+# ---------------------------------------------------------------------------------------
+# argument errors and the HBM budget
+# ---------------------------------------------------------------------------------------
+
+def test_errors_and_budget(orc, single_object):
+    from paper_2312_08715_gb300 import b3d
+    wl = single_object
+    sc = wl.scene
+    ctx = gpu_context(sc, observed(orc, wl))
+    P = torch.as_tensor(wl.hidden[None], device="cuda")
+    out = torch.empty(1, device="cuda")
+    with pytest.raises(b3d.B3DError) as e:
+        b3d.b3d_score_batch(ctx.h, 0, 1, P, b3d.lik_params(half_window=9), out)
+    assert e.value.status == b3d.B3D_EINVAL
+    with pytest.raises(b3d.B3DError) as e:
+        b3d.b3d_score_batch(ctx.h, 3, 1, P, b3d.lik_params(), out)
+    assert e.value.status == b3d.B3D_ENOTFOUND
+    with pytest.raises(b3d.B3DError) as e:
+        b3d.b3d_score_batch(ctx.h, 0, -1, P, b3d.lik_params(), out)
+    assert e.value.status == b3d.B3D_EINVAL
+    b3d.b3d_score_batch(ctx.h, 0, 0, P, b3d.lik_params(), out)  # n = 0 is a no-op
+    ctx.sync()
+    small = b3d.Context(0, hbm_budget_bytes=64 * 1024)
+    with pytest.raises(b3d.B3DError) as e:
+        small.load_mesh(sc.meshes[0])
+    assert e.value.status == b3d.B3D_EBUDGET
+    small.close()
+    ctx.close()
