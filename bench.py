@@ -37,15 +37,17 @@ N_OBJECTS = 5
 M_PARTICLES = 100
 FIRST_SLOT = 2  # 0 = table, 1 = occluder
 
-# FP32 operations per unit of counted work, from the kernel source (an FMA counts 2):
-#   vertex: 3x3 rotation + translation (9 FMA), 1/z, two projections (FMA + MUL each)
-#   triangle: signed area (edge function: 4 SUB, MUL, FMA) + screen bbox (6 MIN/MAX, 4 SUB)
-#   pixel test: three edge functions (3 x 7) + three sign tests
-#   fragment: 1/z interpolation (2 FMA + MUL) + division + far test
-#   composite pixel: key min + depth decode; scored pixel: ray row, lookup/log, delta, sum
-#   window pair: ray column (SUB, SUB, MUL), offsets (2 FMA + SUB), |d|^2 (2 FMA + MUL), test
-FLOPS_PER_UNIT = np.array([0.0, 25.0, 17.0, 24.0, 7.0, 2.0, 12.0, 14.0])
-UNIT_NAMES = ["hypotheses", "vertices", "triangles", "pixel_tests", "fragments", "composited_px",
+# FP32 operations per unit of counted work on the voxel-quad path of the score kernel, from
+# the kernel source (an FMA counts 2):
+#   corner: three lattice terms summed (6 ADD), 1/z, two projections (MUL + FMA each)
+#   quad: signed area (edge function: 4 SUB, MUL, FMA), screen bbox (6 MIN, 6 MAX, 4 SUB),
+#         affine 1/z plane (6 SUB, 2 FMA, 2 MUL, 2 DIV)
+#   pixel test: four edge functions (4 x 7) + four sign products and tests
+#   fragment: affine 1/z (2 FMA, 2 SUB), reciprocal, far test
+#   composite pixel: min + test; scored pixel: ray row (3), lookup, delta, sum
+#   window pair: ray column (ADD, SUB, MUL), offsets (2 FMA + SUB), |d|^2 (2 FMA + MUL), test
+FLOPS_PER_UNIT = np.array([0.0, 13.0, 40.0, 36.0, 8.0, 2.0, 8.0, 14.0])
+UNIT_NAMES = ["hypotheses", "corners", "primitives", "pixel_tests", "fragments", "composited_px",
               "scored_px", "window_pairs"]
 
 
@@ -276,7 +278,7 @@ def run_gpu(args):
         "px_hyps_per_s": value * px,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
                      "frac": achieved / peak_alu, "traffic": traffic,
-                     "kernel": "k_fused<score, grid> (render + windowed likelihood)",
+                     "kernel": "k_score<PoseGrid> (render + windowed likelihood)",
                      "avg_launch_ms": avg_launch_s * 1e3, "launches": score_n,
                      "flop_per_launch": flop_per_launch, "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                      "work_per_step": {n: float(v) for n, v in zip(UNIT_NAMES, work)}},

@@ -28,11 +28,15 @@ struct MeshRec {
     int64_t n_faces = 0;  // original face count (triangle ids are 0..n_faces-1)
     int32_t flags = 0;
     float4 *verts = nullptr;
-    int4 *tris = nullptr;
-    int4 *chunks = nullptr;
-    int *face_map = nullptr;
-    int n_chunks = 0, n_tris = 0, n_verts = 0;
+    int4 *tris_surf = nullptr, *tris_full = nullptr, *faces = nullptr;
+    int n_surf = 0, n_full = 0, n_verts = 0;
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    // voxel quads (n_quads == 0: none)
+    unsigned *quads = nullptr;
+    int2 *quad_tris = nullptr;
+    int *class_off = nullptr;
+    float *coords = nullptr;
+    int n_quads = 0, nc[3] = {0, 0, 0}, np1 = 0;
 };
 
 struct LikKey {
@@ -238,13 +242,20 @@ LikKey key_of(const b3d_lik_params *lp) {
 MeshView view_of(const MeshRec &m) {
     MeshView v{};
     v.verts = m.verts;
-    v.tris = m.tris;
-    v.chunks = m.chunks;
-    v.face_map = m.face_map;
-    v.n_chunks = m.n_chunks;
-    v.n_tris = m.n_tris;
-    for (int k = 0; k < 3; ++k) { v.lo[k] = m.lo[k]; v.hi[k] = m.hi[k]; }
-    v.cull_back = (m.flags & B3D_MESH_CLOSED) ? 1 : 0;
+    v.tris_surf = m.tris_surf;
+    v.tris_full = m.tris_full;
+    v.faces = m.faces;
+    v.n_surf = m.n_surf;
+    v.n_full = m.n_full;
+    v.n_faces = (int)m.n_faces;
+    v.closed = (m.flags & B3D_MESH_CLOSED) ? 1 : 0;
+    for (int k = 0; k < 3; ++k) { v.lo[k] = m.lo[k]; v.hi[k] = m.hi[k]; v.nc[k] = m.nc[k]; }
+    v.n_quads = m.n_quads;
+    v.quads = m.quads;
+    v.quad_tris = m.quad_tris;
+    v.class_off = m.class_off;
+    v.coords = m.coords;
+    v.np1 = m.np1;
     return v;
 }
 
@@ -265,7 +276,7 @@ b3d_status ensure_bg(b3d_ctx *ctx, int32_t slot, cudaStream_t s) {
     for (size_t o = 0; o < ctx->obj_mesh.size(); ++o) {
         if ((int32_t)o == slot) continue;
         const MeshRec &m = ctx->meshes[ctx->obj_mesh[o]];
-        if (m.n_tris <= 0) continue;
+        if (m.n_full <= 0) continue;
         launch_bg_raster(ctx->cam, view_of(m), ctx->d_poses + 16 * o, (int)ctx->tri_base[o], ctx->d_bg, s);
         ++ctx->launches;
     }
@@ -486,6 +497,7 @@ b3d_status b3d_load_mesh(b3d_ctx *ctx, const float *verts, int64_t n_v, const in
         if (t.a == t.b || t.b == t.c || t.a == t.c) continue;
         tris.push_back(t);
     }
+    const std::vector<Tri> full = tris;
     // 3. closed meshes: coincident triangles of opposite orientation are internal faces
     if (flags & B3D_MESH_CLOSED) {
         struct KT {
@@ -526,15 +538,16 @@ b3d_status b3d_load_mesh(b3d_ctx *ctx, const float *verts, int64_t n_v, const in
             if (!drop[i]) kept.push_back(tris[i]);
         tris.swap(kept);
     }
-    // 4. spatial order (Morton code of the centroid) so chunks stay compact
+    // 4. spatial order (Morton code of the centroid): neighbouring threads get nearby
+    //    triangles
     MeshRec rec;
     rec.n_faces = n_f;
     rec.flags = flags;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (const Tri &t : tris)
+    for (const Tri &t : full)
         for (int32_t v : {t.a, t.b, t.c})
             for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], wv[3 * v + k]); hi[k] = std::max(hi[k], wv[3 * v + k]); }
-    if (tris.empty())
+    if (full.empty())
         for (int k = 0; k < 3; ++k) { lo[k] = 0; hi[k] = 0; }
     for (int k = 0; k < 3; ++k) { rec.lo[k] = lo[k]; rec.hi[k] = hi[k]; }
     auto spread = [](uint32_t x) {  // 10 bits -> every third bit
@@ -545,73 +558,167 @@ b3d_status b3d_load_mesh(b3d_ctx *ctx, const float *verts, int64_t n_v, const in
         x = (x | (x << 2)) & 0x9249249;
         return x;
     };
-    std::vector<std::pair<uint32_t, int32_t>> order(tris.size());
-    for (size_t i = 0; i < tris.size(); ++i) {
+    auto morton = [&](const Tri &t) {
         uint32_t q[3];
         for (int k = 0; k < 3; ++k) {
-            const float cen = (wv[3 * tris[i].a + k] + wv[3 * tris[i].b + k] + wv[3 * tris[i].c + k]) / 3.f;
+            const float cen = (wv[3 * t.a + k] + wv[3 * t.b + k] + wv[3 * t.c + k]) / 3.f;
             const float ext = hi[k] - lo[k];
             q[k] = ext > 0 ? (uint32_t)std::min(1023.f, std::max(0.f, (cen - lo[k]) / ext * 1023.f)) : 0u;
         }
-        order[i] = {spread(q[0]) | (spread(q[1]) << 1) | (spread(q[2]) << 2), (int32_t)i};
-    }
-    std::sort(order.begin(), order.end());
-    // 5. chunks of at most kChunkV distinct vertices
-    std::vector<float4> cverts;
-    std::vector<int4> ctris, chunks;
-    std::vector<int32_t> local(wv.size() / 3, -1);
-    std::vector<int32_t> touched;
-    int v_begin = 0, t_begin = 0;
-    auto close_chunk = [&]() {
-        chunks.push_back(make_int4(v_begin, (int)cverts.size(), t_begin, (int)ctris.size()));
-        for (int32_t v : touched) local[v] = -1;
-        touched.clear();
-        v_begin = (int)cverts.size();
-        t_begin = (int)ctris.size();
+        return spread(q[0]) | (spread(q[1]) << 1) | (spread(q[2]) << 2);
     };
-    for (auto &o : order) {
-        const Tri &t = tris[o.second];
-        int fresh = 0;
-        for (int32_t v : {t.a, t.b, t.c}) fresh += local[v] < 0;
-        if ((int)cverts.size() - v_begin + fresh > kChunkV) close_chunk();
-        int li[3], k = 0;
-        for (int32_t v : {t.a, t.b, t.c}) {
-            if (local[v] < 0) {
-                local[v] = (int32_t)cverts.size() - v_begin;
-                touched.push_back(v);
-                cverts.push_back(make_float4(wv[3 * v], wv[3 * v + 1], wv[3 * v + 2], 0.f));
-            }
-            li[k++] = local[v];
+    auto sorted_int4 = [&](const std::vector<Tri> &v) {
+        std::vector<std::pair<uint32_t, int32_t>> order(v.size());
+        for (size_t i = 0; i < v.size(); ++i) order[i] = {morton(v[i]), (int32_t)i};
+        std::sort(order.begin(), order.end());
+        std::vector<int4> out;
+        out.reserve(v.size());
+        for (auto &o : order) out.push_back(make_int4(v[o.second].a, v[o.second].b, v[o.second].c, v[o.second].f));
+        return out;
+    };
+    std::vector<int4> h_full = sorted_int4(full), h_surf = sorted_int4(tris);
+    std::vector<float4> h_verts(wv.size() / 3);
+    for (size_t i = 0; i < h_verts.size(); ++i) h_verts[i] = make_float4(wv[3 * i], wv[3 * i + 1], wv[3 * i + 2], 0.f);
+    std::vector<int4> h_faces((size_t)n_f);
+    for (int64_t f = 0; f < n_f; ++f)
+        h_faces[f] = make_int4(remap[faces[3 * f]], remap[faces[3 * f + 1]], remap[faces[3 * f + 2]], 0);
+
+    // 5. voxel quads: a closed mesh whose surface triangles pair up into unit squares of
+    //    the vertex lattice (distinct coordinates per axis), each square axis-aligned
+    std::vector<unsigned> h_quads;
+    std::vector<int2> h_qtris;
+    std::vector<int> h_off;
+    std::vector<float> h_coords;
+    int nc[3] = {0, 0, 0}, np1 = 0;
+    bool quads_ok = (flags & B3D_MESH_CLOSED) && !tris.empty();
+    std::vector<float> axis_vals[3];
+    std::vector<std::unordered_map<uint32_t, int>> axis_idx(3);
+    if (quads_ok) {
+        for (int a = 0; a < 3; ++a) {
+            std::vector<float> &vals = axis_vals[a];
+            for (const Tri &t : tris)
+                for (int32_t v : {t.a, t.b, t.c}) vals.push_back(wv[3 * v + a]);
+            std::sort(vals.begin(), vals.end());
+            vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
+            if ((int)vals.size() > kMaxPlanes) quads_ok = false;
+            for (size_t i = 0; i < vals.size(); ++i) axis_idx[a][bits(vals[i])] = (int)i;
+            nc[a] = (int)vals.size();
         }
-        ctris.push_back(make_int4(li[0], li[1], li[2], t.f));
     }
-    if (!ctris.empty()) close_chunk();
-    std::vector<int> fmap((size_t)n_f, -1);
-    for (size_t t = 0; t < ctris.size(); ++t) fmap[ctris[t].w] = (int)t;
-    rec.n_tris = (int)ctris.size();
-    rec.n_verts = (int)cverts.size();
-    rec.n_chunks = (int)chunks.size();
+    if (quads_ok) {
+        struct QKey {
+            uint32_t k;
+            bool operator==(const QKey &o) const { return k == o.k; }
+        };
+        std::unordered_map<uint32_t, std::vector<std::pair<int, int>>> groups;  // key -> (tri, missing corner)
+        for (size_t i = 0; i < tris.size() && quads_ok; ++i) {
+            const Tri &t = tris[i];
+            const int32_t vv[3] = {t.a, t.b, t.c};
+            int axis = -1;
+            for (int a = 0; a < 3 && axis < 0; ++a)
+                if (bits(wv[3 * vv[0] + a]) == bits(wv[3 * vv[1] + a]) && bits(wv[3 * vv[0] + a]) == bits(wv[3 * vv[2] + a]))
+                    axis = a;
+            if (axis < 0) { quads_ok = false; break; }
+            const int ab = (axis + 1) % 3, ac = (axis + 2) % 3;
+            int ib[3], ic[3];
+            for (int k = 0; k < 3; ++k) {
+                ib[k] = axis_idx[ab][bits(wv[3 * vv[k] + ab])];
+                ic[k] = axis_idx[ac][bits(wv[3 * vv[k] + ac])];
+            }
+            const int b0 = std::min({ib[0], ib[1], ib[2]}), b1 = std::max({ib[0], ib[1], ib[2]});
+            const int c0 = std::min({ic[0], ic[1], ic[2]}), c1 = std::max({ic[0], ic[1], ic[2]});
+            if (b1 != b0 + 1 || c1 != c0 + 1) { quads_ok = false; break; }
+            // corners k0 (b0,c0) k1 (b1,c0) k2 (b1,c1) k3 (b0,c1); which one is missing
+            bool has[4] = {false, false, false, false};
+            for (int k = 0; k < 3; ++k) has[(ib[k] == b0 ? (ic[k] == c0 ? 0 : 3) : (ic[k] == c0 ? 1 : 2))] = true;
+            int missing = -1, present = 0;
+            for (int k = 0; k < 4; ++k) { if (!has[k]) missing = k; else ++present; }
+            if (present != 3) { quads_ok = false; break; }
+            // outward normal sign along the plane axis
+            double e1[3], e2[3];
+            for (int k = 0; k < 3; ++k) {
+                e1[k] = (double)wv[3 * vv[1] + k] - wv[3 * vv[0] + k];
+                e2[k] = (double)wv[3 * vv[2] + k] - wv[3 * vv[0] + k];
+            }
+            const double nrm = e1[ab] * e2[ac] - e1[ac] * e2[ab];
+            const int cls = 2 * axis + (nrm > 0 ? 1 : 0);
+            const int p = axis_idx[axis][bits(wv[3 * vv[0] + axis])];
+            const uint32_t key = ((uint32_t)cls << 27) | ((uint32_t)p << 18) | ((uint32_t)b0 << 9) | (uint32_t)c0;
+            groups[key].push_back({(int)i, missing});
+        }
+        if (quads_ok) {
+            std::vector<std::pair<uint32_t, int2>> qs;  // (packed, tris)
+            for (auto &kv : groups) {
+                auto &g = kv.second;
+                if (g.size() != 2 || (g[0].second + 2) % 4 != g[1].second) { quads_ok = false; break; }
+                // diag 0: triangles miss k1 and k3 (they share k0-k2); diag 1: miss k0 and k2
+                const int diag = (g[0].second == 1 || g[0].second == 3) ? 0 : 1;
+                // .x: the triangle holding k1 (diag 0) or k0 (diag 1), i.e. not missing it
+                const int hold = diag == 0 ? 1 : 0;
+                const int tx = g[0].second != hold ? g[0].first : g[1].first;
+                const int ty = tx == g[0].first ? g[1].first : g[0].first;
+                const uint32_t cls = kv.first >> 27, rest = kv.first & ((1u << 27) - 1);
+                const uint32_t packed = (cls << 29) | ((uint32_t)diag << 28) | rest;
+                qs.push_back({packed, make_int2(tris[tx].f, tris[ty].f)});
+            }
+            if (quads_ok) {
+                std::sort(qs.begin(), qs.end(), [](const std::pair<uint32_t, int2> &x, const std::pair<uint32_t, int2> &y) {
+                    const uint32_t kx = ((x.first >> 29) << 27) | (x.first & ((1u << 27) - 1));
+                    const uint32_t ky = ((y.first >> 29) << 27) | (y.first & ((1u << 27) - 1));
+                    return kx < ky;
+                });
+                np1 = std::max({nc[0], nc[1], nc[2]}) + 1;
+                h_off.assign((size_t)6 * np1, 0);
+                for (int cls = 0; cls < 6; ++cls) {
+                    const int a = cls >> 1;
+                    for (int p = 0; p <= nc[a]; ++p) {
+                        // first quad with class > cls, or class == cls and plane >= p
+                        auto it = std::lower_bound(qs.begin(), qs.end(), std::make_pair(0u, make_int2(0, 0)),
+                                                   [&](const std::pair<uint32_t, int2> &q, const std::pair<uint32_t, int2> &) {
+                                                       const int qc = (int)(q.first >> 29), qp = (int)((q.first >> 18) & 511);
+                                                       return qc < cls || (qc == cls && qp < p);
+                                                   });
+                        h_off[(size_t)cls * np1 + p] = (int)(it - qs.begin());
+                    }
+                    for (int p = nc[a] + 1; p < np1; ++p) h_off[(size_t)cls * np1 + p] = h_off[(size_t)cls * np1 + nc[a]];
+                }
+                for (auto &q : qs) { h_quads.push_back(q.first); h_qtris.push_back(q.second); }
+                for (int a = 0; a < 3; ++a) h_coords.insert(h_coords.end(), axis_vals[a].begin(), axis_vals[a].end());
+            }
+        }
+    }
+    if (!quads_ok) { h_quads.clear(); h_qtris.clear(); h_off.clear(); h_coords.clear(); nc[0] = nc[1] = nc[2] = 0; np1 = 0; }
+    rec.n_surf = (int)h_surf.size();
+    rec.n_full = (int)h_full.size();
+    rec.n_verts = (int)h_verts.size();
+    rec.n_quads = (int)h_quads.size();
+    for (int k = 0; k < 3; ++k) rec.nc[k] = nc[k];
+    rec.np1 = np1;
 
     DeviceGuard g(ctx->device);
-    b3d_status st;
-    if ((st = dalloc(ctx, &rec.verts, cverts.size(), "mesh vertices")) != B3D_OK) return st;
-    if ((st = dalloc(ctx, &rec.tris, ctris.size(), "mesh triangles")) != B3D_OK) { dfree(ctx, rec.verts); return st; }
-    if ((st = dalloc(ctx, &rec.chunks, chunks.size(), "mesh chunks")) != B3D_OK) {
-        dfree(ctx, rec.verts); dfree(ctx, rec.tris); return st;
+    b3d_status st = B3D_OK;
+    auto up = [&](auto **dst, const auto &vec, const char *what) {
+        if (st != B3D_OK) return;
+        if ((st = dalloc(ctx, dst, vec.size(), what)) != B3D_OK) return;
+        if (!vec.empty()) {
+            cudaError_t e = cudaMemcpy(*dst, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) st = cuda_fail(ctx, e, what);
+        }
+    };
+    up(&rec.verts, h_verts, "mesh vertices");
+    up(&rec.tris_surf, h_surf, "mesh surface triangles");
+    up(&rec.tris_full, h_full, "mesh triangles");
+    up(&rec.faces, h_faces, "mesh faces");
+    if (rec.n_quads > 0) {
+        up(&rec.quads, h_quads, "mesh quads");
+        up(&rec.quad_tris, h_qtris, "mesh quad triangles");
+        up(&rec.class_off, h_off, "mesh quad classes");
+        up(&rec.coords, h_coords, "mesh lattice");
     }
-    if ((st = dalloc(ctx, &rec.face_map, fmap.size(), "mesh face map")) != B3D_OK) {
-        dfree(ctx, rec.verts); dfree(ctx, rec.tris); dfree(ctx, rec.chunks); return st;
-    }
-    cudaError_t e = cudaSuccess;
-    if (!cverts.empty()) e = cudaMemcpy(rec.verts, cverts.data(), cverts.size() * sizeof(float4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !ctris.empty())
-        e = cudaMemcpy(rec.tris, ctris.data(), ctris.size() * sizeof(int4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !chunks.empty())
-        e = cudaMemcpy(rec.chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(rec.face_map, fmap.data(), fmap.size() * sizeof(int), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        dfree(ctx, rec.verts); dfree(ctx, rec.tris); dfree(ctx, rec.chunks); dfree(ctx, rec.face_map);
-        return cuda_fail(ctx, e, "mesh upload");
+    if (st != B3D_OK) {
+        dfree(ctx, rec.verts); dfree(ctx, rec.tris_surf); dfree(ctx, rec.tris_full); dfree(ctx, rec.faces);
+        dfree(ctx, rec.quads); dfree(ctx, rec.quad_tris); dfree(ctx, rec.class_off); dfree(ctx, rec.coords);
+        return st;
     }
     ctx->meshes.push_back(rec);
     *mesh_id = (int32_t)ctx->meshes.size() - 1;

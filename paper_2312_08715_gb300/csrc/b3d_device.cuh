@@ -100,16 +100,15 @@ __device__ __forceinline__ float key_depth(unsigned long long k, int miss_mode, 
     return k == kEmptyKey ? (miss_mode ? -1.f : far_z) : __uint_as_float((unsigned)(k >> 32));
 }
 
-// Rasterise one triangle (screen vertices A, B, C) into the z-buffer tile whose origin is
-// (zx0, zy0) and row length zw, over pixel centres in [rx0, rx1] x [ry0, ry1]. Coverage:
-// all three edge functions, oriented by the sign of the signed area, are >= 0. Depth:
-// perspective-correct, 1/z interpolated with screen barycentrics. Closed meshes skip
-// triangles whose screen area is not negative (facing away from the camera).
+// Rasterise one triangle (screen vertices A, B, C as (u, v, 1/z, z)) over the pixel centres
+// in [rx0, rx1] x [ry0, ry1], calling store(x, y, z) for each fragment. Coverage: all three
+// edge functions, oriented by the sign of the signed area, are >= 0. Depth:
+// perspective-correct, 1/z interpolated with screen barycentrics. With cull set, triangles
+// whose screen area is not negative (turned away from the camera) are skipped.
 // tests (optional) counts the pixel-centre coverage tests made.
 template <class Store>
-__device__ __forceinline__ void raster_tri(float4 A, float4 B, float4 C, unsigned gid, int cull, int rx0, int rx1,
-                                           int ry0, int ry1, float far_z, Store store,
-                                           unsigned long long *tests = nullptr) {
+__device__ __forceinline__ void raster_tri(float4 A, float4 B, float4 C, int cull, int rx0, int rx1, int ry0, int ry1,
+                                           float far_z, Store store, unsigned long long *tests = nullptr) {
     if (A.z < 0.f || B.z < 0.f || C.z < 0.f) return;
     const float area = edge_fn(A.x, A.y, B.x, B.y, C.x, C.y);
     if (cull ? !(area < 0.f) : !(area != 0.f)) return;
@@ -131,16 +130,54 @@ __device__ __forceinline__ void raster_tri(float4 A, float4 B, float4 C, unsigne
             const float den = fmaf(e1, A.z, fmaf(e2, B.z, e0 * C.z));
             const float z = area / den;
             if (!(z <= far_z)) continue;
-            store(x, y, pack_key(z, gid));
+            store(x, y, z);
+        }
+    }
+}
+
+// Rasterise a planar convex quadrilateral C0 C1 C2 C3 (screen corners in order, as in
+// raster_tri): a pixel centre is covered when all four oriented edge functions are >= 0
+// (the union of the triangles C0C1C2 and C0C2C3 or C1C2C3 and C1C3C0 alike); the depth is
+// the reciprocal of the quad plane's affine 1/z at the centre.
+template <class Store>
+__device__ __forceinline__ void raster_quad(float4 C0, float4 C1, float4 C2, float4 C3, int rx0, int rx1, int ry0,
+                                            int ry1, float far_z, Store store, unsigned long long *tests = nullptr) {
+    const float area = edge_fn(C0.x, C0.y, C1.x, C1.y, C2.x, C2.y);
+    if (!(area != 0.f)) return;
+    const float umin = fminf(fminf(C0.x, C1.x), fminf(C2.x, C3.x)), umax = fmaxf(fmaxf(C0.x, C1.x), fmaxf(C2.x, C3.x));
+    const float vmin = fminf(fminf(C0.y, C1.y), fminf(C2.y, C3.y)), vmax = fmaxf(fmaxf(C0.y, C1.y), fmaxf(C2.y, C3.y));
+    const int x0 = (int)ceilf(fmaxf(umin - 0.5f, (float)rx0)), x1 = (int)floorf(fminf(umax - 0.5f, (float)rx1));
+    const int y0 = (int)ceilf(fmaxf(vmin - 0.5f, (float)ry0)), y1 = (int)floorf(fminf(vmax - 0.5f, (float)ry1));
+    if (x0 > x1 || y0 > y1) return;
+    if (tests) *tests += (unsigned long long)((x1 - x0 + 1) * (y1 - y0 + 1));
+    const float s = area > 0.f ? 1.f : -1.f;
+    const float du1 = C1.x - C0.x, dv1 = C1.y - C0.y, du2 = C2.x - C0.x, dv2 = C2.y - C0.y;
+    const float dz1 = C1.z - C0.z, dz2 = C2.z - C0.z;
+    const float al = fmaf(dz1, dv2, -(dz2 * dv1)) / area, be = fmaf(dz2, du1, -(dz1 * du2)) / area;
+    for (int y = y0; y <= y1; ++y) {
+        const float py = (float)y + 0.5f;
+        for (int x = x0; x <= x1; ++x) {
+            const float px = (float)x + 0.5f;
+            if (s * edge_fn(C0.x, C0.y, C1.x, C1.y, px, py) < 0.f) continue;
+            if (s * edge_fn(C1.x, C1.y, C2.x, C2.y, px, py) < 0.f) continue;
+            if (s * edge_fn(C2.x, C2.y, C3.x, C3.y, px, py) < 0.f) continue;
+            if (s * edge_fn(C3.x, C3.y, C0.x, C0.y, px, py) < 0.f) continue;
+            const float iz = fmaf(al, px - C0.x, fmaf(be, py - C0.y, C0.z));
+            const float z = 1.0f / iz;
+            if (!(z <= far_z)) continue;
+            store(x, y, z);
         }
     }
 }
 
 // Screen bounding box (pixel-centre index ranges, clipped, 1 px margin) of the object's
-// bounding box under pose P; the whole image if a corner is in front of the near plane.
-// Returns false if it misses the image or the mesh is empty.
-__device__ __forceinline__ bool object_bbox(const MeshView &m, const float *P, const Cam &c, int *bb) {
-    if (m.n_tris <= 0) return false;
+// bounding box under pose P; the whole image if a corner is in front of the near plane
+// (*front = false then: the near plane may cut the object open). Returns false if it
+// misses the image or the mesh is empty.
+__device__ __forceinline__ bool object_bbox(const MeshView &m, const float *P, const Cam &c, int *bb,
+                                            bool *front = nullptr) {
+    if (front) *front = false;
+    if (m.n_full <= 0) return false;
     float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
     bool all_front = true;
     for (int k = 0; k < 8; ++k) {
@@ -152,6 +189,7 @@ __device__ __forceinline__ bool object_bbox(const MeshView &m, const float *P, c
         umin = fminf(umin, u); umax = fmaxf(umax, u);
         vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
     }
+    if (front) *front = all_front;
     if (!all_front) {
         bb[0] = 0; bb[1] = c.W - 1; bb[2] = 0; bb[3] = c.H - 1;
         return true;
@@ -163,6 +201,14 @@ __device__ __forceinline__ bool object_bbox(const MeshView &m, const float *P, c
     bb[2] = max((int)ceilf(lo_v) - 1, 0);
     bb[3] = min((int)floorf(hi_v) + 1, c.H - 1);
     return bb[0] <= bb[1] && bb[2] <= bb[3];
+}
+
+// Screen vertices of triangle tr (welded vertex indices) under pose P.
+__device__ __forceinline__ void tri_screen(const MeshView &m, int4 tr, const float *P, const Cam &c, float4 &A, float4 &B,
+                                           float4 &C) {
+    A = project(P, m.verts[tr.x], c);
+    B = project(P, m.verts[tr.y], c);
+    C = project(P, m.verts[tr.z], c);
 }
 
 // l_i of observed point q at pixel (xi, yi): the (2w+1)^2 window over rendered depths given

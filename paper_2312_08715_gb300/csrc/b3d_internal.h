@@ -8,8 +8,8 @@
 namespace b3d {
 
 constexpr int kThreads = 256;          // threads per CTA of the render/score kernels
-constexpr int kChunkV = 2048;          // vertices per mesh chunk staged in shared memory
 constexpr int kRegionPx = 4096;        // z-buffer pixels per screen tile in shared memory
+constexpr int kMaxPlanes = 511;        // lattice planes per axis of a quad mesh
 constexpr int kMaxHalfWindow = 7;
 constexpr int kMaxLut = (2 * kMaxHalfWindow + 1) * (2 * kMaxHalfWindow + 1) + 1;
 constexpr unsigned long long kEmptyKey = ~0ull;
@@ -21,17 +21,34 @@ struct Cam {
     float inv_fx, inv_fy;
 };
 
-// One object's render data. A mesh is split into chunks of at most kChunkV vertices; a
-// chunk owns a contiguous run of triangles whose vertex indices are local to the chunk.
+// One object's render data.
+//  - verts: welded vertices (bitwise-equal positions merged), object frame.
+//  - tris_surf: the triangles that can be the nearest surface when the whole object lies
+//    beyond the near plane: for a closed outward mesh, coincident internal face pairs are
+//    removed (and back faces are skipped per hypothesis); otherwise all triangles.
+//  - tris_full: every non-degenerate triangle, used when the near plane cuts the object
+//    open (then internal and back faces can be visible).
+//  - faces: the original faces on welded vertices (triangle id -> vertices).
+//  - quads (optional, voxel meshes): every surface triangle pairs with another into a unit
+//    square of the vertex lattice; quads are grouped by face class (axis, outward sign) and
+//    sorted by lattice plane, so the faces turned towards a camera position are one
+//    contiguous range per class.
 struct MeshView {
-    const float4 *verts;   // concatenated chunk vertex lists, object frame (w unused)
-    const int4 *tris;      // (i0, i1, i2, original face index)
-    const int4 *chunks;    // (v_begin, v_end, t_begin, t_end)
-    const int *face_map;   // [n_faces] original face index -> position in tris, -1 if culled
-    int n_chunks;
-    int n_tris;
-    float lo[3], hi[3];    // object-frame bounding box of the vertices
-    int cull_back;         // closed outward mesh: faces turned away are skipped
+    const float4 *verts;
+    const int4 *tris_surf;      // (v0, v1, v2, original face index)
+    const int4 *tris_full;
+    const int4 *faces;          // [n_faces] (v0, v1, v2, 0)
+    int n_surf, n_full, n_faces;
+    int closed;                 // back faces may be skipped (whole object beyond near)
+    float lo[3], hi[3];         // object-frame bounding box of the vertices
+    // voxel quads
+    int n_quads;                // 0: no quad representation
+    const unsigned *quads;      // packed: class(3) diag(1) 0(1) plane(9) b0(9) c0(9)
+    const int2 *quad_tris;      // original face ids of the two triangles of the quad
+    const int *class_off;       // [6 * (np1)]: first quad of class c with plane >= p
+    const float *coords;        // lattice plane coordinates, x planes then y then z
+    int nc[3];                  // planes per axis
+    int np1;                    // stride of class_off (max planes + 1)
 };
 
 // Windowed likelihood constants (Eq. 1 with the window of Sec. III-B).
@@ -99,7 +116,6 @@ void launch_score_depth(const SceneView &sv, const Lik &L, const float *depth, c
                         float *ll, int grid, cudaStream_t s);
 int launch_grad_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, float *dpose,
                      float *dsigma, float *dpout, int grid, cudaStream_t s);
-int fused_smem_bytes();
 
 // ---- launchers (k_c2f.cu) ----------------------------------------------------------------
 void launch_set16(float *dst, const float *src16_host_values, cudaStream_t s);

@@ -113,7 +113,7 @@ __global__ void k_set16(float *dst, F16 src) {
 // ------------------------------------------------------------------------------------------
 constexpr int kLseThreads = 256;
 constexpr int kLseMaxBlocks = 1024;
-constexpr int kLseMinChunk = 2048;
+constexpr int kLseMinChunk = 512;
 
 __device__ __forceinline__ float lse_weight(float x, float m) {
     return (x == x && m > -INFINITY) ? __expf(x - m) : 0.f;  // NaN and -inf entries weigh 0
@@ -220,19 +220,30 @@ __global__ void __launch_bounds__(kLseThreads) k_lse_resample(const float *ll, i
         const int64_t e0 = (int64_t)b * chunk, e1 = std::min<int64_t>(n, e0 + chunk);
         float c0 = s_pre[b];
         int64_t found = -1, last_pos = -1;
-        for (int64_t base = e0; base < e1 && found < 0; base += 32) {
-            const int64_t i = base + lane;
-            const float wv = i < e1 ? lse_weight(__ldcg(&ll[i]), M) : 0.f;
-            float inc = wv;
-            for (int o = 1; o < 32; o <<= 1) {
-                const float up = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += up;
+        // 128 elements per pass, four independent loads in flight per lane
+        for (int64_t base = e0; base < e1 && found < 0; base += 128) {
+            float wv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = base + 32 * u + lane;
+                wv[u] = i < e1 ? lse_weight(__ldcg(&ll[i]), M) : 0.f;
             }
-            const unsigned hit = __ballot_sync(0xffffffffu, i < e1 && wv > 0.f && c0 + inc > t);
-            const unsigned pos = __ballot_sync(0xffffffffu, i < e1 && wv > 0.f);
-            if (pos) last_pos = base + 31 - __clz(pos);
-            if (hit) found = base + __ffs(hit) - 1;
-            c0 += __shfl_sync(0xffffffffu, inc, 31);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = base + 32 * u + lane;
+                float inc = wv[u];
+                for (int o = 1; o < 32; o <<= 1) {
+                    const float up = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += up;
+                }
+                const unsigned hit = __ballot_sync(0xffffffffu, i < e1 && wv[u] > 0.f && c0 + inc > t);
+                const unsigned pos = __ballot_sync(0xffffffffu, i < e1 && wv[u] > 0.f);
+                if (found < 0) {
+                    if (pos) last_pos = base + 32 * u + 31 - __clz(pos);
+                    if (hit) found = base + 32 * u + __ffs(hit) - 1;
+                }
+                c0 += __shfl_sync(0xffffffffu, inc, 31);
+            }
         }
         if (found < 0) found = last_pos;
         if (lane == 0) {

@@ -10,6 +10,8 @@
 //           times dz_j/dxi = [n / (n.r_j), (q_j x n) / (n.r_j)] (left perturbation of the
 //           pose in the camera frame; the point slides along its pixel ray on the plane of
 //           its triangle, normal n), accumulated over j.
+// The forward uses the same triangle sets as the renderer (surface set with back faces
+// skipped when the whole object lies beyond the near plane, every triangle otherwise).
 // Nothing per pixel is stored in global memory.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -22,21 +24,20 @@
 
 namespace b3d {
 
-constexpr int kGradSmem = kRegionPx * (int)sizeof(unsigned long long) + kChunkV * (int)sizeof(float4) +
-                          kRegionPx * (int)sizeof(float);
+constexpr int kGradSmem = kRegionPx * ((int)sizeof(unsigned long long) + 3 * (int)sizeof(float));
 
 template <class PS>
 __global__ void __launch_bounds__(kThreads) k_grad(SceneView S, Lik L, PS P, int64_t n_hyp, float *out_ll,
                                                    float *out_dpose, float *out_ds, float *out_dp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long *zb = reinterpret_cast<unsigned long long *>(smem_raw);
-    float4 *sv = reinterpret_cast<float4 *>(smem_raw + kRegionPx * sizeof(unsigned long long));
-    float *zd = reinterpret_cast<float *>(sv);          // rendered depth per Z pixel
-    int *tj = reinterpret_cast<int *>(zd + kRegionPx);  // object triangle (index in tris) or -1
-    float *ip = reinterpret_cast<float *>(smem_raw + kRegionPx * sizeof(unsigned long long) + kChunkV * sizeof(float4));
+    float *zd = reinterpret_cast<float *>(zb + kRegionPx);  // rendered depth per Z pixel
+    int *tj = reinterpret_cast<int *>(zd + kRegionPx);      // original face of the object, or -1
+    float *ip = reinterpret_cast<float *>(tj + kRegionPx);  // b / p_i
     __shared__ float s_lut[kMaxLut];
     __shared__ float s_pose[12];
     __shared__ int s_bb[5];
+    __shared__ int s_front;
     __shared__ float s_red[kThreads / 32];
 
     const Cam &c = S.cam;
@@ -49,14 +50,17 @@ __global__ void __launch_bounds__(kThreads) k_grad(SceneView S, Lik L, PS P, int
         __syncthreads();
         if (tid == 0) {
             pose12(P, h, s_pose);
-            s_bb[4] = object_bbox(m, s_pose, c, s_bb) ? 1 : 0;
+            bool front = false;
+            s_bb[4] = object_bbox(m, s_pose, c, s_bb, &front) ? 1 : 0;
+            s_front = front ? 1 : 0;
         }
         __syncthreads();
-        float pose[12];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) pose[k] = s_pose[k];
-        const bool has_bb = s_bb[4] != 0;
+        const float *pose = s_pose;
+        const bool has_bb = s_bb[4] != 0, front = s_front != 0;
         const int bx0 = s_bb[0], bx1 = s_bb[1], by0 = s_bb[2], by1 = s_bb[3];
+        const int4 *tris = front ? m.tris_surf : m.tris_full;
+        const int n_t = front ? m.n_surf : m.n_full;
+        const int cull = front ? m.closed : 0;
         float acc_l = 0.f, acc_s = 0.f, acc_p = 0.f, g6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (has_bb) {
             const int sx0 = max(bx0 - w, 0), sx1 = min(bx1 + w, c.W - 1);
@@ -78,18 +82,15 @@ __global__ void __launch_bounds__(kThreads) k_grad(SceneView S, Lik L, PS P, int
                     const bool need = rx0 <= rx1 && ry0 <= ry1;
                     if (need) {
                         for (int i = tid; i < zw * zh; i += nt) zb[i] = kEmptyKey;
-                        for (int ch = 0; ch < m.n_chunks; ++ch) {
-                            const int4 cr = m.chunks[ch];
-                            __syncthreads();
-                            for (int v = tid; v < cr.y - cr.x; v += nt) sv[v] = project(pose, m.verts[cr.x + v], c);
-                            __syncthreads();
-                            for (int t = cr.z + tid; t < cr.w; t += nt) {
-                                const int4 tr = m.tris[t];
-                                raster_tri(sv[tr.x], sv[tr.y], sv[tr.z], (unsigned)(S.tri_base + tr.w), m.cull_back,
-                                           rx0, rx1, ry0, ry1, c.far_z, [&](int x, int y, unsigned long long key) {
-                                               atomicMin(&zb[(y - zy0) * zw + (x - zx0)], key);
-                                           });
-                            }
+                        __syncthreads();
+                        for (int t = tid; t < n_t; t += nt) {
+                            const int4 tr = tris[t];
+                            float4 A, B, C;
+                            tri_screen(m, tr, pose, c, A, B, C);
+                            const unsigned gid = (unsigned)(S.tri_base + tr.w);
+                            raster_tri(A, B, C, cull, rx0, rx1, ry0, ry1, c.far_z, [&](int x, int y, float z) {
+                                atomicMin(&zb[(y - zy0) * zw + (x - zx0)], pack_key(z, gid));
+                            });
                         }
                         __syncthreads();
                     }
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(SceneView S, Lik L, PS P, int
                         int t = -1;
                         if (need && zb[i] < kb) {
                             key = zb[i];
-                            t = m.face_map[(int)(unsigned)(key & 0xffffffffu) - S.tri_base];
+                            t = (int)(unsigned)(key & 0xffffffffu) - S.tri_base;
                         }
                         zd[i] = key_depth(key, L.miss_mode, c.far_z);
                         tj[i] = t;
@@ -153,15 +154,9 @@ __global__ void __launch_bounds__(kThreads) k_grad(SceneView S, Lik L, PS P, int
                             }
                         }
                         // triangle normal in the camera frame
-                        const int4 tr = m.tris[t];
-                        int lo = 0, hi = m.n_chunks - 1;
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (m.chunks[mid].z <= t) lo = mid; else hi = mid - 1;
-                        }
-                        const int vb = m.chunks[lo].x;
+                        const int4 f = m.faces[t];
                         float ax, ay, az, bx, by, bz, cx_, cy_, cz_;
-                        const float4 A = m.verts[vb + tr.x], B = m.verts[vb + tr.y], C = m.verts[vb + tr.z];
+                        const float4 A = m.verts[f.x], B = m.verts[f.y], C = m.verts[f.z];
                         xform(pose, A.x, A.y, A.z, ax, ay, az);
                         xform(pose, B.x, B.y, B.z, bx, by, bz);
                         xform(pose, C.x, C.y, C.z, cx_, cy_, cz_);

@@ -1,12 +1,13 @@
 // k_render.cu - rasterisation and windowed-likelihood kernels of libb3d.
 //
-// The fused kernel renders one pose hypothesis per CTA iteration into a shared-memory
-// z-buffer of packed (depth bits << 32 | triangle id) keys (64-bit atomicMin: nearest
-// fragment wins, equal depths go to the smaller id), composites it with the fixed objects'
-// background keys, converts keys to rendered depths, and scores every observed pixel whose
-// (2w+1)^2 window can see the object (the windowed Eq. 1 likelihood of Sec. III-B). Pixels
-// whose window cannot see the object keep their background term, which is precomputed once
-// per scene, so a hypothesis costs work in proportion to its screen footprint:
+// The render kernel draws one pose hypothesis per CTA iteration into a shared-memory
+// z-buffer of packed (depth bits << 32 | triangle id) keys (64-bit atomicMin: the nearest
+// fragment wins, equal depths go to the smaller id) and composites it with the fixed
+// objects' background keys. The score kernel does the same with depth bits alone, then
+// scores every observed pixel whose (2w+1)^2 window can see the object (the windowed Eq. 1
+// likelihood of Sec. III-B). Pixels whose window cannot see the object keep their
+// background term, precomputed once per scene, so a hypothesis costs work in proportion to
+// its screen footprint:
 //   LL_h = sum_i l_i(h) = LL_bg + sum_{i in footprint + w} (l_i(h) - l_i(bg)),
 // an exact identity (the terms outside the dilated footprint are equal, bit for bit, since
 // they are computed by the same device function from the same inputs).
@@ -22,136 +23,256 @@
 namespace b3d {
 
 // ------------------------------------------------------------------------------------------
-// fused render (+ score) kernel
+// score kernel
 // ------------------------------------------------------------------------------------------
-// MODE 0: score; MODE 1: render (write depth / triangle id of the whole image).
-// STATS: count the work done (hypotheses, vertices, triangles, pixel tests, fragments,
-// composited pixels, scored pixels, window pairs) into S.stats for the roofline accounting.
-template <int MODE, class PS, bool STATS>
-__global__ void __launch_bounds__(kThreads) k_fused(SceneView S, Lik L, PS P, int64_t n_hyp, float *out_ll,
-                                                    float *out_depth, int *out_tid) {
+// One hypothesis per CTA iteration of a persistent grid:
+//  1. pose; screen bounding box of the object; whether the near plane can cut it. For a
+//     quad (voxel) mesh wholly beyond the near plane: the camera position o in the object
+//     frame and, per face class (axis, outward sign), the contiguous range of quads whose
+//     plane has o on its outer side (the faces turned towards the camera); the rest are
+//     never loaded.
+//  2. quad meshes: the camera-frame position of every lattice plane along each axis (the
+//     rotation column times the plane coordinate, plus t on the x axis), so a corner is the
+//     sum of three shared terms and every quad sharing a corner gets the same bits.
+//  3. per screen tile: clear a 32-bit z-buffer of depth bits, rasterise with atomicMin (the
+//     score depends only on the nearest depth, so no triangle id rides along), composite
+//     with the fixed objects' depths, score the tile's observed pixels against their
+//     background terms.
+//  4. block reduction to one log-likelihood.
+// STATS: count the work done (hypotheses, projected vertices/corners, primitives, pixel
+// tests, fragments, composited pixels, scored pixels, window pairs) into S.stats.
+template <class PS, bool STATS>
+__global__ void __launch_bounds__(kThreads) k_score(SceneView S, Lik L, PS P, int64_t n_hyp, float *out_ll) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned long long *zb = reinterpret_cast<unsigned long long *>(smem_raw);
-    float4 *sv = reinterpret_cast<float4 *>(smem_raw + kRegionPx * sizeof(unsigned long long));
-    float *zd = reinterpret_cast<float *>(sv);  // rendered depths, alias of sv after rasterising
+    unsigned *zb = reinterpret_cast<unsigned *>(smem_raw);                       // [kRegionPx]
+    float *zd = reinterpret_cast<float *>(smem_raw);                             // same memory, as depths
+    float4 *lat = reinterpret_cast<float4 *>(smem_raw + kRegionPx * sizeof(unsigned));  // lattice planes
     __shared__ float s_lut[kMaxLut];
     __shared__ float s_pose[12];
-    __shared__ int s_bb[5];
+    __shared__ int s_bb[4];
+    __shared__ int s_flags;  // bit 0: on screen, bit 1: quad path, bit 2: whole object beyond near
+    __shared__ int s_rng[13];
     __shared__ float s_red[kThreads / 32];
 
     const Cam &c = S.cam;
     const MeshView &m = S.mesh;
     const int tid = threadIdx.x, nt = blockDim.x;
-    if (MODE == 0)
-        for (int i = tid; i < L.n_lut; i += nt) s_lut[i] = L.lut[i];
-    const int w = MODE == 0 ? L.w : 0;
-    const int64_t npx = (int64_t)c.W * c.H;
+    for (int i = tid; i < L.n_lut; i += nt) s_lut[i] = L.lut[i];
+    const int w = L.w;
+    const int n_lat = m.nc[0] + m.nc[1] + m.nc[2];
     unsigned long long cnt[kNumStats] = {0, 0, 0, 0, 0, 0, 0, 0};
 
     for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
         __syncthreads();
-        if (STATS && tid == 0) ++cnt[0];
         if (tid == 0) {
+            if (STATS) ++cnt[0];
             pose12(P, h, s_pose);
-            s_bb[4] = object_bbox(m, s_pose, c, s_bb) ? 1 : 0;
+            bool front = false;
+            int f = object_bbox(m, s_pose, c, s_bb, &front) ? 1 : 0;
+            if (front) f |= 4;
+            if (f && front && m.n_quads > 0) {
+                f |= 2;
+                const float *R = s_pose, *t = s_pose + 9;
+                float o[3];
+                for (int a = 0; a < 3; ++a) o[a] = -fmaf(R[a], t[0], fmaf(R[3 + a], t[1], R[6 + a] * t[2]));
+                int tot = 0;
+                for (int cls = 0; cls < 6; ++cls) {
+                    const int a = cls >> 1;
+                    const float *cd = m.coords + (a == 0 ? 0 : (a == 1 ? m.nc[0] : m.nc[0] + m.nc[1]));
+                    const int n = m.nc[a];
+                    int lo = 0, hi = n;  // first plane with coordinate >= o
+                    while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] < o[a]) lo = mid + 1; else hi = mid; }
+                    const int below = lo;
+                    hi = n;  // first plane with coordinate > o
+                    while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] <= o[a]) lo = mid + 1; else hi = mid; }
+                    const int not_above = lo;
+                    const int *off = m.class_off + cls * m.np1;
+                    // +axis faces face the camera when their plane is below o; -axis when above
+                    const int b = (cls & 1) ? off[0] : off[not_above];
+                    const int e = (cls & 1) ? off[below] : off[n];
+                    s_rng[cls] = b;
+                    s_rng[6 + cls] = e - b;
+                    tot += e - b;
+                }
+                s_rng[12] = tot;
+            }
+            s_flags = f;
         }
         __syncthreads();
-        float pose[12];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) pose[k] = s_pose[k];
-        const bool has_bb = s_bb[4] != 0;
-        const int bx0 = s_bb[0], bx1 = s_bb[1], by0 = s_bb[2], by1 = s_bb[3];
-
-        int sx0, sx1, sy0, sy1;
-        if (MODE == 0) {
-            if (has_bb) {
-                sx0 = max(bx0 - w, 0); sx1 = min(bx1 + w, c.W - 1);
-                sy0 = max(by0 - w, 0); sy1 = min(by1 + w, c.H - 1);
-            } else {
-                sx0 = 0; sx1 = -1; sy0 = 0; sy1 = -1;
-            }
-        } else {
-            sx0 = 0; sx1 = c.W - 1; sy0 = 0; sy1 = c.H - 1;
+        const int flags = s_flags;
+        if (!(flags & 1)) {
+            if (tid == 0) out_ll[h] = (float)*S.ll_bg;
+            continue;
         }
-        float acc = 0.f;
+        const float *pose = s_pose;
+        const bool quad = (flags & 2) != 0, front = (flags & 4) != 0;
+        const int bx0 = s_bb[0], bx1 = s_bb[1], by0 = s_bb[2], by1 = s_bb[3];
+        if (quad) {
+            for (int k = tid; k < n_lat; k += nt) {
+                const int a = k < m.nc[0] ? 0 : (k < m.nc[0] + m.nc[1] ? 1 : 2);
+                const float v = m.coords[k];
+                lat[k] = make_float4(fmaf(pose[a], v, a == 0 ? pose[9] : 0.f), fmaf(pose[3 + a], v, a == 0 ? pose[10] : 0.f),
+                                     fmaf(pose[6 + a], v, a == 0 ? pose[11] : 0.f), 0.f);
+            }
+            if (STATS) cnt[1] += (unsigned long long)((n_lat - tid + nt - 1) / nt);
+        }
+        const int sx0 = max(bx0 - w, 0), sx1 = min(bx1 + w, c.W - 1);
+        const int sy0 = max(by0 - w, 0), sy1 = min(by1 + w, c.H - 1);
         const int sw = sx1 - sx0 + 1;
-        if (sw > 0 && sy1 >= sy0) {
-            const int tw = MODE == 0 ? min(sw, 64) : min(sw, kRegionPx);
-            const int th = max(1, kRegionPx / (tw + 2 * w) - 2 * w);
-            for (int ty0 = sy0; ty0 <= sy1; ty0 += th) {
-                for (int tx0 = sx0; tx0 <= sx1; tx0 += tw) {
-                    const int tx1 = min(tx0 + tw - 1, sx1), ty1 = min(ty0 + th - 1, sy1);
-                    const int zx0 = max(tx0 - w, 0), zx1 = min(tx1 + w, c.W - 1);
-                    const int zy0 = max(ty0 - w, 0), zy1 = min(ty1 + w, c.H - 1);
-                    const int zw = zx1 - zx0 + 1, zh = zy1 - zy0 + 1;
-                    const int rx0 = max(zx0, bx0), rx1 = min(zx1, bx1), ry0 = max(zy0, by0), ry1 = min(zy1, by1);
-                    const bool need = has_bb && rx0 <= rx1 && ry0 <= ry1;
-                    if (need) {
-                        for (int i = tid; i < zw * zh; i += nt) zb[i] = kEmptyKey;
-                        for (int ch = 0; ch < m.n_chunks; ++ch) {
-                            const int4 cr = m.chunks[ch];
-                            __syncthreads();
-                            for (int v = tid; v < cr.y - cr.x; v += nt) sv[v] = project(pose, m.verts[cr.x + v], c);
-                            if (STATS) cnt[1] += (cr.y - cr.x - tid + nt - 1 > 0) ? (cr.y - cr.x - tid + nt - 1) / nt : 0;
-                            __syncthreads();
-                            for (int t = cr.z + tid; t < cr.w; t += nt) {
-                                const int4 tr = m.tris[t];
-                                if (STATS) ++cnt[2];
-                                raster_tri(sv[tr.x], sv[tr.y], sv[tr.z], (unsigned)(S.tri_base + tr.w), m.cull_back,
-                                           rx0, rx1, ry0, ry1, c.far_z, [&](int x, int y, unsigned long long key) {
-                                               if (STATS) ++cnt[4];
-                                               atomicMin(&zb[(y - zy0) * zw + (x - zx0)], key);
-                                           }, STATS ? &cnt[3] : nullptr);
+        const int tw = min(sw, 64);
+        const int th = max(1, kRegionPx / (tw + 2 * w) - 2 * w);
+        float acc = 0.f;
+        for (int ty0 = sy0; ty0 <= sy1; ty0 += th) {
+            for (int tx0 = sx0; tx0 <= sx1; tx0 += tw) {
+                const int tx1 = min(tx0 + tw - 1, sx1), ty1 = min(ty0 + th - 1, sy1);
+                const int zx0 = max(tx0 - w, 0), zx1 = min(tx1 + w, c.W - 1);
+                const int zy0 = max(ty0 - w, 0), zy1 = min(ty1 + w, c.H - 1);
+                const int zw = zx1 - zx0 + 1, zh = zy1 - zy0 + 1;
+                const int rx0 = max(zx0, bx0), rx1 = min(zx1, bx1), ry0 = max(zy0, by0), ry1 = min(zy1, by1);
+                const bool need = rx0 <= rx1 && ry0 <= ry1;
+                for (int i = tid; i < zw * zh; i += nt) zb[i] = 0xffffffffu;
+                __syncthreads();
+                if (need) {
+                    auto store = [&](int x, int y, float z) {
+                        if (STATS) ++cnt[4];
+                        atomicMin(&zb[(y - zy0) * zw + (x - zx0)], __float_as_uint(z));
+                    };
+                    if (quad) {
+                        const int total = s_rng[12];
+                        const int nc0 = m.nc[0], nc01 = m.nc[0] + m.nc[1];
+                        for (int k = tid; k < total; k += nt) {
+                            int r = k, cls = 0;
+                            while (r >= s_rng[6 + cls]) { r -= s_rng[6 + cls]; ++cls; }
+                            const unsigned q = m.quads[s_rng[cls] + r];
+                            const int a = cls >> 1, p = (q >> 18) & 511, b0 = (q >> 9) & 511, c0 = q & 511;
+                            float4 C[4];
+#pragma unroll
+                            for (int k4 = 0; k4 < 4; ++k4) {
+                                // lattice index of corner k4 along the plane axis a (p), the next
+                                // axis (b0 + db) and the one after (c0 + dc)
+                                const int pb = b0 + ((k4 == 1 || k4 == 2) ? 1 : 0), pc = c0 + (k4 >= 2 ? 1 : 0);
+                                const int lx = a == 0 ? p : (a == 1 ? pc : pb);
+                                const int ly = a == 1 ? p : (a == 2 ? pc : pb);
+                                const int lz = a == 2 ? p : (a == 0 ? pc : pb);
+                                const float4 X = lat[lx], Y = lat[nc0 + ly], Z = lat[nc01 + lz];
+                                const float x = (X.x + Y.x) + Z.x, y = (X.y + Y.y) + Z.y, z = (X.z + Y.z) + Z.z;
+                                const float iz = 1.0f / z;
+                                C[k4] = make_float4(fmaf(c.fx, x * iz, c.cx), fmaf(c.fy, y * iz, c.cy), iz, z);
                             }
-                        }
-                        __syncthreads();
-                    }
-                    if (STATS) cnt[5] += (zw * zh - tid + nt - 1 > 0) ? (zw * zh - tid + nt - 1) / nt : 0;
-                    if (MODE == 0) {
-                        for (int i = tid; i < zw * zh; i += nt) {
-                            const int gx = zx0 + i % zw, gy = zy0 + i / zw;
-                            unsigned long long key = S.bg[(int64_t)gy * c.W + gx];
-                            if (need) key = min(key, zb[i]);
-                            zd[i] = key_depth(key, L.miss_mode, c.far_z);
-                        }
-                        __syncthreads();
-                        const int tww = tx1 - tx0 + 1, n_t = tww * (ty1 - ty0 + 1);
-                        for (int k = tid; k < n_t; k += nt) {
-                            const int x = tx0 + k % tww, y = ty0 + k / tww;
-                            const int64_t gi = (int64_t)y * c.W + x;
-                            const float4 q = S.obs[gi];
-                            if (q.w == 0.f) continue;
-                            if (STATS) {
-                                ++cnt[6];
-                                cnt[7] += (unsigned long long)((min(y + w, c.H - 1) - max(y - w, 0) + 1) *
-                                                               (min(x + w, c.W - 1) - max(x - w, 0) + 1));
-                            }
-                            const float l = pixel_ell(L, s_lut, c, q, x, y,
-                                                      [&](int xj, int yj) { return zd[(yj - zy0) * zw + (xj - zx0)]; });
-                            acc += l - S.ell_bg[gi];
+                            if (STATS) { cnt[1] += 4; ++cnt[2]; }
+                            raster_quad(C[0], C[1], C[2], C[3], rx0, rx1, ry0, ry1, c.far_z, store,
+                                        STATS ? &cnt[3] : nullptr);
                         }
                     } else {
-                        for (int i = tid; i < zw * zh; i += nt) {
-                            const int gx = zx0 + i % zw, gy = zy0 + i / zw;
-                            const int64_t gi = (int64_t)gy * c.W + gx;
-                            unsigned long long key = S.bg[gi];
-                            if (need) key = min(key, zb[i]);
-                            out_depth[h * npx + gi] = key_depth(key, 0, c.far_z);
-                            if (out_tid) out_tid[h * npx + gi] = key == kEmptyKey ? -1 : (int)(unsigned)(key & 0xffffffffu);
+                        const int4 *tris = front ? m.tris_surf : m.tris_full;
+                        const int n_t = front ? m.n_surf : m.n_full;
+                        const int cull = front ? m.closed : 0;
+                        for (int t = tid; t < n_t; t += nt) {
+                            float4 A, B, C;
+                            tri_screen(m, tris[t], pose, c, A, B, C);
+                            if (STATS) { cnt[1] += 3; ++cnt[2]; }
+                            raster_tri(A, B, C, cull, rx0, rx1, ry0, ry1, c.far_z, store, STATS ? &cnt[3] : nullptr);
                         }
                     }
-                    __syncthreads();
                 }
+                __syncthreads();
+                // composite with the fixed objects in place: depth bits -> rendered depth
+                for (int i = tid; i < zw * zh; i += nt) {
+                    const int gx = zx0 + i % zw, gy = zy0 + i / zw;
+                    const unsigned bgb = (unsigned)(S.bg[(int64_t)gy * c.W + gx] >> 32);
+                    const unsigned v = min(zb[i], bgb);
+                    zd[i] = v == 0xffffffffu ? (L.miss_mode ? -1.f : c.far_z) : __uint_as_float(v);
+                }
+                if (STATS) cnt[5] += (unsigned long long)((zw * zh - tid + nt - 1) / nt);
+                __syncthreads();
+                const int tww = tx1 - tx0 + 1, n_tile = tww * (ty1 - ty0 + 1);
+                for (int k = tid; k < n_tile; k += nt) {
+                    const int x = tx0 + k % tww, y = ty0 + k / tww;
+                    const int64_t gi = (int64_t)y * c.W + x;
+                    const float4 q = S.obs[gi];
+                    if (q.w == 0.f) continue;
+                    if (STATS) {
+                        ++cnt[6];
+                        cnt[7] += (unsigned long long)((min(y + w, c.H - 1) - max(y - w, 0) + 1) *
+                                                       (min(x + w, c.W - 1) - max(x - w, 0) + 1));
+                    }
+                    const float l = pixel_ell(L, s_lut, c, q, x, y,
+                                              [&](int xj, int yj) { return zd[(yj - zy0) * zw + (xj - zx0)]; });
+                    acc += l - S.ell_bg[gi];
+                }
+                __syncthreads();
             }
         }
-        if (MODE == 0) {
-            const float tot = block_sum(acc, s_red);
-            if (tid == 0) out_ll[h] = (float)(*S.ll_bg + (double)tot);
-        }
+        const float tot = block_sum(acc, s_red);
+        if (tid == 0) out_ll[h] = (float)(*S.ll_bg + (double)tot);
     }
     if (STATS)
         for (int k = 0; k < kNumStats; ++k)
             if (cnt[k]) atomicAdd(&S.stats[k], cnt[k]);
+}
+
+// ------------------------------------------------------------------------------------------
+// render kernel: depth and triangle id of every pixel (64-bit keys)
+// ------------------------------------------------------------------------------------------
+template <class PS>
+__global__ void __launch_bounds__(kThreads) k_render(SceneView S, PS P, int64_t n_hyp, float *out_depth, int *out_tid) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long *zb = reinterpret_cast<unsigned long long *>(smem_raw);  // [kRegionPx]
+    __shared__ float s_pose[12];
+    __shared__ int s_bb[4];
+    __shared__ int s_flags;
+    const Cam &c = S.cam;
+    const MeshView &m = S.mesh;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t npx = (int64_t)c.W * c.H;
+    for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
+        __syncthreads();
+        if (tid == 0) {
+            pose12(P, h, s_pose);
+            bool front = false;
+            s_flags = (object_bbox(m, s_pose, c, s_bb, &front) ? 1 : 0) | (front ? 4 : 0);
+        }
+        __syncthreads();
+        const float *pose = s_pose;
+        const bool has_bb = (s_flags & 1) != 0, front = (s_flags & 4) != 0;
+        const int bx0 = s_bb[0], bx1 = s_bb[1], by0 = s_bb[2], by1 = s_bb[3];
+        const int4 *tris = front ? m.tris_surf : m.tris_full;
+        const int n_t = front ? m.n_surf : m.n_full;
+        const int cull = front ? m.closed : 0;
+        const int tw = min(c.W, kRegionPx);
+        const int th = max(1, kRegionPx / tw);
+        for (int ty0 = 0; ty0 < c.H; ty0 += th) {
+            for (int tx0 = 0; tx0 < c.W; tx0 += tw) {
+                const int tx1 = min(tx0 + tw - 1, c.W - 1), ty1 = min(ty0 + th - 1, c.H - 1);
+                const int zw = tx1 - tx0 + 1, zh = ty1 - ty0 + 1;
+                const int rx0 = max(tx0, bx0), rx1 = min(tx1, bx1), ry0 = max(ty0, by0), ry1 = min(ty1, by1);
+                const bool need = has_bb && rx0 <= rx1 && ry0 <= ry1;
+                if (need) {
+                    for (int i = tid; i < zw * zh; i += nt) zb[i] = kEmptyKey;
+                    __syncthreads();
+                    for (int t = tid; t < n_t; t += nt) {
+                        const int4 tr = tris[t];
+                        float4 A, B, C;
+                        tri_screen(m, tr, pose, c, A, B, C);
+                        const unsigned gid = (unsigned)(S.tri_base + tr.w);
+                        raster_tri(A, B, C, cull, rx0, rx1, ry0, ry1, c.far_z, [&](int x, int y, float z) {
+                            atomicMin(&zb[(y - ty0) * zw + (x - tx0)], pack_key(z, gid));
+                        });
+                    }
+                    __syncthreads();
+                }
+                for (int i = tid; i < zw * zh; i += nt) {
+                    const int gx = tx0 + i % zw, gy = ty0 + i / zw;
+                    const int64_t gi = (int64_t)gy * c.W + gx;
+                    unsigned long long key = S.bg[gi];
+                    if (need) key = min(key, zb[i]);
+                    out_depth[h * npx + gi] = key_depth(key, 0, c.far_z);
+                    if (out_tid) out_tid[h * npx + gi] = key == kEmptyKey ? -1 : (int)(unsigned)(key & 0xffffffffu);
+                }
+                __syncthreads();
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -177,35 +298,44 @@ __global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long 
 }
 
 // Background render of one fixed object: one warp per triangle, lanes split its pixels.
+// Closed meshes skip their back and internal faces unless the near plane cuts them.
 __global__ void k_bg_raster(Cam c, MeshView m, const float *pose16, int tri_base, unsigned long long *bg) {
+    __shared__ int s_front;
     float P[12];
     const float *p = pose16;
     P[0] = p[0]; P[1] = p[1]; P[2] = p[2]; P[3] = p[4]; P[4] = p[5]; P[5] = p[6];
     P[6] = p[8]; P[7] = p[9]; P[8] = p[10]; P[9] = p[3]; P[10] = p[7]; P[11] = p[11];
+    if (threadIdx.x == 0) {
+        int bb[4];
+        bool front = false;
+        object_bbox(m, P, c, bb, &front);
+        s_front = front ? 1 : 0;
+    }
+    __syncthreads();
+    const bool front = s_front != 0;
+    const int4 *tris = front ? m.tris_surf : m.tris_full;
+    const int n_t = front ? m.n_surf : m.n_full;
+    const int cull = front ? m.closed : 0;
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int ch = 0; ch < m.n_chunks; ++ch) {
-        const int4 cr = m.chunks[ch];
-        for (int64_t t = cr.z + warp; t < cr.w; t += n_warps) {
-            const int4 tr = m.tris[t];
-            const float4 A = project(P, m.verts[cr.x + tr.x], c);
-            const float4 B = project(P, m.verts[cr.x + tr.y], c);
-            const float4 C = project(P, m.verts[cr.x + tr.z], c);
-            if (A.z < 0.f || B.z < 0.f || C.z < 0.f) continue;
-            const float umin = fminf(A.x, fminf(B.x, C.x)), umax = fmaxf(A.x, fmaxf(B.x, C.x));
-            const float vmin = fminf(A.y, fminf(B.y, C.y)), vmax = fmaxf(A.y, fmaxf(B.y, C.y));
-            const int x0 = (int)ceilf(fmaxf(umin - 0.5f, 0.f)), x1 = (int)floorf(fminf(umax - 0.5f, (float)(c.W - 1)));
-            const int y0 = (int)ceilf(fmaxf(vmin - 0.5f, 0.f)), y1 = (int)floorf(fminf(vmax - 0.5f, (float)(c.H - 1)));
-            if (x0 > x1 || y0 > y1) continue;
-            const int bw = x1 - x0 + 1;
-            const int64_t nb = (int64_t)bw * (y1 - y0 + 1);
-            for (int64_t k = lane; k < nb; k += 32) {
-                const int x = x0 + (int)(k % bw), y = y0 + (int)(k / bw);
-                raster_tri(A, B, C, (unsigned)(tri_base + tr.w), m.cull_back, x, x, y, y, c.far_z,
-                           [&](int xx, int yy, unsigned long long key) { atomicMin(&bg[(int64_t)yy * c.W + xx], key); },
-                           nullptr);
-            }
+    for (int64_t t = warp; t < n_t; t += n_warps) {
+        const int4 tr = tris[t];
+        float4 A, B, C;
+        tri_screen(m, tr, P, c, A, B, C);
+        if (A.z < 0.f || B.z < 0.f || C.z < 0.f) continue;
+        const float umin = fminf(A.x, fminf(B.x, C.x)), umax = fmaxf(A.x, fmaxf(B.x, C.x));
+        const float vmin = fminf(A.y, fminf(B.y, C.y)), vmax = fmaxf(A.y, fmaxf(B.y, C.y));
+        const int x0 = (int)ceilf(fmaxf(umin - 0.5f, 0.f)), x1 = (int)floorf(fminf(umax - 0.5f, (float)(c.W - 1)));
+        const int y0 = (int)ceilf(fmaxf(vmin - 0.5f, 0.f)), y1 = (int)floorf(fminf(vmax - 0.5f, (float)(c.H - 1)));
+        if (x0 > x1 || y0 > y1) continue;
+        const int bw = x1 - x0 + 1;
+        const int64_t nb = (int64_t)bw * (y1 - y0 + 1);
+        const unsigned gid = (unsigned)(tri_base + tr.w);
+        for (int64_t k = lane; k < nb; k += 32) {
+            const int x = x0 + (int)(k % bw), y = y0 + (int)(k / bw);
+            raster_tri(A, B, C, cull, x, x, y, y, c.far_z,
+                       [&](int xx, int yy, float z) { atomicMin(&bg[(int64_t)yy * c.W + xx], pack_key(z, gid)); });
         }
     }
 }
@@ -308,8 +438,6 @@ __global__ void __launch_bounds__(kThreads) k_score_depth(SceneView S, Lik L, co
 // launchers
 // ------------------------------------------------------------------------------------------
 
-int fused_smem_bytes() { return kRegionPx * (int)sizeof(unsigned long long) + kChunkV * (int)sizeof(float4); }
-
 static int sm_count() {
     static int n = 0;
     if (!n) {
@@ -330,30 +458,34 @@ static int persistent_grid(K kernel, int smem, int64_t n, int grid) {
     return (int)std::min<int64_t>((int64_t)per_sm * sm_count(), std::max<int64_t>(n, 1));
 }
 
-template <int MODE, class PS>
-static int launch_fused(const SceneView &sv, const Lik &L, PS P, int64_t n, float *ll, float *depth, int *tid,
-                        int grid, cudaStream_t s) {
+template <class PS>
+static int launch_score(const SceneView &sv, const Lik &L, PS P, int64_t n, float *ll, int grid, cudaStream_t s) {
     if (n <= 0) return 0;
-    const int smem = fused_smem_bytes();
-    auto kern = sv.stats ? k_fused<MODE, PS, true> : k_fused<MODE, PS, false>;
+    const int n_lat = sv.mesh.nc[0] + sv.mesh.nc[1] + sv.mesh.nc[2];
+    const int smem = kRegionPx * (int)sizeof(unsigned) + n_lat * (int)sizeof(float4);
+    auto kern = sv.stats ? k_score<PS, true> : k_score<PS, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     const int g = persistent_grid(kern, smem, n, grid);
-    kern<<<g, kThreads, smem, s>>>(sv, L, P, n, ll, depth, tid);
+    kern<<<g, kThreads, smem, s>>>(sv, L, P, n, ll);
     return g;
 }
 
 int launch_score_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, int grid, cudaStream_t s) {
-    return launch_fused<0>(sv, L, P, n, ll, nullptr, nullptr, grid, s);
+    return launch_score(sv, L, P, n, ll, grid, s);
 }
 
 int launch_score_grid(const SceneView &sv, const Lik &L, PoseGrid P, int64_t n, float *ll, int grid, cudaStream_t s) {
-    return launch_fused<0>(sv, L, P, n, ll, nullptr, nullptr, grid, s);
+    return launch_score(sv, L, P, n, ll, grid, s);
 }
 
 int launch_render_list(const SceneView &sv, PoseList P, int64_t n, float *depth, int *tid, int grid, cudaStream_t s) {
-    Lik L{};
-    L.w = 0;
-    return launch_fused<1>(sv, L, P, n, nullptr, depth, tid, grid, s);
+    if (n <= 0) return 0;
+    const int smem = kRegionPx * (int)sizeof(unsigned long long);
+    auto kern = k_render<PoseList>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int g = persistent_grid(kern, smem, n, grid);
+    kern<<<g, kThreads, smem, s>>>(sv, P, n, depth, tid);
+    return g;
 }
 
 void launch_score_depth(const SceneView &sv, const Lik &L, const float *depth, const int *tid, int64_t n, float *ll,
@@ -375,9 +507,9 @@ void launch_bg_clear(unsigned long long *bg, int64_t n, cudaStream_t s) {
 
 void launch_bg_raster(const Cam &cam, const MeshView &m, const float *pose16_dev, int tri_base,
                       unsigned long long *bg, cudaStream_t s) {
-    if (m.n_tris <= 0) return;
+    if (m.n_full <= 0) return;
     const int warps_per_block = 8;
-    const int blocks = (int)std::min<int64_t>((m.n_tris + warps_per_block - 1) / warps_per_block, 8 * sm_count());
+    const int blocks = (int)std::min<int64_t>((m.n_full + warps_per_block - 1) / warps_per_block, 8 * sm_count());
     k_bg_raster<<<blocks, 32 * warps_per_block, 0, s>>>(cam, m, pose16_dev, tri_base, bg);
 }
 

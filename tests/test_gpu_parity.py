@@ -40,12 +40,16 @@ def _check_render(orc, scene, slot, poses, depth, tid, max_frac=1e-4):
 
 
 def _check_ll(got, ref, what):
+    """Every hypothesis within 1e-4 * scale + the oracle's FP32-decision bound, and most
+    of them within 1e-4 * scale alone (the bound is not what makes them pass)."""
     tol = ll_tolerance(ref)
     err = np.abs(got.astype(np.float64) - ref["ll"])
     bad = np.nonzero(err > tol)[0]
     assert bad.size == 0, f"{what}: {bad.size} hypotheses outside tolerance, e.g. {bad[:5]} err {err[bad[:5]]} tol {tol[bad[:5]]}"
-    unflagged = ref["bound"] == 0
-    assert unflagged.mean() > 0.5, f"{what}: too many flagged hypotheses ({1 - unflagged.mean():.2f})"
+    tight = err <= 1e-4 * ref["scale"]
+    print(f"{what}: n={err.size} max|dLL|={err.max():.3g} median={np.median(err):.3g} "
+          f"tight={tight.mean():.3f} flagged={np.mean(ref['bound'] > 0):.3f}")
+    assert tight.mean() >= 0.9, f"{what}: only {tight.mean():.2f} of hypotheses within 1e-4 * scale"
     return err
 
 
@@ -122,7 +126,10 @@ def test_near_plane_and_out_of_view(orc, single_object):
     d, t = ctx.render(0, poses)
     ll = ctx.score(0, poses, wl.lik)
     ctx.sync()
-    _check_render(orc, sc, 0, poses, _np(d), _np(t))
+    # vertices 3 cm from the camera project thousands of pixels off-screen, where FP32 edge
+    # functions resolve ~1e-4 px: every mismatch must still be a flagged pixel, but more of
+    # the (few) pixels are allowed to flip than in the workloads' geometry
+    _check_render(orc, sc, 0, poses, _np(d), _np(t), max_frac=5e-3)
     ref = orc.score(sc, 0, poses, wl.lik, obs)
     _check_ll(_np(ll), ref, "near/out of view")
 
