@@ -157,6 +157,15 @@ class Parse:
         self.logq = torch.empty((N_OBJECTS, M_PARTICLES), dtype=torch.float32, device=dev)
         self.priors = pri
 
+    def autotune(self, obs_dev):
+        """Pick the score kernel's launch shape on the first object's first stage."""
+        from paper_2312_08715_gb300 import b3d
+        ctx, wl = self.ctx, self.wl
+        b3d.b3d_set_scene(ctx.h, b3d.intrinsics(wl.scene.camera), self.ids[:FIRST_SLOT + 1],
+                          self.host_poses[:FIRST_SLOT + 1], obs_dev, ctx.stream)
+        return b3d.b3d_autotune(ctx.h, FIRST_SLOT, self.priors[FIRST_SLOT], wl.grid_frame,
+                                b3d.stage_params(wl.stages[0]), b3d.lik_params(**wl.lik), ctx.stream)
+
     def run(self, obs_dev, seed=0):
         from paper_2312_08715_gb300 import b3d
         ctx, wl = self.ctx, self.wl
@@ -204,6 +213,8 @@ def run_gpu(args):
     obs_dev = torch.as_tensor(obs_np, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+
+    tuning = parse.autotune(obs_dev)  # untimed: launch shape of the score kernel
 
     # calibration (untimed): work counted by the kernels for one step
     b3d.b3d_set_instrumentation(ctx.h, b3d.B3D_INSTR_WORK)
@@ -274,7 +285,8 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_dict(wl, {"parallelism": f"replicas x{world} (independent scenes)"}),
+        "config": config_dict(wl, {"parallelism": f"replicas x{world} (independent scenes)",
+                                   "score_kernel_tuning": tuning}),
         "px_hyps_per_s": value * px,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
                      "frac": achieved / peak_alu, "traffic": traffic,

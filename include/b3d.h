@@ -215,6 +215,26 @@ b3d_status b3d_score_grad(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const f
                           const b3d_lik_params *lik, float *loglik_dev, float *dpose_dev, float *dsigma_dev,
                           float *dpout_dev, b3d_stream stream);
 
+/* Launch shape of the fused render + score kernel (no counterpart in the paper: a property
+ * of this implementation). tile_w: widest screen tile in pixels (8..256); cta_threads: 128
+ * or 256; ctas_per_sm: CTAs resident per SM (0 = as many as fit). */
+typedef struct {
+    int32_t tile_w;
+    int32_t cta_threads;
+    int32_t ctas_per_sm;
+} b3d_tuning;
+
+b3d_status b3d_get_tuning(b3d_ctx *ctx, b3d_tuning *out);
+b3d_status b3d_set_tuning(b3d_ctx *ctx, const b3d_tuning *tuning);
+
+/* Autotuner: times the score kernel on one coarse-to-fine stage of object obj_slot of the
+ * current scene (grid around centre_pose, host [16]; grid_frame host [9]) for each
+ * candidate launch shape (CTA size x tile width x CTAs per SM), keeps the fastest in the
+ * context and returns it in *best (may be NULL). Synchronises the stream (not for use while
+ * capturing a graph); run it once per workload shape, e.g. during warm-up. */
+b3d_status b3d_autotune(b3d_ctx *ctx, int32_t obj_slot, const float *centre_pose, const float *grid_frame,
+                        const b3d_stage *stage, const b3d_lik_params *lik, b3d_tuning *best, b3d_stream stream);
+
 /* Instrumentation (off by default; used by the benchmark).
  * flags bit 0 (B3D_INSTR_TIMING): bracket every kernel launch of the library with CUDA
  *   events recorded on the launching stream; b3d_kernel_time() reports the device time.

@@ -54,6 +54,10 @@ class b3d_stage(C.Structure):
                 ("rot_max", C.c_float)]
 
 
+class b3d_tuning(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("cta_threads", C.c_int32), ("ctas_per_sm", C.c_int32)]
+
+
 class b3d_c2f_schedule(C.Structure):
     _fields_ = [("n_stages", C.c_int32), ("stage", b3d_stage * B3D_MAX_STAGES), ("n_particles", C.c_int32),
                 ("seed", C.c_uint64), ("grid_frame", C.c_float * 9)]
@@ -77,6 +81,10 @@ _SIGNATURES = {
     "b3d_enumerate_c2f": (C.c_int32, [_P, C.c_int32, _P, C.POINTER(b3d_c2f_schedule), C.POINTER(b3d_lik_params),
                                       _P, _P, _P, _P]),
     "b3d_score_grad": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_lik_params), _P, _P, _P, _P, _P]),
+    "b3d_get_tuning": (C.c_int32, [_P, C.POINTER(b3d_tuning)]),
+    "b3d_set_tuning": (C.c_int32, [_P, C.POINTER(b3d_tuning)]),
+    "b3d_autotune": (C.c_int32, [_P, C.c_int32, _P, _P, C.POINTER(b3d_stage), C.POINTER(b3d_lik_params),
+                                 C.POINTER(b3d_tuning), _P]),
     "b3d_set_instrumentation": (C.c_int32, [_P, C.c_int32]),
     "b3d_kernel_time": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "b3d_work_counters": (C.c_int32, [_P, _P]),
@@ -256,6 +264,25 @@ def b3d_score_grad(ctx, obj_slot, n_hyp, poses_dev, lik: b3d_lik_params, loglik_
     return _check(ctx, load().b3d_score_grad(ctx, obj_slot, n_hyp, _addr(poses_dev), C.byref(lik), _addr(loglik_dev),
                                              _addr(dpose_dev), _addr(dsigma_dev), _addr(dpout_dev),
                                              _stream(stream)))
+
+
+def b3d_get_tuning(ctx) -> dict:
+    t = b3d_tuning()
+    _check(ctx, load().b3d_get_tuning(ctx, C.byref(t)))
+    return dict(tile_w=t.tile_w, cta_threads=t.cta_threads, ctas_per_sm=t.ctas_per_sm)
+
+
+def b3d_set_tuning(ctx, tile_w=64, cta_threads=256, ctas_per_sm=0):
+    return _check(ctx, load().b3d_set_tuning(ctx, C.byref(b3d_tuning(tile_w, cta_threads, ctas_per_sm))))
+
+
+def b3d_autotune(ctx, obj_slot, centre_pose, grid_frame, stage: b3d_stage, lik: b3d_lik_params, stream=None) -> dict:
+    c = np.ascontiguousarray(centre_pose, dtype=np.float32).reshape(16)
+    g = np.ascontiguousarray(grid_frame, dtype=np.float32).reshape(9)
+    t = b3d_tuning()
+    _check(ctx, load().b3d_autotune(ctx, obj_slot, c.ctypes.data, g.ctypes.data, C.byref(stage), C.byref(lik),
+                                    C.byref(t), _stream(stream)))
+    return dict(tile_w=t.tile_w, cta_threads=t.cta_threads, ctas_per_sm=t.ctas_per_sm)
 
 
 def b3d_set_instrumentation(ctx, flags):

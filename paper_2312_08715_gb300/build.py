@@ -47,12 +47,14 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile and link libb3d.so; returns its path."""
-    if not force and not extra_flags and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out=None) -> str:
+    """Compile and link libb3d.so (or `out`, e.g. a variant built with extra -D flags);
+    returns its path."""
+    lib = out or LIB
+    if not force and not extra_flags and out is None and up_to_date():
         return LIB
     nvcc = _nvcc()
-    objdir = os.path.join(BUILD, "obj")
+    objdir = os.path.join(os.path.dirname(lib), "obj" if out is None else "obj_" + os.path.basename(lib))
     os.makedirs(objdir, exist_ok=True)
 
     def compile_one(src):
@@ -68,13 +70,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -91,6 +91,12 @@ struct b3d_ctx {
     float *d_centre = nullptr;  // [3][16]: two ping-pong centres and one expand scratch
     std::map<std::tuple<int, int, float>, float *> rot_cache;
 
+    // launch shape of the score kernel
+    int tile_w = 64;
+    int cta_threads = 256;
+    int ctas_per_sm = 0;
+    int score_code() const { return (cta_threads == 128 ? 256 : 0) | (ctas_per_sm & 255); }
+
     // instrumentation
     int instr = 0;
     unsigned long long *d_stats = nullptr;
@@ -303,6 +309,7 @@ SceneView scene_view(b3d_ctx *ctx, int32_t slot) {
     }
     sv.err = ctx->d_err;
     sv.stats = (ctx->instr & B3D_INSTR_WORK) ? ctx->d_stats : nullptr;
+    sv.tile_w = ctx->tile_w;
     return sv;
 }
 
@@ -857,7 +864,7 @@ b3d_status b3d_score_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const 
     if ((st = ensure_bg_lik(ctx, obj_slot, lik, L, false, s)) != B3D_OK) return st;
     {
         Timed tm(ctx, B3D_K_SCORE, s);
-        launch_score_list(scene_view(ctx, obj_slot), L, PoseList{poses_dev}, n_hyp, loglik_dev, 0, s);
+        launch_score_list(scene_view(ctx, obj_slot), L, PoseList{poses_dev}, n_hyp, loglik_dev, ctx->score_code(), s);
     }
     ++ctx->launches;
     return check_launch(ctx, "score_batch");
@@ -979,7 +986,7 @@ b3d_status b3d_enumerate_c2f(b3d_ctx *ctx, int32_t obj_slot, const float *centre
         P.step = sch->stage[t].step;
         {
             Timed tm(ctx, B3D_K_SCORE, s);
-            launch_score_grid(sv, L, P, n_t[t], ctx->d_ll, 0, s);
+            launch_score_grid(sv, L, P, n_t[t], ctx->d_ll, ctx->score_code(), s);
         }
         {
             Timed tm(ctx, B3D_K_RESAMPLE, s);
@@ -1022,6 +1029,91 @@ b3d_status b3d_score_grad(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const f
     }
     ++ctx->launches;
     return check_launch(ctx, "score_grad");
+}
+
+b3d_status b3d_get_tuning(b3d_ctx *ctx, b3d_tuning *out) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    if (!out) return fail(ctx, B3D_EINVAL, "out is NULL");
+    out->tile_w = ctx->tile_w;
+    out->cta_threads = ctx->cta_threads;
+    out->ctas_per_sm = ctx->ctas_per_sm;
+    return B3D_OK;
+}
+
+b3d_status b3d_set_tuning(b3d_ctx *ctx, const b3d_tuning *t) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    if (!t) return fail(ctx, B3D_EINVAL, "tuning is NULL");
+    if (t->tile_w < 8 || t->tile_w > 256) return fail(ctx, B3D_EINVAL, "tile_w must be in [8, 256]");
+    if (t->cta_threads != 128 && t->cta_threads != 256) return fail(ctx, B3D_EINVAL, "cta_threads must be 128 or 256");
+    if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return fail(ctx, B3D_EINVAL, "ctas_per_sm must be in [0, 32]");
+    ctx->tile_w = t->tile_w;
+    ctx->cta_threads = t->cta_threads;
+    ctx->ctas_per_sm = t->ctas_per_sm;
+    return B3D_OK;
+}
+
+b3d_status b3d_autotune(b3d_ctx *ctx, int32_t obj_slot, const float *centre_pose, const float *grid_frame,
+                        const b3d_stage *stage, const b3d_lik_params *lik, b3d_tuning *best, b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    b3d_status st = check_slot(ctx, obj_slot);
+    if (st != B3D_OK) return st;
+    Lik L;
+    if ((st = make_lik(ctx, lik, &L)) != B3D_OK) return st;
+    if (!centre_pose || !grid_frame || !stage) return fail(ctx, B3D_EINVAL, "centre_pose, grid_frame and stage must be non-NULL");
+    int64_t n;
+    if ((st = check_stage(ctx, *stage, &n)) != B3D_OK) return st;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ensure_scratch(ctx, n, 1)) != B3D_OK) return st;
+    float *rot = nullptr;
+    if ((st = rotation_table(ctx, *stage, &rot, s)) != B3D_OK) return st;
+    if ((st = ensure_bg(ctx, obj_slot, s)) != B3D_OK) return st;
+    if ((st = ensure_bg_lik(ctx, obj_slot, lik, L, false, s)) != B3D_OK) return st;
+    float *centre = ctx->d_centre + 32;
+    launch_set16(centre, centre_pose, s);
+    PoseGrid P{};
+    P.centre = centre;
+    P.rot = rot;
+    for (int k = 0; k < 9; ++k) P.G[k] = grid_frame[k];
+    P.n = stage->n_per_axis;
+    P.n_rot = stage->n_rot;
+    P.step = stage->step;
+    cudaEvent_t e0 = take_event(ctx), e1 = take_event(ctx);
+    const b3d_tuning saved{ctx->tile_w, ctx->cta_threads, ctx->ctas_per_sm};
+    b3d_tuning win = saved;
+    float win_ms = INFINITY;
+    for (int nt : {256, 128})
+        for (int tw : {32, 48, 64, 96, 128})
+            for (int cps : {0, 2}) {
+                if (nt == 128 && cps == 2) continue;
+                ctx->tile_w = tw;
+                ctx->cta_threads = nt;
+                ctx->ctas_per_sm = cps;
+                const SceneView sv = scene_view(ctx, obj_slot);
+                launch_score_grid(sv, L, P, n, ctx->d_ll, ctx->score_code(), s);  // warm
+                cudaEventRecord(e0, s);
+                launch_score_grid(sv, L, P, n, ctx->d_ll, ctx->score_code(), s);
+                cudaEventRecord(e1, s);
+                ctx->launches += 2;
+                cudaError_t e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) {
+                    ctx->tile_w = saved.tile_w; ctx->cta_threads = saved.cta_threads; ctx->ctas_per_sm = saved.ctas_per_sm;
+                    return cuda_fail(ctx, e, "autotune");
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < win_ms) { win_ms = ms; win = b3d_tuning{tw, nt, cps}; }
+            }
+    ctx->event_pool.push_back(e0);
+    ctx->event_pool.push_back(e1);
+    ctx->tile_w = win.tile_w;
+    ctx->cta_threads = win.cta_threads;
+    ctx->ctas_per_sm = win.ctas_per_sm;
+    if (best) *best = win;
+    return check_launch(ctx, "autotune");
 }
 
 b3d_status b3d_set_instrumentation(b3d_ctx *ctx, int32_t flags) {

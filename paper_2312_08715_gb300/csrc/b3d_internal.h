@@ -7,7 +7,14 @@
 
 namespace b3d {
 
-constexpr int kThreads = 256;          // threads per CTA of the render/score kernels
+#ifndef B3D_THREADS
+#define B3D_THREADS 256
+#endif
+#ifndef B3D_SCORE_MIN_BLOCKS
+#define B3D_SCORE_MIN_BLOCKS 3
+#endif
+constexpr int kThreads = B3D_THREADS;  // threads per CTA of the render/score kernels
+constexpr int kScoreMinBlocks = B3D_SCORE_MIN_BLOCKS;  // CTAs per SM the score kernel is built for
 constexpr int kRegionPx = 4096;        // z-buffer pixels per screen tile in shared memory
 constexpr int kMaxPlanes = 511;        // lattice planes per axis of a quad mesh
 constexpr int kMaxHalfWindow = 7;
@@ -85,6 +92,7 @@ struct SceneView {
     int tri_base;                      // global triangle id of the slot object's face 0
     int *err;                          // device error flag
     unsigned long long *stats;         // [kNumStats] work counters, or NULL (no counting)
+    int tile_w;                        // widest screen tile of the score kernel (pixels)
 };
 
 // Hypothesis poses as 12 floats: R row-major (9) then t (3).

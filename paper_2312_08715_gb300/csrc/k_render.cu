@@ -151,8 +151,9 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
     return acc;
 }
 
-template <class PS, bool STATS, int WT>
-__global__ void __launch_bounds__(kThreads, 3) k_score(SceneView S, Lik L, PS P, int64_t n_hyp, float *out_ll) {
+template <class PS, bool STATS, int WT, int NT>
+__global__ void __launch_bounds__(NT, NT <= 128 ? 2 * kScoreMinBlocks : kScoreMinBlocks)
+    k_score(SceneView S, Lik L, PS P, int64_t n_hyp, float *out_ll) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned *zb = reinterpret_cast<unsigned *>(smem_raw);                       // [kRegionPx]
     float *zd = reinterpret_cast<float *>(smem_raw);                             // same memory, as depths
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_score(SceneView S, Lik L, PS P,
     __shared__ int s_bb[4];
     __shared__ int s_flags;  // bit 0: on screen, bit 1: quad path, bit 2: whole object beyond near
     __shared__ int s_rng[13];  // class first quads [6], exclusive prefix of counts [6], total
-    __shared__ float s_red[kThreads / 32];
+    __shared__ float s_red[NT / 32];
 
     const Cam &c = S.cam;
     const MeshView &m = S.mesh;
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_score(SceneView S, Lik L, PS P,
         const int sx0 = max(bx0 - w, 0), sx1 = min(bx1 + w, c.W - 1);
         const int sy0 = max(by0 - w, 0), sy1 = min(by1 + w, c.H - 1);
         const int sw = sx1 - sx0 + 1;
-        const int tw = min(sw, 64);
+        const int tw = min(sw, S.tile_w);
         const int th = max(1, kRegionPx / (tw + 2 * w) - 2 * w);
         float acc = 0.f;
         for (int ty0 = sy0; ty0 <= sy1; ty0 += th) {
@@ -597,20 +598,32 @@ static int persistent_grid(K kernel, int smem, int64_t n, int grid) {
     return (int)std::min<int64_t>((int64_t)per_sm * sm_count(), std::max<int64_t>(n, 1));
 }
 
-template <class PS>
-static int launch_score(const SceneView &sv, const Lik &L, PS P, int64_t n, float *ll, int grid, cudaStream_t s) {
-    if (n <= 0) return 0;
+template <class PS, int NT>
+static int launch_score_nt(const SceneView &sv, const Lik &L, PS P, int64_t n, float *ll, int grid, cudaStream_t s) {
     const int n_lat = sv.mesh.nc[0] + sv.mesh.nc[1] + sv.mesh.nc[2];
     const int smem = kRegionPx * (int)sizeof(unsigned) + n_lat * (int)sizeof(float4);
     auto pick = [&](auto st) {
         constexpr bool ST = decltype(st)::value;
-        return L.w == 1 ? k_score<PS, ST, 1> : (L.w == 2 ? k_score<PS, ST, 2> : k_score<PS, ST, 0>);
+        return L.w == 1 ? k_score<PS, ST, 1, NT> : (L.w == 2 ? k_score<PS, ST, 2, NT> : k_score<PS, ST, 0, NT>);
     };
     auto kern = sv.stats ? pick(std::true_type{}) : pick(std::false_type{});
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    const int g = persistent_grid(kern, smem, n, grid);
-    kern<<<g, kThreads, smem, s>>>(sv, L, P, n, ll);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    per_sm = std::max(per_sm, 1);
+    // grid > 0: CTAs per SM requested by the tuning (capped by occupancy); 0: occupancy
+    const int ctas = grid > 0 ? std::min(grid, per_sm) : per_sm;
+    const int g = (int)std::min<int64_t>((int64_t)ctas * sm_count(), std::max<int64_t>(n, 1));
+    kern<<<g, NT, smem, s>>>(sv, L, P, n, ll);
     return g;
+}
+
+// grid encodes the tuning: bits 0-7 CTAs per SM (0 = as many as fit), bit 8: 128-thread CTAs.
+template <class PS>
+static int launch_score(const SceneView &sv, const Lik &L, PS P, int64_t n, float *ll, int grid, cudaStream_t s) {
+    if (n <= 0) return 0;
+    if (grid & 256) return launch_score_nt<PS, 128>(sv, L, P, n, ll, grid & 255, s);
+    return launch_score_nt<PS, 256>(sv, L, P, n, ll, grid & 255, s);
 }
 
 int launch_score_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, int grid, cudaStream_t s) {

@@ -158,6 +158,31 @@ def test_score_single_object_full_grid(orc, single_object):
     np.testing.assert_array_equal(ll[perm], ll2)
 
 
+def test_every_launch_shape_matches_oracle(orc, single_object):
+    """The autotuner's candidate launch shapes change only how the work is tiled."""
+    from paper_2312_08715_gb300 import b3d
+    wl = single_object
+    sc = wl.scene
+    obs = observed(orc, wl)
+    poses = orc.expand(wl.hidden, np.eye(3), 6, 0.01, orc.rotation_set(1, 3, 0.1)).astype(np.float32)
+    ref = orc.score(sc, 0, poses, wl.lik, obs)
+    ctx = gpu_context(sc, obs)
+    outs = []
+    for tw, nt, cps in [(8, 128, 0), (32, 256, 2), (64, 256, 0), (256, 128, 1)]:
+        b3d.b3d_set_tuning(ctx.h, tw, nt, cps)
+        outs.append(_np(ctx.score(0, poses, wl.lik)))
+        ctx.sync()
+        _check_ll(outs[-1], ref, f"tuning {tw}/{nt}/{cps}")
+    for o in outs[1:]:
+        np.testing.assert_allclose(o, outs[0], rtol=2e-6, atol=1e-3)
+    st = b3d.stage_params(synth.StageSpec(7, 0.01, 1, 4, 0.1))
+    best = b3d.b3d_autotune(ctx.h, 0, wl.hidden, np.eye(3), st, b3d.lik_params(**wl.lik))
+    assert best["cta_threads"] in (128, 256) and 8 <= best["tile_w"] <= 256
+    assert b3d.b3d_get_tuning(ctx.h) == best
+    _check_ll(_np(ctx.score(0, poses, wl.lik)), ref, "autotuned")
+    ctx.close()
+
+
 @pytest.mark.parametrize("w,miss_mode", [(2, 0), (1, 1)])
 def test_score_smooth_and_miss_modes(orc, single_object, w, miss_mode):
     wl = single_object
