@@ -189,6 +189,26 @@ b3d_status b3d_expand_hypotheses(b3d_ctx *ctx, const float *centre_pose, const f
 b3d_status b3d_lse_resample(b3d_ctx *ctx, int64_t n, const float *loglik_dev, int32_t m, uint64_t seed,
                             int32_t stage, float *logz_dev, int32_t *idx_dev, float *logq_dev, b3d_stream stream);
 
+/* Log-sum-exp and resampling for callers that cannot allocate device memory. The paper has
+ * no counterpart: this is a library service. It computes exactly what b3d_lse_resample
+ * computes (same kernel, same definition of idx/logq/logz), without a context and without
+ * allocating: the kernel's scratch (1024 partial sums and a completion counter, 8 KB) is a
+ * fixed array inside the library that every GPU loading the library holds until the
+ * process exits. Callers that cannot allocate include code running while a CUDA graph is
+ * captured (allocation is not capturable), code under another framework's allocator lock
+ * or hard memory cap, and embeddings that forbid the library from allocating.
+ *   - Works on the calling thread's current device. The first call on a device looks up
+ *     the array's device address (once per device); make that first call before any
+ *     stream capture begins.
+ *   - Every call shares the one array and clears its counter on `stream` first; calls
+ *     that overlap on the GPU (other streams, other threads) race: serialise them.
+ *   - n must be in [1, B3D_NOALLOC_MAX_SCORES] (else B3D_EINVAL), m >= 0, outputs as in
+ *     b3d_lse_resample. If every score is -inf, idx is -1 and logz is -inf. Returns
+ *     B3D_EINVAL or B3D_ECUDA on error; there is no context, so no b3d_last_error text. */
+#define B3D_NOALLOC_MAX_SCORES 2147483647LL
+b3d_status b3d_lse_resample_noalloc(int64_t n, const float *loglik_dev, int32_t m, uint64_t seed, int32_t stage,
+                                    float *logz_dev, int32_t *idx_dev, float *logq_dev, b3d_stream stream);
+
 /* Coarse-to-fine enumeration of object obj_slot's pose (Sec. III-B). Stage t expands
  * its grid around centre_t (centre_0 = centre_pose, host [16]), scores every hypothesis
  * with lik (scoring strategy: the cell centre, weight 1), draws n_particles cells by

@@ -30,6 +30,7 @@ B3D_EDEVICE = -7
 B3D_MAX_STAGES = 8
 B3D_MAX_HALF_WINDOW = 7
 B3D_MESH_CLOSED = 1
+B3D_NOALLOC_MAX_SCORES = 2147483647
 B3D_INSTR_TIMING = 1
 B3D_INSTR_WORK = 2
 B3D_K_SCORE, B3D_K_RENDER, B3D_K_SCORE_DEPTH, B3D_K_RESAMPLE, B3D_K_SELECT, B3D_K_GRAD, B3D_K_SCENE = range(7)
@@ -81,6 +82,7 @@ _SIGNATURES = {
     "b3d_enumerate_c2f": (C.c_int32, [_P, C.c_int32, _P, C.POINTER(b3d_c2f_schedule), C.POINTER(b3d_lik_params),
                                       _P, _P, _P, _P]),
     "b3d_score_grad": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_lik_params), _P, _P, _P, _P, _P]),
+    "b3d_lse_resample_noalloc": (C.c_int32, [C.c_int64, _P, C.c_int32, C.c_uint64, C.c_int32, _P, _P, _P, _P]),
     "b3d_get_tuning": (C.c_int32, [_P, C.POINTER(b3d_tuning)]),
     "b3d_set_tuning": (C.c_int32, [_P, C.POINTER(b3d_tuning)]),
     "b3d_autotune": (C.c_int32, [_P, C.c_int32, _P, _P, C.POINTER(b3d_stage), C.POINTER(b3d_lik_params),
@@ -249,6 +251,16 @@ def b3d_expand_hypotheses(ctx, centre_pose, grid_frame, stage: b3d_stage, poses_
 def b3d_lse_resample(ctx, n, loglik_dev, m, seed, stage, logz_dev, idx_dev, logq_dev, stream=None):
     return _check(ctx, load().b3d_lse_resample(ctx, n, _addr(loglik_dev), m, seed, stage, _addr(logz_dev),
                                                _addr(idx_dev), _addr(logq_dev), _stream(stream)))
+
+
+def b3d_lse_resample_noalloc(n, loglik_dev, m, seed, stage, logz_dev, idx_dev, logq_dev, stream=None):
+    """Context-free, allocation-free log-sum-exp + resampling (scratch is a fixed array in
+    the library; calls that overlap on the GPU race). Raises B3DError on a non-zero status."""
+    st = load().b3d_lse_resample_noalloc(n, _addr(loglik_dev), m, seed, stage, _addr(logz_dev), _addr(idx_dev),
+                                         _addr(logq_dev), _stream(stream))
+    if st != B3D_OK:
+        raise B3DError(st, "b3d_lse_resample_noalloc failed (no context: status only)")
+    return st
 
 
 def b3d_enumerate_c2f(ctx, obj_slot, centre_pose, sch: b3d_c2f_schedule, lik: b3d_lik_params, particles_dev,
