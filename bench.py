@@ -61,6 +61,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--trial", type=int, default=0)
+    ap.add_argument("--path", default="fused", choices=["fused", "materialised"],
+                    help="materialised: render every first-stage hypothesis of the first object to HBM, "
+                         "then score the stored images (the render-then-score form)")
     return ap.parse_args()
 
 
@@ -440,8 +443,78 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_materialised(args):
+    """The render-then-score form on the first stage of the first object: 145,800 depth
+    images (160x120 float32, 11.2 GB) written to HBM by b3d_render_batch and read back by
+    b3d_score_depth_batch. One step = both launches."""
+    import torch
+    from paper_2312_08715_gb300 import b3d
+    dev = torch.device("cuda", 0)
+    wl = workload(args.trial)
+    setup_ctx = b3d.Context(0)
+    obs_np = gpu_observation(setup_ctx, wl, torch)
+    setup_ctx.close()
+    ctx = b3d.Context(0)
+    parse = Parse(ctx, wl, torch)
+    obs_dev = torch.as_tensor(obs_np, device=dev)
+    b3d.b3d_set_scene(ctx.h, b3d.intrinsics(wl.scene.camera), parse.ids[:FIRST_SLOT + 1],
+                      parse.host_poses[:FIRST_SLOT + 1], obs_dev, ctx.stream)
+    poses = ctx.expand(parse.priors[FIRST_SLOT], wl.grid_frame, wl.stages[0])
+    n = poses.shape[0]
+    H, W = wl.scene.camera.height, wl.scene.camera.width
+    depth = torch.empty((n, H, W), dtype=torch.float32, device=dev)
+    ll = torch.empty(n, dtype=torch.float32, device=dev)
+    lik = b3d.lik_params(**wl.lik)
+    stream = ctx.stream
+
+    def step():
+        b3d.b3d_render_batch(ctx.h, FIRST_SLOT, n, poses, depth, None, stream)
+        b3d.b3d_score_depth_batch(ctx.h, n, depth, None, lik, ll, stream)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    b3d.b3d_set_instrumentation(ctx.h, b3d.B3D_INSTR_TIMING)
+    for k in range(b3d.B3D_K_COUNT):
+        b3d.b3d_kernel_time(ctx.h, k)
+    torch.cuda.synchronize(dev)
+    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler() as clk:
+        a.record(stream)
+        for _ in range(args.steps):
+            step()
+        b_.record(stream)
+        torch.cuda.synchronize(dev)
+    total_ms = a.elapsed_time(b_)
+    r_ms, r_n = b3d.b3d_kernel_time(ctx.h, b3d.B3D_K_RENDER)
+    s_ms, s_n = b3d.b3d_kernel_time(ctx.h, b3d.B3D_K_SCORE_DEPTH)
+    ctx.sync()
+    px = H * W
+    peak = _measured_peaks().get("hbm_gbs", 6800.0)
+    wr = 4.0 * px * n / (r_ms / r_n / 1e3) / 1e9
+    rd = (4.0 * px + 4.0) * n / (s_ms / s_n / 1e3) / 1e9
+    print(json.dumps({
+        "metric": METRIC, "value": n * args.steps / (total_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "path": "materialised",
+        "config": config_dict(wl, {"workload": "render-then-score form: first stage of the first object, 145,800 "
+                                               "hypotheses, depth images in HBM",
+                                   "hyps_per_step": n, "l2": "images (11.2 GB) exceed L2"}),
+        "render": {"ms": r_ms / r_n, "write_gbs": wr, "frac_of_hbm": wr / peak},
+        "score_depth": {"ms": s_ms / s_n, "read_gbs": rd, "frac_of_hbm": rd / peak},
+        "roofline": {"bound": "hbm", "achieved": 8.0 * px * n / (total_ms / args.steps / 1e3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": 8.0 * px * n / (total_ms / args.steps / 1e3) / 1e9 / peak,
+                     "traffic": None, "note": "8 B per pixel-hypothesis (4 B written + 4 B read) over the step"},
+        "clocks": clk.summary(),
+    }), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse_args()
+    if args.path == "materialised" and args.impl == "b3d":
+        run_materialised(args)
+        return
     if args.warmup < 3 and args.impl == "b3d":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
