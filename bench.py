@@ -354,7 +354,7 @@ def _measured_peaks():
 
 def _kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("k_render.cu", "b3d_device.cuh", "b3d_internal.h"):
+    for f in ("k_score.cuh", "b3d_device.cuh", "b3d_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2312_08715_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -236,12 +236,15 @@ b3d_status b3d_score_grad(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const f
                           float *dpout_dev, b3d_stream stream);
 
 /* Launch shape of the fused render + score kernel (no counterpart in the paper: a property
- * of this implementation). tile_w: widest screen tile in pixels (8..256); cta_threads: 128
- * or 256; ctas_per_sm: CTAs resident per SM (0 = as many as fit). */
+ * of this implementation). tile_w: widest screen tile in pixels (8..256); cta_threads: 32,
+ * 64, 128 or 256 (one hypothesis per CTA at a time); ctas_per_sm: CTAs resident per SM
+ * (0 = as many as fit); high_occupancy: 1 selects the build whose registers are capped so
+ * that more CTAs fit on an SM, 0 the regular one. */
 typedef struct {
     int32_t tile_w;
     int32_t cta_threads;
     int32_t ctas_per_sm;
+    int32_t high_occupancy;
 } b3d_tuning;
 
 b3d_status b3d_get_tuning(b3d_ctx *ctx, b3d_tuning *out);

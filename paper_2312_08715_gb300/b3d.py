@@ -56,7 +56,8 @@ class b3d_stage(C.Structure):
 
 
 class b3d_tuning(C.Structure):
-    _fields_ = [("tile_w", C.c_int32), ("cta_threads", C.c_int32), ("ctas_per_sm", C.c_int32)]
+    _fields_ = [("tile_w", C.c_int32), ("cta_threads", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("high_occupancy", C.c_int32)]
 
 
 class b3d_c2f_schedule(C.Structure):
@@ -281,11 +282,12 @@ def b3d_score_grad(ctx, obj_slot, n_hyp, poses_dev, lik: b3d_lik_params, loglik_
 def b3d_get_tuning(ctx) -> dict:
     t = b3d_tuning()
     _check(ctx, load().b3d_get_tuning(ctx, C.byref(t)))
-    return dict(tile_w=t.tile_w, cta_threads=t.cta_threads, ctas_per_sm=t.ctas_per_sm)
+    return dict(tile_w=t.tile_w, cta_threads=t.cta_threads, ctas_per_sm=t.ctas_per_sm, high_occupancy=t.high_occupancy)
 
 
-def b3d_set_tuning(ctx, tile_w=64, cta_threads=256, ctas_per_sm=0):
-    return _check(ctx, load().b3d_set_tuning(ctx, C.byref(b3d_tuning(tile_w, cta_threads, ctas_per_sm))))
+def b3d_set_tuning(ctx, tile_w=64, cta_threads=256, ctas_per_sm=0, high_occupancy=0):
+    return _check(ctx, load().b3d_set_tuning(ctx, C.byref(b3d_tuning(tile_w, cta_threads, ctas_per_sm,
+                                                                       high_occupancy))))
 
 
 def b3d_autotune(ctx, obj_slot, centre_pose, grid_frame, stage: b3d_stage, lik: b3d_lik_params, stream=None) -> dict:
@@ -294,7 +296,7 @@ def b3d_autotune(ctx, obj_slot, centre_pose, grid_frame, stage: b3d_stage, lik: 
     t = b3d_tuning()
     _check(ctx, load().b3d_autotune(ctx, obj_slot, c.ctypes.data, g.ctypes.data, C.byref(stage), C.byref(lik),
                                     C.byref(t), _stream(stream)))
-    return dict(tile_w=t.tile_w, cta_threads=t.cta_threads, ctas_per_sm=t.ctas_per_sm)
+    return dict(tile_w=t.tile_w, cta_threads=t.cta_threads, ctas_per_sm=t.ctas_per_sm, high_occupancy=t.high_occupancy)
 
 
 def b3d_set_instrumentation(ctx, flags):

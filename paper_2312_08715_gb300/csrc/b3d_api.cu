@@ -32,8 +32,7 @@ struct MeshRec {
     int n_surf = 0, n_full = 0, n_verts = 0;
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     // voxel quads (n_quads == 0: none)
-    unsigned *quads = nullptr;
-    int2 *quad_tris = nullptr;
+    uint2 *quads = nullptr;
     int *class_off = nullptr;
     float *coords = nullptr;
     int n_quads = 0, nc[3] = {0, 0, 0}, np1 = 0;
@@ -95,7 +94,11 @@ struct b3d_ctx {
     int tile_w = 64;
     int cta_threads = 256;
     int ctas_per_sm = 0;
-    int score_code() const { return (cta_threads == 128 ? 256 : 0) | (ctas_per_sm & 255); }
+    int high_occupancy = 0;
+    int score_code() const {
+        const int nt = cta_threads == 128 ? 1 : (cta_threads == 64 ? 2 : (cta_threads == 32 ? 3 : 0));
+        return ((nt + (high_occupancy ? 4 : 0)) << 8) | (ctas_per_sm & 255);
+    }
 
     // instrumentation
     int instr = 0;
@@ -258,7 +261,6 @@ MeshView view_of(const MeshRec &m) {
     for (int k = 0; k < 3; ++k) { v.lo[k] = m.lo[k]; v.hi[k] = m.hi[k]; v.nc[k] = m.nc[k]; }
     v.n_quads = m.n_quads;
     v.quads = m.quads;
-    v.quad_tris = m.quad_tris;
     v.class_off = m.class_off;
     v.coords = m.coords;
     v.np1 = m.np1;
@@ -590,10 +592,10 @@ b3d_status b3d_load_mesh(b3d_ctx *ctx, const float *verts, int64_t n_v, const in
     for (int64_t f = 0; f < n_f; ++f)
         h_faces[f] = make_int4(remap[faces[3 * f]], remap[faces[3 * f + 1]], remap[faces[3 * f + 2]], 0);
 
-    // 5. voxel quads: a closed mesh whose surface triangles pair up into unit squares of
-    //    the vertex lattice (distinct coordinates per axis), each square axis-aligned
-    std::vector<unsigned> h_quads;
-    std::vector<int2> h_qtris;
+    // 5. voxel rectangles: a closed mesh whose surface triangles pair up into unit squares of
+    //    the vertex lattice (distinct coordinates per axis), each square axis-aligned; the
+    //    squares of each plane are merged into maximal rectangles
+    std::vector<uint2> h_quads;
     std::vector<int> h_off;
     std::vector<float> h_coords;
     int nc[3] = {0, 0, 0}, np1 = 0;
@@ -654,47 +656,69 @@ b3d_status b3d_load_mesh(b3d_ctx *ctx, const float *verts, int64_t n_v, const in
             groups[key].push_back({(int)i, missing});
         }
         if (quads_ok) {
-            std::vector<std::pair<uint32_t, int2>> qs;  // (packed, tris)
+            // every unit square must be exactly two triangles split along a diagonal
+            std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> planes;  // (class, plane) -> squares
             for (auto &kv : groups) {
                 auto &g = kv.second;
                 if (g.size() != 2 || (g[0].second + 2) % 4 != g[1].second) { quads_ok = false; break; }
-                // diag 0: triangles miss k1 and k3 (they share k0-k2); diag 1: miss k0 and k2
-                const int diag = (g[0].second == 1 || g[0].second == 3) ? 0 : 1;
-                // .x: the triangle holding k1 (diag 0) or k0 (diag 1), i.e. not missing it
-                const int hold = diag == 0 ? 1 : 0;
-                const int tx = g[0].second != hold ? g[0].first : g[1].first;
-                const int ty = tx == g[0].first ? g[1].first : g[0].first;
-                const uint32_t cls = kv.first >> 27, rest = kv.first & ((1u << 27) - 1);
-                const uint32_t packed = (cls << 29) | ((uint32_t)diag << 28) | rest;
-                qs.push_back({packed, make_int2(tris[tx].f, tris[ty].f)});
+                const int cls = (int)(kv.first >> 27), p = (int)((kv.first >> 18) & 511);
+                planes[{cls, p}].push_back({(int)((kv.first >> 9) & 511), (int)(kv.first & 511)});
             }
             if (quads_ok) {
-                std::sort(qs.begin(), qs.end(), [](const std::pair<uint32_t, int2> &x, const std::pair<uint32_t, int2> &y) {
-                    const uint32_t kx = ((x.first >> 29) << 27) | (x.first & ((1u << 27) - 1));
-                    const uint32_t ky = ((y.first >> 29) << 27) | (y.first & ((1u << 27) - 1));
-                    return kx < ky;
-                });
+                // greedy merge of each plane's squares into maximal rectangles (same plane and
+                // outward side, so the union renders exactly as the squares do)
+                std::vector<uint2> rects;
+                for (auto &pl : planes) {
+                    const int cls = pl.first.first, p = pl.first.second;
+                    int bmin = INT32_MAX, bmax = -1, cmin = INT32_MAX, cmax = -1;
+                    for (auto &sq : pl.second) {
+                        bmin = std::min(bmin, sq.first); bmax = std::max(bmax, sq.first);
+                        cmin = std::min(cmin, sq.second); cmax = std::max(cmax, sq.second);
+                    }
+                    const int nb = bmax - bmin + 1, ncs = cmax - cmin + 1;
+                    std::vector<char> occ((size_t)nb * ncs, 0);
+                    for (auto &sq : pl.second) occ[(size_t)(sq.first - bmin) * ncs + (sq.second - cmin)] = 1;
+                    for (int b = 0; b < nb; ++b)
+                        for (int c = 0; c < ncs; ++c) {
+                            if (!occ[(size_t)b * ncs + c]) continue;
+                            int wc = 1;
+                            while (c + wc < ncs && occ[(size_t)b * ncs + c + wc]) ++wc;
+                            int hb = 1;
+                            for (;;) {
+                                if (b + hb >= nb) break;
+                                bool row = true;
+                                for (int k = 0; k < wc && row; ++k) row = occ[(size_t)(b + hb) * ncs + c + k] != 0;
+                                if (!row) break;
+                                ++hb;
+                            }
+                            for (int bb = 0; bb < hb; ++bb)
+                                for (int k = 0; k < wc; ++k) occ[(size_t)(b + bb) * ncs + c + k] = 0;
+                            const uint32_t b0 = (uint32_t)(b + bmin), c0 = (uint32_t)(c + cmin);
+                            rects.push_back(make_uint2(((uint32_t)cls << 29) | ((uint32_t)p << 18) | (b0 << 9) | c0,
+                                                       ((uint32_t)hb << 9) | (uint32_t)wc));
+                        }
+                }
+                // rectangles are already grouped by (class, plane) in ascending order
                 np1 = std::max({nc[0], nc[1], nc[2]}) + 1;
                 h_off.assign((size_t)6 * np1, 0);
                 for (int cls = 0; cls < 6; ++cls) {
                     const int a = cls >> 1;
-                    for (int p = 0; p <= nc[a]; ++p) {
-                        // first quad with class > cls, or class == cls and plane >= p
-                        auto it = std::lower_bound(qs.begin(), qs.end(), std::make_pair(0u, make_int2(0, 0)),
-                                                   [&](const std::pair<uint32_t, int2> &q, const std::pair<uint32_t, int2> &) {
-                                                       const int qc = (int)(q.first >> 29), qp = (int)((q.first >> 18) & 511);
-                                                       return qc < cls || (qc == cls && qp < p);
-                                                   });
-                        h_off[(size_t)cls * np1 + p] = (int)(it - qs.begin());
+                    for (int p = 0; p < np1; ++p) {
+                        const int pp = std::min(p, nc[a]);
+                        // first rectangle with class > cls, or class == cls and plane >= pp
+                        auto it = std::lower_bound(rects.begin(), rects.end(), 0, [&](const uint2 &q, int) {
+                            const int qc = (int)(q.x >> 29), qp = (int)((q.x >> 18) & 511);
+                            return qc < cls || (qc == cls && qp < pp);
+                        });
+                        h_off[(size_t)cls * np1 + p] = (int)(it - rects.begin());
                     }
-                    for (int p = nc[a] + 1; p < np1; ++p) h_off[(size_t)cls * np1 + p] = h_off[(size_t)cls * np1 + nc[a]];
                 }
-                for (auto &q : qs) { h_quads.push_back(q.first); h_qtris.push_back(q.second); }
+                h_quads = std::move(rects);
                 for (int a = 0; a < 3; ++a) h_coords.insert(h_coords.end(), axis_vals[a].begin(), axis_vals[a].end());
             }
         }
     }
-    if (!quads_ok) { h_quads.clear(); h_qtris.clear(); h_off.clear(); h_coords.clear(); nc[0] = nc[1] = nc[2] = 0; np1 = 0; }
+    if (!quads_ok) { h_quads.clear(); h_off.clear(); h_coords.clear(); nc[0] = nc[1] = nc[2] = 0; np1 = 0; }
     rec.n_surf = (int)h_surf.size();
     rec.n_full = (int)h_full.size();
     rec.n_verts = (int)h_verts.size();
@@ -717,14 +741,13 @@ b3d_status b3d_load_mesh(b3d_ctx *ctx, const float *verts, int64_t n_v, const in
     up(&rec.tris_full, h_full, "mesh triangles");
     up(&rec.faces, h_faces, "mesh faces");
     if (rec.n_quads > 0) {
-        up(&rec.quads, h_quads, "mesh quads");
-        up(&rec.quad_tris, h_qtris, "mesh quad triangles");
+        up(&rec.quads, h_quads, "mesh rectangles");
         up(&rec.class_off, h_off, "mesh quad classes");
         up(&rec.coords, h_coords, "mesh lattice");
     }
     if (st != B3D_OK) {
         dfree(ctx, rec.verts); dfree(ctx, rec.tris_surf); dfree(ctx, rec.tris_full); dfree(ctx, rec.faces);
-        dfree(ctx, rec.quads); dfree(ctx, rec.quad_tris); dfree(ctx, rec.class_off); dfree(ctx, rec.coords);
+        dfree(ctx, rec.quads); dfree(ctx, rec.class_off); dfree(ctx, rec.coords);
         return st;
     }
     ctx->meshes.push_back(rec);
@@ -1038,6 +1061,7 @@ b3d_status b3d_get_tuning(b3d_ctx *ctx, b3d_tuning *out) {
     out->tile_w = ctx->tile_w;
     out->cta_threads = ctx->cta_threads;
     out->ctas_per_sm = ctx->ctas_per_sm;
+    out->high_occupancy = ctx->high_occupancy;
     return B3D_OK;
 }
 
@@ -1046,11 +1070,14 @@ b3d_status b3d_set_tuning(b3d_ctx *ctx, const b3d_tuning *t) {
     ctx->err.clear();
     if (!t) return fail(ctx, B3D_EINVAL, "tuning is NULL");
     if (t->tile_w < 8 || t->tile_w > 256) return fail(ctx, B3D_EINVAL, "tile_w must be in [8, 256]");
-    if (t->cta_threads != 128 && t->cta_threads != 256) return fail(ctx, B3D_EINVAL, "cta_threads must be 128 or 256");
+    if (t->cta_threads != 32 && t->cta_threads != 64 && t->cta_threads != 128 && t->cta_threads != 256)
+        return fail(ctx, B3D_EINVAL, "cta_threads must be 32, 64, 128 or 256");
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return fail(ctx, B3D_EINVAL, "ctas_per_sm must be in [0, 32]");
+    if (t->high_occupancy != 0 && t->high_occupancy != 1) return fail(ctx, B3D_EINVAL, "high_occupancy must be 0 or 1");
     ctx->tile_w = t->tile_w;
     ctx->cta_threads = t->cta_threads;
     ctx->ctas_per_sm = t->ctas_per_sm;
+    ctx->high_occupancy = t->high_occupancy;
     return B3D_OK;
 }
 
@@ -1082,16 +1109,17 @@ b3d_status b3d_autotune(b3d_ctx *ctx, int32_t obj_slot, const float *centre_pose
     P.n_rot = stage->n_rot;
     P.step = stage->step;
     cudaEvent_t e0 = take_event(ctx), e1 = take_event(ctx);
-    const b3d_tuning saved{ctx->tile_w, ctx->cta_threads, ctx->ctas_per_sm};
+    const b3d_tuning saved{ctx->tile_w, ctx->cta_threads, ctx->ctas_per_sm, ctx->high_occupancy};
     b3d_tuning win = saved;
     float win_ms = INFINITY;
-    for (int nt : {256, 128})
-        for (int tw : {32, 48, 64, 96, 128})
-            for (int cps : {0, 2}) {
-                if (nt == 128 && cps == 2) continue;
+    for (int hi : {0, 1})
+        for (int nt : {256, 128, 64, 32})
+            for (int tw : {32, 64, 96, 128}) {
+                const int cps = 0;
                 ctx->tile_w = tw;
                 ctx->cta_threads = nt;
                 ctx->ctas_per_sm = cps;
+                ctx->high_occupancy = hi;
                 const SceneView sv = scene_view(ctx, obj_slot);
                 launch_score_grid(sv, L, P, n, ctx->d_ll, ctx->score_code(), s);  // warm
                 cudaEventRecord(e0, s);
@@ -1101,17 +1129,19 @@ b3d_status b3d_autotune(b3d_ctx *ctx, int32_t obj_slot, const float *centre_pose
                 cudaError_t e = cudaEventSynchronize(e1);
                 if (e != cudaSuccess) {
                     ctx->tile_w = saved.tile_w; ctx->cta_threads = saved.cta_threads; ctx->ctas_per_sm = saved.ctas_per_sm;
+                    ctx->high_occupancy = saved.high_occupancy;
                     return cuda_fail(ctx, e, "autotune");
                 }
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < win_ms) { win_ms = ms; win = b3d_tuning{tw, nt, cps}; }
+                if (ms < win_ms) { win_ms = ms; win = b3d_tuning{tw, nt, cps, hi}; }
             }
     ctx->event_pool.push_back(e0);
     ctx->event_pool.push_back(e1);
     ctx->tile_w = win.tile_w;
     ctx->cta_threads = win.cta_threads;
     ctx->ctas_per_sm = win.ctas_per_sm;
+    ctx->high_occupancy = win.high_occupancy;
     if (best) *best = win;
     return check_launch(ctx, "autotune");
 }

@@ -36,10 +36,11 @@ struct Cam {
 //  - tris_full: every non-degenerate triangle, used when the near plane cuts the object
 //    open (then internal and back faces can be visible).
 //  - faces: the original faces on welded vertices (triangle id -> vertices).
-//  - quads (optional, voxel meshes): every surface triangle pairs with another into a unit
-//    square of the vertex lattice; quads are grouped by face class (axis, outward sign) and
-//    sorted by lattice plane, so the faces turned towards a camera position are one
-//    contiguous range per class.
+//  - rectangles (optional, voxel meshes): every surface triangle pairs with another into a
+//    unit square of the vertex lattice, and the coplanar squares of each lattice plane and
+//    outward side are merged into maximal rectangles; rectangles are grouped by face class
+//    (axis, outward sign) and sorted by lattice plane, so the faces turned towards a camera
+//    position are one contiguous range per class.
 struct MeshView {
     const float4 *verts;
     const int4 *tris_surf;      // (v0, v1, v2, original face index)
@@ -48,11 +49,10 @@ struct MeshView {
     int n_surf, n_full, n_faces;
     int closed;                 // back faces may be skipped (whole object beyond near)
     float lo[3], hi[3];         // object-frame bounding box of the vertices
-    // voxel quads
-    int n_quads;                // 0: no quad representation
-    const unsigned *quads;      // packed: class(3) diag(1) 0(1) plane(9) b0(9) c0(9)
-    const int2 *quad_tris;      // original face ids of the two triangles of the quad
-    const int *class_off;       // [6 * (np1)]: first quad of class c with plane >= p
+    // voxel rectangles
+    int n_quads;                // 0: no rectangle representation
+    const uint2 *quads;         // .x: class(3) 0(2) plane(9) b0(9) c0(9); .y: b extent(9) c extent(9)
+    const int *class_off;       // [6 * (np1)]: first rectangle of class c with plane >= p
     const float *coords;        // lattice plane coordinates, x planes then y then z
     int nc[3];                  // planes per axis
     int np1;                    // stride of class_off (max planes + 1)

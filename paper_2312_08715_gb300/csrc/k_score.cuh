@@ -1,0 +1,493 @@
+// k_score.cuh - the fused render + score kernel of libb3d and its launcher, a template
+// instantiated per launch shape in the k_score_*.cu translation units (compiled in parallel).
+//
+// One hypothesis per CTA iteration of a persistent grid renders the object into a
+// shared-memory z-buffer of depth bits, composites it with the fixed objects' depths and
+// scores, against their background terms, the observed pixels whose window can see it:
+//   LL_h = LL_bg + sum_{i in footprint + w} (l_i(h) - l_i(bg)),
+// an exact identity (unchanged pixels are formed by the same expressions in the same order
+// as the background table, so their terms cancel bit for bit).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "b3d_device.cuh"
+#include "b3d_internal.h"
+
+namespace b3d {
+
+// launch shape that also gets a work-counting build (for the roofline accounting)
+constexpr int kStatsNT = 128, kStatsMinB = 6;
+
+inline int score_sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// ------------------------------------------------------------------------------------------
+// score kernel
+// ------------------------------------------------------------------------------------------
+// One hypothesis per CTA iteration of a persistent grid:
+//  1. pose; screen bounding box of the object; whether the near plane can cut it. For a
+//     quad (voxel) mesh wholly beyond the near plane: the camera position o in the object
+//     frame and, per face class (axis, outward sign), the contiguous range of quads whose
+//     plane has o on its outer side (the faces turned towards the camera); the rest are
+//     never loaded.
+//  2. quad meshes: the camera-frame position of every lattice plane along each axis (the
+//     rotation column times the plane coordinate, plus t on the x axis), so a corner is the
+//     sum of three shared terms and every quad sharing a corner gets the same bits.
+//  3. per screen tile: clear a 32-bit z-buffer of depth bits, rasterise with atomicMin (the
+//     score depends only on the nearest depth, so no triangle id rides along), composite
+//     with the fixed objects' depths, score the tile's observed pixels against their
+//     background terms.
+//  4. block reduction to one log-likelihood.
+// STATS: count the work done (hypotheses, projected vertices/corners, primitives, pixel
+// tests, fragments, composited pixels, scored pixels, window pairs) into S.stats.
+// WT: the half window compiled in (1 or 2: sliding-window scoring), 0: runtime L.w.
+
+// Screen corner of a camera-frame point; approximate reciprocal (the same bits for the same
+// point in every quad that shares it).
+__device__ __forceinline__ float4 screen_pt(float x, float y, float z, const Cam &c) {
+    const float iz = __fdividef(1.0f, z);
+    return make_float4(fmaf(c.fx, x * iz, c.cx), fmaf(c.fy, y * iz, c.cy), iz, z);
+}
+
+__device__ __forceinline__ float4 sum3(const float4 &X, const float4 &Y, const float4 &Z) {
+    return make_float4((X.x + Y.x) + Z.x, (X.y + Y.y) + Z.y, (X.z + Y.z) + Z.z, 0.f);
+}
+
+// Quad raster with per-pixel coverage and depth (see raster_quad); the pixel loop is
+// flattened (no division) and the plane uses one approximate reciprocal.
+template <class Store>
+__device__ __forceinline__ void raster_quad_fast(float4 C0, float4 C1, float4 C2, float4 C3, int rx0, int rx1, int ry0,
+                                                 int ry1, float far_z, Store store, unsigned long long *tests) {
+    const float area = edge_fn(C0.x, C0.y, C1.x, C1.y, C2.x, C2.y);
+    if (!(area != 0.f)) return;
+    const float umin = fminf(fminf(C0.x, C1.x), fminf(C2.x, C3.x)), umax = fmaxf(fmaxf(C0.x, C1.x), fmaxf(C2.x, C3.x));
+    const float vmin = fminf(fminf(C0.y, C1.y), fminf(C2.y, C3.y)), vmax = fmaxf(fmaxf(C0.y, C1.y), fmaxf(C2.y, C3.y));
+    const int x0 = (int)ceilf(fmaxf(umin - 0.5f, (float)rx0)), x1 = (int)floorf(fminf(umax - 0.5f, (float)rx1));
+    const int y0 = (int)ceilf(fmaxf(vmin - 0.5f, (float)ry0)), y1 = (int)floorf(fminf(vmax - 0.5f, (float)ry1));
+    if (x0 > x1 || y0 > y1) return;
+    const int cnt = (x1 - x0 + 1) * (y1 - y0 + 1);
+    if (tests) *tests += (unsigned long long)cnt;
+    const float s = area > 0.f ? 1.f : -1.f;
+    const float inv = __fdividef(1.0f, area);
+    const float du1 = C1.x - C0.x, dv1 = C1.y - C0.y, du2 = C2.x - C0.x, dv2 = C2.y - C0.y;
+    const float dz1 = C1.z - C0.z, dz2 = C2.z - C0.z;
+    const float al = fmaf(dz1, dv2, -(dz2 * dv1)) * inv, be = fmaf(dz2, du1, -(dz1 * du2)) * inv;
+    int x = x0, y = y0;
+    for (int k = 0; k < cnt; ++k) {
+        const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+        const bool in = s * edge_fn(C0.x, C0.y, C1.x, C1.y, px, py) >= 0.f && s * edge_fn(C1.x, C1.y, C2.x, C2.y, px, py) >= 0.f &&
+                        s * edge_fn(C2.x, C2.y, C3.x, C3.y, px, py) >= 0.f && s * edge_fn(C3.x, C3.y, C0.x, C0.y, px, py) >= 0.f;
+        if (in) {
+            const float z = __fdividef(1.0f, fmaf(al, px - C0.x, fmaf(be, py - C0.y, C0.z)));
+            if (z <= far_z) store(x, y, z);
+        }
+        if (++x > x1) { x = x0; ++y; }
+    }
+}
+
+// Sum of l_i - l_i(bg) over pixel column x, rows [ya, yb], with the (2W+1)^2 window of
+// rendered depths slid down the column in registers. Window slots outside the image (and
+// pixels without a point) hold -1 and contribute nothing; the terms are formed in the same
+// order and by the same expressions as pixel_ell, so unchanged pixels give 0 exactly.
+template <int W>
+__device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, const float *lut, const Cam &c,
+                                              const float *zd, int zx0, int zy0, int zw, int x, int ya, int yb,
+                                              unsigned long long *n_px, unsigned long long *n_pairs) {
+    constexpr int D = 2 * W + 1;
+    float rx[D], ry[D], win[D][D];
+    bool colok[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const int xj = x + d - W;
+        colok[d] = xj >= 0 && xj < c.W;
+        rx[d] = ((float)xj + 0.5f - c.cx) * c.inv_fx;
+    }
+    auto load_row = [&](int yj, float *row) {
+        const bool rowok = yj >= 0 && yj < c.H;
+#pragma unroll
+        for (int d = 0; d < D; ++d) row[d] = (rowok && colok[d]) ? zd[(yj - zy0) * zw + (x + d - W - zx0)] : -1.f;
+    };
+#pragma unroll
+    for (int r = 1; r < D; ++r) {
+        load_row(ya - W + r - 1, win[r]);
+        ry[r] = ((float)(ya - W + r - 1) + 0.5f - c.cy) * c.inv_fy;
+    }
+    float acc = 0.f;
+    for (int y = ya; y <= yb; ++y) {
+#pragma unroll
+        for (int r = 0; r + 1 < D; ++r) {
+            ry[r] = ry[r + 1];
+#pragma unroll
+            for (int d = 0; d < D; ++d) win[r][d] = win[r + 1][d];
+        }
+        load_row(y + W, win[D - 1]);
+        ry[D - 1] = ((float)(y + W) + 0.5f - c.cy) * c.inv_fy;
+        const int64_t gi = (int64_t)y * c.W + x;
+        const float4 q = S.obs[gi];
+        if (q.w == 0.f) continue;
+        int n = 0;
+        float Ssum = 0.f;
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const float z = win[r][d];
+                const float ex = fmaf(-z, rx[d], q.x), ey = fmaf(-z, ry[r], q.y), ez = q.z - z;
+                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                if (L.kind == 0) n += (z >= 0.f && d2 <= L.r2) ? 1 : 0;
+                else if (z >= 0.f) Ssum += __expf(-d2 * L.inv2s2);
+            }
+        }
+        const float l = L.kind == 0 ? lut[n] : __logf(fmaf(L.bg, Ssum, L.a));
+        acc += l - S.ell_bg[gi];
+        if (n_px) {
+            ++*n_px;
+            *n_pairs += (unsigned long long)((min(y + W, c.H - 1) - max(y - W, 0) + 1) *
+                                             (min(x + W, c.W - 1) - max(x - W, 0) + 1));
+        }
+    }
+    return acc;
+}
+
+// z-buffer pixels per tile for a CTA of NT threads
+template <int NT>
+constexpr int score_region() { return NT <= 64 ? 2048 : kRegionPx; }
+constexpr int kStageStride = 5;  // float4 per staged rectangle: conflict-free reads across owners
+
+template <class PS, bool STATS, int WT, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    k_score(SceneView S, Lik L, PS P, int64_t n_hyp, float *out_ll) {
+    constexpr int REG = score_region<NT>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned *zb = reinterpret_cast<unsigned *>(smem_raw);                       // [kRegionPx]
+    float *zd = reinterpret_cast<float *>(smem_raw);                             // same memory, as depths
+    float4 *lat = reinterpret_cast<float4 *>(smem_raw + REG * sizeof(unsigned));  // lattice planes
+    __shared__ float s_lut[kMaxLut];
+    __shared__ float s_pose[12];
+    __shared__ int s_bb[4];
+    __shared__ int s_fbb[4];   // bounding box of the tile's fragments
+    __shared__ int s_flags;  // bit 0: on screen, bit 1: rectangle path, bit 2: whole object beyond near
+    __shared__ int s_rng[13];  // class first rectangles [6], exclusive prefix of counts [6], total
+    __shared__ float s_red[NT / 32];
+    __shared__ float4 s_stage[NT * kStageStride];  // per lane: a rectangle's corners, plane, pixel box
+
+    const Cam &c = S.cam;
+    const MeshView &m = S.mesh;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < L.n_lut; i += nt) s_lut[i] = L.lut[i];
+    const int w = WT > 0 ? WT : L.w;
+    const int n_lat = m.nc[0] + m.nc[1] + m.nc[2];
+    const int nc0 = m.nc[0], nc01 = m.nc[0] + m.nc[1];
+    auto lat_off = [&](int a) { return a == 0 ? 0 : (a == 1 ? nc0 : nc01); };
+    unsigned long long cnt[kNumStats] = {0, 0, 0, 0, 0, 0, 0, 0};
+
+    for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
+        __syncthreads();
+        if (tid == 0) {
+            if (STATS) ++cnt[0];
+            pose12(P, h, s_pose);
+            bool front = false;
+            int f = object_bbox(m, s_pose, c, s_bb, &front) ? 1 : 0;
+            if (front) f |= 4;
+            if (f && front && m.n_quads > 0) {
+                f |= 2;
+                const float *R = s_pose, *t = s_pose + 9;
+                float o[3];
+                for (int a = 0; a < 3; ++a) o[a] = -fmaf(R[a], t[0], fmaf(R[3 + a], t[1], R[6 + a] * t[2]));
+                int tot = 0;
+                for (int cls = 0; cls < 6; ++cls) {
+                    const int a = cls >> 1;
+                    const float *cd = m.coords + lat_off(a);
+                    const int n = m.nc[a];
+                    int lo = 0, hi = n;  // first plane with coordinate >= o
+                    while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] < o[a]) lo = mid + 1; else hi = mid; }
+                    const int below = lo;
+                    hi = n;  // first plane with coordinate > o
+                    while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] <= o[a]) lo = mid + 1; else hi = mid; }
+                    const int not_above = lo;
+                    const int *off = m.class_off + cls * m.np1;
+                    // +axis faces face the camera when their plane is below o; -axis when above
+                    const int b = (cls & 1) ? off[0] : off[not_above];
+                    const int e = (cls & 1) ? off[below] : off[n];
+                    s_rng[cls] = b;
+                    s_rng[6 + cls] = tot;
+                    tot += e - b;
+                }
+                s_rng[12] = tot;
+            }
+            s_flags = f;
+        }
+        __syncthreads();
+        const int flags = s_flags;
+        if (!(flags & 1)) {
+            if (tid == 0) out_ll[h] = (float)*S.ll_bg;
+            continue;
+        }
+        const float *pose = s_pose;
+        const bool quad = (flags & 2) != 0, front = (flags & 4) != 0;
+        const int bx0 = s_bb[0], bx1 = s_bb[1], by0 = s_bb[2], by1 = s_bb[3];
+        if (quad) {
+            for (int k = tid; k < n_lat; k += nt) {
+                const int a = k < nc0 ? 0 : (k < nc01 ? 1 : 2);
+                const float v = m.coords[k];
+                lat[k] = make_float4(fmaf(pose[a], v, a == 0 ? pose[9] : 0.f), fmaf(pose[3 + a], v, a == 0 ? pose[10] : 0.f),
+                                     fmaf(pose[6 + a], v, a == 0 ? pose[11] : 0.f), 0.f);
+            }
+            if (STATS) cnt[1] += (unsigned long long)((n_lat - tid + nt - 1) / nt);
+        }
+        const int sx0 = max(bx0 - w, 0), sx1 = min(bx1 + w, c.W - 1);
+        const int sy0 = max(by0 - w, 0), sy1 = min(by1 + w, c.H - 1);
+        const int sw = sx1 - sx0 + 1;
+        const int tw = min(sw, S.tile_w);
+        const int th = max(1, REG / (tw + 2 * w) - 2 * w);
+        float acc = 0.f;
+        for (int ty0 = sy0; ty0 <= sy1; ty0 += th) {
+            for (int tx0 = sx0; tx0 <= sx1; tx0 += tw) {
+                const int tx1 = min(tx0 + tw - 1, sx1), ty1 = min(ty0 + th - 1, sy1);
+                const int zx0 = max(tx0 - w, 0), zx1 = min(tx1 + w, c.W - 1);
+                const int zy0 = max(ty0 - w, 0), zy1 = min(ty1 + w, c.H - 1);
+                const int zw = zx1 - zx0 + 1, zh = zy1 - zy0 + 1, nz = zw * zh;
+                const int rx0 = max(zx0, bx0), rx1 = min(zx1, bx1), ry0 = max(zy0, by0), ry1 = min(zy1, by1);
+                const bool need = rx0 <= rx1 && ry0 <= ry1;
+                for (int i = tid; i < nz; i += nt) zb[i] = 0xffffffffu;
+                if (tid == 0) { s_fbb[0] = INT32_MAX; s_fbb[1] = -1; s_fbb[2] = INT32_MAX; s_fbb[3] = -1; }
+                __syncthreads();
+                if (need) {
+                    int fx0 = INT32_MAX, fx1 = -1, fy0 = INT32_MAX, fy1 = -1;  // this lane's fragments
+                    auto store = [&](int x, int y, float z) {
+                        if (STATS) ++cnt[4];
+                        atomicMin(&zb[(y - zy0) * zw + (x - zx0)], __float_as_uint(z));
+                        fx0 = min(fx0, x); fx1 = max(fx1, x); fy0 = min(fy0, y); fy1 = max(fy1, y);
+                    };
+                    if (quad) {
+                        // Each warp takes 32 rectangles at a time: every lane projects one and
+                        // stages its screen corners, plane and pixel box; then the warp shares out
+                        // the pixel-centre candidates of all 32 among its lanes.
+                        const int total = s_rng[12];
+                        float4 *stg = s_stage + (wid * 32) * kStageStride;
+                        for (int base = wid * 32; base < total; base += nt) {
+                            const int k = base + lane;
+                            int cand = 0;
+                            if (k < total) {
+                                int cls = 0;
+#pragma unroll
+                                for (int j = 1; j < 6; ++j) cls += k >= s_rng[6 + j] ? 1 : 0;
+                                const uint2 q = m.quads[s_rng[cls] + (k - s_rng[6 + cls])];
+                                const int a = cls >> 1, p = (q.x >> 18) & 511, b0 = (q.x >> 9) & 511, c0 = q.x & 511;
+                                const int b1 = b0 + (int)((q.y >> 9) & 511), c1 = c0 + (int)(q.y & 511);
+                                const int ab = a == 2 ? 0 : a + 1, ac = a == 0 ? 2 : a - 1;
+                                // the plane term is shared by all corners, the in-plane terms take two
+                                // values each; corners are summed in x, y, z order
+                                const float4 Tp = lat[lat_off(a) + p];
+                                const float4 Tb0 = lat[lat_off(ab) + b0], Tb1 = lat[lat_off(ab) + b1];
+                                const float4 Tc0 = lat[lat_off(ac) + c0], Tc1 = lat[lat_off(ac) + c1];
+                                float4 W0, W1, W2, W3;  // corners k0 (b0,c0) k1 (b1,c0) k2 (b1,c1) k3 (b0,c1)
+                                if (a == 0) {
+                                    W0 = sum3(Tp, Tb0, Tc0); W1 = sum3(Tp, Tb1, Tc0); W2 = sum3(Tp, Tb1, Tc1); W3 = sum3(Tp, Tb0, Tc1);
+                                } else if (a == 1) {
+                                    W0 = sum3(Tc0, Tp, Tb0); W1 = sum3(Tc0, Tp, Tb1); W2 = sum3(Tc1, Tp, Tb1); W3 = sum3(Tc1, Tp, Tb0);
+                                } else {
+                                    W0 = sum3(Tb0, Tc0, Tp); W1 = sum3(Tb1, Tc0, Tp); W2 = sum3(Tb1, Tc1, Tp); W3 = sum3(Tb0, Tc1, Tp);
+                                }
+                                const float4 C0 = screen_pt(W0.x, W0.y, W0.z, c), C1 = screen_pt(W1.x, W1.y, W1.z, c);
+                                const float4 C2 = screen_pt(W2.x, W2.y, W2.z, c), C3 = screen_pt(W3.x, W3.y, W3.z, c);
+                                if (STATS) { cnt[1] += 4; ++cnt[2]; }
+                                const float area = edge_fn(C0.x, C0.y, C1.x, C1.y, C2.x, C2.y);
+                                if (area != 0.f) {
+                                    const float umin = fminf(fminf(C0.x, C1.x), fminf(C2.x, C3.x));
+                                    const float umax = fmaxf(fmaxf(C0.x, C1.x), fmaxf(C2.x, C3.x));
+                                    const float vmin = fminf(fminf(C0.y, C1.y), fminf(C2.y, C3.y));
+                                    const float vmax = fmaxf(fmaxf(C0.y, C1.y), fmaxf(C2.y, C3.y));
+                                    const int x0 = (int)ceilf(fmaxf(umin - 0.5f, (float)rx0));
+                                    const int x1 = (int)floorf(fminf(umax - 0.5f, (float)rx1));
+                                    const int y0 = (int)ceilf(fmaxf(vmin - 0.5f, (float)ry0));
+                                    const int y1 = (int)floorf(fminf(vmax - 0.5f, (float)ry1));
+                                    if (x0 <= x1 && y0 <= y1) {
+                                        cand = (x1 - x0 + 1) * (y1 - y0 + 1);
+                                        const float inv = __fdividef(1.0f, area);
+                                        const float du1 = C1.x - C0.x, dv1 = C1.y - C0.y, du2 = C2.x - C0.x, dv2 = C2.y - C0.y;
+                                        const float dz1 = C1.z - C0.z, dz2 = C2.z - C0.z;
+                                        const float al = fmaf(dz1, dv2, -(dz2 * dv1)) * inv;
+                                        const float be = fmaf(dz2, du1, -(dz1 * du2)) * inv;
+                                        stg[lane * kStageStride + 0] = make_float4(C0.x, C0.y, C1.x, C1.y);
+                                        stg[lane * kStageStride + 1] = make_float4(C2.x, C2.y, C3.x, C3.y);
+                                        stg[lane * kStageStride + 2] = make_float4(al, be, C0.z, area > 0.f ? 1.f : -1.f);
+                                        // the candidate's row is floor((k + 1/2) / width), exact in float
+                                        // for the region's sizes (margin 1/(2 width) >> rounding)
+                                        stg[lane * kStageStride + 3] = make_float4(
+                                            __int_as_float(x0), __int_as_float(y0), __int_as_float(x1 - x0 + 1),
+                                            1.0f / (float)(x1 - x0 + 1));
+                                    }
+                                }
+                            }
+                            if (STATS) cnt[3] += (unsigned long long)cand;
+                            int incl = cand;
+#pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const int up = __shfl_up_sync(0xffffffffu, incl, o);
+                                if (lane >= o) incl += up;
+                            }
+                            const int n_cand = __shfl_sync(0xffffffffu, incl, 31);
+                            const int excl = incl - cand;
+                            __syncwarp();
+                            for (int r0 = 0; r0 < n_cand; r0 += 32) {
+                                const int j = r0 + lane;
+                                int lo = 0, hi = 31;  // the first lane whose inclusive count exceeds j
+#pragma unroll
+                                for (int st = 0; st < 5; ++st) {
+                                    const int mid = (lo + hi) >> 1;
+                                    if (__shfl_sync(0xffffffffu, incl, mid) > j) hi = mid; else lo = mid + 1;
+                                }
+                                const int kk = j - __shfl_sync(0xffffffffu, excl, lo);
+                                if (j < n_cand) {
+                                    const float4 A = stg[lo * kStageStride + 0], B = stg[lo * kStageStride + 1],
+                                                 Pl = stg[lo * kStageStride + 2], Bx = stg[lo * kStageStride + 3];
+                                    const int bw = __float_as_int(Bx.z), row = (int)(((float)kk + 0.5f) * Bx.w);
+                                    const int x = __float_as_int(Bx.x) + (kk - row * bw), y = __float_as_int(Bx.y) + row;
+                                    const float px = (float)x + 0.5f, py = (float)y + 0.5f, sg = Pl.w;
+                                    if (sg * edge_fn(A.x, A.y, A.z, A.w, px, py) >= 0.f &&
+                                        sg * edge_fn(A.z, A.w, B.x, B.y, px, py) >= 0.f &&
+                                        sg * edge_fn(B.x, B.y, B.z, B.w, px, py) >= 0.f &&
+                                        sg * edge_fn(B.z, B.w, A.x, A.y, px, py) >= 0.f) {
+                                        const float z = __fdividef(1.0f, fmaf(Pl.x, px - A.x, fmaf(Pl.y, py - A.y, Pl.z)));
+                                        if (z <= c.far_z) store(x, y, z);
+                                    }
+                                }
+                            }
+                            __syncwarp();
+                        }
+                    } else {
+                        const int4 *tris = front ? m.tris_surf : m.tris_full;
+                        const int n_t = front ? m.n_surf : m.n_full;
+                        const int cull = front ? m.closed : 0;
+                        for (int t = tid; t < n_t; t += nt) {
+                            float4 A, B, C;
+                            tri_screen(m, tris[t], pose, c, A, B, C);
+                            if (STATS) { cnt[1] += 3; ++cnt[2]; }
+                            raster_tri(A, B, C, cull, rx0, rx1, ry0, ry1, c.far_z, store, STATS ? &cnt[3] : nullptr);
+                        }
+                    }
+                    // the tile's fragment box: pixels outside it +- w keep their background terms
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        fx0 = min(fx0, __shfl_xor_sync(0xffffffffu, fx0, o));
+                        fx1 = max(fx1, __shfl_xor_sync(0xffffffffu, fx1, o));
+                        fy0 = min(fy0, __shfl_xor_sync(0xffffffffu, fy0, o));
+                        fy1 = max(fy1, __shfl_xor_sync(0xffffffffu, fy1, o));
+                    }
+                    if (lane == 0 && fx1 >= 0) {
+                        atomicMin(&s_fbb[0], fx0); atomicMax(&s_fbb[1], fx1);
+                        atomicMin(&s_fbb[2], fy0); atomicMax(&s_fbb[3], fy1);
+                    }
+                }
+                __syncthreads();
+                if (s_fbb[1] < 0) {  // nothing of the object in this tile: every term is unchanged
+                    __syncthreads();
+                    continue;
+                }
+                // composite with the fixed objects in place (depth bits -> rendered depth) over
+                // the fragment box + 2w, the depths the scored windows read
+                const int cx0 = max(s_fbb[0] - 2 * w, zx0), cx1 = min(s_fbb[1] + 2 * w, zx1);
+                const int cy0 = max(s_fbb[2] - 2 * w, zy0), cy1 = min(s_fbb[3] + 2 * w, zy1);
+                {
+                    const int cw = cx1 - cx0 + 1, n_c = cw * (cy1 - cy0 + 1);
+                    const int dq = nt / cw, dr = nt - dq * cw;
+                    int y = tid / cw, x = tid - y * cw;
+                    for (int i = tid; i < n_c; i += nt) {
+                        const int gx = cx0 + x, gy = cy0 + y;
+                        const int zi = (gy - zy0) * zw + (gx - zx0);
+                        const unsigned bgb = (unsigned)(S.bg[(int64_t)gy * c.W + gx] >> 32);
+                        const unsigned v = min(zb[zi], bgb);
+                        zd[zi] = v == 0xffffffffu ? (L.miss_mode ? -1.f : c.far_z) : __uint_as_float(v);
+                        x += dr;
+                        y += dq;
+                        if (x >= cw) { x -= cw; ++y; }
+                    }
+                    if (STATS) cnt[5] += (unsigned long long)((n_c - tid + nt - 1) / nt);
+                }
+                __syncthreads();
+                // score the tile's pixels within the fragment box + w
+                const int qx0 = max(s_fbb[0] - w, tx0), qx1 = min(s_fbb[1] + w, tx1);
+                const int qy0 = max(s_fbb[2] - w, ty0), qy1 = min(s_fbb[3] + w, ty1);
+                const int tww = qx1 - qx0 + 1, thh = qy1 - qy0 + 1;
+                if (WT > 0) {
+                    // thread -> (column, run of rows)
+                    const int nseg = max(1, nt / tww);
+                    const int rps = (thh + nseg - 1) / nseg;
+                    const int seg = tid / tww, col = tid - seg * tww;
+                    if (seg < nseg && col < tww) {
+                        const int ya = qy0 + seg * rps, yb = min(ya + rps - 1, qy1);
+                        if (ya <= yb)
+                            acc += score_column<WT>(S, L, s_lut, c, zd, zx0, zy0, zw, qx0 + col, ya, yb,
+                                                    STATS ? &cnt[6] : nullptr, STATS ? &cnt[7] : nullptr);
+                    }
+                } else {
+                    const int n_tile = tww * thh;
+                    const int dq = nt / tww, dr = nt - dq * tww;
+                    int y = tid / tww, x = tid - y * tww;
+                    for (int k = tid; k < n_tile; k += nt) {
+                        const int gx = qx0 + x, gy = qy0 + y;
+                        const int64_t gi = (int64_t)gy * c.W + gx;
+                        const float4 q = S.obs[gi];
+                        if (q.w != 0.f) {
+                            if (STATS) {
+                                ++cnt[6];
+                                cnt[7] += (unsigned long long)((min(gy + w, c.H - 1) - max(gy - w, 0) + 1) *
+                                                               (min(gx + w, c.W - 1) - max(gx - w, 0) + 1));
+                            }
+                            const float l = pixel_ell(L, s_lut, c, q, gx, gy,
+                                                      [&](int xj, int yj) { return zd[(yj - zy0) * zw + (xj - zx0)]; });
+                            acc += l - S.ell_bg[gi];
+                        }
+                        x += dr;
+                        y += dq;
+                        if (x >= tww) { x -= tww; ++y; }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        const float tot = block_sum(acc, s_red);
+        if (tid == 0) out_ll[h] = (float)(*S.ll_bg + (double)tot);
+    }
+    if (STATS)
+        for (int k = 0; k < kNumStats; ++k)
+            if (cnt[k]) atomicAdd(&S.stats[k], cnt[k]);
+}
+
+template <class PS, int NT, int MINB>
+int launch_score_nt(const SceneView &sv, const Lik &L, PS P, int64_t n, float *ll, int grid, cudaStream_t s) {
+    const int n_lat = sv.mesh.nc[0] + sv.mesh.nc[1] + sv.mesh.nc[2];
+    const int smem = score_region<NT>() * (int)sizeof(unsigned) + n_lat * (int)sizeof(float4);
+    // work counting is compiled for one launch shape only (kStatsNT, kStatsMinB)
+    constexpr bool ST = NT == kStatsNT && MINB == kStatsMinB;
+    auto kern = L.w == 1 ? k_score<PS, false, 1, NT, MINB> : (L.w == 2 ? k_score<PS, false, 2, NT, MINB> : k_score<PS, false, 0, NT, MINB>);
+    if constexpr (ST) {
+        if (sv.stats) kern = L.w == 1 ? k_score<PS, true, 1, NT, MINB> : (L.w == 2 ? k_score<PS, true, 2, NT, MINB> : k_score<PS, true, 0, NT, MINB>);
+    }
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    per_sm = std::max(per_sm, 1);
+    // grid > 0: CTAs per SM requested by the tuning (capped by occupancy); 0: occupancy
+    const int ctas = grid > 0 ? std::min(grid, per_sm) : per_sm;
+    const int g = (int)std::min<int64_t>((int64_t)ctas * score_sm_count(), std::max<int64_t>(n, 1));
+    kern<<<g, NT, smem, s>>>(sv, L, P, n, ll);
+    return g;
+}
+
+}  // namespace b3d

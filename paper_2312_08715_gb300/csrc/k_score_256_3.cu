@@ -1,0 +1,10 @@
+// k_score_256_3.cu - score kernel instantiated for 256-thread CTAs, registers capped for
+// 3 CTAs per SM.
+#include "k_score.cuh"
+
+namespace b3d {
+template int launch_score_nt<PoseList, 256, 3>(const SceneView &, const Lik &, PoseList, int64_t, float *, int,
+                                                  cudaStream_t);
+template int launch_score_nt<PoseGrid, 256, 3>(const SceneView &, const Lik &, PoseGrid, int64_t, float *, int,
+                                                  cudaStream_t);
+}  // namespace b3d

@@ -1,0 +1,10 @@
+// k_score_32_16.cu - score kernel instantiated for 32-thread CTAs, registers capped for
+// 16 CTAs per SM.
+#include "k_score.cuh"
+
+namespace b3d {
+template int launch_score_nt<PoseList, 32, 16>(const SceneView &, const Lik &, PoseList, int64_t, float *, int,
+                                                  cudaStream_t);
+template int launch_score_nt<PoseGrid, 32, 16>(const SceneView &, const Lik &, PoseGrid, int64_t, float *, int,
+                                                  cudaStream_t);
+}  // namespace b3d

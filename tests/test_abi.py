@@ -67,6 +67,7 @@ int main(void) {
   printf("%zu %zu %zu %zu\\n", offsetof(b3d_c2f_schedule, stage), offsetof(b3d_c2f_schedule, n_particles),
          offsetof(b3d_c2f_schedule, seed), offsetof(b3d_c2f_schedule, grid_frame));
   printf("%zu %zu\\n", offsetof(b3d_lik_params, volume), offsetof(b3d_lik_params, miss_mode));
+  printf("%zu %zu\\n", sizeof(b3d_tuning), offsetof(b3d_tuning, high_occupancy));
   return 0;
 }
 """)
@@ -78,7 +79,8 @@ int main(void) {
             C.sizeof(b3d.b3d_c2f_schedule),
             b3d.b3d_c2f_schedule.stage.offset, b3d.b3d_c2f_schedule.n_particles.offset,
             b3d.b3d_c2f_schedule.seed.offset, b3d.b3d_c2f_schedule.grid_frame.offset,
-            b3d.b3d_lik_params.volume.offset, b3d.b3d_lik_params.miss_mode.offset]
+            b3d.b3d_lik_params.volume.offset, b3d.b3d_lik_params.miss_mode.offset,
+            C.sizeof(b3d.b3d_tuning), b3d.b3d_tuning.high_occupancy.offset]
     assert got == want
 
 

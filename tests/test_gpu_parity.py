@@ -168,16 +168,17 @@ def test_every_launch_shape_matches_oracle(orc, single_object):
     ref = orc.score(sc, 0, poses, wl.lik, obs)
     ctx = gpu_context(sc, obs)
     outs = []
-    for tw, nt, cps in [(8, 128, 0), (32, 256, 2), (64, 256, 0), (256, 128, 1)]:
-        b3d.b3d_set_tuning(ctx.h, tw, nt, cps)
+    for tw, nt, cps, hi in [(8, 128, 0, 0), (32, 256, 2, 0), (64, 256, 0, 1), (256, 128, 1, 1), (48, 64, 0, 0),
+                            (96, 32, 0, 1), (8, 32, 3, 0), (40, 64, 0, 1)]:
+        b3d.b3d_set_tuning(ctx.h, tw, nt, cps, hi)
         outs.append(_np(ctx.score(0, poses, wl.lik)))
         ctx.sync()
-        _check_ll(outs[-1], ref, f"tuning {tw}/{nt}/{cps}")
+        _check_ll(outs[-1], ref, f"tuning {tw}/{nt}/{cps}/{hi}")
     for o in outs[1:]:
         np.testing.assert_allclose(o, outs[0], rtol=2e-6, atol=1e-3)
     st = b3d.stage_params(synth.StageSpec(7, 0.01, 1, 4, 0.1))
     best = b3d.b3d_autotune(ctx.h, 0, wl.hidden, np.eye(3), st, b3d.lik_params(**wl.lik))
-    assert best["cta_threads"] in (128, 256) and 8 <= best["tile_w"] <= 256
+    assert best["cta_threads"] in (32, 64, 128, 256) and 8 <= best["tile_w"] <= 256
     assert b3d.b3d_get_tuning(ctx.h) == best
     _check_ll(_np(ctx.score(0, poses, wl.lik)), ref, "autotuned")
     ctx.close()
