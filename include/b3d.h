@@ -225,6 +225,45 @@ b3d_status b3d_enumerate_c2f(b3d_ctx *ctx, int32_t obj_slot, const float *centre
                              const b3d_c2f_schedule *schedule, const b3d_lik_params *lik, float *particles_dev,
                              float *logw_dev, float *logq_dev, b3d_stream stream);
 
+/* Batched form (the paper has one scene at a time; this is how many independent scenes
+ * share one GPU): the hypotheses of every item, each item a scene held by its own context
+ * (its current b3d_set_scene) on the owner's device, are rendered and scored in ONE
+ * persistent launch whose CTAs take batch_chunk hypotheses at a time from a work queue over
+ * (scene, hypothesis chunk). Items may differ in image size, meshes, object slot and
+ * hypothesis count; the likelihood is shared (its frustum volume is each scene's own).
+ * Scores equal those of b3d_score_batch on each scene alone. The owner's context supplies
+ * the launch shape (b3d_tuning) and the scratch; scratch is sized on first use, after
+ * which the call can be captured into a CUDA graph (it allocates nothing and only copies its
+ * descriptors from pinned host memory). */
+typedef struct {
+    b3d_ctx *scene;          /* context holding the scene */
+    int32_t obj_slot;
+    int64_t n_hyp;
+    const float *poses_dev;  /* [n_hyp, 16] */
+    float *loglik_dev;       /* [n_hyp] */
+} b3d_score_item;
+
+b3d_status b3d_score_multi(b3d_ctx *owner, int32_t n_items, const b3d_score_item *items, const b3d_lik_params *lik,
+                           b3d_stream stream);
+
+/* Batched coarse-to-fine enumeration: every item runs b3d_enumerate_c2f on its own scene and
+ * schedule (all schedules with the same number of stages); each stage is one batched score
+ * launch, one batched log-sum-exp + resampling launch and one batched selection launch over
+ * all items. Outputs per item as b3d_enumerate_c2f. Same graph-capture rule as
+ * b3d_score_multi. */
+typedef struct {
+    b3d_ctx *scene;
+    int32_t obj_slot;
+    float centre_pose[16];
+    b3d_c2f_schedule schedule;
+    float *particles_dev;  /* [M, 16] */
+    float *logw_dev;       /* [M] */
+    float *logq_dev;       /* [M] */
+} b3d_c2f_item;
+
+b3d_status b3d_enumerate_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_item *items, const b3d_lik_params *lik,
+                               b3d_stream stream);
+
 /* Forward and backward of the smooth (kind 1) likelihood for n_hyp poses: loglik_dev [n],
  * dpose_dev [n, 6] = d loglik / d xi at xi = 0 for the left perturbation
  * T(xi) = Exp([v, w]^) T in the camera frame, ordered (v, w), with visibility held fixed
@@ -239,12 +278,13 @@ b3d_status b3d_score_grad(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const f
  * of this implementation). tile_w: widest screen tile in pixels (8..256); cta_threads: 32,
  * 64, 128 or 256 (one hypothesis per CTA at a time); ctas_per_sm: CTAs resident per SM
  * (0 = as many as fit); high_occupancy: 1 selects the build whose registers are capped so
- * that more CTAs fit on an SM, 0 the regular one. */
+ * that more CTAs fit on an SM, 0 the regular one; batch_chunk (1..1024): see b3d_score_multi. */
 typedef struct {
     int32_t tile_w;
     int32_t cta_threads;
     int32_t ctas_per_sm;
     int32_t high_occupancy;
+    int32_t batch_chunk; /* batched form: hypotheses a CTA takes from the work queue at a time */
 } b3d_tuning;
 
 b3d_status b3d_get_tuning(b3d_ctx *ctx, b3d_tuning *out);

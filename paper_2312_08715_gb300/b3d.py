@@ -57,12 +57,23 @@ class b3d_stage(C.Structure):
 
 class b3d_tuning(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("cta_threads", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("high_occupancy", C.c_int32)]
+                ("high_occupancy", C.c_int32), ("batch_chunk", C.c_int32)]
 
 
 class b3d_c2f_schedule(C.Structure):
     _fields_ = [("n_stages", C.c_int32), ("stage", b3d_stage * B3D_MAX_STAGES), ("n_particles", C.c_int32),
                 ("seed", C.c_uint64), ("grid_frame", C.c_float * 9)]
+
+
+class b3d_score_item(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("obj_slot", C.c_int32), ("n_hyp", C.c_int64), ("poses_dev", C.c_void_p),
+                ("loglik_dev", C.c_void_p)]
+
+
+class b3d_c2f_item(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("obj_slot", C.c_int32), ("centre_pose", C.c_float * 16),
+                ("schedule", b3d_c2f_schedule), ("particles_dev", C.c_void_p), ("logw_dev", C.c_void_p),
+                ("logq_dev", C.c_void_p)]
 
 
 _P = C.c_void_p
@@ -82,6 +93,8 @@ _SIGNATURES = {
     "b3d_lse_resample": (C.c_int32, [_P, C.c_int64, _P, C.c_int32, C.c_uint64, C.c_int32, _P, _P, _P, _P]),
     "b3d_enumerate_c2f": (C.c_int32, [_P, C.c_int32, _P, C.POINTER(b3d_c2f_schedule), C.POINTER(b3d_lik_params),
                                       _P, _P, _P, _P]),
+    "b3d_score_multi": (C.c_int32, [_P, C.c_int32, C.POINTER(b3d_score_item), C.POINTER(b3d_lik_params), _P]),
+    "b3d_enumerate_multi": (C.c_int32, [_P, C.c_int32, C.POINTER(b3d_c2f_item), C.POINTER(b3d_lik_params), _P]),
     "b3d_score_grad": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_lik_params), _P, _P, _P, _P, _P]),
     "b3d_lse_resample_noalloc": (C.c_int32, [C.c_int64, _P, C.c_int32, C.c_uint64, C.c_int32, _P, _P, _P, _P]),
     "b3d_get_tuning": (C.c_int32, [_P, C.POINTER(b3d_tuning)]),
@@ -282,12 +295,13 @@ def b3d_score_grad(ctx, obj_slot, n_hyp, poses_dev, lik: b3d_lik_params, loglik_
 def b3d_get_tuning(ctx) -> dict:
     t = b3d_tuning()
     _check(ctx, load().b3d_get_tuning(ctx, C.byref(t)))
-    return dict(tile_w=t.tile_w, cta_threads=t.cta_threads, ctas_per_sm=t.ctas_per_sm, high_occupancy=t.high_occupancy)
+    return dict(tile_w=t.tile_w, cta_threads=t.cta_threads, ctas_per_sm=t.ctas_per_sm, high_occupancy=t.high_occupancy,
+                batch_chunk=t.batch_chunk)
 
 
-def b3d_set_tuning(ctx, tile_w=64, cta_threads=256, ctas_per_sm=0, high_occupancy=0):
+def b3d_set_tuning(ctx, tile_w=64, cta_threads=256, ctas_per_sm=0, high_occupancy=0, batch_chunk=4):
     return _check(ctx, load().b3d_set_tuning(ctx, C.byref(b3d_tuning(tile_w, cta_threads, ctas_per_sm,
-                                                                       high_occupancy))))
+                                                                       high_occupancy, batch_chunk))))
 
 
 def b3d_autotune(ctx, obj_slot, centre_pose, grid_frame, stage: b3d_stage, lik: b3d_lik_params, stream=None) -> dict:
@@ -296,7 +310,34 @@ def b3d_autotune(ctx, obj_slot, centre_pose, grid_frame, stage: b3d_stage, lik: 
     t = b3d_tuning()
     _check(ctx, load().b3d_autotune(ctx, obj_slot, c.ctypes.data, g.ctypes.data, C.byref(stage), C.byref(lik),
                                     C.byref(t), _stream(stream)))
-    return dict(tile_w=t.tile_w, cta_threads=t.cta_threads, ctas_per_sm=t.ctas_per_sm, high_occupancy=t.high_occupancy)
+    return dict(tile_w=t.tile_w, cta_threads=t.cta_threads, ctas_per_sm=t.ctas_per_sm, high_occupancy=t.high_occupancy,
+                batch_chunk=t.batch_chunk)
+
+
+def b3d_score_multi(owner, items, lik: b3d_lik_params, stream=None):
+    """items: sequence of (scene ctx handle, obj_slot, n_hyp, poses_dev, loglik_dev)."""
+    arr = (b3d_score_item * len(items))(*[b3d_score_item(sc, slot, n, _addr(p), _addr(o)) for sc, slot, n, p, o in items])
+    return _check(owner, load().b3d_score_multi(owner, len(items), arr, C.byref(lik), _stream(stream)))
+
+
+def c2f_item(scene, obj_slot, centre_pose, sch: b3d_c2f_schedule, particles_dev, logw_dev, logq_dev) -> b3d_c2f_item:
+    it = b3d_c2f_item()
+    it.scene = scene
+    it.obj_slot = int(obj_slot)
+    c = np.asarray(centre_pose, dtype=np.float32).reshape(16)
+    for k in range(16):
+        it.centre_pose[k] = float(c[k])
+    it.schedule = sch
+    it.particles_dev = _addr(particles_dev)
+    it.logw_dev = _addr(logw_dev)
+    it.logq_dev = _addr(logq_dev)
+    return it
+
+
+def b3d_enumerate_multi(owner, items, lik: b3d_lik_params, stream=None):
+    """items: sequence of b3d_c2f_item (see c2f_item)."""
+    arr = (b3d_c2f_item * len(items))(*items)
+    return _check(owner, load().b3d_enumerate_multi(owner, len(items), arr, C.byref(lik), _stream(stream)))
 
 
 def b3d_set_instrumentation(ctx, flags):

@@ -100,6 +100,28 @@ struct b3d_ctx {
         return ((nt + (high_occupancy ? 4 : 0)) << 8) | (ctas_per_sm & 255);
     }
 
+    // batched form (this context as owner): descriptors, scores and resampling scratch
+    int batch_chunk = 4;
+    unsigned char *d_batch = nullptr;
+    size_t batch_cap = 0;
+    unsigned char *h_batch[2] = {nullptr, nullptr};
+    size_t h_batch_cap[2] = {0, 0};
+    cudaEvent_t batch_ev[2] = {nullptr, nullptr};
+    int batch_flip = 0;
+    float *d_bll = nullptr;
+    int64_t bll_cap = 0;
+    float2 *d_bpart = nullptr;
+    int64_t bpart_cap = 0;
+    unsigned *d_bcnt = nullptr;
+    int64_t bcnt_cap = 0;
+    unsigned long long *d_bwork = nullptr;
+    int64_t bwork_cap = 0;
+    int *d_bidx = nullptr;
+    float *d_blogq = nullptr;
+    int64_t bidx_cap = 0;
+    float *d_blogz = nullptr;
+    int64_t blogz_cap = 0;
+
     // instrumentation
     int instr = 0;
     unsigned long long *d_stats = nullptr;
@@ -390,6 +412,74 @@ b3d_status check_stage(b3d_ctx *ctx, const b3d_stage &st, int64_t *n_out) {
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 
+template <class T>
+b3d_status grow(b3d_ctx *ctx, T *&p, int64_t &cap, int64_t need, const char *what, bool zero = false) {
+    if (need <= cap && p) return B3D_OK;
+    dfree(ctx, p);
+    cap = 0;
+    b3d_status st = dalloc(ctx, &p, (size_t)std::max<int64_t>(need, 1), what);
+    if (st != B3D_OK) return st;
+    if (zero) {
+        cudaError_t e = cudaMemset(p, 0, sizeof(T) * (size_t)std::max<int64_t>(need, 1));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    }
+    cap = need;
+    return B3D_OK;
+}
+
+bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Pinned staging buffer for one batched call's descriptors (double-buffered: a buffer is
+// rewritten only after the copy that last read it has run).
+b3d_status batch_staging(b3d_ctx *ctx, size_t bytes, cudaStream_t s, unsigned char **host, int *slot) {
+    const int b = ctx->batch_flip;
+    if (ctx->batch_ev[b] && !stream_capturing(s)) cudaEventSynchronize(ctx->batch_ev[b]);
+    if (ctx->h_batch_cap[b] < bytes) {
+        // both buffers grow together, so a later call (possibly under graph capture) finds its
+        // buffer allocated
+        if (stream_capturing(s)) return fail(ctx, B3D_EINVAL, "batched call must run once with these sizes before capture");
+        for (int k = 0; k < 2; ++k) {
+            if (ctx->batch_ev[k]) cudaEventSynchronize(ctx->batch_ev[k]);
+            if (ctx->h_batch[k]) cudaFreeHost(ctx->h_batch[k]);
+            ctx->h_batch[k] = nullptr;
+            ctx->h_batch_cap[k] = 0;
+            cudaError_t e = cudaMallocHost((void **)&ctx->h_batch[k], bytes);
+            if (e != cudaSuccess) { cudaGetLastError(); return fail(ctx, B3D_ENOMEM, "pinned staging allocation failed"); }
+            ctx->h_batch_cap[k] = bytes;
+        }
+    }
+    if (ctx->batch_cap < bytes) {
+        dfree(ctx, ctx->d_batch);
+        ctx->batch_cap = 0;
+        b3d_status st = dalloc(ctx, &ctx->d_batch, bytes, "batch descriptors");
+        if (st != B3D_OK) return st;
+        ctx->batch_cap = bytes;
+    }
+    *host = ctx->h_batch[b];
+    *slot = b;
+    return B3D_OK;
+}
+
+b3d_status batch_upload(b3d_ctx *ctx, int slot, size_t bytes, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(ctx->d_batch, ctx->h_batch[slot], bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch descriptor upload");
+    if (!stream_capturing(s)) {
+        if (!ctx->batch_ev[slot]) cudaEventCreateWithFlags(&ctx->batch_ev[slot], cudaEventDisableTiming);
+        cudaEventRecord(ctx->batch_ev[slot], s);
+    }
+    ctx->batch_flip ^= 1;
+    return B3D_OK;
+}
+
 }  // namespace
 
 // ==========================================================================================
@@ -441,6 +531,10 @@ b3d_status b3d_destroy(b3d_ctx *ctx) {
         for (auto &v : ctx->pending)
             for (auto &ab : v) { cudaEventDestroy(ab.first); cudaEventDestroy(ab.second); }
         for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+        for (int k = 0; k < 2; ++k) {
+            if (ctx->h_batch[k]) cudaFreeHost(ctx->h_batch[k]);
+            if (ctx->batch_ev[k]) cudaEventDestroy(ctx->batch_ev[k]);
+        }
     }
     delete ctx;
     return B3D_OK;
@@ -1027,6 +1121,274 @@ b3d_status b3d_enumerate_c2f(b3d_ctx *ctx, int32_t obj_slot, const float *centre
     return check_launch(ctx, "enumerate_c2f");
 }
 
+b3d_status b3d_score_multi(b3d_ctx *owner, int32_t n_items, const b3d_score_item *items, const b3d_lik_params *lik,
+                           b3d_stream stream) {
+    if (!owner) return B3D_EINVAL;
+    owner->err.clear();
+    if (n_items < 1 || !items) return fail(owner, B3D_EINVAL, "need n_items >= 1 and items");
+    Lik L0;
+    b3d_status st;
+    std::vector<Lik> Ls((size_t)n_items);
+    int64_t total = 0;
+    int max_lat = 0;
+    for (int32_t i = 0; i < n_items; ++i) {
+        const b3d_score_item &it = items[i];
+        if (!it.scene || it.scene->device != owner->device)
+            return fail(owner, B3D_EINVAL, "item " + std::to_string(i) + ": scene context missing or on another device");
+        if ((st = check_slot(it.scene, it.obj_slot)) != B3D_OK) return fail(owner, st, "item " + std::to_string(i) + ": " + it.scene->err);
+        if ((st = make_lik(it.scene, lik, &Ls[i])) != B3D_OK) return fail(owner, st, it.scene->err);
+        if (it.n_hyp < 0 || it.n_hyp > INT32_MAX) return fail(owner, B3D_EINVAL, "item n_hyp out of range");
+        if (it.n_hyp > 0 && (!it.poses_dev || !it.loglik_dev || !aligned16(it.poses_dev)))
+            return fail(owner, B3D_EINVAL, "item poses_dev (16-byte aligned) and loglik_dev must be non-NULL");
+        total += it.n_hyp;
+        const MeshRec &m = it.scene->meshes[it.scene->obj_mesh[it.obj_slot]];
+        max_lat = std::max(max_lat, m.nc[0] + m.nc[1] + m.nc[2]);
+    }
+    (void)L0;
+    if (total == 0) return B3D_OK;
+    DeviceGuard g(owner->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int32_t i = 0; i < n_items; ++i) {
+        if ((st = ensure_bg(items[i].scene, items[i].obj_slot, s)) != B3D_OK) return fail(owner, st, items[i].scene->err);
+        if ((st = ensure_bg_lik(items[i].scene, items[i].obj_slot, lik, Ls[i], false, s)) != B3D_OK)
+            return fail(owner, st, items[i].scene->err);
+    }
+    if ((st = grow(owner, owner->d_bwork, owner->bwork_cap, 8, "work counters")) != B3D_OK) return st;
+    // heavier scenes first in the work queue (hypotheses x pixels)
+    std::vector<int> order((size_t)n_items);
+    for (int i = 0; i < n_items; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const double ca = (double)items[a].n_hyp * items[a].scene->cam.W * items[a].scene->cam.H;
+        const double cb = (double)items[b].n_hyp * items[b].scene->cam.W * items[b].scene->cam.H;
+        return ca > cb;
+    });
+    const size_t off_items = 0, off_begin = align16(sizeof(BatchItem) * n_items);
+    const size_t bytes = off_begin + align16(sizeof(int64_t) * (n_items + 1));
+    unsigned char *h = nullptr;
+    int slot = 0;
+    if ((st = batch_staging(owner, bytes, s, &h, &slot)) != B3D_OK) return st;
+    BatchItem *bi = reinterpret_cast<BatchItem *>(h + off_items);
+    int64_t *ib = reinterpret_cast<int64_t *>(h + off_begin);
+    int64_t acc = 0;
+    for (int k = 0; k < n_items; ++k) {
+        const b3d_score_item &it = items[order[k]];
+        BatchItem b;
+        memset(&b, 0, sizeof b);
+        b.S = scene_view(it.scene, it.obj_slot);
+        b.S.tile_w = owner->tile_w;
+        b.S.stats = nullptr;
+        b.L = Ls[order[k]];
+        b.list = PoseList{it.poses_dev};
+        b.pose_kind = 0;
+        b.n_hyp = (int)it.n_hyp;
+        b.out_ll = it.loglik_dev;
+        bi[k] = b;
+        ib[k] = acc;
+        acc += it.n_hyp;
+    }
+    ib[n_items] = acc;
+    if ((st = batch_upload(owner, slot, bytes, s)) != B3D_OK) return st;
+    {
+        Timed tm(owner, B3D_K_SCORE, s);
+        cudaMemsetAsync(owner->d_bwork, 0, sizeof(unsigned long long), s);
+        launch_score_multi(reinterpret_cast<const BatchItem *>(owner->d_batch + off_items), n_items,
+                           reinterpret_cast<const int64_t *>(owner->d_batch + off_begin), total, owner->batch_chunk,
+                           owner->d_bwork, lik->half_window, max_lat, owner->score_code(), s);
+    }
+    ++owner->launches;
+    return check_launch(owner, "score_multi");
+}
+
+b3d_status b3d_enumerate_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_item *items, const b3d_lik_params *lik,
+                               b3d_stream stream) {
+    if (!owner) return B3D_EINVAL;
+    owner->err.clear();
+    if (n_items < 1 || !items) return fail(owner, B3D_EINVAL, "need n_items >= 1 and items");
+    b3d_status st;
+    const int T = items[0].schedule.n_stages;
+    if (T < 1 || T > B3D_MAX_STAGES) return fail(owner, B3D_EINVAL, "n_stages must be in [1, 8]");
+    std::vector<Lik> Ls((size_t)n_items);
+    std::vector<int64_t> nh((size_t)n_items * T);
+    int max_lat = 0;
+    int64_t sum_m = 0;
+    for (int32_t i = 0; i < n_items; ++i) {
+        const b3d_c2f_item &it = items[i];
+        const std::string tag = "item " + std::to_string(i) + ": ";
+        if (!it.scene || it.scene->device != owner->device)
+            return fail(owner, B3D_EINVAL, tag + "scene context missing or on another device");
+        if ((st = check_slot(it.scene, it.obj_slot)) != B3D_OK) return fail(owner, st, tag + it.scene->err);
+        if ((st = make_lik(it.scene, lik, &Ls[i])) != B3D_OK) return fail(owner, st, tag + it.scene->err);
+        const b3d_c2f_schedule &sch = it.schedule;
+        if (sch.n_stages != T) return fail(owner, B3D_EINVAL, tag + "every schedule needs the same number of stages");
+        if (sch.n_particles < 1 || sch.n_particles > (1 << 20)) return fail(owner, B3D_EINVAL, tag + "n_particles out of range");
+        if (!it.particles_dev || !it.logw_dev || !it.logq_dev) return fail(owner, B3D_EINVAL, tag + "outputs must be non-NULL");
+        if (!finite_all(it.centre_pose, 16) || !finite_all(sch.grid_frame, 9)) return fail(owner, B3D_EINVAL, tag + "non-finite centre or grid frame");
+        for (int t = 0; t < T; ++t)
+            if ((st = check_stage(owner, sch.stage[t], &nh[(size_t)i * T + t])) != B3D_OK) return st;
+        const MeshRec &m = it.scene->meshes[it.scene->obj_mesh[it.obj_slot]];
+        max_lat = std::max(max_lat, m.nc[0] + m.nc[1] + m.nc[2]);
+        sum_m += sch.n_particles;
+    }
+    DeviceGuard g(owner->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<float *> rot((size_t)n_items * T);
+    for (int32_t i = 0; i < n_items; ++i) {
+        b3d_ctx *sc = items[i].scene;
+        if ((st = ensure_bg(sc, items[i].obj_slot, s)) != B3D_OK) return fail(owner, st, sc->err);
+        if ((st = ensure_bg_lik(sc, items[i].obj_slot, lik, Ls[i], false, s)) != B3D_OK) return fail(owner, st, sc->err);
+        for (int t = 0; t < T; ++t)
+            if ((st = rotation_table(sc, items[i].schedule.stage[t], &rot[(size_t)i * T + t], s)) != B3D_OK)
+                return fail(owner, st, sc->err);
+    }
+    // scratch: scores of one stage, resampling partials and counters, draws, normalisers
+    int64_t need_ll = 0, need_part = 0;
+    for (int t = 0; t < T; ++t) {
+        int64_t a = 0, b = 0;
+        for (int32_t i = 0; i < n_items; ++i) { a += nh[(size_t)i * T + t]; b += lse_blocks(nh[(size_t)i * T + t]); }
+        need_ll = std::max(need_ll, a);
+        need_part = std::max(need_part, b);
+    }
+    if ((st = grow(owner, owner->d_bll, owner->bll_cap, need_ll, "batched scores")) != B3D_OK) return st;
+    if ((st = grow(owner, owner->d_bpart, owner->bpart_cap, need_part, "batched partials")) != B3D_OK) return st;
+    if ((st = grow(owner, owner->d_bcnt, owner->bcnt_cap, n_items, "batched counters", true)) != B3D_OK) return st;
+    if ((st = grow(owner, owner->d_bwork, owner->bwork_cap, 8, "work counters")) != B3D_OK) return st;
+    if (owner->bidx_cap < sum_m) {
+        dfree(owner, owner->d_blogq);
+        int64_t c2 = 0;
+        if ((st = grow(owner, owner->d_bidx, owner->bidx_cap, sum_m, "batched draws")) != B3D_OK) return st;
+        if ((st = grow(owner, owner->d_blogq, c2, sum_m, "batched draw log-probabilities")) != B3D_OK) return st;
+    }
+    if ((st = grow(owner, owner->d_blogz, owner->blogz_cap, (int64_t)n_items * T, "batched normalisers")) != B3D_OK) return st;
+    // heavier scenes first in the work queue (first-stage hypotheses x pixels)
+    std::vector<int> order((size_t)n_items);
+    for (int i = 0; i < n_items; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const double ca = (double)nh[(size_t)a * T] * items[a].scene->cam.W * items[a].scene->cam.H;
+        const double cb = (double)nh[(size_t)b * T] * items[b].scene->cam.W * items[b].scene->cam.H;
+        return ca > cb;
+    });
+    // staging layout: centres | BatchItem[T][n] | LseItem[T][n] | SelectItem[T][n] | item_begin[T][n+1] | block_begin[T][n+1]
+    const size_t o_cent = 0;
+    const size_t o_bi = o_cent + align16(sizeof(float) * 32 * n_items);
+    const size_t o_li = o_bi + align16(sizeof(BatchItem) * (size_t)T * n_items);
+    const size_t o_si = o_li + align16(sizeof(LseItem) * (size_t)T * n_items);
+    const size_t o_ib = o_si + align16(sizeof(SelectItem) * (size_t)T * n_items);
+    const size_t o_bb = o_ib + align16(sizeof(int64_t) * (size_t)T * (n_items + 1));
+    const size_t bytes = o_bb + align16(sizeof(int) * (size_t)T * (n_items + 1));
+    unsigned char *h = nullptr;
+    int slot = 0;
+    if ((st = batch_staging(owner, bytes, s, &h, &slot)) != B3D_OK) return st;
+    unsigned char *d = owner->d_batch;
+    float *hc = reinterpret_cast<float *>(h + o_cent);
+    float *dc = reinterpret_cast<float *>(d + o_cent);
+    std::vector<int64_t> midx((size_t)n_items);
+    int64_t macc = 0;
+    for (int k = 0; k < n_items; ++k) {
+        const int i = order[k];
+        memcpy(hc + 32 * k, items[i].centre_pose, 16 * sizeof(float));
+        midx[k] = macc;
+        macc += items[i].schedule.n_particles;
+    }
+    std::vector<int64_t> totals(T);
+    std::vector<int> blocks(T);
+    for (int t = 0; t < T; ++t) {
+        BatchItem *bi = reinterpret_cast<BatchItem *>(h + o_bi) + (size_t)t * n_items;
+        LseItem *li = reinterpret_cast<LseItem *>(h + o_li) + (size_t)t * n_items;
+        SelectItem *si = reinterpret_cast<SelectItem *>(h + o_si) + (size_t)t * n_items;
+        int64_t *ib = reinterpret_cast<int64_t *>(h + o_ib) + (size_t)t * (n_items + 1);
+        int *bb = reinterpret_cast<int *>(h + o_bb) + (size_t)t * (n_items + 1);
+        int64_t acc = 0;
+        int bacc = 0;
+        int64_t pacc = 0;
+        for (int k = 0; k < n_items; ++k) {
+            const int i = order[k];
+            const b3d_c2f_item &it = items[i];
+            const b3d_stage &stg = it.schedule.stage[t];
+            const int64_t n = nh[(size_t)i * T + t];
+            PoseGrid P{};
+            P.centre = dc + 32 * k + 16 * (t & 1);
+            P.rot = rot[(size_t)i * T + t];
+            for (int q = 0; q < 9; ++q) P.G[q] = it.schedule.grid_frame[q];
+            P.n = stg.n_per_axis;
+            P.n_rot = stg.n_rot;
+            P.step = stg.step;
+            BatchItem b;
+            memset(&b, 0, sizeof b);
+            b.S = scene_view(it.scene, it.obj_slot);
+            b.S.tile_w = owner->tile_w;
+            b.S.stats = nullptr;
+            b.L = Ls[i];
+            b.grid = P;
+            b.pose_kind = 1;
+            b.n_hyp = (int)n;
+            b.out_ll = owner->d_bll + acc;
+            bi[k] = b;
+            ib[k] = acc;
+            const int nb = lse_blocks(n);
+            LseItem l;
+            memset(&l, 0, sizeof l);
+            l.ll = owner->d_bll + acc;
+            l.n = n;
+            l.n_blocks = nb;
+            l.chunk = (int)((n + nb - 1) / nb);
+            l.block_begin = bacc;
+            l.m = it.schedule.n_particles;
+            l.seed = (unsigned long long)it.schedule.seed;
+            l.stage = t;
+            l.part = owner->d_bpart + pacc;
+            l.counter = owner->d_bcnt + k;
+            l.logz = owner->d_blogz + (size_t)k * T + t;
+            l.idx = owner->d_bidx + midx[k];
+            l.logq = owner->d_blogq + midx[k];
+            li[k] = l;
+            bb[k] = bacc;
+            SelectItem sv;
+            memset(&sv, 0, sizeof sv);
+            sv.ll = l.ll;
+            sv.idx = l.idx;
+            sv.m = l.m;
+            sv.grid = P;
+            sv.logz = l.logz;
+            sv.centre_next = dc + 32 * k + 16 * ((t + 1) & 1);
+            sv.particles = it.particles_dev;
+            sv.logw = it.logw_dev;
+            sv.logq = it.logq_dev;
+            sv.seed = l.seed;
+            sv.n_stages = T;
+            si[k] = sv;
+            acc += n;
+            bacc += nb;
+            pacc += nb;
+        }
+        ib[n_items] = acc;
+        bb[n_items] = bacc;
+        totals[t] = acc;
+        blocks[t] = bacc;
+    }
+    if ((st = batch_upload(owner, slot, bytes, s)) != B3D_OK) return st;
+    cudaMemsetAsync(owner->d_bwork, 0, sizeof(unsigned long long) * 8, s);
+    for (int t = 0; t < T; ++t) {
+        {
+            Timed tm(owner, B3D_K_SCORE, s);
+            launch_score_multi(reinterpret_cast<const BatchItem *>(d + o_bi) + (size_t)t * n_items, n_items,
+                               reinterpret_cast<const int64_t *>(d + o_ib) + (size_t)t * (n_items + 1), totals[t],
+                               owner->batch_chunk, owner->d_bwork + t, lik->half_window, max_lat, owner->score_code(), s);
+        }
+        {
+            Timed tm(owner, B3D_K_RESAMPLE, s);
+            launch_lse_multi(reinterpret_cast<const LseItem *>(d + o_li) + (size_t)t * n_items, n_items, blocks[t],
+                             reinterpret_cast<const int *>(d + o_bb) + (size_t)t * (n_items + 1), owner->d_err, s);
+        }
+        {
+            Timed tm(owner, B3D_K_SELECT, s);
+            launch_select_multi(reinterpret_cast<const SelectItem *>(d + o_si) + (size_t)t * n_items, n_items,
+                                t == T - 1, s);
+        }
+        owner->launches += 3;
+    }
+    return check_launch(owner, "enumerate_multi");
+}
+
 b3d_status b3d_score_grad(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const float *poses_dev,
                           const b3d_lik_params *lik, float *loglik_dev, float *dpose_dev, float *dsigma_dev,
                           float *dpout_dev, b3d_stream stream) {
@@ -1062,6 +1424,7 @@ b3d_status b3d_get_tuning(b3d_ctx *ctx, b3d_tuning *out) {
     out->cta_threads = ctx->cta_threads;
     out->ctas_per_sm = ctx->ctas_per_sm;
     out->high_occupancy = ctx->high_occupancy;
+    out->batch_chunk = ctx->batch_chunk;
     return B3D_OK;
 }
 
@@ -1074,6 +1437,8 @@ b3d_status b3d_set_tuning(b3d_ctx *ctx, const b3d_tuning *t) {
         return fail(ctx, B3D_EINVAL, "cta_threads must be 32, 64, 128 or 256");
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return fail(ctx, B3D_EINVAL, "ctas_per_sm must be in [0, 32]");
     if (t->high_occupancy != 0 && t->high_occupancy != 1) return fail(ctx, B3D_EINVAL, "high_occupancy must be 0 or 1");
+    if (t->batch_chunk < 1 || t->batch_chunk > 1024) return fail(ctx, B3D_EINVAL, "batch_chunk must be in [1, 1024]");
+    ctx->batch_chunk = t->batch_chunk;
     ctx->tile_w = t->tile_w;
     ctx->cta_threads = t->cta_threads;
     ctx->ctas_per_sm = t->ctas_per_sm;
@@ -1109,7 +1474,7 @@ b3d_status b3d_autotune(b3d_ctx *ctx, int32_t obj_slot, const float *centre_pose
     P.n_rot = stage->n_rot;
     P.step = stage->step;
     cudaEvent_t e0 = take_event(ctx), e1 = take_event(ctx);
-    const b3d_tuning saved{ctx->tile_w, ctx->cta_threads, ctx->ctas_per_sm, ctx->high_occupancy};
+    const b3d_tuning saved{ctx->tile_w, ctx->cta_threads, ctx->ctas_per_sm, ctx->high_occupancy, ctx->batch_chunk};
     b3d_tuning win = saved;
     float win_ms = INFINITY;
     for (int hi : {0, 1})
@@ -1134,7 +1499,7 @@ b3d_status b3d_autotune(b3d_ctx *ctx, int32_t obj_slot, const float *centre_pose
                 }
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < win_ms) { win_ms = ms; win = b3d_tuning{tw, nt, cps, hi}; }
+                if (ms < win_ms) { win_ms = ms; win = b3d_tuning{tw, nt, cps, hi, ctx->batch_chunk}; }
             }
     ctx->event_pool.push_back(e0);
     ctx->event_pool.push_back(e1);

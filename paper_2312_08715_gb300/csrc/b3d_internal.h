@@ -109,6 +109,56 @@ struct PoseGrid {
     float step;
 };
 
+// One scene of a batched launch (device memory): its view, likelihood constants, the poses
+// of its hypotheses (a list or a coarse-to-fine grid) and where its scores go. Its size is a
+// multiple of 16 bytes: kernels copy descriptors of an array of them as float4.
+struct __align__(16) BatchItem {
+    SceneView S;
+    Lik L;
+    PoseList list;
+    PoseGrid grid;
+    int pose_kind;      // 0: list, 1: grid
+    int n_hyp;
+    float *out_ll;
+};
+static_assert(sizeof(BatchItem) % 16 == 0, "BatchItem must tile float4 copies");
+
+// One scene's segment of a batched log-sum-exp + resampling launch.
+struct LseItem {
+    const float *ll;
+    int64_t n;
+    int chunk, block_begin, n_blocks, m;
+    unsigned long long seed;
+    int stage;
+    float2 *part;
+    unsigned *counter;
+    float *logz;
+    int *idx;
+    float *logq;
+};
+
+// One scene's centre selection / particles of a batched coarse-to-fine stage.
+struct SelectItem {
+    const float *ll;
+    const int *idx;
+    int m;
+    PoseGrid grid;
+    const float *logz;
+    float *centre_next;
+    float *particles, *logw, *logq;
+    unsigned long long seed;
+    int n_stages;
+};
+
+// Dynamic shared memory opt-in and resident CTAs per SM of a kernel, set and queried once
+// per kernel and size (no runtime calls afterwards, e.g. while a graph is captured).
+int kernel_ctas_per_sm_impl(const void *kernel, int threads, int smem);  // cached by (kernel, threads, smem)
+
+template <class K>
+inline int kernel_ctas_per_sm(K kernel, int threads, int smem) {
+    return kernel_ctas_per_sm_impl(reinterpret_cast<const void *>(kernel), threads, smem);
+}
+
 // ---- launchers (k_render.cu) -------------------------------------------------------------
 void launch_obs_points(const Cam &cam, const float *depth, float4 *obs, cudaStream_t s);
 void launch_bg_clear(unsigned long long *bg, int64_t n, cudaStream_t s);
@@ -125,7 +175,16 @@ void launch_score_depth(const SceneView &sv, const Lik &L, const float *depth, c
 int launch_grad_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, float *dpose,
                      float *dsigma, float *dpout, int grid, cudaStream_t s);
 
+// Batched score launch over items [0, n_items) of `items` (device), their hypotheses
+// flattened in item order with item_begin[n_items + 1] (device) the offsets; CTAs take
+// `chunk` hypotheses at a time from *counter (zeroed by the caller before the launch).
+int launch_score_multi(const BatchItem *items, int n_items, const int64_t *item_begin, int64_t total, int chunk,
+                       unsigned long long *counter, int w, int max_lat, int grid, cudaStream_t s);
+
 // ---- launchers (k_c2f.cu) ----------------------------------------------------------------
+void launch_lse_multi(const LseItem *items, int n_items, int total_blocks, const int *block_begin, int *err,
+                      cudaStream_t s);
+void launch_select_multi(const SelectItem *items, int n_items, int last, cudaStream_t s);
 void launch_set16(float *dst, const float *src16_host_values, cudaStream_t s);
 void launch_rotation_set(int kind, int n, double rot_max, float *out, cudaStream_t s);
 void launch_expand(PoseGrid P, int64_t n, float *poses, cudaStream_t s);

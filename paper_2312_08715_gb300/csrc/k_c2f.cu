@@ -125,17 +125,23 @@ __device__ __forceinline__ float lse_weight(float x, float m) {
 // draw k: t = u_k S, chunk by binary search on the chunk prefix, element by a warp scan of
 // exp(ll - M) within the chunk (first inclusive prefix > t). The counter is reset for the
 // next launch.
-__global__ void __launch_bounds__(kLseThreads) k_lse_resample(const float *ll, int64_t n, int chunk, int m,
-                                                              unsigned long long seed, int stage, float2 *part,
-                                                              unsigned *counter, float *logz, int *idx, float *logq,
-                                                              int *err) {
-    __shared__ float s_red[kLseThreads / 32];
-    __shared__ float s_w[kLseMaxBlocks];
-    __shared__ float s_pre[kLseMaxBlocks];  // exclusive prefix of s_w
-    __shared__ float s_M, s_S;
-    __shared__ bool s_last;
+struct LseShared {
+    float red[kLseThreads / 32];
+    float w[kLseMaxBlocks];
+    float pre[kLseMaxBlocks];  // exclusive prefix of w
+    float M, S;
+    bool last;
+};
+
+// Block bid of nb blocks working on one score vector (see k_lse_resample).
+__device__ __forceinline__ void lse_body(LseShared &sh, int bid, int nb, const float *ll, int64_t n, int chunk, int m,
+                                         unsigned long long seed, int stage, float2 *part, unsigned *counter,
+                                         float *logz, int *idx, float *logq, int *err) {
+    float *s_red = sh.red, *s_w = sh.w, *s_pre = sh.pre;
+    float &s_M = sh.M, &s_S = sh.S;
+    bool &s_last = sh.last;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = kLseThreads / 32;
-    const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = std::min<int64_t>(n, b0 + chunk);
+    const int64_t b0 = (int64_t)bid * chunk, b1 = std::min<int64_t>(n, b0 + chunk);
 
     // phase A
     float mx = -INFINITY;
@@ -159,17 +165,17 @@ __global__ void __launch_bounds__(kLseThreads) k_lse_resample(const float *ll, i
     if (tid == 0) {
         float v = 0.f;
         for (int k = 0; k < nw; ++k) v += s_red[k];
-        part[blockIdx.x] = make_float2(mb, v);
+        part[bid] = make_float2(mb, v);
         __threadfence();
         const unsigned ticket = atomicAdd(counter, 1u);
-        s_last = ticket == gridDim.x - 1;
+        s_last = ticket == (unsigned)nb - 1;
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
 
     // phase B
-    const int B = gridDim.x;
+    const int B = nb;
     float gm = -INFINITY;
     for (int b = tid; b < B; b += kLseThreads) gm = fmaxf(gm, __ldcg(&part[b].x));
     for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
@@ -253,6 +259,31 @@ __global__ void __launch_bounds__(kLseThreads) k_lse_resample(const float *ll, i
     }
 }
 
+__global__ void __launch_bounds__(kLseThreads) k_lse_resample(const float *ll, int64_t n, int chunk, int m,
+                                                              unsigned long long seed, int stage, float2 *part,
+                                                              unsigned *counter, float *logz, int *idx, float *logq,
+                                                              int *err) {
+    __shared__ LseShared sh;
+    lse_body(sh, blockIdx.x, gridDim.x, ll, n, chunk, m, seed, stage, part, counter, logz, idx, logq, err);
+}
+
+// Batched: the blocks of every scene's score vector in one grid; block_begin[i] is the
+// first block of item i.
+__global__ void __launch_bounds__(kLseThreads) k_lse_multi(const LseItem *items, int n_items, const int *block_begin,
+                                                           int *err) {
+    __shared__ LseShared sh;
+    __shared__ int s_it;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_items - 1;
+        while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (block_begin[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1; }
+        s_it = lo;
+    }
+    __syncthreads();
+    const LseItem it = items[s_it];
+    lse_body(sh, (int)blockIdx.x - it.block_begin, it.n_blocks, it.ll, it.n, it.chunk, it.m, it.seed, it.stage, it.part,
+             it.counter, it.logz, it.idx, it.logq, err);
+}
+
 int lse_blocks(int64_t n) {
     const int64_t b = (n + kLseMinChunk - 1) / kLseMinChunk;
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, kLseMaxBlocks));
@@ -272,11 +303,10 @@ void launch_lse_resample(const float *ll, int64_t n, int m, uint64_t seed, int s
 // Not last: centre_next = pose of the drawn cell with the highest score (ties to the smaller
 // index). Last: particle k = pose of drawn cell idx_k with t += G ((u - 1/2) step), its
 // score and proposal log density score - logZ - 3 log(step).
-__global__ void k_c2f_select(const float *ll, const int *idx, int m, PoseGrid P, const float *logz, int last,
-                             unsigned long long seed, int n_stages, float *centre_next, float *particles, float *logw,
-                             float *logq) {
-    __shared__ float s_v[256];
-    __shared__ int s_i[256];
+__device__ __forceinline__ void select_body(float *s_v, int *s_i, const float *ll, const int *idx, int m,
+                                            const PoseGrid &P, const float *logz, int last, unsigned long long seed,
+                                            int n_stages, float *centre_next, float *particles, float *logw,
+                                            float *logq) {
     const int tid = threadIdx.x;
     if (!last) {
         float bv = -INFINITY;
@@ -323,6 +353,23 @@ __global__ void k_c2f_select(const float *ll, const int *idx, int m, PoseGrid P,
     }
 }
 
+__global__ void k_c2f_select(const float *ll, const int *idx, int m, PoseGrid P, const float *logz, int last,
+                             unsigned long long seed, int n_stages, float *centre_next, float *particles, float *logw,
+                             float *logq) {
+    __shared__ float s_v[256];
+    __shared__ int s_i[256];
+    select_body(s_v, s_i, ll, idx, m, P, logz, last, seed, n_stages, centre_next, particles, logw, logq);
+}
+
+// Batched: one block per scene.
+__global__ void k_select_multi(const SelectItem *items, int last) {
+    __shared__ float s_v[256];
+    __shared__ int s_i[256];
+    const SelectItem &it = items[blockIdx.x];
+    select_body(s_v, s_i, it.ll, it.idx, it.m, it.grid, it.logz, last, it.seed, it.n_stages, it.centre_next,
+                it.particles, it.logw, it.logq);
+}
+
 // ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
@@ -345,6 +392,17 @@ void launch_c2f_select(const float *ll, const int *idx, int m, PoseGrid P, const
                        int n_stages, float *centre_next, float *particles, float *logw, float *logq, cudaStream_t s) {
     k_c2f_select<<<1, 256, 0, s>>>(ll, idx, m, P, logz, last, (unsigned long long)seed, n_stages, centre_next,
                                    particles, logw, logq);
+}
+
+void launch_lse_multi(const LseItem *items, int n_items, int total_blocks, const int *block_begin, int *err,
+                      cudaStream_t s) {
+    if (n_items <= 0 || total_blocks <= 0) return;
+    k_lse_multi<<<total_blocks, kLseThreads, 0, s>>>(items, n_items, block_begin, err);
+}
+
+void launch_select_multi(const SelectItem *items, int n_items, int last, cudaStream_t s) {
+    if (n_items <= 0) return;
+    k_select_multi<<<n_items, 256, 0, s>>>(items, last);
 }
 
 void launch_copy16(const float *src, float *dst, cudaStream_t s) {

@@ -197,14 +197,17 @@ int launch_grad_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, f
                      float *dpout, int grid, cudaStream_t s) {
     if (n <= 0) return 0;
     auto kern = k_grad<PoseList>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kGradSmem);
+    const int per_sm = kernel_ctas_per_sm(kern, kThreads, kGradSmem);
     int g = grid;
     if (g <= 0) {
-        int per_sm = 0, dev = 0, sms = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, kGradSmem);
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        g = std::max(1, per_sm) * std::max(1, sms);
+        static int sms = 0;
+        if (!sms) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            sms = std::max(1, sms);
+        }
+        g = per_sm * sms;
     }
     g = (int)std::min<int64_t>(g, n);
     kern<<<g, kThreads, kGradSmem, s>>>(sv, L, P, n, ll, dpose, dsigma, dpout);

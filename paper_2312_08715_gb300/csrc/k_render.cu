@@ -16,6 +16,9 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "b3d_device.cuh"
@@ -251,6 +254,23 @@ __global__ void __launch_bounds__(kThreads) k_score_depth(SceneView S, Lik L, co
 // launchers
 // ------------------------------------------------------------------------------------------
 
+int kernel_ctas_per_sm_impl(const void *kernel, int threads, int smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, int, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(kernel, threads, smem, dev);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    per_sm = per_sm > 0 ? per_sm : 1;
+    cache.emplace(key, per_sm);
+    return per_sm;
+}
+
 static int sm_count() {
     static int n = 0;
     if (!n) {
@@ -265,9 +285,7 @@ static int sm_count() {
 template <class K>
 static int persistent_grid(K kernel, int smem, int64_t n, int grid) {
     if (grid > 0) return (int)std::min<int64_t>(grid, std::max<int64_t>(n, 1));
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
-    if (per_sm <= 0) per_sm = 1;
+    const int per_sm = kernel_ctas_per_sm(kernel, kThreads, smem);
     return (int)std::min<int64_t>((int64_t)per_sm * sm_count(), std::max<int64_t>(n, 1));
 }
 
@@ -289,6 +307,22 @@ static int launch_score(const SceneView &sv, const Lik &L, PS P, int64_t n, floa
     }
 }
 
+int launch_score_multi(const BatchItem *items, int n_items, const int64_t *item_begin, int64_t total, int chunk,
+                       unsigned long long *counter, int w, int max_lat, int grid, cudaStream_t s) {
+    if (total <= 0) return 0;
+    const int c = grid & 255;
+    switch ((grid >> 8) & 15) {
+    case 1: return launch_score_multi_nt<128, 6>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);
+    case 2: return launch_score_multi_nt<64, 10>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);
+    case 3: return launch_score_multi_nt<32, 16>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);
+    case 4: return launch_score_multi_nt<256, 4>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);
+    case 5: return launch_score_multi_nt<128, 8>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);
+    case 6: return launch_score_multi_nt<64, 14>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);
+    case 7: return launch_score_multi_nt<32, 24>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);
+    default: return launch_score_multi_nt<256, 3>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);
+    }
+}
+
 int launch_score_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, int grid, cudaStream_t s) {
     return launch_score(sv, L, P, n, ll, grid, s);
 }
@@ -301,7 +335,6 @@ int launch_render_list(const SceneView &sv, PoseList P, int64_t n, float *depth,
     if (n <= 0) return 0;
     const int smem = kRegionPx * (int)sizeof(unsigned long long);
     auto kern = k_render<PoseList>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     const int g = persistent_grid(kern, smem, n, grid);
     kern<<<g, kThreads, smem, s>>>(sv, P, n, depth, tid);
     return g;

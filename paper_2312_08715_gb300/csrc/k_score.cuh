@@ -168,305 +168,387 @@ template <int NT>
 constexpr int score_region() { return NT <= 64 ? 2048 : kRegionPx; }
 constexpr int kStageStride = 5;  // float4 per staged rectangle: conflict-free reads across owners
 
+// Per-CTA shared state of one hypothesis.
+template <int NT>
+struct ScoreShared {
+    float pose[12];
+    int bb[4];
+    int fbb[4];   // bounding box of the tile's fragments
+    int flags;    // bit 0: on screen, bit 1: rectangle path, bit 2: whole object beyond near
+    int rng[13];  // class first rectangles [6], exclusive prefix of counts [6], total
+    float red[NT / 32];
+};
+
+// Scores the hypothesis whose pose thread 0 has put in sh.pose: returns, in thread 0, the
+// sum of l_i - l_i(bg) over the pixels whose window can see the object (0 when it is off
+// screen). All threads of the CTA must call it.
+template <bool STATS, int WT, int NT>
+__device__ __forceinline__ float score_body(const SceneView &S, const Lik &L, const float *s_lut, ScoreShared<NT> &sh,
+                                            float4 *s_stage, unsigned *zb, float4 *lat, unsigned long long *cnt) {
+    constexpr int REG = score_region<NT>();
+    float *zd = reinterpret_cast<float *>(zb);  // same memory, as depths
+    const Cam &c = S.cam;
+    const MeshView &m = S.mesh;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    const int w = WT > 0 ? WT : L.w;
+    const int n_lat = m.nc[0] + m.nc[1] + m.nc[2];
+    const int nc0 = m.nc[0], nc01 = m.nc[0] + m.nc[1];
+    auto lat_off = [&](int a) { return a == 0 ? 0 : (a == 1 ? nc0 : nc01); };
+    if (tid == 0) {
+        bool front = false;
+        int f = object_bbox(m, sh.pose, c, sh.bb, &front) ? 1 : 0;
+        if (front) f |= 4;
+        if (f && front && m.n_quads > 0) {
+            f |= 2;
+            const float *R = sh.pose, *t = sh.pose + 9;
+            float o[3];
+            for (int a = 0; a < 3; ++a) o[a] = -fmaf(R[a], t[0], fmaf(R[3 + a], t[1], R[6 + a] * t[2]));
+            int tot = 0;
+            for (int cls = 0; cls < 6; ++cls) {
+                const int a = cls >> 1;
+                const float *cd = m.coords + lat_off(a);
+                const int n = m.nc[a];
+                int lo = 0, hi = n;  // first plane with coordinate >= o
+                while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] < o[a]) lo = mid + 1; else hi = mid; }
+                const int below = lo;
+                hi = n;  // first plane with coordinate > o
+                while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] <= o[a]) lo = mid + 1; else hi = mid; }
+                const int not_above = lo;
+                const int *off = m.class_off + cls * m.np1;
+                // +axis faces face the camera when their plane is below o; -axis when above
+                const int b = (cls & 1) ? off[0] : off[not_above];
+                const int e = (cls & 1) ? off[below] : off[n];
+                sh.rng[cls] = b;
+                sh.rng[6 + cls] = tot;
+                tot += e - b;
+            }
+            sh.rng[12] = tot;
+        }
+        sh.flags = f;
+    }
+    __syncthreads();
+    const int flags = sh.flags;
+    if (!(flags & 1)) return 0.f;
+    const float *pose = sh.pose;
+    const bool quad = (flags & 2) != 0, front = (flags & 4) != 0;
+    const int bx0 = sh.bb[0], bx1 = sh.bb[1], by0 = sh.bb[2], by1 = sh.bb[3];
+    if (quad) {
+        for (int k = tid; k < n_lat; k += nt) {
+            const int a = k < nc0 ? 0 : (k < nc01 ? 1 : 2);
+            const float v = m.coords[k];
+            lat[k] = make_float4(fmaf(pose[a], v, a == 0 ? pose[9] : 0.f), fmaf(pose[3 + a], v, a == 0 ? pose[10] : 0.f),
+                                 fmaf(pose[6 + a], v, a == 0 ? pose[11] : 0.f), 0.f);
+        }
+        if (STATS) cnt[1] += (unsigned long long)((n_lat - tid + nt - 1) / nt);
+    }
+    const int sx0 = max(bx0 - w, 0), sx1 = min(bx1 + w, c.W - 1);
+    const int sy0 = max(by0 - w, 0), sy1 = min(by1 + w, c.H - 1);
+    const int sw = sx1 - sx0 + 1;
+    const int tw = min(sw, S.tile_w);
+    const int th = max(1, REG / (tw + 2 * w) - 2 * w);
+    float acc = 0.f;
+    for (int ty0 = sy0; ty0 <= sy1; ty0 += th) {
+        for (int tx0 = sx0; tx0 <= sx1; tx0 += tw) {
+            const int tx1 = min(tx0 + tw - 1, sx1), ty1 = min(ty0 + th - 1, sy1);
+            const int zx0 = max(tx0 - w, 0), zx1 = min(tx1 + w, c.W - 1);
+            const int zy0 = max(ty0 - w, 0), zy1 = min(ty1 + w, c.H - 1);
+            const int zw = zx1 - zx0 + 1, zh = zy1 - zy0 + 1, nz = zw * zh;
+            const int rx0 = max(zx0, bx0), rx1 = min(zx1, bx1), ry0 = max(zy0, by0), ry1 = min(zy1, by1);
+            const bool need = rx0 <= rx1 && ry0 <= ry1;
+            for (int i = tid; i < nz; i += nt) zb[i] = 0xffffffffu;
+            if (tid == 0) { sh.fbb[0] = INT32_MAX; sh.fbb[1] = -1; sh.fbb[2] = INT32_MAX; sh.fbb[3] = -1; }
+            __syncthreads();
+            if (need) {
+                int fx0 = INT32_MAX, fx1 = -1, fy0 = INT32_MAX, fy1 = -1;  // this lane's fragments
+                auto store = [&](int x, int y, float z) {
+                    if (STATS) ++cnt[4];
+                    atomicMin(&zb[(y - zy0) * zw + (x - zx0)], __float_as_uint(z));
+                    fx0 = min(fx0, x); fx1 = max(fx1, x); fy0 = min(fy0, y); fy1 = max(fy1, y);
+                };
+                if (quad) {
+                    // Each warp takes 32 rectangles at a time: every lane projects one and
+                    // stages its screen corners, plane and pixel box; then the warp shares out
+                    // the pixel-centre candidates of all 32 among its lanes.
+                    const int total = sh.rng[12];
+                    float4 *stg = s_stage + (wid * 32) * kStageStride;
+                    for (int base = wid * 32; base < total; base += nt) {
+                        const int k = base + lane;
+                        int cand = 0;
+                        if (k < total) {
+                            int cls = 0;
+#pragma unroll
+                            for (int j = 1; j < 6; ++j) cls += k >= sh.rng[6 + j] ? 1 : 0;
+                            const uint2 q = m.quads[sh.rng[cls] + (k - sh.rng[6 + cls])];
+                            const int a = cls >> 1, p = (q.x >> 18) & 511, b0 = (q.x >> 9) & 511, c0 = q.x & 511;
+                            const int b1 = b0 + (int)((q.y >> 9) & 511), c1 = c0 + (int)(q.y & 511);
+                            const int ab = a == 2 ? 0 : a + 1, ac = a == 0 ? 2 : a - 1;
+                            // the plane term is shared by all corners, the in-plane terms take two
+                            // values each; corners are summed in x, y, z order
+                            const float4 Tp = lat[lat_off(a) + p];
+                            const float4 Tb0 = lat[lat_off(ab) + b0], Tb1 = lat[lat_off(ab) + b1];
+                            const float4 Tc0 = lat[lat_off(ac) + c0], Tc1 = lat[lat_off(ac) + c1];
+                            float4 W0, W1, W2, W3;  // corners k0 (b0,c0) k1 (b1,c0) k2 (b1,c1) k3 (b0,c1)
+                            if (a == 0) {
+                                W0 = sum3(Tp, Tb0, Tc0); W1 = sum3(Tp, Tb1, Tc0); W2 = sum3(Tp, Tb1, Tc1); W3 = sum3(Tp, Tb0, Tc1);
+                            } else if (a == 1) {
+                                W0 = sum3(Tc0, Tp, Tb0); W1 = sum3(Tc0, Tp, Tb1); W2 = sum3(Tc1, Tp, Tb1); W3 = sum3(Tc1, Tp, Tb0);
+                            } else {
+                                W0 = sum3(Tb0, Tc0, Tp); W1 = sum3(Tb1, Tc0, Tp); W2 = sum3(Tb1, Tc1, Tp); W3 = sum3(Tb0, Tc1, Tp);
+                            }
+                            const float4 C0 = screen_pt(W0.x, W0.y, W0.z, c), C1 = screen_pt(W1.x, W1.y, W1.z, c);
+                            const float4 C2 = screen_pt(W2.x, W2.y, W2.z, c), C3 = screen_pt(W3.x, W3.y, W3.z, c);
+                            if (STATS) { cnt[1] += 4; ++cnt[2]; }
+                            const float area = edge_fn(C0.x, C0.y, C1.x, C1.y, C2.x, C2.y);
+                            if (area != 0.f) {
+                                const float umin = fminf(fminf(C0.x, C1.x), fminf(C2.x, C3.x));
+                                const float umax = fmaxf(fmaxf(C0.x, C1.x), fmaxf(C2.x, C3.x));
+                                const float vmin = fminf(fminf(C0.y, C1.y), fminf(C2.y, C3.y));
+                                const float vmax = fmaxf(fmaxf(C0.y, C1.y), fmaxf(C2.y, C3.y));
+                                const int x0 = (int)ceilf(fmaxf(umin - 0.5f, (float)rx0));
+                                const int x1 = (int)floorf(fminf(umax - 0.5f, (float)rx1));
+                                const int y0 = (int)ceilf(fmaxf(vmin - 0.5f, (float)ry0));
+                                const int y1 = (int)floorf(fminf(vmax - 0.5f, (float)ry1));
+                                if (x0 <= x1 && y0 <= y1) {
+                                    cand = (x1 - x0 + 1) * (y1 - y0 + 1);
+                                    const float inv = __fdividef(1.0f, area);
+                                    const float du1 = C1.x - C0.x, dv1 = C1.y - C0.y, du2 = C2.x - C0.x, dv2 = C2.y - C0.y;
+                                    const float dz1 = C1.z - C0.z, dz2 = C2.z - C0.z;
+                                    const float al = fmaf(dz1, dv2, -(dz2 * dv1)) * inv;
+                                    const float be = fmaf(dz2, du1, -(dz1 * du2)) * inv;
+                                    stg[lane * kStageStride + 0] = make_float4(C0.x, C0.y, C1.x, C1.y);
+                                    stg[lane * kStageStride + 1] = make_float4(C2.x, C2.y, C3.x, C3.y);
+                                    stg[lane * kStageStride + 2] = make_float4(al, be, C0.z, area > 0.f ? 1.f : -1.f);
+                                    // the candidate's row is floor((k + 1/2) / width), exact in float
+                                    // for the region's sizes (margin 1/(2 width) >> rounding)
+                                    stg[lane * kStageStride + 3] = make_float4(
+                                        __int_as_float(x0), __int_as_float(y0), __int_as_float(x1 - x0 + 1),
+                                        1.0f / (float)(x1 - x0 + 1));
+                                }
+                            }
+                        }
+                        if (STATS) cnt[3] += (unsigned long long)cand;
+                        int incl = cand;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int up = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += up;
+                        }
+                        const int n_cand = __shfl_sync(0xffffffffu, incl, 31);
+                        const int excl = incl - cand;
+                        __syncwarp();
+                        for (int r0 = 0; r0 < n_cand; r0 += 32) {
+                            const int j = r0 + lane;
+                            int lo = 0, hi = 31;  // the first lane whose inclusive count exceeds j
+#pragma unroll
+                            for (int st = 0; st < 5; ++st) {
+                                const int mid = (lo + hi) >> 1;
+                                if (__shfl_sync(0xffffffffu, incl, mid) > j) hi = mid; else lo = mid + 1;
+                            }
+                            const int kk = j - __shfl_sync(0xffffffffu, excl, lo);
+                            if (j < n_cand) {
+                                const float4 A = stg[lo * kStageStride + 0], B = stg[lo * kStageStride + 1],
+                                             Pl = stg[lo * kStageStride + 2], Bx = stg[lo * kStageStride + 3];
+                                const int bw = __float_as_int(Bx.z), row = (int)(((float)kk + 0.5f) * Bx.w);
+                                const int x = __float_as_int(Bx.x) + (kk - row * bw), y = __float_as_int(Bx.y) + row;
+                                const float px = (float)x + 0.5f, py = (float)y + 0.5f, sg = Pl.w;
+                                if (sg * edge_fn(A.x, A.y, A.z, A.w, px, py) >= 0.f &&
+                                    sg * edge_fn(A.z, A.w, B.x, B.y, px, py) >= 0.f &&
+                                    sg * edge_fn(B.x, B.y, B.z, B.w, px, py) >= 0.f &&
+                                    sg * edge_fn(B.z, B.w, A.x, A.y, px, py) >= 0.f) {
+                                    const float z = __fdividef(1.0f, fmaf(Pl.x, px - A.x, fmaf(Pl.y, py - A.y, Pl.z)));
+                                    if (z <= c.far_z) store(x, y, z);
+                                }
+                            }
+                        }
+                        __syncwarp();
+                    }
+                } else {
+                    const int4 *tris = front ? m.tris_surf : m.tris_full;
+                    const int n_t = front ? m.n_surf : m.n_full;
+                    const int cull = front ? m.closed : 0;
+                    for (int t = tid; t < n_t; t += nt) {
+                        float4 A, B, C;
+                        tri_screen(m, tris[t], pose, c, A, B, C);
+                        if (STATS) { cnt[1] += 3; ++cnt[2]; }
+                        raster_tri(A, B, C, cull, rx0, rx1, ry0, ry1, c.far_z, store, STATS ? &cnt[3] : nullptr);
+                    }
+                }
+                // the tile's fragment box: pixels outside it +- w keep their background terms
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    fx0 = min(fx0, __shfl_xor_sync(0xffffffffu, fx0, o));
+                    fx1 = max(fx1, __shfl_xor_sync(0xffffffffu, fx1, o));
+                    fy0 = min(fy0, __shfl_xor_sync(0xffffffffu, fy0, o));
+                    fy1 = max(fy1, __shfl_xor_sync(0xffffffffu, fy1, o));
+                }
+                if (lane == 0 && fx1 >= 0) {
+                    atomicMin(&sh.fbb[0], fx0); atomicMax(&sh.fbb[1], fx1);
+                    atomicMin(&sh.fbb[2], fy0); atomicMax(&sh.fbb[3], fy1);
+                }
+            }
+            __syncthreads();
+            if (sh.fbb[1] < 0) {  // nothing of the object in this tile: every term is unchanged
+                __syncthreads();
+                continue;
+            }
+            // composite with the fixed objects in place (depth bits -> rendered depth) over
+            // the fragment box + 2w, the depths the scored windows read
+            const int cx0 = max(sh.fbb[0] - 2 * w, zx0), cx1 = min(sh.fbb[1] + 2 * w, zx1);
+            const int cy0 = max(sh.fbb[2] - 2 * w, zy0), cy1 = min(sh.fbb[3] + 2 * w, zy1);
+            {
+                const int cw = cx1 - cx0 + 1, n_c = cw * (cy1 - cy0 + 1);
+                const int dq = nt / cw, dr = nt - dq * cw;
+                int y = tid / cw, x = tid - y * cw;
+                for (int i = tid; i < n_c; i += nt) {
+                    const int gx = cx0 + x, gy = cy0 + y;
+                    const int zi = (gy - zy0) * zw + (gx - zx0);
+                    const unsigned bgb = (unsigned)(S.bg[(int64_t)gy * c.W + gx] >> 32);
+                    const unsigned v = min(zb[zi], bgb);
+                    zd[zi] = v == 0xffffffffu ? (L.miss_mode ? -1.f : c.far_z) : __uint_as_float(v);
+                    x += dr;
+                    y += dq;
+                    if (x >= cw) { x -= cw; ++y; }
+                }
+                if (STATS) cnt[5] += (unsigned long long)((n_c - tid + nt - 1) / nt);
+            }
+            __syncthreads();
+            // score the tile's pixels within the fragment box + w
+            const int qx0 = max(sh.fbb[0] - w, tx0), qx1 = min(sh.fbb[1] + w, tx1);
+            const int qy0 = max(sh.fbb[2] - w, ty0), qy1 = min(sh.fbb[3] + w, ty1);
+            const int tww = qx1 - qx0 + 1, thh = qy1 - qy0 + 1;
+            if (WT > 0) {
+                // thread -> (column, run of rows)
+                const int nseg = max(1, nt / tww);
+                const int rps = (thh + nseg - 1) / nseg;
+                const int seg = tid / tww, col = tid - seg * tww;
+                if (seg < nseg && col < tww) {
+                    const int ya = qy0 + seg * rps, yb = min(ya + rps - 1, qy1);
+                    if (ya <= yb)
+                        acc += score_column<WT>(S, L, s_lut, c, zd, zx0, zy0, zw, qx0 + col, ya, yb,
+                                                STATS ? &cnt[6] : nullptr, STATS ? &cnt[7] : nullptr);
+                }
+            } else {
+                const int n_tile = tww * thh;
+                const int dq = nt / tww, dr = nt - dq * tww;
+                int y = tid / tww, x = tid - y * tww;
+                for (int k = tid; k < n_tile; k += nt) {
+                    const int gx = qx0 + x, gy = qy0 + y;
+                    const int64_t gi = (int64_t)gy * c.W + gx;
+                    const float4 q = S.obs[gi];
+                    if (q.w != 0.f) {
+                        if (STATS) {
+                            ++cnt[6];
+                            cnt[7] += (unsigned long long)((min(gy + w, c.H - 1) - max(gy - w, 0) + 1) *
+                                                           (min(gx + w, c.W - 1) - max(gx - w, 0) + 1));
+                        }
+                        const float l = pixel_ell(L, s_lut, c, q, gx, gy,
+                                                  [&](int xj, int yj) { return zd[(yj - zy0) * zw + (xj - zx0)]; });
+                        acc += l - S.ell_bg[gi];
+                    }
+                    x += dr;
+                    y += dq;
+                    if (x >= tww) { x -= tww; ++y; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    return block_sum(acc, sh.red);
+}
+
 template <class PS, bool STATS, int WT, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
     k_score(SceneView S, Lik L, PS P, int64_t n_hyp, float *out_ll) {
     constexpr int REG = score_region<NT>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned *zb = reinterpret_cast<unsigned *>(smem_raw);                       // [kRegionPx]
-    float *zd = reinterpret_cast<float *>(smem_raw);                             // same memory, as depths
+    unsigned *zb = reinterpret_cast<unsigned *>(smem_raw);                        // [REG]
     float4 *lat = reinterpret_cast<float4 *>(smem_raw + REG * sizeof(unsigned));  // lattice planes
     __shared__ float s_lut[kMaxLut];
-    __shared__ float s_pose[12];
-    __shared__ int s_bb[4];
-    __shared__ int s_fbb[4];   // bounding box of the tile's fragments
-    __shared__ int s_flags;  // bit 0: on screen, bit 1: rectangle path, bit 2: whole object beyond near
-    __shared__ int s_rng[13];  // class first rectangles [6], exclusive prefix of counts [6], total
-    __shared__ float s_red[NT / 32];
+    __shared__ ScoreShared<NT> sh;
     __shared__ float4 s_stage[NT * kStageStride];  // per lane: a rectangle's corners, plane, pixel box
-
-    const Cam &c = S.cam;
-    const MeshView &m = S.mesh;
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
-    for (int i = tid; i < L.n_lut; i += nt) s_lut[i] = L.lut[i];
-    const int w = WT > 0 ? WT : L.w;
-    const int n_lat = m.nc[0] + m.nc[1] + m.nc[2];
-    const int nc0 = m.nc[0], nc01 = m.nc[0] + m.nc[1];
-    auto lat_off = [&](int a) { return a == 0 ? 0 : (a == 1 ? nc0 : nc01); };
+    const int tid = threadIdx.x;
+    for (int i = tid; i < L.n_lut; i += blockDim.x) s_lut[i] = L.lut[i];
     unsigned long long cnt[kNumStats] = {0, 0, 0, 0, 0, 0, 0, 0};
-
     for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
         __syncthreads();
         if (tid == 0) {
             if (STATS) ++cnt[0];
-            pose12(P, h, s_pose);
-            bool front = false;
-            int f = object_bbox(m, s_pose, c, s_bb, &front) ? 1 : 0;
-            if (front) f |= 4;
-            if (f && front && m.n_quads > 0) {
-                f |= 2;
-                const float *R = s_pose, *t = s_pose + 9;
-                float o[3];
-                for (int a = 0; a < 3; ++a) o[a] = -fmaf(R[a], t[0], fmaf(R[3 + a], t[1], R[6 + a] * t[2]));
-                int tot = 0;
-                for (int cls = 0; cls < 6; ++cls) {
-                    const int a = cls >> 1;
-                    const float *cd = m.coords + lat_off(a);
-                    const int n = m.nc[a];
-                    int lo = 0, hi = n;  // first plane with coordinate >= o
-                    while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] < o[a]) lo = mid + 1; else hi = mid; }
-                    const int below = lo;
-                    hi = n;  // first plane with coordinate > o
-                    while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] <= o[a]) lo = mid + 1; else hi = mid; }
-                    const int not_above = lo;
-                    const int *off = m.class_off + cls * m.np1;
-                    // +axis faces face the camera when their plane is below o; -axis when above
-                    const int b = (cls & 1) ? off[0] : off[not_above];
-                    const int e = (cls & 1) ? off[below] : off[n];
-                    s_rng[cls] = b;
-                    s_rng[6 + cls] = tot;
-                    tot += e - b;
-                }
-                s_rng[12] = tot;
-            }
-            s_flags = f;
+            pose12(P, h, sh.pose);
         }
-        __syncthreads();
-        const int flags = s_flags;
-        if (!(flags & 1)) {
-            if (tid == 0) out_ll[h] = (float)*S.ll_bg;
-            continue;
-        }
-        const float *pose = s_pose;
-        const bool quad = (flags & 2) != 0, front = (flags & 4) != 0;
-        const int bx0 = s_bb[0], bx1 = s_bb[1], by0 = s_bb[2], by1 = s_bb[3];
-        if (quad) {
-            for (int k = tid; k < n_lat; k += nt) {
-                const int a = k < nc0 ? 0 : (k < nc01 ? 1 : 2);
-                const float v = m.coords[k];
-                lat[k] = make_float4(fmaf(pose[a], v, a == 0 ? pose[9] : 0.f), fmaf(pose[3 + a], v, a == 0 ? pose[10] : 0.f),
-                                     fmaf(pose[6 + a], v, a == 0 ? pose[11] : 0.f), 0.f);
-            }
-            if (STATS) cnt[1] += (unsigned long long)((n_lat - tid + nt - 1) / nt);
-        }
-        const int sx0 = max(bx0 - w, 0), sx1 = min(bx1 + w, c.W - 1);
-        const int sy0 = max(by0 - w, 0), sy1 = min(by1 + w, c.H - 1);
-        const int sw = sx1 - sx0 + 1;
-        const int tw = min(sw, S.tile_w);
-        const int th = max(1, REG / (tw + 2 * w) - 2 * w);
-        float acc = 0.f;
-        for (int ty0 = sy0; ty0 <= sy1; ty0 += th) {
-            for (int tx0 = sx0; tx0 <= sx1; tx0 += tw) {
-                const int tx1 = min(tx0 + tw - 1, sx1), ty1 = min(ty0 + th - 1, sy1);
-                const int zx0 = max(tx0 - w, 0), zx1 = min(tx1 + w, c.W - 1);
-                const int zy0 = max(ty0 - w, 0), zy1 = min(ty1 + w, c.H - 1);
-                const int zw = zx1 - zx0 + 1, zh = zy1 - zy0 + 1, nz = zw * zh;
-                const int rx0 = max(zx0, bx0), rx1 = min(zx1, bx1), ry0 = max(zy0, by0), ry1 = min(zy1, by1);
-                const bool need = rx0 <= rx1 && ry0 <= ry1;
-                for (int i = tid; i < nz; i += nt) zb[i] = 0xffffffffu;
-                if (tid == 0) { s_fbb[0] = INT32_MAX; s_fbb[1] = -1; s_fbb[2] = INT32_MAX; s_fbb[3] = -1; }
-                __syncthreads();
-                if (need) {
-                    int fx0 = INT32_MAX, fx1 = -1, fy0 = INT32_MAX, fy1 = -1;  // this lane's fragments
-                    auto store = [&](int x, int y, float z) {
-                        if (STATS) ++cnt[4];
-                        atomicMin(&zb[(y - zy0) * zw + (x - zx0)], __float_as_uint(z));
-                        fx0 = min(fx0, x); fx1 = max(fx1, x); fy0 = min(fy0, y); fy1 = max(fy1, y);
-                    };
-                    if (quad) {
-                        // Each warp takes 32 rectangles at a time: every lane projects one and
-                        // stages its screen corners, plane and pixel box; then the warp shares out
-                        // the pixel-centre candidates of all 32 among its lanes.
-                        const int total = s_rng[12];
-                        float4 *stg = s_stage + (wid * 32) * kStageStride;
-                        for (int base = wid * 32; base < total; base += nt) {
-                            const int k = base + lane;
-                            int cand = 0;
-                            if (k < total) {
-                                int cls = 0;
-#pragma unroll
-                                for (int j = 1; j < 6; ++j) cls += k >= s_rng[6 + j] ? 1 : 0;
-                                const uint2 q = m.quads[s_rng[cls] + (k - s_rng[6 + cls])];
-                                const int a = cls >> 1, p = (q.x >> 18) & 511, b0 = (q.x >> 9) & 511, c0 = q.x & 511;
-                                const int b1 = b0 + (int)((q.y >> 9) & 511), c1 = c0 + (int)(q.y & 511);
-                                const int ab = a == 2 ? 0 : a + 1, ac = a == 0 ? 2 : a - 1;
-                                // the plane term is shared by all corners, the in-plane terms take two
-                                // values each; corners are summed in x, y, z order
-                                const float4 Tp = lat[lat_off(a) + p];
-                                const float4 Tb0 = lat[lat_off(ab) + b0], Tb1 = lat[lat_off(ab) + b1];
-                                const float4 Tc0 = lat[lat_off(ac) + c0], Tc1 = lat[lat_off(ac) + c1];
-                                float4 W0, W1, W2, W3;  // corners k0 (b0,c0) k1 (b1,c0) k2 (b1,c1) k3 (b0,c1)
-                                if (a == 0) {
-                                    W0 = sum3(Tp, Tb0, Tc0); W1 = sum3(Tp, Tb1, Tc0); W2 = sum3(Tp, Tb1, Tc1); W3 = sum3(Tp, Tb0, Tc1);
-                                } else if (a == 1) {
-                                    W0 = sum3(Tc0, Tp, Tb0); W1 = sum3(Tc0, Tp, Tb1); W2 = sum3(Tc1, Tp, Tb1); W3 = sum3(Tc1, Tp, Tb0);
-                                } else {
-                                    W0 = sum3(Tb0, Tc0, Tp); W1 = sum3(Tb1, Tc0, Tp); W2 = sum3(Tb1, Tc1, Tp); W3 = sum3(Tb0, Tc1, Tp);
-                                }
-                                const float4 C0 = screen_pt(W0.x, W0.y, W0.z, c), C1 = screen_pt(W1.x, W1.y, W1.z, c);
-                                const float4 C2 = screen_pt(W2.x, W2.y, W2.z, c), C3 = screen_pt(W3.x, W3.y, W3.z, c);
-                                if (STATS) { cnt[1] += 4; ++cnt[2]; }
-                                const float area = edge_fn(C0.x, C0.y, C1.x, C1.y, C2.x, C2.y);
-                                if (area != 0.f) {
-                                    const float umin = fminf(fminf(C0.x, C1.x), fminf(C2.x, C3.x));
-                                    const float umax = fmaxf(fmaxf(C0.x, C1.x), fmaxf(C2.x, C3.x));
-                                    const float vmin = fminf(fminf(C0.y, C1.y), fminf(C2.y, C3.y));
-                                    const float vmax = fmaxf(fmaxf(C0.y, C1.y), fmaxf(C2.y, C3.y));
-                                    const int x0 = (int)ceilf(fmaxf(umin - 0.5f, (float)rx0));
-                                    const int x1 = (int)floorf(fminf(umax - 0.5f, (float)rx1));
-                                    const int y0 = (int)ceilf(fmaxf(vmin - 0.5f, (float)ry0));
-                                    const int y1 = (int)floorf(fminf(vmax - 0.5f, (float)ry1));
-                                    if (x0 <= x1 && y0 <= y1) {
-                                        cand = (x1 - x0 + 1) * (y1 - y0 + 1);
-                                        const float inv = __fdividef(1.0f, area);
-                                        const float du1 = C1.x - C0.x, dv1 = C1.y - C0.y, du2 = C2.x - C0.x, dv2 = C2.y - C0.y;
-                                        const float dz1 = C1.z - C0.z, dz2 = C2.z - C0.z;
-                                        const float al = fmaf(dz1, dv2, -(dz2 * dv1)) * inv;
-                                        const float be = fmaf(dz2, du1, -(dz1 * du2)) * inv;
-                                        stg[lane * kStageStride + 0] = make_float4(C0.x, C0.y, C1.x, C1.y);
-                                        stg[lane * kStageStride + 1] = make_float4(C2.x, C2.y, C3.x, C3.y);
-                                        stg[lane * kStageStride + 2] = make_float4(al, be, C0.z, area > 0.f ? 1.f : -1.f);
-                                        // the candidate's row is floor((k + 1/2) / width), exact in float
-                                        // for the region's sizes (margin 1/(2 width) >> rounding)
-                                        stg[lane * kStageStride + 3] = make_float4(
-                                            __int_as_float(x0), __int_as_float(y0), __int_as_float(x1 - x0 + 1),
-                                            1.0f / (float)(x1 - x0 + 1));
-                                    }
-                                }
-                            }
-                            if (STATS) cnt[3] += (unsigned long long)cand;
-                            int incl = cand;
-#pragma unroll
-                            for (int o = 1; o < 32; o <<= 1) {
-                                const int up = __shfl_up_sync(0xffffffffu, incl, o);
-                                if (lane >= o) incl += up;
-                            }
-                            const int n_cand = __shfl_sync(0xffffffffu, incl, 31);
-                            const int excl = incl - cand;
-                            __syncwarp();
-                            for (int r0 = 0; r0 < n_cand; r0 += 32) {
-                                const int j = r0 + lane;
-                                int lo = 0, hi = 31;  // the first lane whose inclusive count exceeds j
-#pragma unroll
-                                for (int st = 0; st < 5; ++st) {
-                                    const int mid = (lo + hi) >> 1;
-                                    if (__shfl_sync(0xffffffffu, incl, mid) > j) hi = mid; else lo = mid + 1;
-                                }
-                                const int kk = j - __shfl_sync(0xffffffffu, excl, lo);
-                                if (j < n_cand) {
-                                    const float4 A = stg[lo * kStageStride + 0], B = stg[lo * kStageStride + 1],
-                                                 Pl = stg[lo * kStageStride + 2], Bx = stg[lo * kStageStride + 3];
-                                    const int bw = __float_as_int(Bx.z), row = (int)(((float)kk + 0.5f) * Bx.w);
-                                    const int x = __float_as_int(Bx.x) + (kk - row * bw), y = __float_as_int(Bx.y) + row;
-                                    const float px = (float)x + 0.5f, py = (float)y + 0.5f, sg = Pl.w;
-                                    if (sg * edge_fn(A.x, A.y, A.z, A.w, px, py) >= 0.f &&
-                                        sg * edge_fn(A.z, A.w, B.x, B.y, px, py) >= 0.f &&
-                                        sg * edge_fn(B.x, B.y, B.z, B.w, px, py) >= 0.f &&
-                                        sg * edge_fn(B.z, B.w, A.x, A.y, px, py) >= 0.f) {
-                                        const float z = __fdividef(1.0f, fmaf(Pl.x, px - A.x, fmaf(Pl.y, py - A.y, Pl.z)));
-                                        if (z <= c.far_z) store(x, y, z);
-                                    }
-                                }
-                            }
-                            __syncwarp();
-                        }
-                    } else {
-                        const int4 *tris = front ? m.tris_surf : m.tris_full;
-                        const int n_t = front ? m.n_surf : m.n_full;
-                        const int cull = front ? m.closed : 0;
-                        for (int t = tid; t < n_t; t += nt) {
-                            float4 A, B, C;
-                            tri_screen(m, tris[t], pose, c, A, B, C);
-                            if (STATS) { cnt[1] += 3; ++cnt[2]; }
-                            raster_tri(A, B, C, cull, rx0, rx1, ry0, ry1, c.far_z, store, STATS ? &cnt[3] : nullptr);
-                        }
-                    }
-                    // the tile's fragment box: pixels outside it +- w keep their background terms
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        fx0 = min(fx0, __shfl_xor_sync(0xffffffffu, fx0, o));
-                        fx1 = max(fx1, __shfl_xor_sync(0xffffffffu, fx1, o));
-                        fy0 = min(fy0, __shfl_xor_sync(0xffffffffu, fy0, o));
-                        fy1 = max(fy1, __shfl_xor_sync(0xffffffffu, fy1, o));
-                    }
-                    if (lane == 0 && fx1 >= 0) {
-                        atomicMin(&s_fbb[0], fx0); atomicMax(&s_fbb[1], fx1);
-                        atomicMin(&s_fbb[2], fy0); atomicMax(&s_fbb[3], fy1);
-                    }
-                }
-                __syncthreads();
-                if (s_fbb[1] < 0) {  // nothing of the object in this tile: every term is unchanged
-                    __syncthreads();
-                    continue;
-                }
-                // composite with the fixed objects in place (depth bits -> rendered depth) over
-                // the fragment box + 2w, the depths the scored windows read
-                const int cx0 = max(s_fbb[0] - 2 * w, zx0), cx1 = min(s_fbb[1] + 2 * w, zx1);
-                const int cy0 = max(s_fbb[2] - 2 * w, zy0), cy1 = min(s_fbb[3] + 2 * w, zy1);
-                {
-                    const int cw = cx1 - cx0 + 1, n_c = cw * (cy1 - cy0 + 1);
-                    const int dq = nt / cw, dr = nt - dq * cw;
-                    int y = tid / cw, x = tid - y * cw;
-                    for (int i = tid; i < n_c; i += nt) {
-                        const int gx = cx0 + x, gy = cy0 + y;
-                        const int zi = (gy - zy0) * zw + (gx - zx0);
-                        const unsigned bgb = (unsigned)(S.bg[(int64_t)gy * c.W + gx] >> 32);
-                        const unsigned v = min(zb[zi], bgb);
-                        zd[zi] = v == 0xffffffffu ? (L.miss_mode ? -1.f : c.far_z) : __uint_as_float(v);
-                        x += dr;
-                        y += dq;
-                        if (x >= cw) { x -= cw; ++y; }
-                    }
-                    if (STATS) cnt[5] += (unsigned long long)((n_c - tid + nt - 1) / nt);
-                }
-                __syncthreads();
-                // score the tile's pixels within the fragment box + w
-                const int qx0 = max(s_fbb[0] - w, tx0), qx1 = min(s_fbb[1] + w, tx1);
-                const int qy0 = max(s_fbb[2] - w, ty0), qy1 = min(s_fbb[3] + w, ty1);
-                const int tww = qx1 - qx0 + 1, thh = qy1 - qy0 + 1;
-                if (WT > 0) {
-                    // thread -> (column, run of rows)
-                    const int nseg = max(1, nt / tww);
-                    const int rps = (thh + nseg - 1) / nseg;
-                    const int seg = tid / tww, col = tid - seg * tww;
-                    if (seg < nseg && col < tww) {
-                        const int ya = qy0 + seg * rps, yb = min(ya + rps - 1, qy1);
-                        if (ya <= yb)
-                            acc += score_column<WT>(S, L, s_lut, c, zd, zx0, zy0, zw, qx0 + col, ya, yb,
-                                                    STATS ? &cnt[6] : nullptr, STATS ? &cnt[7] : nullptr);
-                    }
-                } else {
-                    const int n_tile = tww * thh;
-                    const int dq = nt / tww, dr = nt - dq * tww;
-                    int y = tid / tww, x = tid - y * tww;
-                    for (int k = tid; k < n_tile; k += nt) {
-                        const int gx = qx0 + x, gy = qy0 + y;
-                        const int64_t gi = (int64_t)gy * c.W + gx;
-                        const float4 q = S.obs[gi];
-                        if (q.w != 0.f) {
-                            if (STATS) {
-                                ++cnt[6];
-                                cnt[7] += (unsigned long long)((min(gy + w, c.H - 1) - max(gy - w, 0) + 1) *
-                                                               (min(gx + w, c.W - 1) - max(gx - w, 0) + 1));
-                            }
-                            const float l = pixel_ell(L, s_lut, c, q, gx, gy,
-                                                      [&](int xj, int yj) { return zd[(yj - zy0) * zw + (xj - zx0)]; });
-                            acc += l - S.ell_bg[gi];
-                        }
-                        x += dr;
-                        y += dq;
-                        if (x >= tww) { x -= tww; ++y; }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        const float tot = block_sum(acc, s_red);
+        const float tot = score_body<STATS, WT, NT>(S, L, s_lut, sh, s_stage, zb, lat, cnt);
         if (tid == 0) out_ll[h] = (float)(*S.ll_bg + (double)tot);
     }
     if (STATS)
         for (int k = 0; k < kNumStats; ++k)
             if (cnt[k]) atomicAdd(&S.stats[k], cnt[k]);
+}
+
+// Batched form: the hypotheses of many scenes (uneven image sizes, meshes and counts) in one
+// persistent launch. CTAs take chunks of hypotheses from a global counter (a work queue
+// over scenes and hypothesis chunks); when a chunk starts a new scene the CTA stages that
+// scene's descriptor in shared memory. Scores are bit-identical to the single-scene kernel.
+template <int WT, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    k_score_multi(const BatchItem *items, int n_items, const int64_t *item_begin, int64_t total, int chunk,
+                  unsigned long long *counter) {
+    constexpr int REG = score_region<NT>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned *zb = reinterpret_cast<unsigned *>(smem_raw);
+    float4 *lat = reinterpret_cast<float4 *>(smem_raw + REG * sizeof(unsigned));
+    __shared__ __align__(16) BatchItem s_item;
+    __shared__ ScoreShared<NT> sh;
+    __shared__ float4 s_stage[NT * kStageStride];
+    __shared__ long long s_work[2];
+    const int tid = threadIdx.x;
+    int cur = -1;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_work[0] = (long long)atomicAdd(counter, 1ull) * chunk;
+        __syncthreads();
+        const int64_t b = s_work[0];
+        if (b >= total) break;
+        const int64_t e = min(b + (int64_t)chunk, total);
+        for (int64_t g = b; g < e;) {
+            __syncthreads();
+            if (tid == 0) {  // the scene holding hypothesis g
+                int lo = 0, hi = n_items - 1;
+                while (lo < hi) { const int mid = (lo + hi + 1) >> 1; if (item_begin[mid] <= g) lo = mid; else hi = mid - 1; }
+                s_work[1] = lo;
+            }
+            __syncthreads();
+            const int it = (int)s_work[1];
+            if (it != cur) {
+                const float4 *src = reinterpret_cast<const float4 *>(items + it);
+                float4 *dst = reinterpret_cast<float4 *>(&s_item);
+                for (int k = tid; k < (int)(sizeof(BatchItem) / sizeof(float4)); k += blockDim.x) dst[k] = src[k];
+                cur = it;
+                __syncthreads();
+            }
+            const int64_t ib = item_begin[it], ie = min(item_begin[it + 1], e);
+            for (; g < ie; ++g) {
+                __syncthreads();
+                if (tid == 0) {
+                    if (s_item.pose_kind == 0) pose12(s_item.list, g - ib, sh.pose);
+                    else pose12(s_item.grid, g - ib, sh.pose);
+                }
+                const float tot = score_body<false, WT, NT>(s_item.S, s_item.L, s_item.L.lut, sh, s_stage, zb, lat, nullptr);
+                if (tid == 0) s_item.out_ll[g - ib] = (float)(*s_item.S.ll_bg + (double)tot);
+            }
+        }
+    }
+}
+
+template <int NT, int MINB>
+int launch_score_multi_nt(const BatchItem *items, int n_items, const int64_t *item_begin, int64_t total, int chunk,
+                          unsigned long long *counter, int w, int max_lat, int grid, cudaStream_t s) {
+    const int smem = score_region<NT>() * (int)sizeof(unsigned) + max_lat * (int)sizeof(float4);
+    auto kern = w == 1 ? k_score_multi<1, NT, MINB> : (w == 2 ? k_score_multi<2, NT, MINB> : k_score_multi<0, NT, MINB>);
+    const int per_sm = kernel_ctas_per_sm(kern, NT, smem);
+    const int ctas = grid > 0 ? std::min(grid, per_sm) : per_sm;
+    const int64_t n_chunks = (total + chunk - 1) / chunk;
+    const int g = (int)std::min<int64_t>((int64_t)ctas * score_sm_count(), std::max<int64_t>(n_chunks, 1));
+    kern<<<g, NT, smem, s>>>(items, n_items, item_begin, total, chunk, counter);
+    return g;
 }
 
 template <class PS, int NT, int MINB>
@@ -479,10 +561,7 @@ int launch_score_nt(const SceneView &sv, const Lik &L, PS P, int64_t n, float *l
     if constexpr (ST) {
         if (sv.stats) kern = L.w == 1 ? k_score<PS, true, 1, NT, MINB> : (L.w == 2 ? k_score<PS, true, 2, NT, MINB> : k_score<PS, true, 0, NT, MINB>);
     }
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
-    per_sm = std::max(per_sm, 1);
+    const int per_sm = kernel_ctas_per_sm(kern, NT, smem);
     // grid > 0: CTAs per SM requested by the tuning (capped by occupancy); 0: occupancy
     const int ctas = grid > 0 ? std::min(grid, per_sm) : per_sm;
     const int g = (int)std::min<int64_t>((int64_t)ctas * score_sm_count(), std::max<int64_t>(n, 1));

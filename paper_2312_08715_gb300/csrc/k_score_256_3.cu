@@ -7,4 +7,6 @@ template int launch_score_nt<PoseList, 256, 3>(const SceneView &, const Lik &, P
                                                   cudaStream_t);
 template int launch_score_nt<PoseGrid, 256, 3>(const SceneView &, const Lik &, PoseGrid, int64_t, float *, int,
                                                   cudaStream_t);
+template int launch_score_multi_nt<256, 3>(const BatchItem *, int, const int64_t *, int64_t, int,
+                                             unsigned long long *, int, int, int, cudaStream_t);
 }  // namespace b3d

@@ -7,4 +7,6 @@ template int launch_score_nt<PoseList, 64, 10>(const SceneView &, const Lik &, P
                                                   cudaStream_t);
 template int launch_score_nt<PoseGrid, 64, 10>(const SceneView &, const Lik &, PoseGrid, int64_t, float *, int,
                                                   cudaStream_t);
+template int launch_score_multi_nt<64, 10>(const BatchItem *, int, const int64_t *, int64_t, int,
+                                             unsigned long long *, int, int, int, cudaStream_t);
 }  // namespace b3d

@@ -68,6 +68,7 @@ int main(void) {
          offsetof(b3d_c2f_schedule, seed), offsetof(b3d_c2f_schedule, grid_frame));
   printf("%zu %zu\\n", offsetof(b3d_lik_params, volume), offsetof(b3d_lik_params, miss_mode));
   printf("%zu %zu\\n", sizeof(b3d_tuning), offsetof(b3d_tuning, high_occupancy));
+  printf("%zu %zu %zu\\n", sizeof(b3d_score_item), sizeof(b3d_c2f_item), offsetof(b3d_c2f_item, particles_dev));
   return 0;
 }
 """)
@@ -80,7 +81,8 @@ int main(void) {
             b3d.b3d_c2f_schedule.stage.offset, b3d.b3d_c2f_schedule.n_particles.offset,
             b3d.b3d_c2f_schedule.seed.offset, b3d.b3d_c2f_schedule.grid_frame.offset,
             b3d.b3d_lik_params.volume.offset, b3d.b3d_lik_params.miss_mode.offset,
-            C.sizeof(b3d.b3d_tuning), b3d.b3d_tuning.high_occupancy.offset]
+            C.sizeof(b3d.b3d_tuning), b3d.b3d_tuning.high_occupancy.offset,
+            C.sizeof(b3d.b3d_score_item), C.sizeof(b3d.b3d_c2f_item), b3d.b3d_c2f_item.particles_dev.offset]
     assert got == want
 
 

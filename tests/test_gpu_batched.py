@@ -1,0 +1,141 @@
+"""Batched form: many scenes of uneven image size, mesh and hypothesis count in one
+persistent launch (work queue over scene and hypothesis chunks) and a batched
+coarse-to-fine enumeration, captured into a CUDA graph. Results must equal the
+single-scene calls bit for bit (same kernel body, same launch shape) and, on a sample,
+the oracle within the parity tolerance."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2312_08715_gb300 import synth
+from _scenes import gpu_context, jitter_poses, ll_tolerance, observed
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _scenes(orc):
+    """Four scenes: 64x48 single object, tabletops at 80x60, 160x120 and 124x93."""
+    out = []
+    wl = synth.single_object_workload(1)
+    out.append((wl, observed(orc, wl), 0))
+    for trial, (W, H) in enumerate([(80, 60), (160, 120), (124, 93)]):
+        wl = synth.tabletop_workload(10 + trial, n_objects=2 + trial, width=W, height=H, f=0.9375 * W)
+        out.append((wl, observed(orc, wl), wl.slot))
+    return out
+
+
+def test_score_multi_equals_single_scene_calls(orc):
+    from paper_2312_08715_gb300 import b3d
+    scenes = _scenes(orc)
+    rng = np.random.default_rng(31)
+    counts = [1000, 37, 2500, 129]
+    ctxs, poses, singles = [], [], []
+    for (wl, obs, slot), n in zip(scenes, counts):
+        ctx = gpu_context(wl.scene, obs)
+        b3d.b3d_set_tuning(ctx.h, 64, 128, 0, 1, 4)
+        P = torch.as_tensor(jitter_poses(rng, wl.hidden, n, trans=0.02, rot_deg=8), device="cuda")
+        singles.append(_np(ctx.score(slot, P, wl.lik)))
+        ctxs.append(ctx)
+        poses.append(P)
+    owner = b3d.Context(0)
+    for chunk in (1, 4, 64):
+        b3d.b3d_set_tuning(owner.h, 64, 128, 0, 1, chunk)
+        outs = [torch.full((n,), float("nan"), device="cuda") for n in counts]
+        items = [(c.h, sc[2], n, p, o) for c, sc, n, p, o in zip(ctxs, scenes, counts, poses, outs)]
+        b3d.b3d_score_multi(owner.h, items, b3d.lik_params(**scenes[0][0].lik), owner.stream)
+        owner.sync()
+        for k in range(len(scenes)):
+            np.testing.assert_array_equal(_np(outs[k]), singles[k])
+    # one scene against the oracle on a sample
+    wl, obs, slot = scenes[2]
+    sel = np.arange(0, 2500, 97)
+    ref = orc.score(wl.scene, slot, _np(poses[2])[sel], wl.lik, obs)
+    err = np.abs(singles[2][sel].astype(np.float64) - ref["ll"])
+    assert (err <= ll_tolerance(ref)).all()
+    for c in ctxs + [owner]:
+        c.close()
+
+
+def _stages():
+    return [synth.StageSpec(5, 0.01, 1, 4, math.radians(6)), synth.StageSpec(5, 0.003, 1, 3, math.radians(2))]
+
+
+def test_enumerate_multi_equals_single_and_replays_as_graph(orc):
+    from paper_2312_08715_gb300 import b3d
+    scenes = _scenes(orc)
+    M = [16, 8, 32, 5]
+    ctxs, items, outs, singles = [], [], [], []
+    for k, ((wl, obs, slot), m) in enumerate(zip(scenes, M)):
+        ctx = gpu_context(wl.scene, obs)
+        b3d.b3d_set_tuning(ctx.h, 64, 128, 0, 1, 4)
+        centre = wl.hidden.astype(np.float64).copy()
+        centre[:3, 3] += [0.01, -0.008, 0.012]
+        G = wl.grid_frame
+        singles.append([_np(x).copy() for x in ctx.enumerate_c2f(slot, centre.astype(np.float32), _stages(), wl.lik,
+                                                                 m, 100 + k, G)])
+        ctx.sync()
+        o = (torch.empty((m, 4, 4), device="cuda"), torch.empty(m, device="cuda"), torch.empty(m, device="cuda"))
+        outs.append(o)
+        sch = b3d.schedule(_stages(), m, 100 + k, G)
+        items.append(b3d.c2f_item(ctx.h, slot, centre.astype(np.float32), sch, *o))
+        ctxs.append(ctx)
+    owner = b3d.Context(0)
+    b3d.b3d_set_tuning(owner.h, 64, 128, 0, 1, 4)
+    lik = b3d.lik_params(**scenes[0][0].lik)
+    b3d.b3d_enumerate_multi(owner.h, items, lik, owner.stream)  # sizes the scratch
+    owner.sync()
+    for k in range(len(scenes)):
+        for got, want in zip(outs[k], singles[k]):
+            np.testing.assert_array_equal(_np(got), want)
+    # capture the whole batched schedule into a CUDA graph and replay it
+    for o in outs:
+        for t in o:
+            t.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            b3d.b3d_enumerate_multi(owner.h, items, lik, side)
+    for rep in range(2):
+        for o in outs:
+            for t in o:
+                t.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for k in range(len(scenes)):
+            for got, want in zip(outs[k], singles[k]):
+                np.testing.assert_array_equal(_np(got), want)
+    owner.sync()
+    for c in ctxs + [owner]:
+        c.close()
+
+
+def test_enumerate_c2f_captures_as_graph(orc, single_object):
+    from paper_2312_08715_gb300 import b3d
+    wl = single_object
+    ctx = gpu_context(wl.scene, observed(orc, wl))
+    centre = wl.hidden.copy()
+    out = (torch.empty((8, 4, 4), device="cuda"), torch.empty(8, device="cuda"), torch.empty(8, device="cuda"))
+    eager = [_np(x).copy() for x in ctx.enumerate_c2f(0, centre, _stages(), wl.lik, 8, 5, np.eye(3), out=out)]
+    ctx.sync()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            b3d.b3d_enumerate_c2f(ctx.h, 0, centre, b3d.schedule(_stages(), 8, 5, np.eye(3)), b3d.lik_params(**wl.lik),
+                                  *out, side)
+    for t in out:
+        t.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    for got, want in zip(out, eager):
+        np.testing.assert_array_equal(_np(got), want)
+    ctx.close()
