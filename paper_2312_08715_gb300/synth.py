@@ -223,12 +223,15 @@ def single_object_workload(trial: int = 0) -> Workload:
 def _blob_cells(rng, pitch, lo=2000, hi=8000):
     """Union of 1-3 random ellipsoids voxelised at ``pitch``; retried until the voxel
     count lies in [lo, hi]. Returns integer cells with the lowest layer at k = 0."""
+    # ellipsoid size scaled to the requested count (1 for the default 2,000-8,000 voxels of
+    # 5 mm, whose 2.5-7.5 cm semi-axes suit it)
+    scale = ((lo + hi) / 2.0 / 5000.0) ** (1.0 / 3.0) * (pitch / 0.005)
     for _ in range(1000):
         n_ell = int(rng.integers(1, 4))
         ells = []
         for _e in range(n_ell):
-            axes = rng.uniform(0.025, 0.075, size=3)
-            centre = np.concatenate([rng.uniform(-0.03, 0.03, size=2), [axes[2]]])
+            axes = rng.uniform(0.025, 0.075, size=3) * scale
+            centre = np.concatenate([rng.uniform(-0.03, 0.03, size=2) * scale, [axes[2]]])
             ells.append((centre, axes))
         ext = max(float(np.max(np.abs(c) + a)) for c, a in ells) + pitch
         n = int(math.ceil(ext / pitch))
@@ -268,12 +271,17 @@ def tabletop_workload(trial: int = 0, n_objects: int = 5, width=160, height=120,
         cells = _blob_cells(rng, pitch, vox_lo, vox_hi)
         objects.append(voxel_mesh(cells, pitch, origin=(0.0, 0.0, 0.0)))
 
+    half = [0.3 + 0.03 * max(0, n_objects - 5)]
+
     def place(radius):
-        for _ in range(10000):
-            xy = rng.uniform(-0.3, 0.3, size=2)
-            if all(np.linalg.norm(xy - p) > radius + r for p, r in placed):
-                placed.append((xy, radius))
-                return xy
+        # rejection sampling in a square that widens when it gets crowded
+        for _ in range(20):
+            for _ in range(2000):
+                xy = rng.uniform(-half[0], half[0], size=2)
+                if all(np.linalg.norm(xy - p) > radius + r for p, r in placed):
+                    placed.append((xy, radius))
+                    return xy
+            half[0] *= 1.2
         raise RuntimeError("placement failed")
 
     occ_r = 0.5 * math.hypot(occ_size[0], occ_size[1])
@@ -324,3 +332,26 @@ def random_ll(rng, n: int, spread: float = 30.0) -> np.ndarray:
     peaks = rng.integers(0, n, size=k)
     ll[peaks] = rng.uniform(-spread, 0.0, size=k)
     return ll.astype(np.float32)
+
+
+def batched_workloads(n_scenes: int = 64, seed_base: int = 2000, pitch: float = 0.005):
+    """Independent tabletop scenes for the batched form, each drawn log-uniform: 1-8
+    objects, 500-20,000 voxels per object, image width 80-320 (4:3, fx = 0.9375 W),
+    1,000-50,000 hypotheses per coarse-to-fine stage (two stages: a 5^3 translation grid of
+    2 cm then 5 mm, times a perturbation set sized to the count)."""
+    out = []
+    for k in range(n_scenes):
+        rng = np.random.default_rng(seed_base + k)
+        n_obj = int(rng.integers(1, 9))
+        W = int(round(float(np.exp(rng.uniform(np.log(80), np.log(320)))) / 4.0)) * 4
+        H = W * 3 // 4
+        v = float(np.exp(rng.uniform(np.log(500), np.log(20000))))
+        n_hyp = float(np.exp(rng.uniform(np.log(1000), np.log(50000))))
+        n_rot = max(1, int(round(n_hyp / 125.0)))
+        wl = tabletop_workload(trial=k, n_objects=n_obj, width=W, height=H, f=0.9375 * W,
+                               vox_lo=int(0.8 * v), vox_hi=int(1.25 * v), seed_base=seed_base + 100000)
+        wl.stages = [StageSpec(5, 0.02, 1, n_rot, math.radians(10.0)),
+                     StageSpec(5, 0.005, 1, n_rot, math.radians(3.0))]
+        wl.name = f"batched scene {k}: {n_obj} objects, {W}x{H}, ~{int(v)} voxels, {125 * n_rot} hypotheses/stage"
+        out.append(wl)
+    return out
