@@ -47,6 +47,8 @@ typedef int32_t b3d_status;
 #define B3D_ETIMEOUT (-5)  /* a bounded wait expired */
 #define B3D_ENOTFOUND (-6) /* unknown mesh id or object slot */
 #define B3D_EDEVICE (-7)   /* a kernel raised the context's device error flag */
+#define B3D_EBUSY (-8)     /* no free slot (server sessions, or a session's frame queue) */
+#define B3D_ECLOSED (-9)   /* the session was closed (or the server stopped) before the frame ran */
 
 #define B3D_MAX_STAGES 8
 #define B3D_MAX_HALF_WINDOW 7
@@ -249,16 +251,19 @@ b3d_status b3d_score_multi(b3d_ctx *owner, int32_t n_items, const b3d_score_item
 /* Batched coarse-to-fine enumeration: every item runs b3d_enumerate_c2f on its own scene and
  * schedule (all schedules with the same number of stages); each stage is one batched score
  * launch, one batched log-sum-exp + resampling launch and one batched selection launch over
- * all items. Outputs per item as b3d_enumerate_c2f. Same graph-capture rule as
- * b3d_score_multi. */
+ * all items. Outputs per item as b3d_enumerate_c2f. An item's centre may be read from
+ * device memory (centre_dev, copied before the first stage, so it may point into the
+ * item's own particles_dev). Same graph-capture rule as b3d_score_multi. */
 typedef struct {
     b3d_ctx *scene;
     int32_t obj_slot;
-    float centre_pose[16];
+    float centre_pose[16];        /* host centre, used when centre_dev is NULL */
+    const float *centre_dev;      /* device [16] centre (e.g. a previous particle), or NULL */
     b3d_c2f_schedule schedule;
     float *particles_dev;  /* [M, 16] */
     float *logw_dev;       /* [M] */
     float *logq_dev;       /* [M] */
+    float *map_dev;        /* [16] or NULL: the highest-scoring cell drawn at the last stage */
 } b3d_c2f_item;
 
 b3d_status b3d_enumerate_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_item *items, const b3d_lik_params *lik,
@@ -329,6 +334,159 @@ b3d_status b3d_work_counters(b3d_ctx *ctx, int64_t *out);
 
 /* Wait for the stream, then report (and clear) the context's device error flag. */
 b3d_status b3d_sync(b3d_ctx *ctx, b3d_stream stream);
+
+/* ==========================================================================================
+ * Serving: a tracking server (the particle-filter tracking loop of Sec. IV, Table 1,
+ * applied to object poses) that accepts depth frames from many concurrent sessions and
+ * batches them continuously.
+ *
+ * Each session owns a scene (its meshes, camera, fixed objects) and, on the device, the
+ * pose estimate and particles of each tracked object. A frame runs, for every tracked
+ * object k, one coarse-to-fine enumeration (the server's schedule) centred on object k's
+ * current estimate, scored against the new depth frame with every other object held at
+ * its estimate from the previous frame; object k's new estimate is the highest-scoring
+ * cell drawn at the last stage, and its particles are kept on the device. All tracked
+ * objects of a frame are enumerated together, in one batched launch.
+ *
+ * Continuous batching: a worker thread issues a batch as soon as fewer than max_inflight
+ * batches are on the device and any session has a queued frame. A batch takes the oldest
+ * queued frame of every ready session (at most one frame per session, at most
+ * max_batch_items tracked objects), so frames that arrive while others run join the next
+ * batch rather than waiting for a fixed schedule. Frames of one session run in submission
+ * order. Every result is independent of which other frames shared its batch: the kernels
+ * compute each item on its own, with a launch shape fixed at server creation, and the
+ * random draws of frame f, object k come from b3d_frame_seed(session seed, f, k).
+ *
+ * Admission: a session is admitted only if its device memory (measured after building
+ * its meshes, scene and per-object buffers) fits in the server's HBM budget next to the
+ * sessions already admitted and the batch scratch reserved at creation; otherwise
+ * b3d_session_open returns B3D_EBUDGET (after waiting up to its timeout for a close).
+ *
+ * Thread safety: every b3d_server_* / b3d_session_* / b3d_frame_* call may be made from
+ * any host thread. Closing a session or destroying the server frees device memory, which
+ * waits for the device.
+ * ========================================================================================== */
+typedef struct b3d_server b3d_server;
+
+typedef struct {
+    int32_t max_sessions;     /* session slots, >= 1 */
+    int32_t max_batch_items;  /* tracked objects per batched launch, >= 1 (batch scratch is
+                                 reserved for this many at creation) */
+    int32_t max_batch_frames; /* frames per batched launch (0: no limit; 1: no batching across
+                                 sessions) */
+    int32_t max_inflight;     /* batches on the device at once, 1..2 (2: the next batch is
+                                 issued while one runs) */
+    int32_t queue_depth;      /* frames a session may have submitted and not completed, 1..64 */
+    int32_t device_timeout_ms; /* a batch not finished after this long fails the server
+                                  (B3D_ETIMEOUT); 0 = 60000 */
+    b3d_lik_params lik;       /* likelihood of every session */
+    b3d_c2f_schedule schedule; /* per object and frame; its seed is replaced by b3d_frame_seed */
+    b3d_tuning tuning;        /* launch shape of the score kernel (tile_w 0: library default) */
+} b3d_server_config;
+
+/* One session's scene. Object k is the mesh verts[k] [n_v[k], 3] / faces[k] [n_f[k], 3]
+ * (host, read during the call; mesh_flags[k] as b3d_load_mesh, or all 0 when NULL) at pose
+ * poses[16 k ..]. Objects 0 .. n_track-1 are tracked: poses[] is their estimate before
+ * frame 0. Objects n_track .. n_obj-1 (a table, walls) stay where poses[] puts them.
+ * grid_frame (row-major cam_from_grid) orients this session's translation grids; all zero
+ * takes the server schedule's. */
+typedef struct {
+    b3d_intrinsics intr;
+    int32_t n_obj;
+    int32_t n_track;  /* 1 .. n_obj */
+    const float *const *verts;
+    const int64_t *n_v;
+    const int32_t *const *faces;
+    const int64_t *n_f;
+    const int32_t *mesh_flags;
+    const float *poses;
+    uint64_t seed;
+    float grid_frame[9];
+} b3d_session_desc;
+
+/* Completion record of one frame. */
+typedef struct {
+    int64_t ticket;
+    int32_t session;
+    int32_t status;          /* B3D_OK, B3D_EDEVICE (a kernel flag), B3D_ECLOSED or B3D_ETIMEOUT */
+    int64_t frame_index;     /* 0-based within the session */
+    double latency_ms;       /* b3d_frame_submit entry -> result on the host */
+    double queue_ms;         /* b3d_frame_submit entry -> issued to the device */
+    int32_t batch_frames;    /* frames in the batch it ran in */
+    int32_t n_track;         /* poses returned */
+} b3d_frame_result;
+
+typedef struct {
+    int64_t frames_done;     /* completed with B3D_OK */
+    int64_t frames_failed;   /* completed with another status */
+    int64_t batches;
+    int64_t hypotheses;      /* scored by completed batches */
+    int32_t sessions;
+    int32_t max_batch_frames_seen;
+    uint64_t hbm_budget, hbm_reserved; /* bytes: budget; sessions + batch scratch admitted */
+    uint64_t hbm_used;       /* bytes the server's contexts hold now */
+} b3d_server_stats;
+
+/* Create a server on `device` with at most hbm_budget_bytes of device memory (0: no
+ * limit); starts its worker and completion threads. B3D_EBUDGET if the batch scratch
+ * alone does not fit. */
+b3d_status b3d_server_create(b3d_server **out, int32_t device, uint64_t hbm_budget_bytes,
+                             const b3d_server_config *cfg);
+
+/* Cancel queued frames (B3D_ECLOSED), wait for batches on the device (bounded by the
+ * device timeout), stop the threads and free everything. */
+b3d_status b3d_server_destroy(b3d_server *srv);
+
+/* Message of the calling thread's last failed server call ("" after success). */
+const char *b3d_server_last_error(void);
+
+/* Build and admit a session. Waits up to timeout_ms (0: no wait) for a slot or budget to
+ * free up; B3D_EBUSY (no slot) or B3D_EBUDGET (no memory) when it does not. */
+b3d_status b3d_session_open(b3d_server *srv, const b3d_session_desc *desc, int32_t timeout_ms,
+                            int32_t *session_id);
+
+/* Cancel the session's queued frames (their results report B3D_ECLOSED), wait for its
+ * frames on the device (B3D_ETIMEOUT after the device timeout) and free it. */
+b3d_status b3d_session_close(b3d_server *srv, int32_t session_id);
+
+/* Queue a depth frame (host [H, W] float32, copied during the call; pixels <= 0 or not
+ * finite are not scored). Waits up to timeout_ms for a free queue entry (B3D_EBUSY when
+ * none frees). *ticket identifies the frame. */
+b3d_status b3d_frame_submit(b3d_server *srv, int32_t session_id, const float *depth, int32_t timeout_ms,
+                            int64_t *ticket);
+
+/* Wait up to timeout_ms for frame `ticket` (B3D_ETIMEOUT if not finished; B3D_ENOTFOUND if
+ * unknown or already collected). On return the result is collected: *res is filled and,
+ * when poses is non-NULL, poses [n_track, 16] (room for poses_capacity floats; B3D_EINVAL,
+ * result kept, when too small) receives the new estimates. The call's status is B3D_OK
+ * whenever a result was returned; the frame's own status is res->status. */
+b3d_status b3d_frame_wait(b3d_server *srv, int64_t ticket, int32_t timeout_ms, b3d_frame_result *res,
+                          float *poses, int32_t poses_capacity);
+
+/* Like b3d_frame_wait for whichever uncollected frame finished first. */
+b3d_status b3d_frame_next(b3d_server *srv, int32_t timeout_ms, b3d_frame_result *res, float *poses,
+                          int32_t poses_capacity);
+
+/* Stop (1) or resume (0) issuing new batches; batches on the device still finish. Frames
+ * keep queueing while paused. */
+b3d_status b3d_server_pause(b3d_server *srv, int32_t paused);
+
+b3d_status b3d_server_get_stats(b3d_server *srv, b3d_server_stats *out);
+
+/* Checkpoint of a session's tracking state: estimates [n_track, 16], particles
+ * [n_track, M, 16] and their log scores [n_track, M] (M = schedule.n_particles; host
+ * arrays; NULL skips one), and the index of the next frame. The session must be idle (no
+ * queued or running frame): B3D_EBUSY otherwise. */
+b3d_status b3d_session_export(b3d_server *srv, int32_t session_id, float *poses, float *particles, float *logw,
+                              int64_t *next_frame);
+/* Restore a checkpoint into an idle session of the same shape (the next frame continues
+ * from it exactly as the exporting session would have). */
+b3d_status b3d_session_import(b3d_server *srv, int32_t session_id, const float *poses, const float *particles,
+                              const float *logw, int64_t next_frame);
+
+/* Seed of the random draws of frame `frame` of object `obj` in a session seeded `seed`
+ * (SplitMix64 finaliser over the three values; pure host function). */
+uint64_t b3d_frame_seed(uint64_t seed, int64_t frame, int32_t obj);
 
 #ifdef __cplusplus
 }

@@ -27,6 +27,8 @@ B3D_ECUDA = -4
 B3D_ETIMEOUT = -5
 B3D_ENOTFOUND = -6
 B3D_EDEVICE = -7
+B3D_EBUSY = -8
+B3D_ECLOSED = -9
 B3D_MAX_STAGES = 8
 B3D_MAX_HALF_WINDOW = 7
 B3D_MESH_CLOSED = 1
@@ -37,7 +39,7 @@ B3D_K_SCORE, B3D_K_RENDER, B3D_K_SCORE_DEPTH, B3D_K_RESAMPLE, B3D_K_SELECT, B3D_
 B3D_K_COUNT = 7
 
 _STATUS = {0: "B3D_OK", -1: "B3D_EINVAL", -2: "B3D_ENOMEM", -3: "B3D_EBUDGET", -4: "B3D_ECUDA",
-           -5: "B3D_ETIMEOUT", -6: "B3D_ENOTFOUND", -7: "B3D_EDEVICE"}
+           -5: "B3D_ETIMEOUT", -6: "B3D_ENOTFOUND", -7: "B3D_EDEVICE", -8: "B3D_EBUSY", -9: "B3D_ECLOSED"}
 
 
 class b3d_intrinsics(C.Structure):
@@ -72,8 +74,33 @@ class b3d_score_item(C.Structure):
 
 class b3d_c2f_item(C.Structure):
     _fields_ = [("scene", C.c_void_p), ("obj_slot", C.c_int32), ("centre_pose", C.c_float * 16),
-                ("schedule", b3d_c2f_schedule), ("particles_dev", C.c_void_p), ("logw_dev", C.c_void_p),
-                ("logq_dev", C.c_void_p)]
+                ("centre_dev", C.c_void_p), ("schedule", b3d_c2f_schedule), ("particles_dev", C.c_void_p),
+                ("logw_dev", C.c_void_p), ("logq_dev", C.c_void_p), ("map_dev", C.c_void_p)]
+
+
+class b3d_server_config(C.Structure):
+    _fields_ = [("max_sessions", C.c_int32), ("max_batch_items", C.c_int32), ("max_batch_frames", C.c_int32),
+                ("max_inflight", C.c_int32),
+                ("queue_depth", C.c_int32), ("device_timeout_ms", C.c_int32), ("lik", b3d_lik_params),
+                ("schedule", b3d_c2f_schedule), ("tuning", b3d_tuning)]
+
+
+class b3d_session_desc(C.Structure):
+    _fields_ = [("intr", b3d_intrinsics), ("n_obj", C.c_int32), ("n_track", C.c_int32), ("verts", C.c_void_p),
+                ("n_v", C.c_void_p), ("faces", C.c_void_p), ("n_f", C.c_void_p), ("mesh_flags", C.c_void_p),
+                ("poses", C.c_void_p), ("seed", C.c_uint64), ("grid_frame", C.c_float * 9)]
+
+
+class b3d_frame_result(C.Structure):
+    _fields_ = [("ticket", C.c_int64), ("session", C.c_int32), ("status", C.c_int32), ("frame_index", C.c_int64),
+                ("latency_ms", C.c_double), ("queue_ms", C.c_double), ("batch_frames", C.c_int32),
+                ("n_track", C.c_int32)]
+
+
+class b3d_server_stats(C.Structure):
+    _fields_ = [("frames_done", C.c_int64), ("frames_failed", C.c_int64), ("batches", C.c_int64),
+                ("hypotheses", C.c_int64), ("sessions", C.c_int32), ("max_batch_frames_seen", C.c_int32),
+                ("hbm_budget", C.c_uint64), ("hbm_reserved", C.c_uint64), ("hbm_used", C.c_uint64)]
 
 
 _P = C.c_void_p
@@ -105,6 +132,19 @@ _SIGNATURES = {
     "b3d_kernel_time": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "b3d_work_counters": (C.c_int32, [_P, _P]),
     "b3d_sync": (C.c_int32, [_P, _P]),
+    "b3d_server_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int32, C.c_uint64, C.POINTER(b3d_server_config)]),
+    "b3d_server_destroy": (C.c_int32, [_P]),
+    "b3d_server_last_error": (C.c_char_p, []),
+    "b3d_session_open": (C.c_int32, [_P, C.POINTER(b3d_session_desc), C.c_int32, C.POINTER(C.c_int32)]),
+    "b3d_session_close": (C.c_int32, [_P, C.c_int32]),
+    "b3d_frame_submit": (C.c_int32, [_P, C.c_int32, _P, C.c_int32, C.POINTER(C.c_int64)]),
+    "b3d_frame_wait": (C.c_int32, [_P, C.c_int64, C.c_int32, C.POINTER(b3d_frame_result), _P, C.c_int32]),
+    "b3d_frame_next": (C.c_int32, [_P, C.c_int32, C.POINTER(b3d_frame_result), _P, C.c_int32]),
+    "b3d_server_pause": (C.c_int32, [_P, C.c_int32]),
+    "b3d_server_get_stats": (C.c_int32, [_P, C.POINTER(b3d_server_stats)]),
+    "b3d_session_export": (C.c_int32, [_P, C.c_int32, _P, _P, _P, C.POINTER(C.c_int64)]),
+    "b3d_session_import": (C.c_int32, [_P, C.c_int32, _P, _P, _P, C.c_int64]),
+    "b3d_frame_seed": (C.c_uint64, [C.c_uint64, C.c_int64, C.c_int32]),
 }
 
 _lib = None
@@ -320,17 +360,20 @@ def b3d_score_multi(owner, items, lik: b3d_lik_params, stream=None):
     return _check(owner, load().b3d_score_multi(owner, len(items), arr, C.byref(lik), _stream(stream)))
 
 
-def c2f_item(scene, obj_slot, centre_pose, sch: b3d_c2f_schedule, particles_dev, logw_dev, logq_dev) -> b3d_c2f_item:
+def c2f_item(scene, obj_slot, centre_pose, sch: b3d_c2f_schedule, particles_dev, logw_dev, logq_dev,
+             centre_dev=None, map_dev=None) -> b3d_c2f_item:
     it = b3d_c2f_item()
     it.scene = scene
     it.obj_slot = int(obj_slot)
-    c = np.asarray(centre_pose, dtype=np.float32).reshape(16)
+    c = np.asarray(centre_pose if centre_pose is not None else np.eye(4), dtype=np.float32).reshape(16)
     for k in range(16):
         it.centre_pose[k] = float(c[k])
+    it.centre_dev = _addr(centre_dev)
     it.schedule = sch
     it.particles_dev = _addr(particles_dev)
     it.logw_dev = _addr(logw_dev)
     it.logq_dev = _addr(logq_dev)
+    it.map_dev = _addr(map_dev)
     return it
 
 
@@ -363,6 +406,196 @@ def b3d_sync(ctx, stream=None):
 # ------------------------------------------------------------------------------------------
 # thin convenience layer (torch tensors for device memory and streams)
 # ------------------------------------------------------------------------------------------
+
+# ------------------------------------------------------------------------------------------
+# serving: the tracking server
+# ------------------------------------------------------------------------------------------
+
+def _scheck(st):
+    if st != B3D_OK:
+        raise B3DError(st, load().b3d_server_last_error().decode())
+    return st
+
+
+def server_config(lik: b3d_lik_params, sch: b3d_c2f_schedule, max_sessions=32, max_batch_items=256, max_inflight=2,
+                  queue_depth=4, device_timeout_ms=0, tuning=None, max_batch_frames=0) -> b3d_server_config:
+    c = b3d_server_config()
+    c.max_sessions = int(max_sessions)
+    c.max_batch_items = int(max_batch_items)
+    c.max_batch_frames = int(max_batch_frames)
+    c.max_inflight = int(max_inflight)
+    c.queue_depth = int(queue_depth)
+    c.device_timeout_ms = int(device_timeout_ms)
+    c.lik = lik
+    c.schedule = sch
+    if tuning is not None:
+        c.tuning = b3d_tuning(int(tuning["tile_w"]), int(tuning["cta_threads"]), int(tuning["ctas_per_sm"]),
+                              int(tuning["high_occupancy"]), int(tuning["batch_chunk"]))
+    return c
+
+
+def b3d_frame_seed(seed, frame, obj) -> int:
+    return int(load().b3d_frame_seed(int(seed), int(frame), int(obj)))
+
+
+def b3d_server_last_error() -> str:
+    return load().b3d_server_last_error().decode()
+
+
+def b3d_server_create(device: int, hbm_budget_bytes: int, cfg: b3d_server_config):
+    out = C.c_void_p()
+    _scheck(load().b3d_server_create(C.byref(out), int(device), int(hbm_budget_bytes), C.byref(cfg)))
+    return out.value
+
+
+def b3d_server_destroy(srv):
+    return _scheck(load().b3d_server_destroy(srv))
+
+
+def b3d_session_open(srv, desc: b3d_session_desc, timeout_ms=0) -> int:
+    sid = C.c_int32(-1)
+    _scheck(load().b3d_session_open(srv, C.byref(desc), int(timeout_ms), C.byref(sid)))
+    return int(sid.value)
+
+
+def b3d_session_close(srv, sid):
+    return _scheck(load().b3d_session_close(srv, int(sid)))
+
+
+def b3d_frame_submit(srv, sid, depth, timeout_ms=0) -> int:
+    D = np.ascontiguousarray(depth, dtype=np.float32)
+    t = C.c_int64(0)
+    _scheck(load().b3d_frame_submit(srv, int(sid), D.ctypes.data, int(timeout_ms), C.byref(t)))
+    return int(t.value)
+
+
+def b3d_frame_wait(srv, ticket, timeout_ms, res: b3d_frame_result, poses):
+    P = poses
+    return _scheck(load().b3d_frame_wait(srv, int(ticket), int(timeout_ms), C.byref(res), _addr(P),
+                                         0 if P is None else int(P.size)))
+
+
+def b3d_frame_next(srv, timeout_ms, res: b3d_frame_result, poses):
+    P = poses
+    return _scheck(load().b3d_frame_next(srv, int(timeout_ms), C.byref(res), _addr(P), 0 if P is None else int(P.size)))
+
+
+def b3d_server_pause(srv, paused):
+    return _scheck(load().b3d_server_pause(srv, 1 if paused else 0))
+
+
+def b3d_server_get_stats(srv) -> dict:
+    s = b3d_server_stats()
+    _scheck(load().b3d_server_get_stats(srv, C.byref(s)))
+    return {k: getattr(s, k) for k, _ in b3d_server_stats._fields_}
+
+
+def b3d_session_export(srv, sid, poses, particles, logw) -> int:
+    nxt = C.c_int64(0)
+    _scheck(load().b3d_session_export(srv, int(sid), _addr(poses), _addr(particles), _addr(logw), C.byref(nxt)))
+    return int(nxt.value)
+
+
+def b3d_session_import(srv, sid, poses, particles, logw, next_frame):
+    return _scheck(load().b3d_session_import(srv, int(sid), _addr(poses), _addr(particles), _addr(logw),
+                                             int(next_frame)))
+
+
+class Server:
+    """Convenience wrapper over the b3d_server_* / b3d_session_* / b3d_frame_* functions
+    (marshalling only)."""
+
+    def __init__(self, cfg: b3d_server_config, device: int = 0, hbm_budget_bytes: int = 0):
+        self.h = b3d_server_create(device, hbm_budget_bytes, cfg)
+        self.cfg = cfg
+        self._n_track = {}
+
+    def close(self):
+        if self.h:
+            b3d_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def open_session(self, cam, meshes, poses, n_track, seed, closed=True, grid_frame=None, timeout_ms=0) -> int:
+        """meshes: list of (verts [n,3], faces [m,3]); poses [n_obj, 4, 4] (tracked first);
+        closed: one flag for all meshes or one per mesh."""
+        vs = [np.ascontiguousarray(v, dtype=np.float32).reshape(-1, 3) for v, _ in meshes]
+        fs = [np.ascontiguousarray(f, dtype=np.int32).reshape(-1, 3) for _, f in meshes]
+        n = len(meshes)
+        vp = (C.c_void_p * n)(*[v.ctypes.data for v in vs])
+        fp = (C.c_void_p * n)(*[f.ctypes.data for f in fs])
+        nv = np.array([v.shape[0] for v in vs], dtype=np.int64)
+        nf = np.array([f.shape[0] for f in fs], dtype=np.int64)
+        cl = [closed] * n if isinstance(closed, bool) else list(closed)
+        fl = np.array([B3D_MESH_CLOSED if c else 0 for c in cl], dtype=np.int32)
+        P = np.ascontiguousarray(poses, dtype=np.float32).reshape(n, 16)
+        d = b3d_session_desc()
+        d.intr = intrinsics(cam)
+        d.n_obj = n
+        d.n_track = int(n_track)
+        d.verts = C.cast(vp, C.c_void_p)
+        d.n_v = nv.ctypes.data
+        d.faces = C.cast(fp, C.c_void_p)
+        d.n_f = nf.ctypes.data
+        d.mesh_flags = fl.ctypes.data
+        d.poses = P.ctypes.data
+        d.seed = int(seed)
+        if grid_frame is not None:
+            g = np.asarray(grid_frame, dtype=np.float32).reshape(9)
+            for k in range(9):
+                d.grid_frame[k] = float(g[k])
+        sid = b3d_session_open(self.h, d, timeout_ms)
+        self._n_track[sid] = int(n_track)
+        return sid
+
+    def close_session(self, sid):
+        b3d_session_close(self.h, sid)
+
+    def submit(self, sid, depth, timeout_ms=0) -> int:
+        return b3d_frame_submit(self.h, sid, depth, timeout_ms)
+
+    def _result(self, res, P):
+        r = {k: getattr(res, k) for k, _ in b3d_frame_result._fields_}
+        r["poses"] = P[:res.n_track].copy()
+        return r
+
+    def wait(self, ticket, timeout_ms=10000) -> dict:
+        res = b3d_frame_result()
+        P = np.zeros((self.cfg.max_batch_items, 4, 4), dtype=np.float32)
+        b3d_frame_wait(self.h, ticket, timeout_ms, res, P)
+        return self._result(res, P)
+
+    def next(self, timeout_ms=10000) -> dict:
+        res = b3d_frame_result()
+        P = np.zeros((self.cfg.max_batch_items, 4, 4), dtype=np.float32)
+        b3d_frame_next(self.h, timeout_ms, res, P)
+        return self._result(res, P)
+
+    def pause(self, paused=True):
+        b3d_server_pause(self.h, paused)
+
+    def stats(self) -> dict:
+        return b3d_server_get_stats(self.h)
+
+    def export_session(self, sid):
+        nt, M = self._n_track[int(sid)], self.cfg.schedule.n_particles
+        poses = np.zeros((nt, 4, 4), np.float32)
+        part = np.zeros((nt, M, 4, 4), np.float32)
+        logw = np.zeros((nt, M), np.float32)
+        nxt = b3d_session_export(self.h, sid, poses, part, logw)
+        return {"poses": poses, "particles": part, "logw": logw, "next_frame": nxt}
+
+    def import_session(self, sid, state):
+        P = np.ascontiguousarray(state["poses"], dtype=np.float32)
+        part = np.ascontiguousarray(state["particles"], dtype=np.float32)
+        lw = np.ascontiguousarray(state["logw"], dtype=np.float32)
+        b3d_session_import(self.h, sid, P, part, lw, state["next_frame"])
+
 
 class Context:
     """Owns a b3d context; methods allocate outputs with torch and call the C ABI."""

@@ -49,6 +49,19 @@ struct LikKey {
 
 thread_local std::string g_create_error;
 
+// Background of one object slot: z-buffer of the other scene objects, the per-pixel terms
+// of the fixed objects alone and their sums. Each slot keeps its own, so hypotheses of
+// different objects of one scene can be scored in the same launch.
+struct BgCache {
+    unsigned long long *bg = nullptr;
+    float *ell = nullptr, *gs = nullptr, *gp = nullptr;
+    double *sums = nullptr, *part = nullptr;  // sums [3]; per-block partials of the table kernel
+    unsigned *counter = nullptr;               // its last-block ticket (zero between launches)
+    int64_t cap = 0, gcap = 0;
+    bool dirty = true, lik_valid = false, grad_valid = false;
+    LikKey key{};
+};
+
 }  // namespace
 
 struct b3d_ctx {
@@ -67,14 +80,9 @@ struct b3d_ctx {
     float *d_poses = nullptr;
     int pose_cap = 0;
     float4 *d_obs = nullptr;
-    unsigned long long *d_bg = nullptr;
-    float *d_ell_bg = nullptr, *d_gs_bg = nullptr, *d_gp_bg = nullptr;
-    double *d_sums = nullptr;
     int64_t px_cap = 0;
-    int bg_slot = -1;
-    bool bg_dirty = true;
-    bool bg_lik_valid = false, bg_grad_valid = false;
-    LikKey bg_key{};
+    // background caches: entry 0 holds every object, entry k + 1 every object but k
+    std::vector<BgCache> bgc;
 
     int *d_err = nullptr;
 
@@ -296,24 +304,55 @@ b3d_status check_slot(b3d_ctx *ctx, int32_t slot) {
     return B3D_OK;
 }
 
+BgCache &bg_cache(b3d_ctx *ctx, int32_t slot) {
+    const size_t k = (size_t)(slot + 1);
+    if (ctx->bgc.size() <= k) ctx->bgc.resize(k + 1);
+    return ctx->bgc[k];
+}
+
+// Mark the background of every slot whose z-buffer holds object `obj` (-1: all slots).
+void bg_invalidate(b3d_ctx *ctx, int32_t obj) {
+    for (size_t k = 0; k < ctx->bgc.size(); ++k)
+        if (obj < 0 || (int32_t)k != obj + 1) ctx->bgc[k].dirty = true;
+}
+
+void bg_invalidate_lik(b3d_ctx *ctx) {
+    for (BgCache &c : ctx->bgc) c.lik_valid = c.grad_valid = false;
+}
+
 // Background z-buffer of every scene object except `slot` (slot = -1: all objects).
 b3d_status ensure_bg(b3d_ctx *ctx, int32_t slot, cudaStream_t s) {
-    if (!ctx->bg_dirty && ctx->bg_slot == slot) return B3D_OK;
+    BgCache &c = bg_cache(ctx, slot);
     const int64_t npx = (int64_t)ctx->cam.W * ctx->cam.H;
+    b3d_status st;
+    if (c.cap < npx) {
+        dfree(ctx, c.bg); dfree(ctx, c.ell); dfree(ctx, c.gs); dfree(ctx, c.gp);
+        c.cap = c.gcap = 0;
+        if ((st = dalloc(ctx, &c.bg, (size_t)npx, "background z-buffer")) != B3D_OK) return st;
+        if ((st = dalloc(ctx, &c.ell, (size_t)npx, "background likelihood")) != B3D_OK) return st;
+        if (!c.sums && (st = dalloc(ctx, &c.sums, 3, "background sums")) != B3D_OK) return st;
+        dfree(ctx, c.part);
+        if ((st = dalloc(ctx, &c.part, (size_t)3 * bg_table_blocks(npx), "background partial sums")) != B3D_OK) return st;
+        if (!c.counter) {
+            if ((st = dalloc(ctx, &c.counter, 1, "background sum ticket")) != B3D_OK) return st;
+            cudaMemsetAsync(c.counter, 0, sizeof(unsigned), s);
+        }
+        c.cap = npx;
+        c.dirty = true;
+    }
+    if (!c.dirty) return B3D_OK;
     Timed tm(ctx, B3D_K_SCENE, s);
-    launch_bg_clear(ctx->d_bg, npx, s);
+    launch_bg_clear(c.bg, npx, s);
     ++ctx->launches;
     for (size_t o = 0; o < ctx->obj_mesh.size(); ++o) {
         if ((int32_t)o == slot) continue;
         const MeshRec &m = ctx->meshes[ctx->obj_mesh[o]];
         if (m.n_full <= 0) continue;
-        launch_bg_raster(ctx->cam, view_of(m), ctx->d_poses + 16 * o, (int)ctx->tri_base[o], ctx->d_bg, s);
+        launch_bg_raster(ctx->cam, view_of(m), ctx->d_poses + 16 * o, (int)ctx->tri_base[o], c.bg, s);
         ++ctx->launches;
     }
-    ctx->bg_slot = slot;
-    ctx->bg_dirty = false;
-    ctx->bg_lik_valid = false;
-    ctx->bg_grad_valid = false;
+    c.dirty = false;
+    c.lik_valid = c.grad_valid = false;
     return check_launch(ctx, "background render");
 }
 
@@ -321,12 +360,15 @@ SceneView scene_view(b3d_ctx *ctx, int32_t slot) {
     SceneView sv{};
     sv.cam = ctx->cam;
     sv.obs = ctx->d_obs;
-    sv.bg = ctx->d_bg;
-    sv.ell_bg = ctx->d_ell_bg;
-    sv.ll_bg = ctx->d_sums;
-    sv.gs_bg = ctx->d_gs_bg;
-    sv.gp_bg = ctx->d_gp_bg;
-    sv.sums_bg = ctx->d_sums;
+    if ((size_t)(slot + 1) < ctx->bgc.size()) {
+        const BgCache &c = ctx->bgc[(size_t)(slot + 1)];
+        sv.bg = c.bg;
+        sv.ell_bg = c.ell;
+        sv.ll_bg = c.sums;
+        sv.gs_bg = c.gs;
+        sv.gp_bg = c.gp;
+        sv.sums_bg = c.sums;
+    }
     if (slot >= 0) {
         sv.mesh = view_of(ctx->meshes[ctx->obj_mesh[slot]]);
         sv.tri_base = (int)ctx->tri_base[slot];
@@ -337,19 +379,30 @@ SceneView scene_view(b3d_ctx *ctx, int32_t slot) {
     return sv;
 }
 
+// Per-pixel terms of the background of `slot` (after ensure_bg) for these likelihood
+// parameters; with grad, also the sigma / p_out derivative tables.
 b3d_status ensure_bg_lik(b3d_ctx *ctx, int32_t slot, const b3d_lik_params *lp, const Lik &L, bool grad,
                          cudaStream_t s) {
+    BgCache &c = bg_cache(ctx, slot);
     const LikKey k = key_of(lp);
-    if (ctx->bg_lik_valid && ctx->bg_key == k && (!grad || ctx->bg_grad_valid)) return B3D_OK;
-    SceneView sv = scene_view(ctx, slot);
     const int64_t npx = (int64_t)ctx->cam.W * ctx->cam.H;
+    b3d_status st;
+    if (grad && c.gcap < npx) {
+        dfree(ctx, c.gs); dfree(ctx, c.gp);
+        c.gcap = 0;
+        if ((st = dalloc(ctx, &c.gs, (size_t)npx, "background sigma gradient")) != B3D_OK) return st;
+        if ((st = dalloc(ctx, &c.gp, (size_t)npx, "background p_out gradient")) != B3D_OK) return st;
+        c.gcap = npx;
+        c.grad_valid = false;
+    }
+    if (c.lik_valid && c.key == k && (!grad || c.grad_valid)) return B3D_OK;
+    SceneView sv = scene_view(ctx, slot);
     Timed tm(ctx, B3D_K_SCENE, s);
-    launch_bg_tables(sv, L, ctx->d_ell_bg, grad ? ctx->d_gs_bg : nullptr, grad ? ctx->d_gp_bg : nullptr, s);
-    launch_bg_sums(ctx->d_ell_bg, grad ? ctx->d_gs_bg : nullptr, grad ? ctx->d_gp_bg : nullptr, npx, ctx->d_sums, s);
-    ctx->launches += 2;
-    ctx->bg_key = k;
-    ctx->bg_lik_valid = true;
-    ctx->bg_grad_valid = grad;
+    launch_bg_tables(sv, L, c.ell, grad ? c.gs : nullptr, grad ? c.gp : nullptr, c.part, c.counter, c.sums, s);
+    ++ctx->launches;
+    c.key = k;
+    c.lik_valid = true;
+    c.grad_valid = grad;
     return check_launch(ctx, "background likelihood tables");
 }
 
@@ -478,6 +531,42 @@ b3d_status batch_upload(b3d_ctx *ctx, int slot, size_t bytes, cudaStream_t s) {
     }
     ctx->batch_flip ^= 1;
     return B3D_OK;
+}
+
+// Staging layout of b3d_enumerate_multi: centres | BatchItem[T][n] | LseItem[T][n] |
+// SelectItem[T][n] | item_begin[T][n+1] | block_begin[T][n+1] | device-centre pairs[n].
+struct MultiLayout {
+    size_t o_cent, o_bi, o_li, o_si, o_ib, o_bb, o_gp, bytes;
+};
+
+MultiLayout multi_layout(int64_t n_items, int T) {
+    MultiLayout l;
+    l.o_cent = 0;
+    l.o_bi = l.o_cent + align16(sizeof(float) * 32 * n_items);
+    l.o_li = l.o_bi + align16(sizeof(BatchItem) * (size_t)T * n_items);
+    l.o_si = l.o_li + align16(sizeof(LseItem) * (size_t)T * n_items);
+    l.o_ib = l.o_si + align16(sizeof(SelectItem) * (size_t)T * n_items);
+    l.o_bb = l.o_ib + align16(sizeof(int64_t) * (size_t)T * (n_items + 1));
+    l.o_gp = l.o_bb + align16(sizeof(int) * (size_t)T * (n_items + 1));
+    l.bytes = l.o_gp + align16(sizeof(float *) * 2 * (size_t)n_items);
+    return l;
+}
+
+// Scores of one stage, resampling partials and counters, draws and normalisers of a
+// batched enumeration (grown to the need, never shrunk).
+b3d_status multi_scratch(b3d_ctx *owner, int64_t need_ll, int64_t need_part, int64_t n_items, int64_t sum_m, int T) {
+    b3d_status st;
+    if ((st = grow(owner, owner->d_bll, owner->bll_cap, need_ll, "batched scores")) != B3D_OK) return st;
+    if ((st = grow(owner, owner->d_bpart, owner->bpart_cap, need_part, "batched partials")) != B3D_OK) return st;
+    if ((st = grow(owner, owner->d_bcnt, owner->bcnt_cap, n_items, "batched counters", true)) != B3D_OK) return st;
+    if ((st = grow(owner, owner->d_bwork, owner->bwork_cap, 8, "work counters")) != B3D_OK) return st;
+    if (owner->bidx_cap < sum_m) {
+        dfree(owner, owner->d_blogq);
+        int64_t c2 = 0;
+        if ((st = grow(owner, owner->d_bidx, owner->bidx_cap, sum_m, "batched draws")) != B3D_OK) return st;
+        if ((st = grow(owner, owner->d_blogq, c2, sum_m, "batched draw log-probabilities")) != B3D_OK) return st;
+    }
+    return grow(owner, owner->d_blogz, owner->blogz_cap, n_items * T, "batched normalisers");
 }
 
 }  // namespace
@@ -875,16 +964,18 @@ b3d_status b3d_set_scene(b3d_ctx *ctx, const b3d_intrinsics *intr, int32_t n_obj
     const int64_t npx = (int64_t)intr->width * intr->height;
     b3d_status st;
     if (npx > ctx->px_cap) {
-        dfree(ctx, ctx->d_obs); dfree(ctx, ctx->d_bg); dfree(ctx, ctx->d_ell_bg); dfree(ctx, ctx->d_gs_bg); dfree(ctx, ctx->d_gp_bg);
+        dfree(ctx, ctx->d_obs);
         ctx->px_cap = 0;
         if ((st = dalloc(ctx, &ctx->d_obs, (size_t)npx, "observed points")) != B3D_OK) return st;
-        if ((st = dalloc(ctx, &ctx->d_bg, (size_t)npx, "background z-buffer")) != B3D_OK) return st;
-        if ((st = dalloc(ctx, &ctx->d_ell_bg, (size_t)npx, "background likelihood")) != B3D_OK) return st;
-        if ((st = dalloc(ctx, &ctx->d_gs_bg, (size_t)npx, "background sigma gradient")) != B3D_OK) return st;
-        if ((st = dalloc(ctx, &ctx->d_gp_bg, (size_t)npx, "background p_out gradient")) != B3D_OK) return st;
         ctx->px_cap = npx;
     }
-    if (!ctx->d_sums && (st = dalloc(ctx, &ctx->d_sums, 3, "background sums")) != B3D_OK) return st;
+    // drop the background caches of slots the new scene does not have
+    while (ctx->bgc.size() > (size_t)n_obj + 1) {
+        BgCache &c = ctx->bgc.back();
+        dfree(ctx, c.bg); dfree(ctx, c.ell); dfree(ctx, c.gs); dfree(ctx, c.gp); dfree(ctx, c.sums);
+        dfree(ctx, c.part); dfree(ctx, c.counter);
+        ctx->bgc.pop_back();
+    }
     if (n_obj > ctx->pose_cap) {
         dfree(ctx, ctx->d_poses);
         ctx->pose_cap = 0;
@@ -908,8 +999,8 @@ b3d_status b3d_set_scene(b3d_ctx *ctx, const b3d_intrinsics *intr, int32_t n_obj
     }
     ++ctx->launches;
     ctx->has_scene = true;
-    ctx->bg_dirty = true;
-    ctx->bg_lik_valid = ctx->bg_grad_valid = false;
+    bg_invalidate(ctx, -1);
+    bg_invalidate_lik(ctx);
     return check_launch(ctx, "set_scene");
 }
 
@@ -924,7 +1015,7 @@ b3d_status b3d_set_observation(b3d_ctx *ctx, const float *obs_depth_dev, b3d_str
         launch_obs_points(ctx->cam, obs_depth_dev, ctx->d_obs, (cudaStream_t)stream);
     }
     ++ctx->launches;
-    ctx->bg_lik_valid = ctx->bg_grad_valid = false;
+    bg_invalidate_lik(ctx);
     return check_launch(ctx, "set_observation");
 }
 
@@ -938,7 +1029,7 @@ b3d_status b3d_set_object_pose_dev(b3d_ctx *ctx, int32_t obj, const float *pose_
     cudaError_t e = cudaMemcpyAsync(ctx->d_poses + 16 * obj, pose_dev, 16 * sizeof(float), cudaMemcpyDeviceToDevice,
                                     (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set_object_pose_dev");
-    ctx->bg_dirty = true;
+    bg_invalidate(ctx, obj);
     return B3D_OK;
 }
 
@@ -1114,7 +1205,8 @@ b3d_status b3d_enumerate_c2f(b3d_ctx *ctx, int32_t obj_slot, const float *centre
         {
             Timed tm(ctx, B3D_K_SELECT, s);
             launch_c2f_select(ctx->d_ll, ctx->d_idx, sch->n_particles, P, ctx->d_logz + t, last, sch->seed,
-                              sch->n_stages, ctx->d_centre + 16 * ((t + 1) & 1), particles_dev, logw_dev, logq_dev, s);
+                              sch->n_stages, last ? nullptr : ctx->d_centre + 16 * ((t + 1) & 1), particles_dev, logw_dev,
+                              logq_dev, s);
         }
         ctx->launches += 3;
     }
@@ -1222,7 +1314,8 @@ b3d_status b3d_enumerate_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_it
         if (sch.n_stages != T) return fail(owner, B3D_EINVAL, tag + "every schedule needs the same number of stages");
         if (sch.n_particles < 1 || sch.n_particles > (1 << 20)) return fail(owner, B3D_EINVAL, tag + "n_particles out of range");
         if (!it.particles_dev || !it.logw_dev || !it.logq_dev) return fail(owner, B3D_EINVAL, tag + "outputs must be non-NULL");
-        if (!finite_all(it.centre_pose, 16) || !finite_all(sch.grid_frame, 9)) return fail(owner, B3D_EINVAL, tag + "non-finite centre or grid frame");
+        if ((!it.centre_dev && !finite_all(it.centre_pose, 16)) || !finite_all(sch.grid_frame, 9))
+            return fail(owner, B3D_EINVAL, tag + "non-finite centre or grid frame");
         for (int t = 0; t < T; ++t)
             if ((st = check_stage(owner, sch.stage[t], &nh[(size_t)i * T + t])) != B3D_OK) return st;
         const MeshRec &m = it.scene->meshes[it.scene->obj_mesh[it.obj_slot]];
@@ -1248,17 +1341,7 @@ b3d_status b3d_enumerate_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_it
         need_ll = std::max(need_ll, a);
         need_part = std::max(need_part, b);
     }
-    if ((st = grow(owner, owner->d_bll, owner->bll_cap, need_ll, "batched scores")) != B3D_OK) return st;
-    if ((st = grow(owner, owner->d_bpart, owner->bpart_cap, need_part, "batched partials")) != B3D_OK) return st;
-    if ((st = grow(owner, owner->d_bcnt, owner->bcnt_cap, n_items, "batched counters", true)) != B3D_OK) return st;
-    if ((st = grow(owner, owner->d_bwork, owner->bwork_cap, 8, "work counters")) != B3D_OK) return st;
-    if (owner->bidx_cap < sum_m) {
-        dfree(owner, owner->d_blogq);
-        int64_t c2 = 0;
-        if ((st = grow(owner, owner->d_bidx, owner->bidx_cap, sum_m, "batched draws")) != B3D_OK) return st;
-        if ((st = grow(owner, owner->d_blogq, c2, sum_m, "batched draw log-probabilities")) != B3D_OK) return st;
-    }
-    if ((st = grow(owner, owner->d_blogz, owner->blogz_cap, (int64_t)n_items * T, "batched normalisers")) != B3D_OK) return st;
+    if ((st = multi_scratch(owner, need_ll, need_part, n_items, sum_m, T)) != B3D_OK) return st;
     // heavier scenes first in the work queue (first-stage hypotheses x pixels)
     std::vector<int> order((size_t)n_items);
     for (int i = 0; i < n_items; ++i) order[i] = i;
@@ -1267,14 +1350,9 @@ b3d_status b3d_enumerate_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_it
         const double cb = (double)nh[(size_t)b * T] * items[b].scene->cam.W * items[b].scene->cam.H;
         return ca > cb;
     });
-    // staging layout: centres | BatchItem[T][n] | LseItem[T][n] | SelectItem[T][n] | item_begin[T][n+1] | block_begin[T][n+1]
-    const size_t o_cent = 0;
-    const size_t o_bi = o_cent + align16(sizeof(float) * 32 * n_items);
-    const size_t o_li = o_bi + align16(sizeof(BatchItem) * (size_t)T * n_items);
-    const size_t o_si = o_li + align16(sizeof(LseItem) * (size_t)T * n_items);
-    const size_t o_ib = o_si + align16(sizeof(SelectItem) * (size_t)T * n_items);
-    const size_t o_bb = o_ib + align16(sizeof(int64_t) * (size_t)T * (n_items + 1));
-    const size_t bytes = o_bb + align16(sizeof(int) * (size_t)T * (n_items + 1));
+    const MultiLayout lay = multi_layout(n_items, T);
+    const size_t o_cent = lay.o_cent, o_bi = lay.o_bi, o_li = lay.o_li, o_si = lay.o_si, o_ib = lay.o_ib,
+                 o_bb = lay.o_bb, o_gp = lay.o_gp, bytes = lay.bytes;
     unsigned char *h = nullptr;
     int slot = 0;
     if ((st = batch_staging(owner, bytes, s, &h, &slot)) != B3D_OK) return st;
@@ -1283,9 +1361,16 @@ b3d_status b3d_enumerate_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_it
     float *dc = reinterpret_cast<float *>(d + o_cent);
     std::vector<int64_t> midx((size_t)n_items);
     int64_t macc = 0;
+    const float **gp = reinterpret_cast<const float **>(h + o_gp);
+    int n_gather = 0;
     for (int k = 0; k < n_items; ++k) {
         const int i = order[k];
         memcpy(hc + 32 * k, items[i].centre_pose, 16 * sizeof(float));
+        if (items[i].centre_dev) {  // device centre: copied into the slot after the upload
+            gp[2 * n_gather] = items[i].centre_dev;
+            gp[2 * n_gather + 1] = dc + 32 * k;
+            ++n_gather;
+        }
         midx[k] = macc;
         macc += items[i].schedule.n_particles;
     }
@@ -1349,7 +1434,7 @@ b3d_status b3d_enumerate_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_it
             sv.m = l.m;
             sv.grid = P;
             sv.logz = l.logz;
-            sv.centre_next = dc + 32 * k + 16 * ((t + 1) & 1);
+            sv.centre_next = t == T - 1 ? it.map_dev : dc + 32 * k + 16 * ((t + 1) & 1);
             sv.particles = it.particles_dev;
             sv.logw = it.logw_dev;
             sv.logq = it.logq_dev;
@@ -1366,6 +1451,10 @@ b3d_status b3d_enumerate_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_it
         blocks[t] = bacc;
     }
     if ((st = batch_upload(owner, slot, bytes, s)) != B3D_OK) return st;
+    if (n_gather > 0) {
+        launch_gather16(reinterpret_cast<const float *const *>(d + o_gp), n_gather, s);
+        ++owner->launches;
+    }
     cudaMemsetAsync(owner->d_bwork, 0, sizeof(unsigned long long) * 8, s);
     for (int t = 0; t < T; ++t) {
         {
@@ -1589,3 +1678,63 @@ b3d_status b3d_sync(b3d_ctx *ctx, b3d_stream stream) {
 }
 
 }  // extern "C"
+
+// ==========================================================================================
+// Context hooks for the tracking server (b3d_server.cu); not part of the C ABI.
+// ==========================================================================================
+namespace b3d {
+
+uint64_t ctx_used_bytes(b3d_ctx *ctx) { return ctx->used; }
+
+void ctx_set_budget(b3d_ctx *ctx, uint64_t budget) { ctx->budget = budget; }
+
+b3d_status ctx_alloc_bytes(b3d_ctx *ctx, size_t bytes, void **out, const char *what) {
+    unsigned char *p = nullptr;
+    DeviceGuard g(ctx->device);
+    b3d_status st = dalloc(ctx, &p, bytes, what);
+    *out = p;
+    return st;
+}
+
+float *ctx_scene_poses(b3d_ctx *ctx) { return ctx->d_poses; }
+
+int *ctx_err_flag(b3d_ctx *ctx) { return ctx->d_err; }
+
+void ctx_poses_changed(b3d_ctx *ctx) { bg_invalidate(ctx, -1); }
+
+b3d_status ctx_prepare_slot(b3d_ctx *ctx, int32_t slot, const b3d_lik_params *lik, const b3d_c2f_schedule *sch,
+                            cudaStream_t s) {
+    b3d_status st = check_slot(ctx, slot);
+    if (st != B3D_OK) return st;
+    Lik L;
+    if ((st = make_lik(ctx, lik, &L)) != B3D_OK) return st;
+    DeviceGuard g(ctx->device);
+    if ((st = ensure_bg(ctx, slot, s)) != B3D_OK) return st;
+    if ((st = ensure_bg_lik(ctx, slot, lik, L, false, s)) != B3D_OK) return st;
+    for (int t = 0; t < sch->n_stages; ++t) {
+        float *rot = nullptr;
+        if ((st = rotation_table(ctx, sch->stage[t], &rot, s)) != B3D_OK) return st;
+    }
+    return B3D_OK;
+}
+
+// Size the owner's batched-enumeration scratch and staging for n_items items of schedule
+// sch, so batched calls up to that size allocate nothing (and never synchronise).
+b3d_status owner_reserve(b3d_ctx *owner, int64_t n_items, const b3d_c2f_schedule *sch) {
+    const int T = sch->n_stages;
+    int64_t max_n = 1;
+    for (int t = 0; t < T; ++t) {
+        const b3d_stage &g = sch->stage[t];
+        max_n = std::max<int64_t>(max_n, (int64_t)g.n_per_axis * g.n_per_axis * g.n_per_axis * g.n_rot);
+    }
+    DeviceGuard g(owner->device);
+    b3d_status st = multi_scratch(owner, n_items * max_n, n_items * lse_blocks(max_n), n_items,
+                                  n_items * sch->n_particles, T);
+    if (st != B3D_OK) return st;
+    unsigned char *h = nullptr;
+    int slot = 0;
+    st = batch_staging(owner, multi_layout(n_items, T).bytes, nullptr, &h, &slot);
+    return st;
+}
+
+}  // namespace b3d

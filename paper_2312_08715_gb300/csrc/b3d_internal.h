@@ -3,7 +3,10 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
+
+#include "b3d.h"
 
 namespace b3d {
 
@@ -164,9 +167,11 @@ void launch_obs_points(const Cam &cam, const float *depth, float4 *obs, cudaStre
 void launch_bg_clear(unsigned long long *bg, int64_t n, cudaStream_t s);
 void launch_bg_raster(const Cam &cam, const MeshView &m, const float *pose16_dev, int tri_base,
                       unsigned long long *bg, cudaStream_t s);
-void launch_bg_tables(const SceneView &sv, const Lik &L, float *ell_bg, float *gs_bg, float *gp_bg,
-                      cudaStream_t s);
-void launch_bg_sums(const float *a, const float *b, const float *c, int64_t n, double *out, cudaStream_t s);
+// Per-pixel background terms and their double-precision sums (sums[0..2]); part holds
+// 3 x bg_table_blocks(W H) doubles, counter one zeroed word (left zeroed).
+int bg_table_blocks(int64_t n);
+void launch_bg_tables(const SceneView &sv, const Lik &L, float *ell_bg, float *gs_bg, float *gp_bg, double *part,
+                      unsigned *counter, double *sums, cudaStream_t s);
 int launch_score_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, int grid, cudaStream_t s);
 int launch_score_grid(const SceneView &sv, const Lik &L, PoseGrid P, int64_t n, float *ll, int grid, cudaStream_t s);
 int launch_render_list(const SceneView &sv, PoseList P, int64_t n, float *depth, int *tid, int grid, cudaStream_t s);
@@ -185,6 +190,8 @@ int launch_score_multi(const BatchItem *items, int n_items, const int64_t *item_
 void launch_lse_multi(const LseItem *items, int n_items, int total_blocks, const int *block_begin, int *err,
                       cudaStream_t s);
 void launch_select_multi(const SelectItem *items, int n_items, int last, cudaStream_t s);
+// dst[i][0..15] = src[i][0..15] for pairs (src, dst) in device memory
+void launch_gather16(const float *const *pairs, int n, cudaStream_t s);
 void launch_set16(float *dst, const float *src16_host_values, cudaStream_t s);
 void launch_rotation_set(int kind, int n, double rot_max, float *out, cudaStream_t s);
 void launch_expand(PoseGrid P, int64_t n, float *poses, cudaStream_t s);
@@ -195,5 +202,18 @@ void launch_c2f_select(const float *ll, const int *idx, int m, PoseGrid P, const
                        uint64_t seed, int n_stages, float *centre_next, float *particles, float *logw,
                        float *logq, cudaStream_t s);
 void launch_copy16(const float *src, float *dst, cudaStream_t s);
+
+// Context hooks used by the tracking server (defined with the context in b3d_api.cu).
+uint64_t ctx_used_bytes(b3d_ctx *ctx);
+void ctx_set_budget(b3d_ctx *ctx, uint64_t budget);
+b3d_status ctx_alloc_bytes(b3d_ctx *ctx, size_t bytes, void **out, const char *what);
+float *ctx_scene_poses(b3d_ctx *ctx);  // device [n_obj, 16]
+int *ctx_err_flag(b3d_ctx *ctx);       // device [1]
+void ctx_poses_changed(b3d_ctx *ctx);  // after writing ctx_scene_poses on the device
+// Allocate and fill everything a batched enumeration of `slot` needs (background caches,
+// likelihood tables, rotation sets), so later calls allocate nothing.
+b3d_status ctx_prepare_slot(b3d_ctx *ctx, int32_t slot, const b3d_lik_params *lik, const b3d_c2f_schedule *sch,
+                            cudaStream_t s);
+b3d_status owner_reserve(b3d_ctx *owner, int64_t n_items, const b3d_c2f_schedule *sch);
 
 }  // namespace b3d

@@ -300,15 +300,15 @@ void launch_lse_resample(const float *ll, int64_t n, int m, uint64_t seed, int s
 // ------------------------------------------------------------------------------------------
 // centre selection / particles
 // ------------------------------------------------------------------------------------------
-// Not last: centre_next = pose of the drawn cell with the highest score (ties to the smaller
-// index). Last: particle k = pose of drawn cell idx_k with t += G ((u - 1/2) step), its
-// score and proposal log density score - logZ - 3 log(step).
+// centre_next (not last; at the last stage only when non-NULL) = pose of the drawn cell with
+// the highest score (ties to the smaller index). Last: particle k = pose of drawn cell idx_k
+// with t += G ((u - 1/2) step), its score and proposal log density score - logZ - 3 log(step).
 __device__ __forceinline__ void select_body(float *s_v, int *s_i, const float *ll, const int *idx, int m,
                                             const PoseGrid &P, const float *logz, int last, unsigned long long seed,
                                             int n_stages, float *centre_next, float *particles, float *logw,
                                             float *logq) {
     const int tid = threadIdx.x;
-    if (!last) {
+    if (!last || centre_next) {
         float bv = -INFINITY;
         int bi = INT32_MAX;
         for (int k = tid; k < m; k += blockDim.x) {
@@ -334,7 +334,7 @@ __device__ __forceinline__ void select_body(float *s_v, int *s_i, const float *l
             pose12(P, best, o);
             write_pose16(o, centre_next);
         }
-        return;
+        if (!last) return;
     }
     const float Z = *logz;
     const float lstep = 3.f * logf(P.step);
@@ -403,6 +403,19 @@ void launch_lse_multi(const LseItem *items, int n_items, int total_blocks, const
 void launch_select_multi(const SelectItem *items, int n_items, int last, cudaStream_t s) {
     if (n_items <= 0) return;
     k_select_multi<<<n_items, 256, 0, s>>>(items, last);
+}
+
+__global__ void k_gather16(const float *const *pairs, int n) {
+    const int i = blockIdx.x, k = threadIdx.x;
+    if (i < n && k < 16) {
+        const float *src = pairs[2 * i];
+        float *dst = const_cast<float *>(pairs[2 * i + 1]);
+        dst[k] = src[k];
+    }
+}
+
+void launch_gather16(const float *const *pairs, int n, cudaStream_t s) {
+    if (n > 0) k_gather16<<<n, 32, 0, s>>>(pairs, n);
 }
 
 void launch_copy16(const float *src, float *dst, cudaStream_t s) {

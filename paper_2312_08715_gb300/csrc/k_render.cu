@@ -156,14 +156,61 @@ __global__ void k_bg_raster(Cam c, MeshView m, const float *pose16, int tri_base
     }
 }
 
+// Background render of a fixed object with few triangles (a table, a box): one thread per
+// pixel tests every triangle, so image-sized triangles spread over the whole grid. The same
+// per-pixel raster_tri call as k_bg_raster, hence the same z-buffer.
+constexpr int kSmallMesh = 32;
+__global__ void k_bg_raster_px(Cam c, MeshView m, const float *pose16, int tri_base, unsigned long long *bg) {
+    __shared__ int s_front;
+    __shared__ float4 s_abc[3 * kSmallMesh];
+    __shared__ unsigned s_gid[kSmallMesh];
+    float P[12];
+    const float *p = pose16;
+    P[0] = p[0]; P[1] = p[1]; P[2] = p[2]; P[3] = p[4]; P[4] = p[5]; P[5] = p[6];
+    P[6] = p[8]; P[7] = p[9]; P[8] = p[10]; P[9] = p[3]; P[10] = p[7]; P[11] = p[11];
+    if (threadIdx.x == 0) {
+        int bb[4];
+        bool front = false;
+        object_bbox(m, P, c, bb, &front);
+        s_front = front ? 1 : 0;
+    }
+    __syncthreads();
+    const bool front = s_front != 0;
+    const int4 *tris = front ? m.tris_surf : m.tris_full;
+    const int n_t = min(front ? m.n_surf : m.n_full, kSmallMesh);
+    const int cull = front ? m.closed : 0;
+    for (int t = threadIdx.x; t < n_t; t += blockDim.x) {
+        const int4 tr = tris[t];
+        tri_screen(m, tr, P, c, s_abc[3 * t], s_abc[3 * t + 1], s_abc[3 * t + 2]);
+        s_gid[t] = (unsigned)(tri_base + tr.w);
+    }
+    __syncthreads();
+    const int64_t n = (int64_t)c.W * c.H;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % c.W), y = (int)(i / c.W);
+        for (int t = 0; t < n_t; ++t) {
+            const unsigned gid = s_gid[t];
+            raster_tri(s_abc[3 * t], s_abc[3 * t + 1], s_abc[3 * t + 2], cull, x, x, y, y, c.far_z,
+                       [&](int xx, int yy, float z) { atomicMin(&bg[(int64_t)yy * c.W + xx], pack_key(z, gid)); });
+        }
+    }
+}
+
 // Per-pixel background terms: l_i of the fixed objects alone and, when requested, the
 // sigma / p_out derivatives of l_i (kind 1).
-__global__ void k_bg_tables(SceneView S, Lik L, float *ell_bg, float *gs_bg, float *gp_bg) {
+// Also sums l_i (and the derivative terms) over the image in double precision, in a fixed
+// order: each block reduces its pixels into part[3 block ..], and the block that finishes
+// last (a ticket on *counter, which it resets) adds the block partials in block order.
+__global__ void __launch_bounds__(256) k_bg_tables(SceneView S, Lik L, float *ell_bg, float *gs_bg, float *gp_bg,
+                                                   double *part, unsigned *counter, double *out) {
     __shared__ float s_lut[kMaxLut];
+    __shared__ double s_red[3][256 / 32];
+    __shared__ bool s_last;
     for (int i = threadIdx.x; i < L.n_lut; i += blockDim.x) s_lut[i] = L.lut[i];
     __syncthreads();
     const Cam &c = S.cam;
     const int64_t n = (int64_t)c.W * c.H;
+    double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float4 q = S.obs[i];
         const int x = (int)(i % c.W), y = (int)(i / c.W);
@@ -178,31 +225,39 @@ __global__ void k_bg_tables(SceneView S, Lik L, float *ell_bg, float *gs_bg, flo
             }
         }
         ell_bg[i] = l;
-        if (gs_bg) { gs_bg[i] = gs; gp_bg[i] = gp; }
-    }
-}
-
-// Sums of up to three arrays in double precision, fixed order (one block).
-__global__ void k_sums(const float *a, const float *b, const float *c, int64_t n, double *out) {
-    __shared__ double red[3][1024 / 32];
-    double s[3] = {0, 0, 0};
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        s[0] += a[i];
-        if (b) s[1] += b[i];
-        if (c) s[2] += c[i];
+        acc[0] += (double)l;
+        if (gs_bg) {
+            gs_bg[i] = gs;
+            gp_bg[i] = gp;
+            acc[1] += (double)gs;
+            acc[2] += (double)gp;
+        }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int k = 0; k < 3; ++k) {
-        double v = s[k];
+        double v = acc[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[k][wid] = v;
+        if (lane == 0) s_red[k][wid] = v;
     }
     __syncthreads();
     if (threadIdx.x < 3) {
-        double v = 0;
-        for (int k = 0; k < nw; ++k) v += red[threadIdx.x][k];
+        double v = 0.0;
+        for (int w = 0; w < nw; ++w) v += s_red[threadIdx.x][w];
+        part[3 * blockIdx.x + threadIdx.x] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x < 3) {
+        const volatile double *vp = part;
+        double v = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) v += vp[3 * b + threadIdx.x];
         out[threadIdx.x] = v;
     }
+    if (threadIdx.x == 0) *counter = 0u;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -360,18 +415,23 @@ void launch_bg_clear(unsigned long long *bg, int64_t n, cudaStream_t s) {
 void launch_bg_raster(const Cam &cam, const MeshView &m, const float *pose16_dev, int tri_base,
                       unsigned long long *bg, cudaStream_t s) {
     if (m.n_full <= 0) return;
+    if (m.n_full <= kSmallMesh) {
+        const int64_t n = (int64_t)cam.W * cam.H;
+        k_bg_raster_px<<<(int)std::min<int64_t>((n + 255) / 256, 8 * sm_count()), 256, 0, s>>>(cam, m, pose16_dev,
+                                                                                              tri_base, bg);
+        return;
+    }
     const int warps_per_block = 8;
     const int blocks = (int)std::min<int64_t>((m.n_full + warps_per_block - 1) / warps_per_block, 8 * sm_count());
     k_bg_raster<<<blocks, 32 * warps_per_block, 0, s>>>(cam, m, pose16_dev, tri_base, bg);
 }
 
-void launch_bg_tables(const SceneView &sv, const Lik &L, float *ell_bg, float *gs_bg, float *gp_bg, cudaStream_t s) {
-    const int64_t n = (int64_t)sv.cam.W * sv.cam.H;
-    k_bg_tables<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(sv, L, ell_bg, gs_bg, gp_bg);
-}
+int bg_table_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096)); }
 
-void launch_bg_sums(const float *a, const float *b, const float *c, int64_t n, double *out, cudaStream_t s) {
-    k_sums<<<1, 1024, 0, s>>>(a, b, c, n, out);
+void launch_bg_tables(const SceneView &sv, const Lik &L, float *ell_bg, float *gs_bg, float *gp_bg, double *part,
+                      unsigned *counter, double *sums, cudaStream_t s) {
+    const int64_t n = (int64_t)sv.cam.W * sv.cam.H;
+    k_bg_tables<<<bg_table_blocks(n), 256, 0, s>>>(sv, L, ell_bg, gs_bg, gp_bg, part, counter, sums);
 }
 
 }  // namespace b3d

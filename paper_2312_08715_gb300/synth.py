@@ -355,3 +355,89 @@ def batched_workloads(n_scenes: int = 64, seed_base: int = 2000, pitch: float = 
         wl.name = f"batched scene {k}: {n_obj} objects, {W}x{H}, ~{int(v)} voxels, {125 * n_rot} hypotheses/stage"
         out.append(wl)
     return out
+
+
+@dataclasses.dataclass
+class TrackingStream:
+    """One session of the tracking loop: a tabletop scene whose first ``n_track`` objects
+    move on smooth random trajectories while the camera and the table stay fixed."""
+    name: str
+    scene: Scene              # meshes (tracked objects first, then the table) at their frame-0 poses
+    n_track: int
+    truth: np.ndarray         # [F, n_obj, 4, 4] float32 true cam_from_obj of every object per frame
+    grid_frame: np.ndarray    # [3, 3] float32 cam_from_table (axes of the translation grid)
+    seed: int                 # the session's seed (random draws of the enumeration)
+    noise_seed: int
+
+    @property
+    def n_frames(self) -> int:
+        return int(self.truth.shape[0])
+
+    def draws(self, frame: int) -> NoiseDraws:
+        rng = np.random.default_rng([self.noise_seed, int(frame)])
+        return noise_draws(rng, self.scene.camera.height, self.scene.camera.width)
+
+    def scene_at(self, frame: int) -> Scene:
+        return Scene(self.scene.camera, self.scene.meshes, self.truth[frame].copy())
+
+
+def tracking_stream(k: int, n_objects: int, width=320, height=240, f=300.0, n_frames=40, vox_lo=2000,
+                    vox_hi=8000, seed_base=4000, max_step=0.012, max_turn_deg=4.0) -> TrackingStream:
+    """Session ``k`` of the serving workload: ``n_objects`` voxel blobs (5 mm pitch) on a 1 m
+    table, camera 0.8 m away and 45 degrees above the table looking at its centre. Each
+    object follows x(t) = x0 + a (sin(w t + p) - sin p) per table axis and the same form in
+    yaw, with a w <= max_step per axis and per frame (so <= sqrt(2) max_step of translation)
+    and yaw amplitude x rate <= max_turn_deg per frame."""
+    rng = np.random.default_rng(seed_base + k)
+    pitch = 0.005
+    cam = Camera(width, height, f, f, width / 2.0, height / 2.0, 0.01, 2.0)
+    cam_from_world = look_at_origin(0.8, math.radians(45.0), rng.uniform(0, 2 * math.pi))
+    objects = [voxel_mesh(_blob_cells(rng, pitch, vox_lo, vox_hi), pitch, origin=(0.0, 0.0, 0.0))
+               for _ in range(n_objects)]
+    placed = []
+    half = 0.12 + 0.03 * n_objects
+    starts = []
+    for m in objects:
+        r = float(np.max(np.linalg.norm(m.verts[:, :2].astype(np.float64), axis=1)))
+        for _ in range(20):
+            ok = False
+            for _ in range(2000):
+                xy = rng.uniform(-half, half, size=2)
+                if all(np.linalg.norm(xy - p) > r + q for p, q in placed):
+                    ok = True
+                    break
+            if ok:
+                break
+            half *= 1.2
+        else:
+            raise RuntimeError("placement failed")
+        placed.append((xy, r))
+        starts.append(xy)
+    t = np.arange(n_frames, dtype=np.float64)
+    truth = np.zeros((n_frames, n_objects + 1, 4, 4), dtype=np.float64)
+    for o, xy in enumerate(starts):
+        a = rng.uniform(0.02, 0.06, size=2)
+        w = rng.uniform(0.5, 1.0, size=2) * max_step / a
+        p = rng.uniform(0, 2 * math.pi, size=2)
+        b = math.radians(rng.uniform(5.0, 20.0))
+        wb = rng.uniform(0.5, 1.0) * math.radians(max_turn_deg) / b
+        pb = rng.uniform(0, 2 * math.pi)
+        th0 = rng.uniform(0, 2 * math.pi)
+        for i, ti in enumerate(t):
+            x = xy[0] + a[0] * (math.sin(w[0] * ti + p[0]) - math.sin(p[0]))
+            y = xy[1] + a[1] * (math.sin(w[1] * ti + p[1]) - math.sin(p[1]))
+            th = th0 + b * (math.sin(wb * ti + pb) - math.sin(pb))
+            truth[i, o] = cam_from_world @ rigid(yaw(th), [x, y, 0.0])
+    truth[:, n_objects] = cam_from_world  # the table
+    meshes = objects + [table_mesh(1.0)]
+    scene = Scene(cam, meshes, truth[0].astype(np.float32))
+    return TrackingStream(name=f"tracking session {k}: {n_objects} objects, {width}x{height}, {n_frames} frames",
+                          scene=scene, n_track=n_objects, truth=truth.astype(np.float32),
+                          grid_frame=cam_from_world[:3, :3].astype(np.float32), seed=seed_base + k,
+                          noise_seed=seed_base + 7919 * (k + 1))
+
+
+def tracking_stage(n_per_axis=5, step=0.01, n_rot=50, rot_max_deg=5.0) -> StageSpec:
+    """The per-frame enumeration of the tracking loop: a translation grid of n_per_axis^3
+    cells around the previous estimate times n_rot rotation perturbations."""
+    return StageSpec(n_per_axis, step, 1, n_rot, math.radians(rot_max_deg))

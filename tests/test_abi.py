@@ -14,7 +14,7 @@ HEADER = os.path.join(ROOT, "include", "b3d.h")
 
 def _declared():
     txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:b3d_status|const char \*|int64_t)\s*(b3d_\w+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:b3d_status|const char \*|int64_t|uint64_t)\s*(b3d_\w+)\s*\(", txt, re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -68,7 +68,13 @@ int main(void) {
          offsetof(b3d_c2f_schedule, seed), offsetof(b3d_c2f_schedule, grid_frame));
   printf("%zu %zu\\n", offsetof(b3d_lik_params, volume), offsetof(b3d_lik_params, miss_mode));
   printf("%zu %zu\\n", sizeof(b3d_tuning), offsetof(b3d_tuning, high_occupancy));
-  printf("%zu %zu %zu\\n", sizeof(b3d_score_item), sizeof(b3d_c2f_item), offsetof(b3d_c2f_item, particles_dev));
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(b3d_score_item), sizeof(b3d_c2f_item), offsetof(b3d_c2f_item, particles_dev),
+         offsetof(b3d_c2f_item, centre_dev), offsetof(b3d_c2f_item, map_dev));
+  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(b3d_server_config), offsetof(b3d_server_config, lik),
+         offsetof(b3d_server_config, schedule), offsetof(b3d_server_config, tuning), sizeof(b3d_session_desc),
+         offsetof(b3d_session_desc, grid_frame));
+  printf("%zu %zu %zu %zu\\n", sizeof(b3d_frame_result), offsetof(b3d_frame_result, latency_ms),
+         sizeof(b3d_server_stats), offsetof(b3d_server_stats, hbm_used));
   return 0;
 }
 """)
@@ -82,7 +88,12 @@ int main(void) {
             b3d.b3d_c2f_schedule.seed.offset, b3d.b3d_c2f_schedule.grid_frame.offset,
             b3d.b3d_lik_params.volume.offset, b3d.b3d_lik_params.miss_mode.offset,
             C.sizeof(b3d.b3d_tuning), b3d.b3d_tuning.high_occupancy.offset,
-            C.sizeof(b3d.b3d_score_item), C.sizeof(b3d.b3d_c2f_item), b3d.b3d_c2f_item.particles_dev.offset]
+            C.sizeof(b3d.b3d_score_item), C.sizeof(b3d.b3d_c2f_item), b3d.b3d_c2f_item.particles_dev.offset,
+            b3d.b3d_c2f_item.centre_dev.offset, b3d.b3d_c2f_item.map_dev.offset,
+            C.sizeof(b3d.b3d_server_config), b3d.b3d_server_config.lik.offset, b3d.b3d_server_config.schedule.offset,
+            b3d.b3d_server_config.tuning.offset, C.sizeof(b3d.b3d_session_desc), b3d.b3d_session_desc.grid_frame.offset,
+            C.sizeof(b3d.b3d_frame_result), b3d.b3d_frame_result.latency_ms.offset, C.sizeof(b3d.b3d_server_stats),
+            b3d.b3d_server_stats.hbm_used.offset]
     assert got == want
 
 

@@ -1,0 +1,280 @@
+"""Tracking server (serving form): depth frames from several sessions batched continuously.
+
+Each result must be the same alone and in the mix, bit for bit (every item of a batched
+launch is computed on its own, with the same launch shape, and its random draws depend only
+on session seed, frame and object), and must equal the library's batched enumeration run by
+hand on the same inputs. Admission, timeouts, cancellation and checkpoints are host logic,
+driven here with host-side injection only: a paused worker, small budgets, closing sessions.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2312_08715_gb300 import synth
+from _scenes import closed_flags
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+W, H, F = 96, 72, 5
+M = 8
+
+
+def _streams(n=4):
+    return [synth.tracking_stream(k, n_objects=1 + k % 3, width=W, height=H, f=90.0, n_frames=F, vox_lo=300,
+                                  vox_hi=800, seed_base=9000) for k in range(n)]
+
+
+def _frames(orc, st):
+    out = []
+    for f in range(st.n_frames):
+        depth, _ = orc.render(st.scene_at(f))
+        out.append(synth.corrupt_depth(depth, st.scene.camera.far, st.draws(f)))
+    return out
+
+
+LIK = dict(kind=0, radius=0.005, p_outlier=0.01, half_window=1)
+STAGE = synth.tracking_stage(3, 0.01, 8, 5.0)
+
+
+def _config(b3d, max_batch_items=64, max_inflight=2, queue_depth=8, max_sessions=32):
+    sch = b3d.schedule([STAGE], M, 0, np.eye(3))
+    return b3d.server_config(b3d.lik_params(**LIK), sch, max_sessions=max_sessions, max_batch_items=max_batch_items,
+                             max_inflight=max_inflight, queue_depth=queue_depth, device_timeout_ms=30000)
+
+
+def _open(srv, st, timeout_ms=0):
+    meshes = [(m.verts, m.faces) for m in st.scene.meshes]
+    return srv.open_session(st.scene.camera, meshes, st.truth[0], st.n_track, st.seed,
+                            closed=closed_flags(st.scene), grid_frame=st.grid_frame, timeout_ms=timeout_ms)
+
+
+@pytest.fixture(scope="module")
+def streams(orc):
+    S = _streams()
+    return S, [_frames(orc, s) for s in S]
+
+
+def _solo(b3d, st, frames):
+    srv = b3d.Server(_config(b3d))
+    sid = _open(srv, st)
+    out = []
+    for d in frames:
+        r = srv.wait(srv.submit(sid, d), 30000)
+        assert r["status"] == 0 and r["batch_frames"] == 1
+        out.append(r["poses"])
+    srv.close()
+    return out
+
+
+@pytest.mark.parametrize("max_batch_items,max_inflight", [(64, 2), (3, 1)])
+def test_results_same_alone_and_in_the_mix(streams, max_batch_items, max_inflight):
+    from paper_2312_08715_gb300 import b3d
+    S, frames = streams
+    solo = [_solo(b3d, st, fr) for st, fr in zip(S, frames)]
+    srv = b3d.Server(_config(b3d, max_batch_items=max_batch_items, max_inflight=max_inflight))
+    sids = [_open(srv, st) for st in S]
+    srv.pause(True)  # queue everything first, so the batches mix sessions
+    tickets = {}
+    for f in range(F):
+        for i, sid in enumerate(sids):
+            tickets[(i, f)] = srv.submit(sid, frames[i][f])
+    srv.pause(False)
+    got = {key: srv.wait(t, 60000) for key, t in tickets.items()}
+    for (i, f), r in got.items():
+        assert r["status"] == 0, r
+        assert r["frame_index"] == f and r["session"] == sids[i]
+        np.testing.assert_array_equal(r["poses"], solo[i][f])
+    st = srv.stats()
+    assert st["frames_done"] == F * len(S) and st["frames_failed"] == 0
+    n_items = sum(s.n_track for s in S)
+    assert st["hypotheses"] == F * n_items * STAGE.n_per_axis ** 3 * STAGE.n_rot
+    if max_batch_items >= n_items:
+        assert st["max_batch_frames_seen"] == len(S)
+    else:
+        assert 1 < st["max_batch_frames_seen"] < len(S)
+    srv.close()
+
+
+def test_frames_that_arrive_while_others_run_join_later_batches(streams):
+    """Sessions submit from their own threads at staggered times; every result still equals
+    the session alone."""
+    from paper_2312_08715_gb300 import b3d
+    S, frames = streams
+    solo = [_solo(b3d, st, fr) for st, fr in zip(S, frames)]
+    srv = b3d.Server(_config(b3d))
+    sids = [_open(srv, st) for st in S]
+    results = {}
+
+    def client(i):
+        time.sleep(0.003 * i)
+        for f in range(F):
+            t = srv.submit(sids[i], frames[i][f], timeout_ms=30000)
+            if f % 2 == 0:
+                results[(i, f)] = srv.wait(t, 60000)
+            else:
+                results[(i, f)] = t
+
+    th = [threading.Thread(target=client, args=(i,)) for i in range(len(S))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for key, r in list(results.items()):
+        if isinstance(r, int):
+            results[key] = srv.wait(r, 60000)
+    for (i, f), r in results.items():
+        assert r["status"] == 0
+        np.testing.assert_array_equal(r["poses"], solo[i][f])
+    srv.close()
+
+
+def test_server_frame_equals_batched_enumeration_by_hand(streams):
+    """Frame 0 of a two-object session: every tracked object enumerated around its
+    estimate with the other objects at theirs, through b3d_enumerate_multi directly."""
+    from paper_2312_08715_gb300 import b3d
+    from _scenes import gpu_context
+    S, frames = streams
+    st, fr = S[1], frames[1]
+    assert st.n_track == 2
+    srv = b3d.Server(_config(b3d))
+    sid = _open(srv, st)
+    r0 = srv.wait(srv.submit(sid, fr[0]), 30000)
+    r1 = srv.wait(srv.submit(sid, fr[1]), 30000)
+    srv.close()
+    ctx = gpu_context(st.scene, fr[0])
+    owner = b3d.Context(0)
+    lik = b3d.lik_params(**LIK)
+    maps = torch.zeros((st.n_track, 4, 4), device="cuda")
+    keep = []
+    items = []
+    for k in range(st.n_track):
+        o = (torch.empty((M, 4, 4), device="cuda"), torch.empty(M, device="cuda"), torch.empty(M, device="cuda"))
+        keep.append(o)
+        sch = b3d.schedule([STAGE], M, b3d.b3d_frame_seed(st.seed, 0, k), st.grid_frame)
+        items.append(b3d.c2f_item(ctx.h, k, st.truth[0][k], sch, *o, map_dev=maps[k]))
+    b3d.b3d_enumerate_multi(owner.h, items, lik, owner.stream)
+    owner.sync()
+    np.testing.assert_array_equal(maps.cpu().numpy(), r0["poses"])
+    # frame 1 starts from those estimates (read on the device) with the objects moved there
+    ctx.set_observation(fr[1])
+    for k in range(st.n_track):
+        b3d.b3d_set_object_pose_dev(ctx.h, k, maps[k], owner.stream)
+    maps1 = torch.zeros_like(maps)
+    items = []
+    for k in range(st.n_track):
+        sch = b3d.schedule([STAGE], M, b3d.b3d_frame_seed(st.seed, 1, k), st.grid_frame)
+        items.append(b3d.c2f_item(ctx.h, k, None, sch, *keep[k], centre_dev=maps[k], map_dev=maps1[k]))
+    b3d.b3d_enumerate_multi(owner.h, items, lik, owner.stream)
+    owner.sync()
+    np.testing.assert_array_equal(maps1.cpu().numpy(), r1["poses"])
+    ctx.close()
+    owner.close()
+
+
+def test_tracking_follows_the_true_poses(streams):
+    from paper_2312_08715_gb300 import b3d
+    S, frames = streams
+    srv = b3d.Server(_config(b3d))
+    errs = []
+    for st, fr in zip(S, frames):
+        sid = _open(srv, st)
+        ts = [srv.submit(sid, d) for d in fr]
+        for f, t in enumerate(ts):
+            r = srv.wait(t, 30000)
+            est = r["poses"][:, :3, 3]
+            errs.append(np.linalg.norm(est - st.truth[f][:st.n_track, :3, 3], axis=1))
+    errs = np.concatenate(errs)
+    # grid step 1 cm, objects moving up to 1.7 cm a frame: the estimate stays within a cell
+    assert float(np.median(errs)) < 0.01, errs
+    assert float(np.max(errs)) < 0.03, errs
+    srv.close()
+
+
+def test_admission_by_hbm_budget_and_slots(streams):
+    from paper_2312_08715_gb300 import b3d
+    S, _ = streams
+    probe = b3d.Server(_config(b3d))
+    base = probe.stats()["hbm_reserved"]
+    _open(probe, S[0])
+    one = probe.stats()["hbm_reserved"] - base
+    probe.close()
+    assert one > 0
+    srv = b3d.Server(_config(b3d), hbm_budget_bytes=base + int(2.5 * one))
+    a = _open(srv, S[0])
+    _open(srv, S[0])
+    with pytest.raises(b3d.B3DError) as e:
+        _open(srv, S[0])
+    assert e.value.status == b3d.B3D_EBUDGET
+    st = srv.stats()
+    assert st["sessions"] == 2 and st["hbm_reserved"] <= st["hbm_budget"] and st["hbm_used"] <= st["hbm_budget"]
+    # an open that waits is admitted once a session closes
+    closer = threading.Timer(0.2, lambda: srv.close_session(a))
+    closer.start()
+    c = _open(srv, S[0], timeout_ms=20000)
+    closer.join()
+    assert srv.stats()["sessions"] == 2 and c != a
+    srv.close()
+    small = b3d.Server(_config(b3d, max_sessions=1))
+    _open(small, S[0])
+    with pytest.raises(b3d.B3DError) as e:
+        _open(small, S[0])
+    assert e.value.status == b3d.B3D_EBUSY
+    small.close()
+
+
+def test_wait_timeout_queue_limit_and_close_cancels(streams):
+    from paper_2312_08715_gb300 import b3d
+    S, frames = streams
+    srv = b3d.Server(_config(b3d, queue_depth=2))
+    sid = _open(srv, S[0])
+    srv.pause(True)  # host-side stall: nothing is issued
+    t0 = srv.submit(sid, frames[0][0])
+    t1 = srv.submit(sid, frames[0][1])
+    with pytest.raises(b3d.B3DError) as e:
+        srv.submit(sid, frames[0][2], timeout_ms=0)
+    assert e.value.status == b3d.B3D_EBUSY
+    with pytest.raises(b3d.B3DError) as e:
+        srv.wait(t0, 100)
+    assert e.value.status == b3d.B3D_ETIMEOUT
+    srv.pause(False)
+    assert srv.wait(t0, 30000)["status"] == 0
+    assert srv.wait(t1, 30000)["status"] == 0
+    with pytest.raises(b3d.B3DError) as e:
+        srv.wait(t1, 0)  # already collected
+    assert e.value.status == b3d.B3D_ENOTFOUND
+    srv.pause(True)
+    t2 = srv.submit(sid, frames[0][2])
+    t3 = srv.submit(sid, frames[0][3])
+    srv.close_session(sid)
+    assert srv.wait(t2, 0)["status"] == b3d.B3D_ECLOSED
+    assert srv.wait(t3, 0)["status"] == b3d.B3D_ECLOSED
+    with pytest.raises(b3d.B3DError) as e:
+        srv.submit(sid, frames[0][4])
+    assert e.value.status == b3d.B3D_ENOTFOUND
+    assert srv.stats()["frames_failed"] == 2
+    srv.close()
+
+
+def test_export_import_continues_exactly(streams):
+    from paper_2312_08715_gb300 import b3d
+    S, frames = streams
+    st, fr = S[2], frames[2]
+    srv = b3d.Server(_config(b3d))
+    a = _open(srv, st)
+    for f in range(3):
+        srv.wait(srv.submit(a, fr[f]), 30000)
+    state = srv.export_session(a)
+    assert state["next_frame"] == 3
+    b = _open(srv, st)
+    srv.import_session(b, state)
+    ra = srv.wait(srv.submit(a, fr[3]), 30000)
+    rb = srv.wait(srv.submit(b, fr[3]), 30000)
+    np.testing.assert_array_equal(ra["poses"], rb["poses"])
+    assert ra["frame_index"] == rb["frame_index"] == 3
+    sa, sb = srv.export_session(a), srv.export_session(b)
+    np.testing.assert_array_equal(sa["particles"], sb["particles"])
+    np.testing.assert_array_equal(sa["logw"], sb["logw"])
+    srv.close()
