@@ -379,6 +379,9 @@ typedef struct {
     int32_t queue_depth;      /* frames a session may have submitted and not completed, 1..64 */
     int32_t device_timeout_ms; /* a batch not finished after this long fails the server
                                   (B3D_ETIMEOUT); 0 = 60000 */
+    int32_t batch_linger_us;  /* while a batch runs, wait up to this long for more frames
+                                 before issuing the next one (0: issue at once); the wait
+                                 ends early once every session has a frame queued */
     b3d_lik_params lik;       /* likelihood of every session */
     b3d_c2f_schedule schedule; /* per object and frame; its seed is replaced by b3d_frame_seed */
     b3d_tuning tuning;        /* launch shape of the score kernel (tile_w 0: library default) */

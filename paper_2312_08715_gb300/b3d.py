@@ -81,7 +81,8 @@ class b3d_c2f_item(C.Structure):
 class b3d_server_config(C.Structure):
     _fields_ = [("max_sessions", C.c_int32), ("max_batch_items", C.c_int32), ("max_batch_frames", C.c_int32),
                 ("max_inflight", C.c_int32),
-                ("queue_depth", C.c_int32), ("device_timeout_ms", C.c_int32), ("lik", b3d_lik_params),
+                ("queue_depth", C.c_int32), ("device_timeout_ms", C.c_int32), ("batch_linger_us", C.c_int32),
+                ("lik", b3d_lik_params),
                 ("schedule", b3d_c2f_schedule), ("tuning", b3d_tuning)]
 
 
@@ -418,7 +419,8 @@ def _scheck(st):
 
 
 def server_config(lik: b3d_lik_params, sch: b3d_c2f_schedule, max_sessions=32, max_batch_items=256, max_inflight=2,
-                  queue_depth=4, device_timeout_ms=0, tuning=None, max_batch_frames=0) -> b3d_server_config:
+                  queue_depth=4, device_timeout_ms=0, tuning=None, max_batch_frames=0,
+                  batch_linger_us=0) -> b3d_server_config:
     c = b3d_server_config()
     c.max_sessions = int(max_sessions)
     c.max_batch_items = int(max_batch_items)
@@ -426,6 +428,7 @@ def server_config(lik: b3d_lik_params, sch: b3d_c2f_schedule, max_sessions=32, m
     c.max_inflight = int(max_inflight)
     c.queue_depth = int(queue_depth)
     c.device_timeout_ms = int(device_timeout_ms)
+    c.batch_linger_us = int(batch_linger_us)
     c.lik = lik
     c.schedule = sch
     if tuning is not None:
@@ -739,7 +742,9 @@ def make_score_smooth():
     class ScoreSmooth(torch.autograd.Function):
         """loglik = score of poses Exp(xi^) T0 under the smooth likelihood with noise
         (sigma, p_out); gradients w.r.t. xi (exact at xi = 0: re-base T0 after each step),
-        sigma and p_out from the library's backward kernel."""
+        sigma and p_out from the library's backward kernel. sigma and p_out may be plain
+        floats (no gradient; the only form that can be captured in a CUDA graph, since a
+        device scalar would be read back to the host) or scalar tensors."""
 
         @staticmethod
         def forward(fctx, xi, sigma, p_out, b3d_ctx, slot, T0, half_window):
@@ -752,6 +757,9 @@ def make_score_smooth():
         @staticmethod
         def backward(fctx, g):
             dpose, ds, dp = fctx.saved_tensors
-            return (g[:, None] * dpose, (g * ds).sum().reshape(()), (g * dp).sum().reshape(()), None, None, None, None)
+            need = fctx.needs_input_grad
+            gs = (g * ds).sum().reshape(()) if need[1] else None
+            gp = (g * dp).sum().reshape(()) if need[2] else None
+            return (g[:, None] * dpose if need[0] else None, gs, gp, None, None, None, None)
 
     return ScoreSmooth

@@ -237,6 +237,15 @@ b3d_status issue_batch(b3d_server *S, const std::vector<Frame> &frames, const st
     return B3D_OK;
 }
 
+// Every session that can take a frame has one queued (no reason to wait for more).
+bool all_queued(b3d_server *S) {
+    for (auto &kv : S->sessions) {
+        const Session *x = kv.second.get();
+        if (x->queue.empty() && !x->held && !x->closing) return false;
+    }
+    return true;
+}
+
 bool worker_ready(b3d_server *S) {
     if (S->stop) return true;
     if (S->paused || S->failed || (int)S->inflight.size() >= S->cfg.max_inflight) return false;
@@ -254,6 +263,13 @@ void worker_loop(b3d_server *S) {
         S->cv_work.wait_for(lk, std::chrono::milliseconds(50), [S] { return worker_ready(S); });
         if (S->stop) break;
         if (!worker_ready(S)) continue;
+        if (!S->inflight.empty() && S->cfg.batch_linger_us > 0) {
+            // the device is busy: let frames that are about to arrive join this batch
+            const auto until = Clock::now() + std::chrono::microseconds(S->cfg.batch_linger_us);
+            S->cv_work.wait_until(lk, until, [S] { return S->stop || S->paused || all_queued(S); });
+            if (S->stop) break;
+            if (!worker_ready(S)) continue;
+        }
         // the oldest queued frame of each ready session, round-robin from S->rr
         std::vector<Frame> frames;
         std::vector<Session *> sess;
@@ -370,6 +386,8 @@ b3d_status validate_config(const b3d_server_config *c) {
     if (c->max_inflight < 1 || c->max_inflight > 2) return srv_fail(B3D_EINVAL, "max_inflight must be 1 or 2");
     if (c->queue_depth < 1 || c->queue_depth > 64) return srv_fail(B3D_EINVAL, "queue_depth must be in [1, 64]");
     if (c->device_timeout_ms < 0) return srv_fail(B3D_EINVAL, "device_timeout_ms must be >= 0");
+    if (c->batch_linger_us < 0 || c->batch_linger_us > 1000000)
+        return srv_fail(B3D_EINVAL, "batch_linger_us must be in [0, 1000000]");
     const b3d_c2f_schedule &sch = c->schedule;
     if (sch.n_stages < 1 || sch.n_stages > B3D_MAX_STAGES) return srv_fail(B3D_EINVAL, "schedule.n_stages must be in [1, 8]");
     if (sch.n_particles < 1 || sch.n_particles > (1 << 20)) return srv_fail(B3D_EINVAL, "schedule.n_particles out of range");
