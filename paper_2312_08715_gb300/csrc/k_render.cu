@@ -251,10 +251,18 @@ __global__ void __launch_bounds__(256) k_bg_tables(SceneView S, Lik L, float *el
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    if (threadIdx.x < 3) {
-        const volatile double *vp = part;
+    // thread t adds the partials of blocks t, t + 256, ... in order; then a fixed tree
+    const volatile double *vp = part;
+    for (int k = 0; k < 3; ++k) {
         double v = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) v += vp[3 * b + threadIdx.x];
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) v += vp[3 * b + k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_red[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double v = 0.0;
+        for (int w = 0; w < nw; ++w) v += s_red[threadIdx.x][w];
         out[threadIdx.x] = v;
     }
     if (threadIdx.x == 0) *counter = 0u;

@@ -166,7 +166,23 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
 // z-buffer pixels per tile for a CTA of NT threads
 template <int NT>
 constexpr int score_region() { return NT <= 64 ? 2048 : kRegionPx; }
-constexpr int kStageStride = 5;  // float4 per staged rectangle: conflict-free reads across owners
+constexpr int kStageStride = 6;  // float4 per staged rectangle: four edges, plane, pixel box
+
+// A rectangle edge a->b staged for the pixel tests: its canonical origin (the
+// lexicographically smaller endpoint, as edge_fn) and direction, with the quad's
+// orientation sign and the canonical swap folded into the direction. Sign flips commute
+// with round-to-nearest, so fmaf(E.z, py - E.y, -(E.w * (px - E.x))) equals
+// s * edge_fn(a, b, p) bit for bit (up to the sign of a zero), and the test is e >= 0.
+__device__ __forceinline__ float4 stage_edge(float ax, float ay, float bx, float by, float s) {
+    const bool sw = (bx < ax) || (bx == ax && by < ay);
+    const float x0 = sw ? bx : ax, y0 = sw ? by : ay, x1 = sw ? ax : bx, y1 = sw ? ay : by;
+    const float sg = sw ? -s : s;
+    return make_float4(x0, y0, sg * (x1 - x0), sg * (y1 - y0));
+}
+
+__device__ __forceinline__ bool staged_inside(const float4 &E, float px, float py) {
+    return fmaf(E.z, py - E.y, -(E.w * (px - E.x))) >= 0.f;
+}
 
 // Per-CTA shared state of one hypothesis.
 template <int NT>
@@ -315,14 +331,19 @@ __device__ __forceinline__ float score_body(const SceneView &S, const Lik &L, co
                                     const float dz1 = C1.z - C0.z, dz2 = C2.z - C0.z;
                                     const float al = fmaf(dz1, dv2, -(dz2 * dv1)) * inv;
                                     const float be = fmaf(dz2, du1, -(dz1 * du2)) * inv;
-                                    stg[lane * kStageStride + 0] = make_float4(C0.x, C0.y, C1.x, C1.y);
-                                    stg[lane * kStageStride + 1] = make_float4(C2.x, C2.y, C3.x, C3.y);
-                                    stg[lane * kStageStride + 2] = make_float4(al, be, C0.z, area > 0.f ? 1.f : -1.f);
+                                    const float sgn = area > 0.f ? 1.f : -1.f;
+                                    float4 *rec = stg + lane * kStageStride;
+                                    rec[0] = stage_edge(C0.x, C0.y, C1.x, C1.y, sgn);
+                                    rec[1] = stage_edge(C1.x, C1.y, C2.x, C2.y, sgn);
+                                    rec[2] = stage_edge(C2.x, C2.y, C3.x, C3.y, sgn);
+                                    rec[3] = stage_edge(C3.x, C3.y, C0.x, C0.y, sgn);
+                                    // 1/z = al px + be py + K over the quad's plane
+                                    const float K = fmaf(-al, C0.x, fmaf(-be, C0.y, C0.z));
                                     // the candidate's row is floor((k + 1/2) / width), exact in float
                                     // for the region's sizes (margin 1/(2 width) >> rounding)
-                                    stg[lane * kStageStride + 3] = make_float4(
-                                        __int_as_float(x0), __int_as_float(y0), __int_as_float(x1 - x0 + 1),
-                                        1.0f / (float)(x1 - x0 + 1));
+                                    rec[4] = make_float4(al, be, K, 1.0f / (float)(x1 - x0 + 1));
+                                    rec[5] = make_float4(__int_as_float(x0), __int_as_float(y0),
+                                                         __int_as_float(x1 - x0 + 1), 0.f);
                                 }
                             }
                         }
@@ -346,16 +367,14 @@ __device__ __forceinline__ float score_body(const SceneView &S, const Lik &L, co
                             }
                             const int kk = j - __shfl_sync(0xffffffffu, excl, lo);
                             if (j < n_cand) {
-                                const float4 A = stg[lo * kStageStride + 0], B = stg[lo * kStageStride + 1],
-                                             Pl = stg[lo * kStageStride + 2], Bx = stg[lo * kStageStride + 3];
-                                const int bw = __float_as_int(Bx.z), row = (int)(((float)kk + 0.5f) * Bx.w);
+                                const float4 *rec = stg + lo * kStageStride;
+                                const float4 Pl = rec[4], Bx = rec[5];
+                                const int bw = __float_as_int(Bx.z), row = (int)(((float)kk + 0.5f) * Pl.w);
                                 const int x = __float_as_int(Bx.x) + (kk - row * bw), y = __float_as_int(Bx.y) + row;
-                                const float px = (float)x + 0.5f, py = (float)y + 0.5f, sg = Pl.w;
-                                if (sg * edge_fn(A.x, A.y, A.z, A.w, px, py) >= 0.f &&
-                                    sg * edge_fn(A.z, A.w, B.x, B.y, px, py) >= 0.f &&
-                                    sg * edge_fn(B.x, B.y, B.z, B.w, px, py) >= 0.f &&
-                                    sg * edge_fn(B.z, B.w, A.x, A.y, px, py) >= 0.f) {
-                                    const float z = __fdividef(1.0f, fmaf(Pl.x, px - A.x, fmaf(Pl.y, py - A.y, Pl.z)));
+                                const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+                                if (staged_inside(rec[0], px, py) && staged_inside(rec[1], px, py) &&
+                                    staged_inside(rec[2], px, py) && staged_inside(rec[3], px, py)) {
+                                    const float z = __fdividef(1.0f, fmaf(Pl.x, px, fmaf(Pl.y, py, Pl.z)));
                                     if (z <= c.far_z) store(x, y, z);
                                 }
                             }

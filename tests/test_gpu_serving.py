@@ -278,3 +278,29 @@ def test_export_import_continues_exactly(streams):
     np.testing.assert_array_equal(sa["particles"], sb["particles"])
     np.testing.assert_array_equal(sa["logw"], sb["logw"])
     srv.close()
+
+
+def test_device_timeout_shorter_than_a_batch_fails_the_server(streams):
+    """The completion thread's bounded wait runs out while a heavy batch is still running
+    normally (a 1 ms limit): its frames report B3D_ETIMEOUT, queued frames are cancelled,
+    and the server refuses new work. Nothing on the device hangs; the batch completes."""
+    from paper_2312_08715_gb300 import b3d
+    S, frames = streams
+    heavy = synth.StageSpec(9, 0.004, 1, 50, 0.1)
+    sch = b3d.schedule([heavy, heavy], M, 0, np.eye(3))
+    cfg = b3d.server_config(b3d.lik_params(**LIK), sch, max_batch_items=64, max_inflight=1, queue_depth=4,
+                            device_timeout_ms=1)
+    srv = b3d.Server(cfg)
+    sids = [_open(srv, st) for st in S]
+    srv.pause(True)
+    first = [srv.submit(sid, frames[i][0]) for i, sid in enumerate(sids)]
+    later = [srv.submit(sid, frames[i][1]) for i, sid in enumerate(sids)]
+    srv.pause(False)
+    got = [srv.wait(t, 60000) for t in first + later]
+    assert all(r["status"] == b3d.B3D_ETIMEOUT for r in got[:len(sids)])
+    assert all(r["status"] in (b3d.B3D_ETIMEOUT, b3d.B3D_ECLOSED) for r in got[len(sids):])
+    with pytest.raises(b3d.B3DError) as e:
+        srv.submit(sids[0], frames[0][2])
+    assert e.value.status == b3d.B3D_EDEVICE
+    srv.close()
+    torch.cuda.synchronize()
