@@ -193,6 +193,7 @@ struct ScoreShared {
     int flags;    // bit 0: on screen, bit 1: rectangle path, bit 2: whole object beyond near
     int rng[13];  // class first rectangles [6], exclusive prefix of counts [6], total
     float red[NT / 32];
+    int own[NT];  // per warp: the lane whose candidate run starts at each position of a window
 };
 
 // Scores the hypothesis whose pose thread 0 has put in sh.pose: returns, in thread 0, the
@@ -210,37 +211,82 @@ __device__ __forceinline__ float score_body(const SceneView &S, const Lik &L, co
     const int n_lat = m.nc[0] + m.nc[1] + m.nc[2];
     const int nc0 = m.nc[0], nc01 = m.nc[0] + m.nc[1];
     auto lat_off = [&](int a) { return a == 0 ? 0 : (a == 1 ? nc0 : nc01); };
-    if (tid == 0) {
-        bool front = false;
-        int f = object_bbox(m, sh.pose, c, sh.bb, &front) ? 1 : 0;
+    if (wid == 0) {
+        // warp 0: lane k < 8 projects corner k of the object's box (the arithmetic of
+        // object_bbox, reduced with exact min / max), lane c < 6 finds face class c's range
+        __syncwarp();
+        const float *P = sh.pose;
+        float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+        bool cfront = true;
+        const bool has = m.n_full > 0;
+        if (has && lane < 8) {
+            const float ox = (lane & 1) ? m.hi[0] : m.lo[0], oy = (lane & 2) ? m.hi[1] : m.lo[1];
+            const float oz = (lane & 4) ? m.hi[2] : m.lo[2];
+            float x, y, z;
+            xform(P, ox, oy, oz, x, y, z);
+            if (!(z >= c.near_z)) {
+                cfront = false;
+            } else {
+                umin = umax = fmaf(c.fx, x / z, c.cx);
+                vmin = vmax = fmaf(c.fy, y / z, c.cy);
+            }
+        }
+        const bool front = has && __all_sync(0xffffffffu, cfront);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, o));
+            umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+            vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+            vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        }
+        int bb0 = 0, bb1 = c.W - 1, bb2 = 0, bb3 = c.H - 1;
+        if (front) {
+            const float lo_u = fmaxf(umin - 0.5f, -2.f), hi_u = fminf(umax - 0.5f, (float)c.W + 1.f);
+            const float lo_v = fmaxf(vmin - 0.5f, -2.f), hi_v = fminf(vmax - 0.5f, (float)c.H + 1.f);
+            bb0 = max((int)ceilf(lo_u) - 1, 0);
+            bb1 = min((int)floorf(hi_u) + 1, c.W - 1);
+            bb2 = max((int)ceilf(lo_v) - 1, 0);
+            bb3 = min((int)floorf(hi_v) + 1, c.H - 1);
+        }
+        int f = has && bb0 <= bb1 && bb2 <= bb3 ? 1 : 0;
         if (front) f |= 4;
         if (f && front && m.n_quads > 0) {
             f |= 2;
-            const float *R = sh.pose, *t = sh.pose + 9;
-            float o[3];
-            for (int a = 0; a < 3; ++a) o[a] = -fmaf(R[a], t[0], fmaf(R[3 + a], t[1], R[6 + a] * t[2]));
-            int tot = 0;
-            for (int cls = 0; cls < 6; ++cls) {
-                const int a = cls >> 1;
+            int cnt = 0, b = 0;
+            if (lane < 6) {
+                const int cls = lane, a = cls >> 1;
+                const float *R = P, *t = P + 9;
+                const float oa = -fmaf(R[a], t[0], fmaf(R[3 + a], t[1], R[6 + a] * t[2]));
                 const float *cd = m.coords + lat_off(a);
                 const int n = m.nc[a];
                 int lo = 0, hi = n;  // first plane with coordinate >= o
-                while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] < o[a]) lo = mid + 1; else hi = mid; }
+                while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] < oa) lo = mid + 1; else hi = mid; }
                 const int below = lo;
                 hi = n;  // first plane with coordinate > o
-                while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] <= o[a]) lo = mid + 1; else hi = mid; }
+                while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] <= oa) lo = mid + 1; else hi = mid; }
                 const int not_above = lo;
                 const int *off = m.class_off + cls * m.np1;
                 // +axis faces face the camera when their plane is below o; -axis when above
-                const int b = (cls & 1) ? off[0] : off[not_above];
+                b = (cls & 1) ? off[0] : off[not_above];
                 const int e = (cls & 1) ? off[below] : off[n];
-                sh.rng[cls] = b;
-                sh.rng[6 + cls] = tot;
-                tot += e - b;
+                cnt = e - b;
             }
-            sh.rng[12] = tot;
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                const int up = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += up;
+            }
+            if (lane < 6) {
+                sh.rng[lane] = b;
+                sh.rng[6 + lane] = incl - cnt;
+            }
+            if (lane == 5) sh.rng[12] = incl;
         }
-        sh.flags = f;
+        if (lane == 0) {
+            sh.bb[0] = bb0; sh.bb[1] = bb1; sh.bb[2] = bb2; sh.bb[3] = bb3;
+            sh.flags = f;
+        }
     }
     __syncthreads();
     const int flags = sh.flags;
@@ -356,16 +402,22 @@ __device__ __forceinline__ float score_body(const SceneView &S, const Lik &L, co
                         }
                         const int n_cand = __shfl_sync(0xffffffffu, incl, 31);
                         const int excl = incl - cand;
+                        int *own = sh.own + wid * 32;
+                        int carry = 0;  // the lane whose run holds the window's first position
                         __syncwarp();
                         for (int r0 = 0; r0 < n_cand; r0 += 32) {
+                            // runs [excl, incl) tile [0, n_cand) in lane order: the owner of
+                            // position j is the lane whose run starts last at or before j
+                            const bool starts = cand > 0 && excl >= r0 && excl < r0 + 32;
+                            if (starts) own[excl - r0] = lane;
+                            const unsigned pos = __reduce_or_sync(0xffffffffu, starts ? 1u << (excl - r0) : 0u);
+                            __syncwarp();
+                            const unsigned upto = pos & (0xffffffffu >> (31 - lane));
+                            const int lo = upto ? own[31 - __clz(upto)] : carry;
+                            carry = __shfl_sync(0xffffffffu, lo, 31);
                             const int j = r0 + lane;
-                            int lo = 0, hi = 31;  // the first lane whose inclusive count exceeds j
-#pragma unroll
-                            for (int st = 0; st < 5; ++st) {
-                                const int mid = (lo + hi) >> 1;
-                                if (__shfl_sync(0xffffffffu, incl, mid) > j) hi = mid; else lo = mid + 1;
-                            }
                             const int kk = j - __shfl_sync(0xffffffffu, excl, lo);
+                            __syncwarp();
                             if (j < n_cand) {
                                 const float4 *rec = stg + lo * kStageStride;
                                 const float4 Pl = rec[4], Bx = rec[5];
