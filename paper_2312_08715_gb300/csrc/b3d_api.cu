@@ -777,7 +777,7 @@ b3d_status b3d_load_mesh(b3d_ctx *ctx, const float *verts, int64_t n_v, const in
 
     // 5. voxel rectangles: a closed mesh whose surface triangles pair up into unit squares of
     //    the vertex lattice (distinct coordinates per axis), each square axis-aligned; the
-    //    squares of each plane are merged into maximal rectangles
+    //    squares of each plane are merged into rectangles of at most 3 x 3 squares
     std::vector<uint2> h_quads;
     std::vector<int> h_off;
     std::vector<float> h_coords;
@@ -848,8 +848,11 @@ b3d_status b3d_load_mesh(b3d_ctx *ctx, const float *verts, int64_t n_v, const in
                 planes[{cls, p}].push_back({(int)((kv.first >> 9) & 511), (int)(kv.first & 511)});
             }
             if (quads_ok) {
-                // greedy merge of each plane's squares into maximal rectangles (same plane and
-                // outward side, so the union renders exactly as the squares do)
+                // greedy merge of each plane's squares into rectangles (same plane and outward
+                // side, so the union renders exactly as the squares do) of at most
+                // kMaxRectExtent squares a side: a long strip seen at an angle has a screen box
+                // many times its area, and the rasteriser tests every pixel of the box
+                constexpr int kMaxRectExtent = 3;
                 std::vector<uint2> rects;
                 for (auto &pl : planes) {
                     const int cls = pl.first.first, p = pl.first.second;
@@ -865,10 +868,10 @@ b3d_status b3d_load_mesh(b3d_ctx *ctx, const float *verts, int64_t n_v, const in
                         for (int c = 0; c < ncs; ++c) {
                             if (!occ[(size_t)b * ncs + c]) continue;
                             int wc = 1;
-                            while (c + wc < ncs && occ[(size_t)b * ncs + c + wc]) ++wc;
+                            while (c + wc < ncs && wc < kMaxRectExtent && occ[(size_t)b * ncs + c + wc]) ++wc;
                             int hb = 1;
                             for (;;) {
-                                if (b + hb >= nb) break;
+                                if (b + hb >= nb || hb >= kMaxRectExtent) break;
                                 bool row = true;
                                 for (int k = 0; k < wc && row; ++k) row = occ[(size_t)(b + hb) * ncs + c + k] != 0;
                                 if (!row) break;

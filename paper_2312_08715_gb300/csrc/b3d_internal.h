@@ -41,7 +41,7 @@ struct Cam {
 //  - faces: the original faces on welded vertices (triangle id -> vertices).
 //  - rectangles (optional, voxel meshes): every surface triangle pairs with another into a
 //    unit square of the vertex lattice, and the coplanar squares of each lattice plane and
-//    outward side are merged into maximal rectangles; rectangles are grouped by face class
+//    outward side are merged into rectangles of at most 3 x 3 squares; rectangles are grouped by face class
 //    (axis, outward sign) and sorted by lattice plane, so the faces turned towards a camera
 //    position are one contiguous range per class.
 struct MeshView {

@@ -127,6 +127,7 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
         ry[r] = ((float)(ya - W + r - 1) + 0.5f - c.cy) * c.inv_fy;
     }
     float acc = 0.f;
+    const bool ball_skips_empty = L.r2 < 0.25f;
     for (int y = ya; y <= yb; ++y) {
 #pragma unroll
         for (int r = 0; r + 1 < D; ++r) {
@@ -141,15 +142,29 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
         if (q.w == 0.f) continue;
         int n = 0;
         float Ssum = 0.f;
+        if (L.kind == 0 && ball_skips_empty) {
+            // an empty slot holds z = -1, a point at least 1 m from q (q.z > 0): it can only
+            // fail the inlier test, so the count needs no separate z >= 0 test
 #pragma unroll
-        for (int r = 0; r < D; ++r) {
+            for (int r = 0; r < D; ++r) {
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const float z = win[r][d];
-                const float ex = fmaf(-z, rx[d], q.x), ey = fmaf(-z, ry[r], q.y), ez = q.z - z;
-                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                if (L.kind == 0) n += (z >= 0.f && d2 <= L.r2) ? 1 : 0;
-                else if (z >= 0.f) Ssum += __expf(-d2 * L.inv2s2);
+                for (int d = 0; d < D; ++d) {
+                    const float z = win[r][d];
+                    const float ex = fmaf(-z, rx[d], q.x), ey = fmaf(-z, ry[r], q.y), ez = q.z - z;
+                    n += fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= L.r2 ? 1 : 0;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const float z = win[r][d];
+                    const float ex = fmaf(-z, rx[d], q.x), ey = fmaf(-z, ry[r], q.y), ez = q.z - z;
+                    const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                    if (L.kind == 0) n += (z >= 0.f && d2 <= L.r2) ? 1 : 0;
+                    else if (z >= 0.f) Ssum += __expf(-d2 * L.inv2s2);
+                }
             }
         }
         const float l = L.kind == 0 ? lut[n] : __logf(fmaf(L.bg, Ssum, L.a));
