@@ -109,13 +109,19 @@ typedef struct {
 
 /* A coarse-to-fine schedule: stages, particles drawn per stage, the seed of the
  * counter-based generator, and G, the rotation (row-major 3x3, cam_from_grid) whose
- * columns are the translation grid's axes in the camera frame. */
+ * columns are the translation grid's axes in the camera frame. path_density selects what
+ * logq reports: 0, the last stage's proposal density of each particle given that stage's
+ * grid (log P_T(cell) - 3 log step_T); 1, the density of the whole coarse-to-fine path
+ * (the sum over stages of the log probability of the cell that centred the next stage,
+ * plus the last stage's term), which is the proposal density q of Sec. III-B when
+ * n_particles = 1 (each particle its own proposal). */
 typedef struct {
     int32_t n_stages;
     b3d_stage stage[B3D_MAX_STAGES];
     int32_t n_particles;
     uint64_t seed;
     float grid_frame[9];
+    int32_t path_density;
 } b3d_c2f_schedule;
 
 /* Create a context on CUDA device `device`. Allocations made on its behalf may total at

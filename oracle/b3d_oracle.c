@@ -686,12 +686,13 @@ int orc_expand(const double *centre, const double *G, int32_t n, double step, co
  */
 int orc_enumerate_c2f(const orc_camera *cam, const orc_scene *sc, int32_t slot, const double *centre0,
                       const double *G, const orc_lik *lk, const double *depth_obs, int32_t n_stages,
-                      const orc_stage *stages, int32_t m, uint64_t seed, double *particles, double *logw,
-                      double *logq, double *centres, double *zs, int32_t *idx_all, int32_t n_threads) {
+                      const orc_stage *stages, int32_t m, uint64_t seed, int32_t path_density, double *particles,
+                      double *logw, double *logq, double *centres, double *zs, int32_t *idx_all, int32_t n_threads) {
     if (!cam || !sc || !centre0 || !G || !lk || !depth_obs || n_stages <= 0 || !stages || m <= 0 || !particles)
         return ORC_EINVAL;
     double centre[16];
     memcpy(centre, centre0, sizeof centre);
+    double path = 0.0;  /* log probability of the cells that centred the later stages */
     int err = ORC_OK;
     int32_t *idx = malloc(sizeof(int32_t) * m);
     double *poses = NULL, *ll = NULL, *rot = NULL;
@@ -718,6 +719,7 @@ int orc_enumerate_c2f(const orc_camera *cam, const orc_scene *sc, int32_t slot, 
             if (ll[idx[k]] > ll[best] || (ll[idx[k]] == ll[best] && idx[k] < best)) best = idx[k];
         if (t + 1 < n_stages) {
             memcpy(centre, poses + 16 * (int64_t)best, sizeof centre);
+            if (path_density) path += ll[best] - Z;
         } else {
             const double s = st->step;
             for (int k = 0; k < m; ++k) {
@@ -727,7 +729,7 @@ int orc_enumerate_c2f(const orc_camera *cam, const orc_scene *sc, int32_t slot, 
                 for (int l = 0; l < 3; ++l) u[l] = (draw_uniform(seed, k, n_stages, 1, l) - 0.5) * s;
                 for (int a = 0; a < 3; ++a) out[4 * a + 3] += G[3 * a + 0] * u[0] + G[3 * a + 1] * u[1] + G[3 * a + 2] * u[2];
                 if (logw) logw[k] = ll[idx[k]];
-                if (logq) logq[k] = ll[idx[k]] - Z - 3.0 * log(s);
+                if (logq) logq[k] = ll[idx[k]] - Z - 3.0 * log(s) + path;
             }
         }
     }

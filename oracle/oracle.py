@@ -8,8 +8,10 @@ inputs of ``paper_2312_08715_gb300.synth``.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
+import types
 
 import numpy as np
 
@@ -212,7 +214,8 @@ def expand(centre, G, n, step, rotset):
     return poses
 
 
-def enumerate_c2f(scene, slot, centre, G, lk: dict, depth_obs, stages, m, seed, n_threads=0, arrays=None):
+def enumerate_c2f(scene, slot, centre, G, lk: dict, depth_obs, stages, m, seed, n_threads=0, arrays=None,
+                  path_density=False):
     sa = arrays or SceneArrays(scene)
     T = len(stages)
     st = (_Stage * T)(*[_Stage(s.n_per_axis, s.step, s.rot_kind, s.n_rot, s.rot_max) for s in stages])
@@ -222,7 +225,8 @@ def enumerate_c2f(scene, slot, centre, G, lk: dict, depth_obs, stages, m, seed, 
     idx = np.empty((T, m), np.int32)
     rc = lib().orc_enumerate_c2f(C.byref(sa.cam), C.byref(sa.st), C.c_int32(slot), _p(_f64(centre).reshape(16)),
                                  _p(_f64(G).reshape(9)), C.byref(lik(**lk)), _p(_f64(depth_obs)), C.c_int32(T), st,
-                                 C.c_int32(m), C.c_uint64(seed), _p(particles), _p(logw), _p(logq), _p(centres),
+                                 C.c_int32(m), C.c_uint64(seed), C.c_int32(1 if path_density else 0), _p(particles),
+                                 _p(logw), _p(logq), _p(centres),
                                  _p(zs), _p(idx), C.c_int32(n_threads))
     assert rc == 0, rc
     return dict(particles=particles, logw=logw, logq=logq, centres=centres, z=zs, idx=idx)
@@ -242,3 +246,54 @@ def score_grad(scene, slot, poses, lk: dict, depth_obs, n_threads=0, arrays=None
 
 def max_threads() -> int:
     return int(lib().orc_max_threads())
+
+
+def smc_parse(scene, n_fixed, centres, G, lk: dict, depth_obs, stages, m, seed, ess_frac=0.5, n_threads=0):
+    """SMC over the number of objects (Sec. III-B, Eq. 2 and 3), each particle proposing the
+    next object's pose with its own single-sample coarse-to-fine search.
+
+    Objects 0 .. n_fixed-1 of ``scene`` are known and fixed; objects n_fixed .. are placed one
+    per step, in order, around ``centres[k]``. The step-k target p_k is the likelihood of the
+    scene holding the fixed objects and the first k+1 placed objects at the particle's poses
+    (uniform priors: constants that cancel between particles). Particle j draws its step-k
+    proposal with seed ``seed + 1000 k + j``; its log density log q is the path density.
+    Log weights: W = LL_1(x) - log q(x_1), then W += LL_k - LL_{k-1} - log q(x_k). When the
+    effective sample size falls below ess_frac * m, the particles are resampled in proportion
+    to their weights (draws of stage k with ``seed``) and every weight becomes their mean.
+    Returns the particles' poses [m, K, 4, 4], log weights, the log evidence estimate
+    (log-mean weight) and, per step, the ESS before resampling and the resampled indices.
+    """
+    K = len(centres)
+    meshes = scene.meshes[:n_fixed + K]
+    poses = np.tile(_f64(scene.poses[:n_fixed + K])[None], (m, 1, 1, 1))
+    logw = np.zeros(m)
+    ll_prev = np.zeros(m)
+    ess_all, idx_all = [], []
+    for k in range(K):
+        slot = n_fixed + k
+        sub_meshes = meshes[:slot + 1]
+        for j in range(m):
+            sub = types.SimpleNamespace(camera=scene.camera, meshes=sub_meshes, poses=poses[j, :slot + 1].copy())
+            arrays = SceneArrays(sub)
+            out = enumerate_c2f(sub, slot, centres[k], G, lk, depth_obs, stages, 1, seed + 1000 * k + j,
+                                n_threads=n_threads, arrays=arrays, path_density=True)
+            x = out["particles"][0]
+            poses[j, slot] = x
+            sub.poses[slot] = x
+            ll = score(sub, slot, x[None], lk, depth_obs, flags=False, n_threads=n_threads,
+                       arrays=SceneArrays(sub))["ll"][0]
+            logw[j] += ll - ll_prev[j] - out["logq"][0]
+            ll_prev[j] = ll
+        z, _ = lse(logw)
+        z2, _ = lse(2 * logw)
+        ess = math.exp(2 * z - z2)
+        ess_all.append(ess)
+        if ess < ess_frac * m:
+            idx, _, _ = resample(logw, m, seed, k)
+            poses, ll_prev = poses[idx].copy(), ll_prev[idx].copy()
+            logw = np.full(m, z - math.log(m))
+            idx_all.append(idx)
+        else:
+            idx_all.append(None)
+    z, _ = lse(logw)
+    return dict(poses=poses[:, n_fixed:], logw=logw, log_evidence=z - math.log(m), ess=ess_all, idx=idx_all)

@@ -64,7 +64,7 @@ class b3d_tuning(C.Structure):
 
 class b3d_c2f_schedule(C.Structure):
     _fields_ = [("n_stages", C.c_int32), ("stage", b3d_stage * B3D_MAX_STAGES), ("n_particles", C.c_int32),
-                ("seed", C.c_uint64), ("grid_frame", C.c_float * 9)]
+                ("seed", C.c_uint64), ("grid_frame", C.c_float * 9), ("path_density", C.c_int32)]
 
 
 class b3d_score_item(C.Structure):
@@ -253,8 +253,9 @@ def stage_params(s) -> b3d_stage:
     return b3d_stage(int(s.n_per_axis), float(s.step), int(s.rot_kind), int(s.n_rot), float(s.rot_max))
 
 
-def schedule(stages, n_particles, seed, grid_frame) -> b3d_c2f_schedule:
+def schedule(stages, n_particles, seed, grid_frame, path_density=False) -> b3d_c2f_schedule:
     sch = b3d_c2f_schedule()
+    sch.path_density = 1 if path_density else 0
     sch.n_stages = len(stages)
     for k, s in enumerate(stages):
         sch.stage[k] = stage_params(s)
@@ -686,14 +687,16 @@ class Context:
         b3d_lse_resample(self.h, ll.numel(), ll, m, seed, stage, logz, idx, logq, self.stream)
         return logz, idx[:m], logq[:m]
 
-    def enumerate_c2f(self, slot, centre, stages, lik: dict, n_particles, seed, grid_frame, out=None):
+    def enumerate_c2f(self, slot, centre, stages, lik: dict, n_particles, seed, grid_frame, out=None,
+                      path_density=False):
         t = self.torch
         if out is None:
             out = (t.empty((n_particles, 4, 4), dtype=t.float32, device=self.device),
                    t.empty(n_particles, dtype=t.float32, device=self.device),
                    t.empty(n_particles, dtype=t.float32, device=self.device))
         particles, logw, logq = out
-        b3d_enumerate_c2f(self.h, slot, centre, schedule(stages, n_particles, seed, grid_frame), lik_params(**lik),
+        b3d_enumerate_c2f(self.h, slot, centre, schedule(stages, n_particles, seed, grid_frame, path_density),
+                          lik_params(**lik),
                           particles, logw, logq, self.stream)
         return particles, logw, logq
 

@@ -1167,6 +1167,7 @@ b3d_status b3d_enumerate_c2f(b3d_ctx *ctx, int32_t obj_slot, const float *centre
         return fail(ctx, B3D_EINVAL, "centre_pose, schedule and the three outputs must be non-NULL");
     if (!finite_all(centre_pose, 16) || !finite_all(sch->grid_frame, 9)) return fail(ctx, B3D_EINVAL, "non-finite centre or grid frame");
     if (sch->n_stages < 1 || sch->n_stages > B3D_MAX_STAGES) return fail(ctx, B3D_EINVAL, "n_stages must be in [1, 8]");
+    if (sch->path_density != 0 && sch->path_density != 1) return fail(ctx, B3D_EINVAL, "path_density must be 0 or 1");
     if (sch->n_particles < 1 || sch->n_particles > (1 << 20)) return fail(ctx, B3D_EINVAL, "n_particles must be in [1, 2^20]");
     int64_t n_max = 0, n_t[B3D_MAX_STAGES];
     for (int t = 0; t < sch->n_stages; ++t) {
@@ -1207,7 +1208,8 @@ b3d_status b3d_enumerate_c2f(b3d_ctx *ctx, int32_t obj_slot, const float *centre
         const int last = t == sch->n_stages - 1;
         {
             Timed tm(ctx, B3D_K_SELECT, s);
-            launch_c2f_select(ctx->d_ll, ctx->d_idx, sch->n_particles, P, ctx->d_logz + t, last, sch->seed,
+            launch_c2f_select(ctx->d_ll, ctx->d_idx, sch->n_particles, P, ctx->d_logz + t, last, sch->path_density, t,
+                              sch->seed,
                               sch->n_stages, last ? nullptr : ctx->d_centre + 16 * ((t + 1) & 1), particles_dev, logw_dev,
                               logq_dev, s);
         }
@@ -1316,6 +1318,7 @@ b3d_status b3d_enumerate_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_it
         const b3d_c2f_schedule &sch = it.schedule;
         if (sch.n_stages != T) return fail(owner, B3D_EINVAL, tag + "every schedule needs the same number of stages");
         if (sch.n_particles < 1 || sch.n_particles > (1 << 20)) return fail(owner, B3D_EINVAL, tag + "n_particles out of range");
+        if (sch.path_density != 0 && sch.path_density != 1) return fail(owner, B3D_EINVAL, tag + "path_density must be 0 or 1");
         if (!it.particles_dev || !it.logw_dev || !it.logq_dev) return fail(owner, B3D_EINVAL, tag + "outputs must be non-NULL");
         if ((!it.centre_dev && !finite_all(it.centre_pose, 16)) || !finite_all(sch.grid_frame, 9))
             return fail(owner, B3D_EINVAL, tag + "non-finite centre or grid frame");
@@ -1443,6 +1446,7 @@ b3d_status b3d_enumerate_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_it
             sv.logq = it.logq_dev;
             sv.seed = l.seed;
             sv.n_stages = T;
+            sv.path = it.schedule.path_density;
             si[k] = sv;
             acc += n;
             bacc += nb;
@@ -1474,7 +1478,7 @@ b3d_status b3d_enumerate_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_it
         {
             Timed tm(owner, B3D_K_SELECT, s);
             launch_select_multi(reinterpret_cast<const SelectItem *>(d + o_si) + (size_t)t * n_items, n_items,
-                                t == T - 1, s);
+                                t == T - 1, t, s);
         }
         owner->launches += 3;
     }

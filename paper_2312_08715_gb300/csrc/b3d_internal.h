@@ -151,6 +151,7 @@ struct SelectItem {
     float *particles, *logw, *logq;
     unsigned long long seed;
     int n_stages;
+    int path;  // accumulate the path density in logq (see b3d_c2f_schedule)
 };
 
 // Dynamic shared memory opt-in and resident CTAs per SM of a kernel, set and queried once
@@ -189,7 +190,7 @@ int launch_score_multi(const BatchItem *items, int n_items, const int64_t *item_
 // ---- launchers (k_c2f.cu) ----------------------------------------------------------------
 void launch_lse_multi(const LseItem *items, int n_items, int total_blocks, const int *block_begin, int *err,
                       cudaStream_t s);
-void launch_select_multi(const SelectItem *items, int n_items, int last, cudaStream_t s);
+void launch_select_multi(const SelectItem *items, int n_items, int last, int stage, cudaStream_t s);
 // dst[i][0..15] = src[i][0..15] for pairs (src, dst) in device memory
 void launch_gather16(const float *const *pairs, int n, cudaStream_t s);
 void launch_set16(float *dst, const float *src16_host_values, cudaStream_t s);
@@ -198,8 +199,8 @@ void launch_expand(PoseGrid P, int64_t n, float *poses, cudaStream_t s);
 int lse_blocks(int64_t n);
 void launch_lse_resample(const float *ll, int64_t n, int m, uint64_t seed, int stage, float2 *part,
                          unsigned *counter, float *logz, int *idx, float *logq, int *err, cudaStream_t s);
-void launch_c2f_select(const float *ll, const int *idx, int m, PoseGrid P, const float *logz, int last,
-                       uint64_t seed, int n_stages, float *centre_next, float *particles, float *logw,
+void launch_c2f_select(const float *ll, const int *idx, int m, PoseGrid P, const float *logz, int last, int path,
+                       int stage, uint64_t seed, int n_stages, float *centre_next, float *particles, float *logw,
                        float *logq, cudaStream_t s);
 void launch_copy16(const float *src, float *dst, cudaStream_t s);
 

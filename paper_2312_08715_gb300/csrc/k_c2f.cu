@@ -303,10 +303,13 @@ void launch_lse_resample(const float *ll, int64_t n, int m, uint64_t seed, int s
 // centre_next (not last; at the last stage only when non-NULL) = pose of the drawn cell with
 // the highest score (ties to the smaller index). Last: particle k = pose of drawn cell idx_k
 // with t += G ((u - 1/2) step), its score and proposal log density score - logZ - 3 log(step).
+// path (with stage > 0 or not last): logq[0] carries, between stages, the sum of the log
+// probabilities (score - logZ) of the cells that centred the later stages; the last stage
+// adds it to every particle's log density.
 __device__ __forceinline__ void select_body(float *s_v, int *s_i, const float *ll, const int *idx, int m,
-                                            const PoseGrid &P, const float *logz, int last, unsigned long long seed,
-                                            int n_stages, float *centre_next, float *particles, float *logw,
-                                            float *logq) {
+                                            const PoseGrid &P, const float *logz, int last, int path, int stage,
+                                            unsigned long long seed, int n_stages, float *centre_next,
+                                            float *particles, float *logw, float *logq) {
     const int tid = threadIdx.x;
     if (!last || centre_next) {
         float bv = -INFINITY;
@@ -333,11 +336,17 @@ __device__ __forceinline__ void select_body(float *s_v, int *s_i, const float *l
             const int best = s_i[0] == INT32_MAX ? 0 : s_i[0];
             pose12(P, best, o);
             write_pose16(o, centre_next);
+            if (path && !last) {
+                const float term = s_i[0] == INT32_MAX ? -INFINITY : ll[best] - *logz;
+                logq[0] = stage == 0 ? term : logq[0] + term;
+            }
         }
         if (!last) return;
     }
     const float Z = *logz;
     const float lstep = 3.f * logf(P.step);
+    const float acc = path && stage > 0 ? logq[0] : 0.f;
+    __syncthreads();
     for (int k = tid; k < m; k += blockDim.x) {
         const int i = idx[k];
         float o[12];
@@ -349,25 +358,25 @@ __device__ __forceinline__ void select_body(float *s_v, int *s_i, const float *l
         write_pose16(o, particles + 16 * (int64_t)k);
         const float v = i < 0 ? -INFINITY : ll[i];
         logw[k] = v;
-        logq[k] = v - Z - lstep;
+        logq[k] = v - Z - lstep + acc;
     }
 }
 
-__global__ void k_c2f_select(const float *ll, const int *idx, int m, PoseGrid P, const float *logz, int last,
-                             unsigned long long seed, int n_stages, float *centre_next, float *particles, float *logw,
-                             float *logq) {
+__global__ void k_c2f_select(const float *ll, const int *idx, int m, PoseGrid P, const float *logz, int last, int path,
+                             int stage, unsigned long long seed, int n_stages, float *centre_next, float *particles,
+                             float *logw, float *logq) {
     __shared__ float s_v[256];
     __shared__ int s_i[256];
-    select_body(s_v, s_i, ll, idx, m, P, logz, last, seed, n_stages, centre_next, particles, logw, logq);
+    select_body(s_v, s_i, ll, idx, m, P, logz, last, path, stage, seed, n_stages, centre_next, particles, logw, logq);
 }
 
 // Batched: one block per scene.
-__global__ void k_select_multi(const SelectItem *items, int last) {
+__global__ void k_select_multi(const SelectItem *items, int last, int stage) {
     __shared__ float s_v[256];
     __shared__ int s_i[256];
     const SelectItem &it = items[blockIdx.x];
-    select_body(s_v, s_i, it.ll, it.idx, it.m, it.grid, it.logz, last, it.seed, it.n_stages, it.centre_next,
-                it.particles, it.logw, it.logq);
+    select_body(s_v, s_i, it.ll, it.idx, it.m, it.grid, it.logz, last, it.path, stage, it.seed, it.n_stages,
+                it.centre_next, it.particles, it.logw, it.logq);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -388,10 +397,11 @@ void launch_expand(PoseGrid P, int64_t n, float *poses, cudaStream_t s) {
     k_expand<<<(int)std::min<int64_t>((n + 255) / 256, 65535), 256, 0, s>>>(P, n, poses);
 }
 
-void launch_c2f_select(const float *ll, const int *idx, int m, PoseGrid P, const float *logz, int last, uint64_t seed,
-                       int n_stages, float *centre_next, float *particles, float *logw, float *logq, cudaStream_t s) {
-    k_c2f_select<<<1, 256, 0, s>>>(ll, idx, m, P, logz, last, (unsigned long long)seed, n_stages, centre_next,
-                                   particles, logw, logq);
+void launch_c2f_select(const float *ll, const int *idx, int m, PoseGrid P, const float *logz, int last, int path,
+                       int stage, uint64_t seed, int n_stages, float *centre_next, float *particles, float *logw,
+                       float *logq, cudaStream_t s) {
+    k_c2f_select<<<1, 256, 0, s>>>(ll, idx, m, P, logz, last, path, stage, (unsigned long long)seed, n_stages,
+                                   centre_next, particles, logw, logq);
 }
 
 void launch_lse_multi(const LseItem *items, int n_items, int total_blocks, const int *block_begin, int *err,
@@ -400,9 +410,9 @@ void launch_lse_multi(const LseItem *items, int n_items, int total_blocks, const
     k_lse_multi<<<total_blocks, kLseThreads, 0, s>>>(items, n_items, block_begin, err);
 }
 
-void launch_select_multi(const SelectItem *items, int n_items, int last, cudaStream_t s) {
+void launch_select_multi(const SelectItem *items, int n_items, int last, int stage, cudaStream_t s) {
     if (n_items <= 0) return;
-    k_select_multi<<<n_items, 256, 0, s>>>(items, last);
+    k_select_multi<<<n_items, 256, 0, s>>>(items, last, stage);
 }
 
 __global__ void k_gather16(const float *const *pairs, int n) {

@@ -64,8 +64,9 @@ def test_struct_layouts_match_the_header(tmp_path):
 #include "b3d.h"
 int main(void) {
   printf("%zu %zu %zu %zu\\n", sizeof(b3d_intrinsics), sizeof(b3d_lik_params), sizeof(b3d_stage), sizeof(b3d_c2f_schedule));
-  printf("%zu %zu %zu %zu\\n", offsetof(b3d_c2f_schedule, stage), offsetof(b3d_c2f_schedule, n_particles),
-         offsetof(b3d_c2f_schedule, seed), offsetof(b3d_c2f_schedule, grid_frame));
+  printf("%zu %zu %zu %zu %zu\\n", offsetof(b3d_c2f_schedule, stage), offsetof(b3d_c2f_schedule, n_particles),
+         offsetof(b3d_c2f_schedule, seed), offsetof(b3d_c2f_schedule, grid_frame),
+         offsetof(b3d_c2f_schedule, path_density));
   printf("%zu %zu\\n", offsetof(b3d_lik_params, volume), offsetof(b3d_lik_params, miss_mode));
   printf("%zu %zu\\n", sizeof(b3d_tuning), offsetof(b3d_tuning, high_occupancy));
   printf("%zu %zu %zu %zu %zu\\n", sizeof(b3d_score_item), sizeof(b3d_c2f_item), offsetof(b3d_c2f_item, particles_dev),
@@ -86,6 +87,7 @@ int main(void) {
             C.sizeof(b3d.b3d_c2f_schedule),
             b3d.b3d_c2f_schedule.stage.offset, b3d.b3d_c2f_schedule.n_particles.offset,
             b3d.b3d_c2f_schedule.seed.offset, b3d.b3d_c2f_schedule.grid_frame.offset,
+            b3d.b3d_c2f_schedule.path_density.offset,
             b3d.b3d_lik_params.volume.offset, b3d.b3d_lik_params.miss_mode.offset,
             C.sizeof(b3d.b3d_tuning), b3d.b3d_tuning.high_occupancy.offset,
             C.sizeof(b3d.b3d_score_item), C.sizeof(b3d.b3d_c2f_item), b3d.b3d_c2f_item.particles_dev.offset,
@@ -103,8 +105,13 @@ def test_oracle_and_product_share_no_code():
     for f in os.listdir(csrc):
         txt = open(os.path.join(csrc, f)).read()
         assert "oracle" not in txt.lower() or f.endswith(".md"), f
-    for f in ("b3d.py", "build.py", "synth.py", "__init__.py"):
-        txt = open(os.path.join(ROOT, "paper_2312_08715_gb300", f)).read()
+    pkg = os.path.join(ROOT, "paper_2312_08715_gb300")
+    for f in sorted(os.listdir(pkg)):
+        if not f.endswith(".py"):
+            continue
+        txt = open(os.path.join(pkg, f)).read()
         assert "import oracle" not in txt and "from oracle" not in txt, f
+    otxt_py = open(os.path.join(ROOT, "oracle", "oracle.py")).read()
+    assert "paper_2312_08715_gb300" not in otxt_py.replace("paper_2312_08715_gb300.synth", "")
     otxt = open(os.path.join(ROOT, "oracle", "b3d_oracle.c")).read()
     assert "b3d.h" not in otxt and "b3d_internal" not in otxt

@@ -307,6 +307,43 @@ def test_enumerate_c2f_matches_oracle(orc, single_object):
     np.testing.assert_allclose(_np(logq), ref["logq"], atol=1e-4 * scale * 4)
 
 
+def test_enumerate_path_density_matches_oracle(orc, single_object):
+    """One particle per proposal and the density of its whole path of cells (Sec. III-B),
+    single-scene and batched (8 proposals in one launch), against the oracle."""
+    from paper_2312_08715_gb300 import b3d
+    wl = single_object
+    sc = wl.scene
+    obs = observed(orc, wl)
+    centre = wl.hidden.astype(np.float64).copy()
+    centre[:3, 3] += [0.006, -0.004, 0.009]
+    stages = [synth.StageSpec(5, 0.008, 1, 3, math.radians(3)), synth.StageSpec(5, 0.002, 1, 2, math.radians(1)),
+              synth.StageSpec(3, 0.0007, 1, 1, 0.0)]
+    ctx = gpu_context(sc, obs)
+    owner = b3d.Context(0)
+    items, outs, refs = [], [], []
+    for k in range(8):
+        ref = orc.enumerate_c2f(sc, 0, centre, np.eye(3), wl.lik, obs, stages, 1, 40 + k, path_density=True)
+        refs.append(ref)
+        o = (torch.empty((1, 4, 4), device="cuda"), torch.empty(1, device="cuda"), torch.empty(1, device="cuda"))
+        outs.append(o)
+        items.append(b3d.c2f_item(ctx.h, 0, centre.astype(np.float32), b3d.schedule(stages, 1, 40 + k, np.eye(3), True),
+                                  *o))
+    b3d.b3d_enumerate_multi(owner.h, items, b3d.lik_params(**wl.lik), owner.stream)
+    single = ctx.enumerate_c2f(0, centre.astype(np.float32), stages, wl.lik, 1, 40, np.eye(3), path_density=True)
+    owner.sync()
+    ctx.sync()
+    for k, (ref, o) in enumerate(zip(refs, outs)):
+        scale = abs(ref["logw"][0])
+        np.testing.assert_allclose(_np(o[0])[0], ref["particles"][0], atol=2e-6)
+        assert abs(float(_np(o[1])[0]) - ref["logw"][0]) <= 4e-4 * scale
+        # the path sums T score differences, each good to the score tolerance
+        assert abs(float(_np(o[2])[0]) - ref["logq"][0]) <= len(stages) * 4e-4 * scale, (k, _np(o[2]), ref["logq"])
+    for got, o in zip(single, outs[0]):
+        np.testing.assert_array_equal(_np(got), _np(o))
+    ctx.close()
+    owner.close()
+
+
 def test_enumerate_c2f_tabletop_tracks_hidden_pose(orc, tabletop):
     """Three stages of 145,800 hypotheses around a tracking prior (<= 2 cm, <= 5 deg off)
     end within a few millimetres of the hidden pose (a sanity check of the whole path)."""

@@ -357,6 +357,40 @@ def test_enumerate_c2f_recovers_hidden_pose(orc, single_object):
     np.testing.assert_allclose(out["logq"], out["logw"] - out["z"][-1] - 3 * math.log(0.0025), atol=1e-9)
 
 
+def test_path_density_matches_path_frequencies(orc, single_object):
+    """With one particle per proposal (Sec. III-B: sample a cell in proportion to its score,
+    recurse into it, then a uniform point in the last cell) the reported path density
+    exp(logq) * step_T^3 is the probability of the sampled path of cells: over 2,000 seeds
+    the frequencies of the paths of a 2-stage, 2^3-cell schedule match it (chi-square), and
+    with one stage it reduces to the last-stage density."""
+    from scipy import stats
+    wl = single_object
+    sc = wl.scene
+    obs = synth.corrupt_depth(orc.render(sc)[0], 2.0, wl.draws)
+    lk = dict(kind=1, radius=0.01, p_outlier=0.01, half_window=1)
+    centre = wl.hidden.astype(np.float64)
+    stages = [synth.StageSpec(2, 0.0002, 1, 1, 0.0), synth.StageSpec(2, 0.0001, 1, 1, 0.0)]
+    n = 2000
+    count, prob = {}, {}
+    for seed in range(n):
+        o = orc.enumerate_c2f(sc, 0, centre, np.eye(3), lk, obs, stages, 1, seed, path_density=True)
+        key = tuple(o["idx"][:, 0])
+        count[key] = count.get(key, 0) + 1
+        prob[key] = math.exp(o["logq"][0] + 3 * math.log(stages[-1].step))
+    keys = sorted(count)
+    assert len(keys) >= 10  # a spread-out proposal, so the test has power
+    p = np.array([prob[k] for k in keys])
+    assert p.sum() <= 1 + 1e-9 and p.sum() > 0.99  # the unseen paths are rare
+    c = np.array([count[k] for k in keys], dtype=np.float64)
+    e = n * p
+    keep = e >= 5
+    chi2 = float(((c[keep] - e[keep]) ** 2 / e[keep]).sum())
+    assert stats.chi2.sf(chi2, int(keep.sum()) - 1) > 1e-3, (chi2, keep.sum())
+    one = orc.enumerate_c2f(sc, 0, centre, np.eye(3), lk, obs, stages[:1], 4, 5, path_density=True)
+    last = orc.enumerate_c2f(sc, 0, centre, np.eye(3), lk, obs, stages[:1], 4, 5)
+    np.testing.assert_array_equal(one["logq"], last["logq"])
+
+
 # ---------------------------------------------------------------------------------------
 # Gradient of the Gaussian-window log-likelihood
 # ---------------------------------------------------------------------------------------
@@ -419,3 +453,51 @@ def test_gradient_of_translation_along_view_axis(orc):
     g = orc.score_grad(scene, 0, pose[None], lk, obs)["dpose"][0]
     assert g[2] > 0  # moving back toward the observation raises the likelihood
     assert abs(g[0]) < 1e-9 * abs(g[2]) and abs(g[1]) < 1e-9 * abs(g[2])
+
+
+# ---------------------------------------------------------------------------------------
+# SMC over the number of objects (Eq. 2 and 3)
+# ---------------------------------------------------------------------------------------
+
+def _two_object_scene(orc):
+    """Two blobs far apart on a 96x72 image (disjoint footprints), camera 0.6 m above."""
+    rng = np.random.default_rng(77)
+    cells = [np.argwhere(rng.random((6, 6, 4)) < 0.7) for _ in range(2)]
+    meshes = [synth.voxel_mesh(c, 0.01, origin=(-0.03, -0.03, -0.02)) for c in cells]
+    cam = synth.Camera(96, 72, 90.0, 90.0, 48.0, 36.0, 0.01, 2.0)
+    poses = np.stack([synth.rigid(np.eye(3), [-0.12, 0.0, 0.6]), synth.rigid(np.eye(3), [0.12, 0.02, 0.6])])
+    sc = synth.Scene(cam, meshes, poses.astype(np.float32))
+    obs = orc.render(sc)[0].astype(np.float32)
+    return sc, obs
+
+
+def test_smc_weights_of_a_near_exact_proposal(orc):
+    """Importance sampling with a proposal proportional to the target gives every particle
+    the same weight, the target's normaliser: with one stage of 1-micron cells, W_1 is
+    log Z + 3 log step (Eq. 2), and the step-2 increment of Eq. 3 is
+    log Z' + 3 log step - LL_1(x_1) for a second object whose footprint is disjoint."""
+    sc, obs = _two_object_scene(orc)
+    lk = dict(kind=1, radius=0.004, p_outlier=0.01, half_window=1)
+    stages = [synth.StageSpec(3, 1e-6, 1, 1, 0.0)]
+    # centres off the render's pixel-aligned true poses, so no pixel centre sits within a
+    # micron's reach of an edge (the likelihood is then smooth across a cell)
+    centres = [sc.poses[0].astype(np.float64), sc.poses[1].astype(np.float64)]
+    centres[0][:3, 3] += [0.00123, -0.00071, 0.00037]
+    centres[1][:3, 3] += [-0.00052, 0.00091, -0.00043]
+    out = orc.smc_parse(sc, 0, centres, np.eye(3), lk, obs, stages, m=3, seed=5, ess_frac=0.0)
+    for j in range(3):
+        one = synth.Scene(sc.camera, sc.meshes[:1], sc.poses[:1].copy())
+        e1 = orc.enumerate_c2f(one, 0, centres[0], np.eye(3), lk, obs, stages, 1, 5 + j, path_density=True)
+        w1 = e1["z"][-1] + 3 * math.log(1e-6)
+        two = synth.Scene(sc.camera, sc.meshes, np.stack([e1["particles"][0], sc.poses[1]]).astype(np.float64))
+        e2 = orc.enumerate_c2f(two, 1, centres[1], np.eye(3), lk, obs, stages, 1, 5 + 1000 + j, path_density=True)
+        one.poses[0] = e1["particles"][0]
+        ll1 = orc.score(one, 0, e1["particles"][:1], lk, obs, flags=False)["ll"][0]
+        w2 = w1 + e2["z"][-1] + 3 * math.log(1e-6) - ll1
+        assert out["logw"][j] == pytest.approx(w2, abs=0.05), (j, out["logw"][j], w2)
+    # with a single step, resampling keeps the mean weight: the evidence does not change
+    a = orc.smc_parse(sc, 0, centres[:1], np.eye(3), lk, obs, stages, m=4, seed=9, ess_frac=0.0)
+    b = orc.smc_parse(sc, 0, centres[:1], np.eye(3), lk, obs, stages, m=4, seed=9, ess_frac=2.0)
+    assert b["idx"][0] is not None and a["idx"][0] is None
+    assert a["log_evidence"] == pytest.approx(b["log_evidence"], abs=1e-9)
+    np.testing.assert_allclose(b["logw"], b["log_evidence"], atol=1e-9)
