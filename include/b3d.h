@@ -285,6 +285,35 @@ b3d_status b3d_score_grad(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const f
                           const b3d_lik_params *lik, float *loglik_dev, float *dpose_dev, float *dsigma_dev,
                           float *dpout_dev, b3d_stream stream);
 
+/* Hierarchical noise (Alg. 1 lines 11-12: p_out ~ U(0,1), sigma ~ U(0, sigma_max), and
+ * "score hypotheses under several noise settings"): a grid of n_radius inlier radii (kind 0)
+ * or Gaussian standard deviations (kind 1) times n_pout outlier probabilities. Setting
+ * g = i * n_pout + j is (radius[i], p_outlier[j]); log_weight[g] is the log of its prior mass
+ * (quadrature weight; all 0 for equal weights). volume, norm, miss_mode as b3d_lik_params. */
+#define B3D_MAX_NOISE_R 4
+#define B3D_MAX_NOISE_P 4
+typedef struct {
+    int32_t kind;
+    int32_t half_window; /* 0..2 */
+    int32_t n_radius;    /* 1..B3D_MAX_NOISE_R */
+    int32_t n_pout;      /* 1..B3D_MAX_NOISE_P */
+    float radius[B3D_MAX_NOISE_R];
+    float p_outlier[B3D_MAX_NOISE_P];
+    float log_weight[B3D_MAX_NOISE_R * B3D_MAX_NOISE_P];
+    float volume;
+    float norm;
+    int32_t miss_mode;
+} b3d_noise_grid;
+
+/* Score n_hyp hypotheses of object obj_slot (poses_dev [n_hyp, 16]) under every setting of
+ * the noise grid in one fused pass (each hypothesis rendered once): loglik_dev
+ * [n_hyp, n_radius * n_pout] (may be NULL) receives the log-likelihood under each setting,
+ * marginal_dev [n_hyp] log sum_g exp(loglik_g + log_weight_g), the likelihood with the noise
+ * marginalised over the grid. */
+b3d_status b3d_score_noise_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const float *poses_dev,
+                                 const b3d_noise_grid *grid, float *loglik_dev, float *marginal_dev,
+                                 b3d_stream stream);
+
 /* Launch shape of the fused render + score kernel (no counterpart in the paper: a property
  * of this implementation). tile_w: widest screen tile in pixels (8..256); cta_threads: 32,
  * 64, 128 or 256 (one hypothesis per CTA at a time); ctas_per_sm: CTAs resident per SM

@@ -297,3 +297,27 @@ def smc_parse(scene, n_fixed, centres, G, lk: dict, depth_obs, stages, m, seed, 
             idx_all.append(None)
     z, _ = lse(logw)
     return dict(poses=poses[:, n_fixed:], logw=logw, log_evidence=z - math.log(m), ess=ess_all, idx=idx_all)
+
+
+def score_noise(scene, slot, poses, kind, radii, p_outliers, half_window, depth_obs, log_weight=None, n_threads=0):
+    """Hierarchical noise (Alg. 1 lines 11-12): the log-likelihood of each hypothesis under
+    every setting (radii[i], p_outliers[j]) at g = i * len(p_outliers) + j, and the marginal
+    log sum_g exp(ll_g + log_weight_g), the noise integrated out over the grid with the
+    settings' prior masses. Returns ll [n, G], marginal [n], and per setting the flags' scale
+    and ambiguity bound [n, G]."""
+    nr, npo = len(radii), len(p_outliers)
+    lw = np.zeros(nr * npo) if log_weight is None else _f64(log_weight).ravel()
+    P = _f64(poses).reshape(-1, 16)
+    ll = np.empty((P.shape[0], nr * npo))
+    scale, bound = np.empty_like(ll), np.empty_like(ll)
+    arrays = SceneArrays(scene)
+    for i, r in enumerate(radii):
+        for j, p in enumerate(p_outliers):
+            out = score(scene, slot, P, dict(kind=kind, radius=float(r), p_outlier=float(p), half_window=half_window),
+                        depth_obs, n_threads=n_threads, arrays=arrays)
+            g = i * npo + j
+            ll[:, g], scale[:, g], bound[:, g] = out["ll"], out["scale"], out["bound"]
+    a = ll + lw[None, :]
+    m = a.max(axis=1)
+    marginal = m + np.log(np.exp(a - m[:, None]).sum(axis=1))
+    return dict(ll=ll, marginal=marginal, scale=scale, bound=bound)

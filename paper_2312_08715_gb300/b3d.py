@@ -31,6 +31,8 @@ B3D_EBUSY = -8
 B3D_ECLOSED = -9
 B3D_MAX_STAGES = 8
 B3D_MAX_HALF_WINDOW = 7
+B3D_MAX_NOISE_R = 4
+B3D_MAX_NOISE_P = 4
 B3D_MESH_CLOSED = 1
 B3D_NOALLOC_MAX_SCORES = 2147483647
 B3D_INSTR_TIMING = 1
@@ -65,6 +67,12 @@ class b3d_tuning(C.Structure):
 class b3d_c2f_schedule(C.Structure):
     _fields_ = [("n_stages", C.c_int32), ("stage", b3d_stage * B3D_MAX_STAGES), ("n_particles", C.c_int32),
                 ("seed", C.c_uint64), ("grid_frame", C.c_float * 9), ("path_density", C.c_int32)]
+
+
+class b3d_noise_grid(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("half_window", C.c_int32), ("n_radius", C.c_int32), ("n_pout", C.c_int32),
+                ("radius", C.c_float * 4), ("p_outlier", C.c_float * 4), ("log_weight", C.c_float * 16),
+                ("volume", C.c_float), ("norm", C.c_float), ("miss_mode", C.c_int32)]
 
 
 class b3d_score_item(C.Structure):
@@ -117,6 +125,7 @@ _SIGNATURES = {
     "b3d_render_batch": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, _P, _P, _P]),
     "b3d_score_batch": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_lik_params), _P, _P]),
     "b3d_score_depth_batch": (C.c_int32, [_P, C.c_int64, _P, _P, C.POINTER(b3d_lik_params), _P, _P]),
+    "b3d_score_noise_batch": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_noise_grid), _P, _P, _P]),
     "b3d_expand_hypotheses": (C.c_int32, [_P, _P, _P, C.POINTER(b3d_stage), _P, _P]),
     "b3d_lse_resample": (C.c_int32, [_P, C.c_int64, _P, C.c_int32, C.c_uint64, C.c_int32, _P, _P, _P, _P]),
     "b3d_enumerate_c2f": (C.c_int32, [_P, C.c_int32, _P, C.POINTER(b3d_c2f_schedule), C.POINTER(b3d_lik_params),
@@ -295,6 +304,29 @@ def b3d_score_batch(ctx, obj_slot, n_hyp, poses_dev, lik: b3d_lik_params, loglik
 def b3d_score_depth_batch(ctx, n_hyp, depth_dev, triid_dev, lik: b3d_lik_params, loglik_dev, stream=None):
     return _check(ctx, load().b3d_score_depth_batch(ctx, n_hyp, _addr(depth_dev), _addr(triid_dev), C.byref(lik),
                                                     _addr(loglik_dev), _stream(stream)))
+
+
+def noise_grid(kind, radii, p_outliers, half_window=1, log_weight=None, volume=0.0, norm=0.0,
+               miss_mode=0) -> b3d_noise_grid:
+    """Grid of len(radii) x len(p_outliers) settings; log_weight [n_r * n_p] (default 0)."""
+    g = b3d_noise_grid()
+    g.kind, g.half_window = int(kind), int(half_window)
+    g.n_radius, g.n_pout = len(radii), len(p_outliers)
+    for i, r in enumerate(radii):
+        g.radius[i] = float(r)
+    for j, p in enumerate(p_outliers):
+        g.p_outlier[j] = float(p)
+    lw = np.zeros(len(radii) * len(p_outliers)) if log_weight is None else np.asarray(log_weight, np.float64).ravel()
+    for k, v in enumerate(lw):
+        g.log_weight[k] = float(v)
+    g.volume, g.norm, g.miss_mode = float(volume), float(norm), int(miss_mode)
+    return g
+
+
+def b3d_score_noise_batch(ctx, obj_slot, n_hyp, poses_dev, grid: b3d_noise_grid, loglik_dev, marginal_dev,
+                          stream=None):
+    return _check(ctx, load().b3d_score_noise_batch(ctx, obj_slot, n_hyp, _addr(poses_dev), C.byref(grid),
+                                                    _addr(loglik_dev), _addr(marginal_dev), _stream(stream)))
 
 
 def b3d_expand_hypotheses(ctx, centre_pose, grid_frame, stage: b3d_stage, poses_dev, stream=None):
@@ -666,6 +698,16 @@ class Context:
         ll = out if out is not None else self.torch.empty(n, dtype=self.torch.float32, device=self.device)
         b3d_score_batch(self.h, slot, n, P, lik_params(**lik), ll, self.stream)
         return ll
+
+    def score_noise(self, slot, poses, grid: b3d_noise_grid):
+        """Returns (loglik [n, n_r * n_p], marginal [n])."""
+        t = self.torch
+        P = self._dev(poses, t.float32).reshape(-1, 16)
+        n = P.shape[0]
+        ll = t.empty((n, grid.n_radius * grid.n_pout), dtype=t.float32, device=self.device)
+        marg = t.empty(n, dtype=t.float32, device=self.device)
+        b3d_score_noise_batch(self.h, slot, n, P, grid, ll, marg, self.stream)
+        return ll, marg
 
     def score_depth(self, depth, lik: dict, tid=None):
         n = depth.shape[0]

@@ -60,6 +60,13 @@ struct BgCache {
     int64_t cap = 0, gcap = 0;
     bool dirty = true, lik_valid = false, grad_valid = false;
     LikKey key{};
+    // noise-grid tables [kMaxNoise][H W], their sums [kMaxNoise], partials and ticket
+    float *nell = nullptr;
+    double *nsums = nullptr, *npart = nullptr;
+    unsigned *ncounter = nullptr;
+    int64_t ncap = 0;
+    bool nvalid = false;
+    b3d_noise_grid nkey{};
 };
 
 }  // namespace
@@ -317,7 +324,7 @@ void bg_invalidate(b3d_ctx *ctx, int32_t obj) {
 }
 
 void bg_invalidate_lik(b3d_ctx *ctx) {
-    for (BgCache &c : ctx->bgc) c.lik_valid = c.grad_valid = false;
+    for (BgCache &c : ctx->bgc) c.lik_valid = c.grad_valid = c.nvalid = false;
 }
 
 // Background z-buffer of every scene object except `slot` (slot = -1: all objects).
@@ -352,7 +359,7 @@ b3d_status ensure_bg(b3d_ctx *ctx, int32_t slot, cudaStream_t s) {
         ++ctx->launches;
     }
     c.dirty = false;
-    c.lik_valid = c.grad_valid = false;
+    c.lik_valid = c.grad_valid = c.nvalid = false;
     return check_launch(ctx, "background render");
 }
 
@@ -404,6 +411,79 @@ b3d_status ensure_bg_lik(b3d_ctx *ctx, int32_t slot, const b3d_lik_params *lp, c
     c.lik_valid = true;
     c.grad_valid = grad;
     return check_launch(ctx, "background likelihood tables");
+}
+
+// Device constants of a noise grid (the same formulas as make_lik, per setting).
+b3d_status make_noise(b3d_ctx *ctx, const b3d_noise_grid *gr, NoiseLik *N) {
+    if (!gr) return fail(ctx, B3D_EINVAL, "noise grid is NULL");
+    if (gr->kind != 0 && gr->kind != 1) return fail(ctx, B3D_EINVAL, "grid.kind must be 0 or 1");
+    if (gr->half_window < 0 || gr->half_window > 2) return fail(ctx, B3D_EINVAL, "grid.half_window must be in [0, 2]");
+    if (gr->n_radius < 1 || gr->n_radius > B3D_MAX_NOISE_R || gr->n_pout < 1 || gr->n_pout > B3D_MAX_NOISE_P)
+        return fail(ctx, B3D_EINVAL, "grid.n_radius and grid.n_pout must be in [1, 4]");
+    if (gr->miss_mode != 0 && gr->miss_mode != 1) return fail(ctx, B3D_EINVAL, "grid.miss_mode must be 0 or 1");
+    if (!std::isfinite(gr->volume) || !std::isfinite(gr->norm)) return fail(ctx, B3D_EINVAL, "grid.volume/norm not finite");
+    for (int i = 0; i < gr->n_radius; ++i)
+        if (!(gr->radius[i] > 0.f) || !std::isfinite(gr->radius[i])) return fail(ctx, B3D_EINVAL, "grid radii must be > 0");
+    for (int j = 0; j < gr->n_pout; ++j)
+        if (!(gr->p_outlier[j] > 0.f && gr->p_outlier[j] < 1.f)) return fail(ctx, B3D_EINVAL, "grid p_outlier must be in (0,1)");
+    if (!finite_all(gr->log_weight, (int64_t)gr->n_radius * gr->n_pout)) return fail(ctx, B3D_EINVAL, "grid log weights not finite");
+    const Cam &c = ctx->cam;
+    const int w = gr->half_window;
+    const double V = gr->volume > 0 ? (double)gr->volume
+                                    : (double)c.W * c.H / ((double)c.fx * c.fy) *
+                                          ((double)c.far_z * c.far_z * c.far_z - (double)c.near_z * c.near_z * c.near_z) / 3.0;
+    const double K = gr->norm > 0 ? (double)gr->norm : (double)((2 * w + 1) * (2 * w + 1));
+    const double pi = 3.14159265358979323846;
+    const int n_lut = (2 * w + 1) * (2 * w + 1) + 1;
+    memset(N, 0, sizeof(NoiseLik));
+    N->kind = gr->kind;
+    N->w = w;
+    N->miss_mode = gr->miss_mode;
+    N->nr = gr->n_radius;
+    N->np = gr->n_pout;
+    for (int j = 0; j < gr->n_pout; ++j) N->a[j] = (float)(gr->p_outlier[j] / V);
+    for (int i = 0; i < gr->n_radius; ++i) {
+        const double r = gr->radius[i];
+        N->r2[i] = (float)(r * r);
+        N->inv2s2[i] = (float)(1.0 / (2.0 * r * r));
+        const double gnorm = pow(2.0 * pi * r * r, -1.5), ball = 4.0 / 3.0 * pi * r * r * r;
+        for (int j = 0; j < gr->n_pout; ++j) {
+            const double p = gr->p_outlier[j];
+            const int g = i * kMaxNoiseP + j;
+            N->bg[g] = (float)((1.0 - p) / K * gnorm);
+            N->logw[g] = gr->log_weight[i * gr->n_pout + j];
+            for (int n = 0; n < n_lut; ++n) N->lut[g * kNoiseLut + n] = (float)log(p / V + (1.0 - p) * n / (K * ball));
+        }
+    }
+    return B3D_OK;
+}
+
+// Per-setting background tables of `slot` (after ensure_bg) for this noise grid.
+b3d_status ensure_bg_noise(b3d_ctx *ctx, int32_t slot, const b3d_noise_grid *gr, const NoiseLik &N, cudaStream_t s) {
+    BgCache &c = bg_cache(ctx, slot);
+    const int64_t npx = (int64_t)ctx->cam.W * ctx->cam.H;
+    b3d_status st;
+    if (c.ncap < npx) {
+        dfree(ctx, c.nell); dfree(ctx, c.npart);
+        c.ncap = 0;
+        if ((st = dalloc(ctx, &c.nell, (size_t)kMaxNoise * npx, "noise-grid background tables")) != B3D_OK) return st;
+        if ((st = dalloc(ctx, &c.npart, (size_t)kMaxNoise * bg_table_blocks(npx), "noise-grid partial sums")) != B3D_OK)
+            return st;
+        if (!c.nsums && (st = dalloc(ctx, &c.nsums, kMaxNoise, "noise-grid background sums")) != B3D_OK) return st;
+        if (!c.ncounter) {
+            if ((st = dalloc(ctx, &c.ncounter, 1, "noise-grid sum ticket")) != B3D_OK) return st;
+            cudaMemsetAsync(c.ncounter, 0, sizeof(unsigned), s);
+        }
+        c.ncap = npx;
+        c.nvalid = false;
+    }
+    if (c.nvalid && memcmp(&c.nkey, gr, sizeof(b3d_noise_grid)) == 0) return B3D_OK;
+    Timed tm(ctx, B3D_K_SCENE, s);
+    launch_bg_noise_tables(scene_view(ctx, slot), N, c.nell, c.npart, c.ncounter, c.nsums, s);
+    ++ctx->launches;
+    c.nkey = *gr;
+    c.nvalid = true;
+    return check_launch(ctx, "noise-grid background tables");
 }
 
 b3d_status ensure_scratch(b3d_ctx *ctx, int64_t n_ll, int m) {
@@ -977,6 +1057,7 @@ b3d_status b3d_set_scene(b3d_ctx *ctx, const b3d_intrinsics *intr, int32_t n_obj
         BgCache &c = ctx->bgc.back();
         dfree(ctx, c.bg); dfree(ctx, c.ell); dfree(ctx, c.gs); dfree(ctx, c.gp); dfree(ctx, c.sums);
         dfree(ctx, c.part); dfree(ctx, c.counter);
+        dfree(ctx, c.nell); dfree(ctx, c.nsums); dfree(ctx, c.npart); dfree(ctx, c.ncounter);
         ctx->bgc.pop_back();
     }
     if (n_obj > ctx->pose_cap) {
@@ -1079,6 +1160,32 @@ b3d_status b3d_score_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const 
     }
     ++ctx->launches;
     return check_launch(ctx, "score_batch");
+}
+
+b3d_status b3d_score_noise_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const float *poses_dev,
+                                 const b3d_noise_grid *grid, float *loglik_dev, float *marginal_dev,
+                                 b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    b3d_status st = check_slot(ctx, obj_slot);
+    if (st != B3D_OK) return st;
+    NoiseLik N;
+    if ((st = make_noise(ctx, grid, &N)) != B3D_OK) return st;
+    if (n_hyp < 0) return fail(ctx, B3D_EINVAL, "n_hyp must be >= 0");
+    if (n_hyp == 0) return B3D_OK;
+    if (!poses_dev || !marginal_dev) return fail(ctx, B3D_EINVAL, "poses_dev and marginal_dev must be non-NULL");
+    if (!aligned16(poses_dev)) return fail(ctx, B3D_EINVAL, "poses_dev must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ensure_bg(ctx, obj_slot, s)) != B3D_OK) return st;
+    if ((st = ensure_bg_noise(ctx, obj_slot, grid, N, s)) != B3D_OK) return st;
+    const BgCache &c = bg_cache(ctx, obj_slot);
+    {
+        Timed tm(ctx, B3D_K_SCORE, s);
+        launch_score_noise(scene_view(ctx, obj_slot), N, poses_dev, n_hyp, c.nell, c.nsums, loglik_dev, marginal_dev, s);
+    }
+    ++ctx->launches;
+    return check_launch(ctx, "score_noise_batch");
 }
 
 b3d_status b3d_score_depth_batch(b3d_ctx *ctx, int64_t n_hyp, const float *depth_dev, const int32_t *triid_dev,

@@ -81,6 +81,20 @@ struct Lik {
     float gnorm;     // (2 pi s^2)^(-3/2)
 };
 
+// A grid of noise settings (hierarchical noise): nr radii (kind 0) or standard deviations
+// (kind 1) times np outlier probabilities; setting g = 4 i + j internally (i < nr, j < np).
+constexpr int kMaxNoiseR = 4, kMaxNoiseP = 4, kMaxNoise = kMaxNoiseR * kMaxNoiseP;
+constexpr int kNoiseLut = 26;  // (2w+1)^2 + 1 for half windows up to 2
+struct NoiseLik {
+    int kind, w, miss_mode, nr, np;
+    float r2[kMaxNoiseR];       // kind 0: r_i^2
+    float inv2s2[kMaxNoiseR];   // kind 1: 1 / (2 s_i^2)
+    float a[kMaxNoiseP];        // p_j / V
+    float bg[kMaxNoise];        // kind 1: (1 - p_j) / K (2 pi s_i^2)^(-3/2)
+    float logw[kMaxNoise];      // prior log weight of the setting
+    float lut[kMaxNoise * kNoiseLut];  // kind 0: log(a_j + (1 - p_j) n / (K (4/3) pi r_i^3))
+};
+
 // The scene as the fused kernels see it, for one hypothesised object (the slot).
 struct SceneView {
     Cam cam;
@@ -203,6 +217,13 @@ void launch_c2f_select(const float *ll, const int *idx, int m, PoseGrid P, const
                        int stage, uint64_t seed, int n_stages, float *centre_next, float *particles, float *logw,
                        float *logq, cudaStream_t s);
 void launch_copy16(const float *src, float *dst, cudaStream_t s);
+
+// Noise-grid scoring (k_score_noise.cu): per-setting background tables and sums (part holds
+// kMaxNoise x blocks doubles, returns blocks), and the fused scoring launch.
+int launch_bg_noise_tables(const SceneView &sv, const NoiseLik &N, float *nell, double *part, unsigned *counter,
+                           double *sums, cudaStream_t s);
+void launch_score_noise(const SceneView &sv, const NoiseLik &N, const float *poses, int64_t n_hyp, const float *nell,
+                        const double *nsums, float *out_ll, float *out_marg, cudaStream_t s);
 
 // Context hooks used by the tracking server (defined with the context in b3d_api.cu).
 uint64_t ctx_used_bytes(b3d_ctx *ctx);

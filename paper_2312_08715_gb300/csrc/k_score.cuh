@@ -211,18 +211,21 @@ struct ScoreShared {
     int own[NT];  // per warp: the lane whose candidate run starts at each position of a window
 };
 
-// Scores the hypothesis whose pose thread 0 has put in sh.pose: returns, in thread 0, the
-// sum of l_i - l_i(bg) over the pixels whose window can see the object (0 when it is off
-// screen). All threads of the CTA must call it.
-template <bool STATS, int WT, int NT>
-__device__ __forceinline__ float score_body(const SceneView &S, const Lik &L, const float *s_lut, ScoreShared<NT> &sh,
-                                            float4 *s_stage, unsigned *zb, float4 *lat, unsigned long long *cnt) {
+// Renders the hypothesis whose pose thread 0 has put in sh.pose, tile by tile, into the
+// shared-memory z-buffer and composites it with the fixed objects' depths (misses: far, or
+// -1 with miss_mode 1); for each tile with fragments calls
+// visit(zd, zx0, zy0, zw, qx0, qx1, qy0, qy1): the tile's depths zd (origin zx0, zy0, row
+// pitch zw) and the pixels to score, those whose half-window w reaches a fragment. Returns
+// false when the object is off screen (nothing visited). All threads of the CTA must call it.
+template <bool STATS, int NT, class Visit>
+__device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss_mode, ScoreShared<NT> &sh,
+                                             float4 *s_stage, unsigned *zb, float4 *lat, unsigned long long *cnt,
+                                             Visit &&visit) {
     constexpr int REG = score_region<NT>();
     float *zd = reinterpret_cast<float *>(zb);  // same memory, as depths
     const Cam &c = S.cam;
     const MeshView &m = S.mesh;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
-    const int w = WT > 0 ? WT : L.w;
     const int n_lat = m.nc[0] + m.nc[1] + m.nc[2];
     const int nc0 = m.nc[0], nc01 = m.nc[0] + m.nc[1];
     auto lat_off = [&](int a) { return a == 0 ? 0 : (a == 1 ? nc0 : nc01); };
@@ -305,7 +308,7 @@ __device__ __forceinline__ float score_body(const SceneView &S, const Lik &L, co
     }
     __syncthreads();
     const int flags = sh.flags;
-    if (!(flags & 1)) return 0.f;
+    if (!(flags & 1)) return false;
     const float *pose = sh.pose;
     const bool quad = (flags & 2) != 0, front = (flags & 4) != 0;
     const int bx0 = sh.bb[0], bx1 = sh.bb[1], by0 = sh.bb[2], by1 = sh.bb[3];
@@ -323,7 +326,6 @@ __device__ __forceinline__ float score_body(const SceneView &S, const Lik &L, co
     const int sw = sx1 - sx0 + 1;
     const int tw = min(sw, S.tile_w);
     const int th = max(1, REG / (tw + 2 * w) - 2 * w);
-    float acc = 0.f;
     for (int ty0 = sy0; ty0 <= sy1; ty0 += th) {
         for (int tx0 = sx0; tx0 <= sx1; tx0 += tw) {
             const int tx1 = min(tx0 + tw - 1, sx1), ty1 = min(ty0 + th - 1, sy1);
@@ -490,7 +492,7 @@ __device__ __forceinline__ float score_body(const SceneView &S, const Lik &L, co
                     const int zi = (gy - zy0) * zw + (gx - zx0);
                     const unsigned bgb = (unsigned)(S.bg[(int64_t)gy * c.W + gx] >> 32);
                     const unsigned v = min(zb[zi], bgb);
-                    zd[zi] = v == 0xffffffffu ? (L.miss_mode ? -1.f : c.far_z) : __uint_as_float(v);
+                    zd[zi] = v == 0xffffffffu ? (miss_mode ? -1.f : c.far_z) : __uint_as_float(v);
                     x += dr;
                     y += dq;
                     if (x >= cw) { x -= cw; ++y; }
@@ -501,6 +503,26 @@ __device__ __forceinline__ float score_body(const SceneView &S, const Lik &L, co
             // score the tile's pixels within the fragment box + w
             const int qx0 = max(sh.fbb[0] - w, tx0), qx1 = min(sh.fbb[1] + w, tx1);
             const int qy0 = max(sh.fbb[2] - w, ty0), qy1 = min(sh.fbb[3] + w, ty1);
+            visit(static_cast<const float *>(zd), zx0, zy0, zw, qx0, qx1, qy0, qy1);
+            __syncthreads();
+        }
+    }
+    return true;
+}
+
+// Scores the hypothesis whose pose thread 0 has put in sh.pose: returns, in thread 0, the
+// sum of l_i - l_i(bg) over the pixels whose window can see the object (0 when it is off
+// screen). All threads of the CTA must call it.
+template <bool STATS, int WT, int NT>
+__device__ __forceinline__ float score_body(const SceneView &S, const Lik &L, const float *s_lut, ScoreShared<NT> &sh,
+                                            float4 *s_stage, unsigned *zb, float4 *lat, unsigned long long *cnt) {
+    const Cam &c = S.cam;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int w = WT > 0 ? WT : L.w;
+    float acc = 0.f;
+    const bool drawn = render_tiles<STATS, NT>(
+        S, w, L.miss_mode, sh, s_stage, zb, lat, cnt,
+        [&](const float *zd, int zx0, int zy0, int zw, int qx0, int qx1, int qy0, int qy1) {
             const int tww = qx1 - qx0 + 1, thh = qy1 - qy0 + 1;
             if (WT > 0) {
                 // thread -> (column, run of rows)
@@ -536,9 +558,8 @@ __device__ __forceinline__ float score_body(const SceneView &S, const Lik &L, co
                     if (x >= tww) { x -= tww; ++y; }
                 }
             }
-            __syncthreads();
-        }
-    }
+        });
+    if (!drawn) return 0.f;
     return block_sum(acc, sh.red);
 }
 

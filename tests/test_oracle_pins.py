@@ -501,3 +501,32 @@ def test_smc_weights_of_a_near_exact_proposal(orc):
     assert b["idx"][0] is not None and a["idx"][0] is None
     assert a["log_evidence"] == pytest.approx(b["log_evidence"], abs=1e-9)
     np.testing.assert_allclose(b["logw"], b["log_evidence"], atol=1e-9)
+
+
+# ---------------------------------------------------------------------------------------
+# Hierarchical noise: scoring over a grid of noise settings
+# ---------------------------------------------------------------------------------------
+
+def test_noise_grid_marginal_special_cases(orc, single_object):
+    """One setting: the marginal is its log-likelihood plus its log weight. Identical
+    settings: plus the log of their total mass. Any grid: between the best weighted term and
+    that plus log G; independent of the order of the settings."""
+    wl = single_object
+    sc = wl.scene
+    obs = synth.corrupt_depth(orc.render(sc)[0], 2.0, wl.draws)
+    poses = np.stack([wl.hidden, wl.hidden @ synth.rigid(np.eye(3), [0.004, 0, 0])]).astype(np.float64)
+    one = orc.score_noise(sc, 0, poses, 0, [0.005], [0.01], 1, obs, log_weight=[-0.7])
+    ref = orc.score(sc, 0, poses, dict(kind=0, radius=0.005, p_outlier=0.01, half_window=1), obs, flags=False)["ll"]
+    np.testing.assert_array_equal(one["ll"][:, 0], ref)
+    np.testing.assert_allclose(one["marginal"], ref - 0.7, rtol=0, atol=1e-9)
+    same = orc.score_noise(sc, 0, poses, 0, [0.005, 0.005], [0.01, 0.01], 1, obs, log_weight=[0.1, -0.3, 0.2, 0.0])
+    np.testing.assert_allclose(same["marginal"], ref + np.log(np.exp([0.1, -0.3, 0.2, 0.0]).sum()), rtol=0, atol=1e-9)
+    r, p = [0.0025, 0.005, 0.01], [0.001, 0.01, 0.1]
+    w = np.log(np.arange(1, 10) / 45.0)
+    g = orc.score_noise(sc, 0, poses, 1, r, p, 1, obs, log_weight=w)
+    best = (g["ll"] + w).max(axis=1)
+    assert (g["marginal"] >= best).all() and (g["marginal"] <= best + math.log(9)).all()
+    perm = [2, 0, 1]
+    w2 = w.reshape(3, 3)[perm].ravel()
+    g2 = orc.score_noise(sc, 0, poses, 1, [r[k] for k in perm], p, 1, obs, log_weight=w2)
+    np.testing.assert_allclose(g2["marginal"], g["marginal"], rtol=0, atol=1e-8)
