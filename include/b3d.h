@@ -285,6 +285,14 @@ b3d_status b3d_score_grad(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const f
                           const b3d_lik_params *lik, float *loglik_dev, float *dpose_dev, float *dsigma_dev,
                           float *dpout_dev, b3d_stream stream);
 
+/* Camera hypotheses (the camera-pose tracking of Sec. IV, Table 1): render n_hyp hypothesised
+ * camera poses poses_dev [n_hyp, 16] (row-major camera_from_world) of the scene, every object
+ * k at H_h P_k where P_k is its scene pose read as world_from_object. Writes depth_dev
+ * [n_hyp, H, W] (far_z where nothing is drawn) and, unless NULL, triid_dev [n_hyp, H, W], as
+ * b3d_render_batch; score them with b3d_score_depth_batch. */
+b3d_status b3d_render_camera_batch(b3d_ctx *ctx, int64_t n_hyp, const float *poses_dev, float *depth_dev,
+                                   int32_t *triid_dev, b3d_stream stream);
+
 /* Hierarchical noise (Alg. 1 lines 11-12: p_out ~ U(0,1), sigma ~ U(0, sigma_max), and
  * "score hypotheses under several noise settings"): a grid of n_radius inlier radii (kind 0)
  * or Gaussian standard deviations (kind 1) times n_pout outlier probabilities. Setting

@@ -126,6 +126,7 @@ _SIGNATURES = {
     "b3d_score_batch": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_lik_params), _P, _P]),
     "b3d_score_depth_batch": (C.c_int32, [_P, C.c_int64, _P, _P, C.POINTER(b3d_lik_params), _P, _P]),
     "b3d_score_noise_batch": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_noise_grid), _P, _P, _P]),
+    "b3d_render_camera_batch": (C.c_int32, [_P, C.c_int64, _P, _P, _P, _P]),
     "b3d_expand_hypotheses": (C.c_int32, [_P, _P, _P, C.POINTER(b3d_stage), _P, _P]),
     "b3d_lse_resample": (C.c_int32, [_P, C.c_int64, _P, C.c_int32, C.c_uint64, C.c_int32, _P, _P, _P, _P]),
     "b3d_enumerate_c2f": (C.c_int32, [_P, C.c_int32, _P, C.POINTER(b3d_c2f_schedule), C.POINTER(b3d_lik_params),
@@ -304,6 +305,11 @@ def b3d_score_batch(ctx, obj_slot, n_hyp, poses_dev, lik: b3d_lik_params, loglik
 def b3d_score_depth_batch(ctx, n_hyp, depth_dev, triid_dev, lik: b3d_lik_params, loglik_dev, stream=None):
     return _check(ctx, load().b3d_score_depth_batch(ctx, n_hyp, _addr(depth_dev), _addr(triid_dev), C.byref(lik),
                                                     _addr(loglik_dev), _stream(stream)))
+
+
+def b3d_render_camera_batch(ctx, n_hyp, poses_dev, depth_dev, triid_dev=None, stream=None):
+    return _check(ctx, load().b3d_render_camera_batch(ctx, n_hyp, _addr(poses_dev), _addr(depth_dev), _addr(triid_dev),
+                                                      _stream(stream)))
 
 
 def noise_grid(kind, radii, p_outliers, half_window=1, log_weight=None, volume=0.0, norm=0.0,
@@ -698,6 +704,20 @@ class Context:
         ll = out if out is not None else self.torch.empty(n, dtype=self.torch.float32, device=self.device)
         b3d_score_batch(self.h, slot, n, P, lik_params(**lik), ll, self.stream)
         return ll
+
+    def render_camera(self, poses, want_tid=True, out=None):
+        """Camera hypotheses poses [n, 4, 4] (camera_from_world); the scene poses are world poses."""
+        t = self.torch
+        P = self._dev(poses, t.float32).reshape(-1, 16)
+        n = P.shape[0]
+        H, W = self.cam.height, self.cam.width
+        if out is None:
+            depth = t.empty((n, H, W), dtype=t.float32, device=self.device)
+            tid = t.empty((n, H, W), dtype=t.int32, device=self.device) if want_tid else None
+        else:
+            depth, tid = out
+        b3d_render_camera_batch(self.h, n, P, depth, tid, self.stream)
+        return depth, tid
 
     def score_noise(self, slot, poses, grid: b3d_noise_grid):
         """Returns (loglik [n, n_r * n_p], marginal [n])."""

@@ -92,6 +92,13 @@ struct b3d_ctx {
     std::vector<BgCache> bgc;
 
     int *d_err = nullptr;
+    // camera-hypothesis render: the scene's mesh views and triangle bases on the device
+    MeshView *d_views = nullptr;
+    int *d_tri_base = nullptr;
+    int views_cap = 0;
+    bool views_dirty = true;
+    std::vector<MeshView> h_views;
+    std::vector<int> h_tri_base;
 
     // coarse-to-fine and resampling scratch
     float *d_ll = nullptr;
@@ -1083,6 +1090,7 @@ b3d_status b3d_set_scene(b3d_ctx *ctx, const b3d_intrinsics *intr, int32_t n_obj
     }
     ++ctx->launches;
     ctx->has_scene = true;
+    ctx->views_dirty = true;
     bg_invalidate(ctx, -1);
     bg_invalidate_lik(ctx);
     return check_launch(ctx, "set_scene");
@@ -1160,6 +1168,49 @@ b3d_status b3d_score_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const 
     }
     ++ctx->launches;
     return check_launch(ctx, "score_batch");
+}
+
+b3d_status b3d_render_camera_batch(b3d_ctx *ctx, int64_t n_hyp, const float *poses_dev, float *depth_dev,
+                                   int32_t *triid_dev, b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    if (!ctx->has_scene) return fail(ctx, B3D_EINVAL, "no scene: call b3d_set_scene first");
+    if (n_hyp < 0) return fail(ctx, B3D_EINVAL, "n_hyp must be >= 0");
+    if (n_hyp == 0) return B3D_OK;
+    if (!poses_dev || !depth_dev) return fail(ctx, B3D_EINVAL, "poses_dev and depth_dev must be non-NULL");
+    if (!aligned16(poses_dev)) return fail(ctx, B3D_EINVAL, "poses_dev must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n_obj = (int)ctx->obj_mesh.size();
+    b3d_status st;
+    if (ctx->views_dirty) {
+        if (n_obj > ctx->views_cap) {
+            dfree(ctx, ctx->d_views); dfree(ctx, ctx->d_tri_base);
+            ctx->views_cap = 0;
+            if ((st = dalloc(ctx, &ctx->d_views, (size_t)n_obj, "scene mesh views")) != B3D_OK) return st;
+            if ((st = dalloc(ctx, &ctx->d_tri_base, (size_t)n_obj, "scene triangle bases")) != B3D_OK) return st;
+            ctx->views_cap = n_obj;
+        }
+        ctx->h_views.resize(n_obj);
+        ctx->h_tri_base.resize(n_obj);
+        for (int k = 0; k < n_obj; ++k) {
+            ctx->h_views[k] = view_of(ctx->meshes[ctx->obj_mesh[k]]);
+            ctx->h_tri_base[k] = (int)ctx->tri_base[k];
+        }
+        cudaError_t e = cudaMemcpyAsync(ctx->d_views, ctx->h_views.data(), sizeof(MeshView) * n_obj,
+                                        cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->d_tri_base, ctx->h_tri_base.data(), sizeof(int) * n_obj, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "scene views upload");
+        ctx->views_dirty = false;
+    }
+    {
+        Timed tm(ctx, B3D_K_RENDER, s);
+        launch_render_camera(ctx->cam, ctx->d_views, ctx->d_tri_base, ctx->d_poses, n_obj, PoseList{poses_dev}, n_hyp,
+                             depth_dev, triid_dev, s);
+    }
+    ++ctx->launches;
+    return check_launch(ctx, "render_camera_batch");
 }
 
 b3d_status b3d_score_noise_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const float *poses_dev,

@@ -218,6 +218,10 @@ void launch_c2f_select(const float *ll, const int *idx, int m, PoseGrid P, const
                        float *logq, cudaStream_t s);
 void launch_copy16(const float *src, float *dst, cudaStream_t s);
 
+// Camera hypotheses (k_render.cu): every object k at H_h world[k], full image, no background.
+int launch_render_camera(const Cam &cam, const MeshView *meshes, const int *tri_base, const float *world, int n_obj,
+                         PoseList P, int64_t n, float *depth, int *tid, cudaStream_t s);
+
 // Noise-grid scoring (k_score_noise.cu): per-setting background tables and sums (part holds
 // kMaxNoise x blocks doubles, returns blocks), and the fused scoring launch.
 int launch_bg_noise_tables(const SceneView &sv, const NoiseLik &N, float *nell, double *part, unsigned *counter,

@@ -91,6 +91,77 @@ __global__ void __launch_bounds__(kThreads) k_render(SceneView S, PS P, int64_t 
     }
 }
 
+// Camera hypotheses: every scene object k at H_h P_k, H_h the hypothesised camera_from_world
+// pose and P_k the object's world pose (the scene poses), rendered into the full image
+// (nothing is fixed, so there is no background).
+__global__ void __launch_bounds__(kThreads) k_render_camera(Cam c, const MeshView *meshes, const int *tri_base,
+                                                            const float *world, int n_obj, PoseList P, int64_t n_hyp,
+                                                            float *out_depth, int *out_tid) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long *zb = reinterpret_cast<unsigned long long *>(smem_raw);  // [kRegionPx]
+    __shared__ float s_pose[12];
+    __shared__ int s_bb[4];
+    __shared__ int s_flags;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t npx = (int64_t)c.W * c.H;
+    const int tw = min(c.W, kRegionPx);
+    const int th = max(1, kRegionPx / tw);
+    for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
+        for (int ty0 = 0; ty0 < c.H; ty0 += th) {
+            for (int tx0 = 0; tx0 < c.W; tx0 += tw) {
+                const int tx1 = min(tx0 + tw - 1, c.W - 1), ty1 = min(ty0 + th - 1, c.H - 1);
+                const int zw = tx1 - tx0 + 1, zh = ty1 - ty0 + 1;
+                __syncthreads();
+                for (int i = tid; i < zw * zh; i += nt) zb[i] = kEmptyKey;
+                for (int k = 0; k < n_obj; ++k) {
+                    __syncthreads();
+                    const MeshView &m = meshes[k];
+                    if (tid == 0) {
+                        // pose of object k in the hypothesised camera: H_h P_k (rotation rows,
+                        // then translation), in the layout of pose12
+                        float Hh[12];
+                        pose12(P, h, Hh);
+                        const float *W = world + 16 * k;
+                        for (int r = 0; r < 3; ++r) {
+                            for (int col = 0; col < 3; ++col)
+                                s_pose[3 * r + col] = fmaf(Hh[3 * r], W[col], fmaf(Hh[3 * r + 1], W[4 + col], Hh[3 * r + 2] * W[8 + col]));
+                            s_pose[9 + r] = fmaf(Hh[3 * r], W[3], fmaf(Hh[3 * r + 1], W[7], fmaf(Hh[3 * r + 2], W[11], Hh[9 + r])));
+                        }
+                        bool front = false;
+                        s_flags = (object_bbox(m, s_pose, c, s_bb, &front) ? 1 : 0) | (front ? 4 : 0);
+                    }
+                    __syncthreads();
+                    const bool front = (s_flags & 4) != 0;
+                    const int rx0 = max(tx0, s_bb[0]), rx1 = min(tx1, s_bb[1]);
+                    const int ry0 = max(ty0, s_bb[2]), ry1 = min(ty1, s_bb[3]);
+                    if (!(s_flags & 1) || rx0 > rx1 || ry0 > ry1) continue;
+                    const int4 *tris = front ? m.tris_surf : m.tris_full;
+                    const int n_t = front ? m.n_surf : m.n_full;
+                    const int cull = front ? m.closed : 0;
+                    const int base = tri_base[k];
+                    for (int t = tid; t < n_t; t += nt) {
+                        const int4 tr = tris[t];
+                        float4 A, B, C;
+                        tri_screen(m, tr, s_pose, c, A, B, C);
+                        const unsigned gid = (unsigned)(base + tr.w);
+                        raster_tri(A, B, C, cull, rx0, rx1, ry0, ry1, c.far_z, [&](int x, int y, float z) {
+                            atomicMin(&zb[(y - ty0) * zw + (x - tx0)], pack_key(z, gid));
+                        });
+                    }
+                }
+                __syncthreads();
+                for (int i = tid; i < zw * zh; i += nt) {
+                    const int gx = tx0 + i % zw, gy = ty0 + i / zw;
+                    const int64_t gi = (int64_t)gy * c.W + gx;
+                    const unsigned long long key = zb[i];
+                    out_depth[h * npx + gi] = key_depth(key, 0, c.far_z);
+                    if (out_tid) out_tid[h * npx + gi] = key == kEmptyKey ? -1 : (int)(unsigned)(key & 0xffffffffu);
+                }
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // scene set-up kernels
 // ------------------------------------------------------------------------------------------
@@ -400,6 +471,16 @@ int launch_render_list(const SceneView &sv, PoseList P, int64_t n, float *depth,
     auto kern = k_render<PoseList>;
     const int g = persistent_grid(kern, smem, n, grid);
     kern<<<g, kThreads, smem, s>>>(sv, P, n, depth, tid);
+    return g;
+}
+
+int launch_render_camera(const Cam &cam, const MeshView *meshes, const int *tri_base, const float *world, int n_obj,
+                         PoseList P, int64_t n, float *depth, int *tid, cudaStream_t s) {
+    if (n <= 0) return 0;
+    const int smem = kRegionPx * (int)sizeof(unsigned long long);
+    auto kern = k_render_camera;
+    const int g = persistent_grid(kern, smem, n, 0);
+    kern<<<g, kThreads, smem, s>>>(cam, meshes, tri_base, world, n_obj, P, n, depth, tid);
     return g;
 }
 

@@ -103,12 +103,20 @@ def box_mesh(size, centre=(0.0, 0.0, 0.0)) -> Mesh:
     return Mesh(verts=verts, faces=_VOXEL_TRIS.astype(np.int32).copy())
 
 
-def table_mesh(size=1.0) -> Mesh:
-    """Table top: a square of side ``size`` at z = 0, two triangles facing +z."""
+def table_mesh(size=1.0, divisions=1) -> Mesh:
+    """Table top: a square of side ``size`` at z = 0 facing +z, split into divisions^2
+    squares of two triangles each."""
     h = 0.5 * size
-    verts = np.array([[-h, -h, 0.0], [h, -h, 0.0], [h, h, 0.0], [-h, h, 0.0]], dtype=np.float32)
-    faces = np.array([[0, 1, 2], [0, 2, 3]], dtype=np.int32)
-    return Mesh(verts=verts, faces=faces)
+    g = np.linspace(-h, h, divisions + 1)
+    X, Y = np.meshgrid(g, g, indexing="xy")
+    verts = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], 1).astype(np.float32)
+    faces = []
+    for r in range(divisions):
+        for c in range(divisions):
+            v0 = r * (divisions + 1) + c
+            v1, v2, v3 = v0 + 1, v0 + divisions + 2, v0 + divisions + 1
+            faces += [[v0, v1, v2], [v0, v2, v3]]
+    return Mesh(verts=verts, faces=np.array(faces, dtype=np.int32))
 
 
 def random_rotation(rng) -> np.ndarray:
@@ -441,3 +449,66 @@ def tracking_stage(n_per_axis=5, step=0.01, n_rot=50, rot_max_deg=5.0) -> StageS
     """The per-frame enumeration of the tracking loop: a translation grid of n_per_axis^3
     cells around the previous estimate times n_rot rotation perturbations."""
     return StageSpec(n_per_axis, step, 1, n_rot, math.radians(rot_max_deg))
+
+
+@dataclasses.dataclass
+class CameraVideo:
+    """Camera-pose tracking video (the setting of Table 1): one object resting on a table at
+    the world origin, the camera panning around it; frame 0's pose is given."""
+    name: str
+    scene: Scene              # meshes (object, table) at their WORLD poses
+    cam_from_world: np.ndarray  # [F, 4, 4] float32 true camera poses
+    seed: int
+
+    @property
+    def n_frames(self) -> int:
+        return int(self.cam_from_world.shape[0])
+
+    def draws(self, frame: int) -> NoiseDraws:
+        rng = np.random.default_rng([self.seed, int(frame)])
+        return noise_draws(rng, self.scene.camera.height, self.scene.camera.width)
+
+    def camera_scene(self, frame: int) -> Scene:
+        """The scene as seen by the camera of ``frame`` (object poses cam_from_obj)."""
+        H = self.cam_from_world[frame].astype(np.float64)
+        poses = np.stack([H @ P for P in self.scene.poses.astype(np.float64)]).astype(np.float32)
+        return Scene(self.scene.camera, self.scene.meshes, poses)
+
+
+def camera_video(k: int, size: int, n_frames=120, vox_lo=8000, vox_hi=16000, seed_base=5000) -> CameraVideo:
+    """Video ``k`` at ``size`` x ``size`` pixels (fx = fy = size): a voxel blob (5 mm pitch)
+    with a random yaw at the origin of a 1 m table (20 x 20 squares), and two boxes placed
+    around it (a blob on a bare plane would leave the camera's orbit angle unobservable);
+    the camera looks at the origin from 0.6 m and 35 degrees up, its azimuth sweeping
+    0.5 degrees a frame with a slow oscillation of elevation (+-3 degrees) and distance
+    (+-3 cm)."""
+    rng = np.random.default_rng(seed_base + k)
+    obj = voxel_mesh(_blob_cells(rng, 0.005, vox_lo, vox_hi), 0.005, origin=(0.0, 0.0, 0.0))
+    boxes = [box_mesh((0.04, 0.12, 0.08), centre=(0.0, 0.0, 0.04)), box_mesh((0.10, 0.03, 0.05), centre=(0.0, 0.0, 0.025))]
+    cam = Camera(size, size, float(size), float(size), size / 2.0, size / 2.0, 0.01, 2.0)
+    world = [rigid(yaw(rng.uniform(0, 2 * math.pi)), [0.0, 0.0, 0.0])]
+    for b, (x, y) in zip(boxes, [(0.16, 0.05), (-0.1, -0.15)]):
+        world.append(rigid(yaw(rng.uniform(0, 2 * math.pi)), [x, y, 0.0]))
+    world.append(np.eye(4))
+    world = np.stack(world)
+    az0, ph = rng.uniform(0, 2 * math.pi), rng.uniform(0, 2 * math.pi)
+    frames = []
+    for f in range(n_frames):
+        az = az0 + math.radians(0.5) * f
+        el = math.radians(35.0 + 3.0 * math.sin(0.05 * f + ph))
+        dist = 0.6 + 0.03 * math.sin(0.031 * f + 2 * ph)
+        frames.append(look_at_origin(dist, el, az))
+    scene = Scene(cam, [obj] + boxes + [table_mesh(1.0, 20)], world.astype(np.float32))
+    return CameraVideo(name=f"camera video {k}: {size}x{size}, {n_frames} frames", scene=scene,
+                       cam_from_world=np.stack(frames).astype(np.float32), seed=seed_base + 31 * k)
+
+
+def camera_stages():
+    """Per-frame coarse-to-fine search around the previous camera pose, rotations and
+    translations in turn: 2,048 rotations about the world origin (+-1 degree), then a 3^3
+    translation grid in camera axes (3 mm); again at +-0.3 degree / 1 mm and +-0.1 degree /
+    0.4 mm. A joint 6-D grid of the same size leaves too coarse a rotation spacing for this
+    sharply peaked likelihood (a 0.1 degree or 1 mm error costs ~300 nats at 64x64)."""
+    return [StageSpec(1, 0.001, 1, 2048, math.radians(1.0)), StageSpec(3, 0.003, 1, 1, 0.0),
+            StageSpec(1, 0.001, 1, 2048, math.radians(0.3)), StageSpec(3, 0.001, 1, 1, 0.0),
+            StageSpec(1, 0.001, 1, 2048, math.radians(0.1)), StageSpec(3, 0.0004, 1, 1, 0.0)]

@@ -1,0 +1,80 @@
+"""Camera-pose tracking (Sec. IV, Table 1): hypothesised camera poses render the whole
+scene (object and table move together in the camera frame) and are scored on the full image;
+a per-frame coarse-to-fine search follows a panning camera."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2312_08715_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _closed(scene):
+    return [m.faces.shape[0] > 2 and m is not scene.meshes[-1] for m in scene.meshes]
+
+
+def _perturb(rng, H, n, trans, rot_deg):
+    out = [H.astype(np.float64)]
+    for _ in range(n - 1):
+        ax = rng.normal(size=3)
+        ax /= np.linalg.norm(ax)
+        a = math.radians(rng.uniform(-rot_deg, rot_deg))
+        K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+        D = np.eye(4)
+        D[:3, :3] = np.eye(3) + math.sin(a) * K + (1 - math.cos(a)) * K @ K
+        D[:3, 3] = rng.uniform(-trans, trans, size=3)
+        out.append(D @ H.astype(np.float64))
+    return np.stack(out).astype(np.float32)
+
+
+@pytest.mark.parametrize("size", [25, 64])
+def test_render_camera_matches_oracle(orc, size):
+    from paper_2312_08715_gb300 import b3d
+    v = synth.camera_video(0, size, n_frames=2)
+    rng = np.random.default_rng(3)
+    Hs = _perturb(rng, v.cam_from_world[0], 6, 0.01, 3.0)
+    ctx = b3d.Context(0)
+    ids = [ctx.load_mesh(m, closed=c) for m, c in zip(v.scene.meshes, _closed(v.scene))]
+    ctx.set_scene(v.scene.camera, ids, v.scene.poses, np.zeros((size, size), np.float32))
+    d, t = ctx.render_camera(Hs)
+    ctx.sync()
+    d, t = d.cpu().numpy(), t.cpu().numpy()
+    n_mis = n_px = 0
+    for k, H in enumerate(Hs):
+        poses = np.stack([H.astype(np.float64) @ P for P in v.scene.poses.astype(np.float64)])
+        sc = synth.Scene(v.scene.camera, v.scene.meshes, poses)
+        od, ot, of = orc.render(sc, edge_tol=1e-4, z_tol=1e-5, want_flags=True)
+        mis = ot != t[k]
+        assert not (mis & ((of & 1) == 0)).any(), f"pose {k}: unflagged id mismatches"
+        agree = ~mis
+        assert (np.abs(d[k][agree] - od[agree]) / od[agree]).max() <= 1e-5
+        n_mis += int(mis.sum())
+        n_px += mis.size
+    assert n_mis <= max(1, 1e-3 * n_px)
+    ctx.close()
+
+
+def test_camera_tracking_follows_the_video(orc):
+    from paper_2312_08715_gb300.camera import CameraTracker
+    v = synth.camera_video(1, 64, n_frames=12)
+    tr = CameraTracker(v.scene.camera, v.scene.meshes, v.scene.poses, _closed(v.scene))
+    lik = dict(kind=0, radius=0.005, p_outlier=0.01, half_window=1)
+    est = v.cam_from_world[0]
+    pos, ang = [], []
+    for f in range(1, v.n_frames):
+        depth = synth.corrupt_depth(orc.render(v.camera_scene(f))[0], v.scene.camera.far, v.draws(f))
+        est, _ = tr.frame(depth, est, synth.camera_stages(), lik, 32, 100 + f)
+        T = v.cam_from_world[f].astype(np.float64)
+        E = est.astype(np.float64)
+        # camera centres in the world frame, and the rotation between the two cameras
+        c_true = -T[:3, :3].T @ T[:3, 3]
+        c_est = -E[:3, :3].T @ E[:3, 3]
+        pos.append(np.linalg.norm(c_true - c_est))
+        R = E[:3, :3] @ T[:3, :3].T
+        ang.append(math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(R) - 1) / 2)))))
+    assert np.median(pos) < 0.01 and max(pos) < 0.03, pos
+    assert np.median(ang) < 2.0 and max(ang) < 5.0, ang
+    tr.close()
