@@ -182,6 +182,15 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
 template <int NT>
 constexpr int score_region() { return NT <= 64 ? 2048 : kRegionPx; }
 constexpr int kStageStride = 6;  // float4 per staged rectangle: four edges, plane, pixel box
+// Pixels a candidate of the cooperative rasteriser covers (a block of kCandX x kCandY): the
+// owner lookup, record loads and index arithmetic are shared by the block's pixel tests.
+#ifndef B3D_CAND_X
+#define B3D_CAND_X 2
+#endif
+#ifndef B3D_CAND_Y
+#define B3D_CAND_Y 1
+#endif
+constexpr int kCandX = B3D_CAND_X, kCandY = B3D_CAND_Y;
 
 // A rectangle edge a->b staged for the pixel tests: its canonical origin (the
 // lexicographically smaller endpoint, as edge_fn) and direction, with the quad's
@@ -388,7 +397,10 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                                 const int y0 = (int)ceilf(fmaxf(vmin - 0.5f, (float)ry0));
                                 const int y1 = (int)floorf(fminf(vmax - 0.5f, (float)ry1));
                                 if (x0 <= x1 && y0 <= y1) {
-                                    cand = (x1 - x0 + 1) * (y1 - y0 + 1);
+                                    // candidates are blocks of kCandX x kCandY pixels
+                                    const int bw2 = (x1 - x0 + kCandX) / kCandX;
+                                    cand = bw2 * ((y1 - y0 + kCandY) / kCandY);
+                                    if (STATS) cnt[3] += (unsigned long long)((x1 - x0 + 1) * (y1 - y0 + 1));
                                     const float inv = __fdividef(1.0f, area);
                                     const float du1 = C1.x - C0.x, dv1 = C1.y - C0.y, du2 = C2.x - C0.x, dv2 = C2.y - C0.y;
                                     const float dz1 = C1.z - C0.z, dz2 = C2.z - C0.z;
@@ -402,15 +414,14 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                                     rec[3] = stage_edge(C3.x, C3.y, C0.x, C0.y, sgn);
                                     // 1/z = al px + be py + K over the quad's plane
                                     const float K = fmaf(-al, C0.x, fmaf(-be, C0.y, C0.z));
-                                    // the candidate's row is floor((k + 1/2) / width), exact in float
-                                    // for the region's sizes (margin 1/(2 width) >> rounding)
-                                    rec[4] = make_float4(al, be, K, 1.0f / (float)(x1 - x0 + 1));
-                                    rec[5] = make_float4(__int_as_float(x0), __int_as_float(y0),
-                                                         __int_as_float(x1 - x0 + 1), 0.f);
+                                    // the candidate's row is floor((k + 1/2) / pairs per row), exact in
+                                    // float for the region's sizes (margin 1/(2 width) >> rounding)
+                                    rec[4] = make_float4(al, be, K, 1.0f / (float)bw2);
+                                    rec[5] = make_float4(__int_as_float(x0), __int_as_float(y0), __int_as_float(bw2),
+                                                         __int_as_float((x1 - x0) | ((y1 - y0) << 16)));
                                 }
                             }
                         }
-                        if (STATS) cnt[3] += (unsigned long long)cand;
                         int incl = cand;
 #pragma unroll
                         for (int o = 1; o < 32; o <<= 1) {
@@ -438,13 +449,26 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                             if (j < n_cand) {
                                 const float4 *rec = stg + lo * kStageStride;
                                 const float4 Pl = rec[4], Bx = rec[5];
-                                const int bw = __float_as_int(Bx.z), row = (int)(((float)kk + 0.5f) * Pl.w);
-                                const int x = __float_as_int(Bx.x) + (kk - row * bw), y = __float_as_int(Bx.y) + row;
-                                const float px = (float)x + 0.5f, py = (float)y + 0.5f;
-                                if (staged_inside(rec[0], px, py) && staged_inside(rec[1], px, py) &&
-                                    staged_inside(rec[2], px, py) && staged_inside(rec[3], px, py)) {
-                                    const float z = __fdividef(1.0f, fmaf(Pl.x, px, fmaf(Pl.y, py, Pl.z)));
-                                    if (z <= c.far_z) store(x, y, z);
+                                const float4 E0 = rec[0], E1 = rec[1], E2 = rec[2], E3 = rec[3];
+                                const int bw2 = __float_as_int(Bx.z), ends = __float_as_int(Bx.w);
+                                const int bx = __float_as_int(Bx.x), by = __float_as_int(Bx.y);
+                                const int xe = bx + (ends & 0xffff), ye = by + (ends >> 16);  // box extent < 2^16
+                                const int row = (int)(((float)kk + 0.5f) * Pl.w);
+                                const int x = bx + kCandX * (kk - row * bw2);
+                                const int y = by + kCandY * row;
+#pragma unroll
+                                for (int e = 0; e < kCandY; ++e) {
+                                    const float py = (float)(y + e) + 0.5f;
+#pragma unroll
+                                    for (int d = 0; d < kCandX; ++d) {
+                                        const float px = (float)(x + d) + 0.5f;
+                                        if (x + d <= xe && y + e <= ye && staged_inside(E0, px, py) &&
+                                            staged_inside(E1, px, py) && staged_inside(E2, px, py) &&
+                                            staged_inside(E3, px, py)) {
+                                            const float z = __fdividef(1.0f, fmaf(Pl.x, px, fmaf(Pl.y, py, Pl.z)));
+                                            if (z <= c.far_z) store(x + d, y + e, z);
+                                        }
+                                    }
                                 }
                             }
                         }
