@@ -298,7 +298,9 @@ def run_gpu(args):
         e2e = run_e2e(args, ctx, parse, obs_np, flush, dev, torch, hyps_step)
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "ms_per_step_p50": float(np.percentile(step_ms, 50)), "ms_per_step_p99": float(np.percentile(step_ms, 99)),
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_dict(wl, {"parallelism": f"replicas x{world} (independent scenes)",
                                    "score_kernel_tuning": tuning}),
