@@ -178,9 +178,10 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
     return acc;
 }
 
-// z-buffer pixels per tile for a CTA of NT threads
+// z-buffer pixels per tile for a CTA of NT threads (measured: 3072 for 128 threads leaves room
+// for one more resident CTA per SM than 4096 while still holding a tabletop footprint in one tile)
 template <int NT>
-constexpr int score_region() { return NT <= 64 ? 2048 : kRegionPx; }
+constexpr int score_region() { return NT <= 64 ? 2048 : (NT == 128 ? 3072 : kRegionPx); }
 constexpr int kStageStride = 6;  // float4 per staged rectangle: four edges, plane, pixel box
 // Pixels a candidate of the cooperative rasteriser covers (a block of kCandX x kCandY): the
 // owner lookup, record loads and index arithmetic are shared by the block's pixel tests.
@@ -333,7 +334,8 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
     const int sx0 = max(bx0 - w, 0), sx1 = min(bx1 + w, c.W - 1);
     const int sy0 = max(by0 - w, 0), sy1 = min(by1 + w, c.H - 1);
     const int sw = sx1 - sx0 + 1;
-    const int tw = min(sw, S.tile_w);
+    // the tile plus its halo must fit the region even one row high: (tw + 2w)(1 + 2w) <= REG
+    const int tw = min(min(sw, S.tile_w), REG / (1 + 2 * w) - 2 * w);
     const int th = max(1, REG / (tw + 2 * w) - 2 * w);
     for (int ty0 = sy0; ty0 <= sy1; ty0 += th) {
         for (int tx0 = sx0; tx0 <= sx1; tx0 += tw) {

@@ -113,6 +113,28 @@ def test_render_large_footprint_and_ragged_image(orc):
         _check_ll(ll, orc.score(sc, 0, poses, lik, obs), "large footprint")
 
 
+@pytest.mark.parametrize("nt,hi", [(64, 0), (128, 1), (256, 0)])
+def test_widest_tile_with_the_largest_window(orc, nt, hi):
+    """tile_w 256 with the largest half window (7): the kernel narrows the tile so the tile and
+    its halo fit its shared-memory region; an object covering most of a 160x120 image."""
+    from paper_2312_08715_gb300 import b3d
+    rng = np.random.default_rng(14)
+    cells = np.array(np.unravel_index(rng.permutation(512)[:300], (8, 8, 8))).T
+    mesh = synth.voxel_mesh(cells, 0.02, origin=(-0.08, -0.08, -0.08))
+    cam = synth.Camera(160, 120, 150.0, 150.0, 80.0, 60.0, 0.01, 2.0)
+    pose = synth.rigid(synth.random_rotation(rng), [0.01, -0.02, 0.22]).astype(np.float32)
+    sc = synth.Scene(cam, [mesh], pose[None].copy())
+    obs = synth.corrupt_depth(orc.render(sc)[0], cam.far, synth.noise_draws(rng, 120, 160))
+    ctx = gpu_context(sc, obs)
+    b3d.b3d_set_tuning(ctx.h, tile_w=256, cta_threads=nt, ctas_per_sm=0, high_occupancy=hi, batch_chunk=4)
+    poses = jitter_poses(rng, pose, 6, trans=0.01, rot_deg=5)
+    lik = dict(kind=1, radius=0.004, p_outlier=0.01, half_window=7)
+    ll = _np(ctx.score(0, poses, lik))
+    ctx.sync()
+    _check_ll(ll, orc.score(sc, 0, poses, lik, obs), f"tile 256, w 7, {nt} threads")
+    ctx.close()
+
+
 def test_near_plane_and_out_of_view(orc, single_object):
     wl = single_object
     sc = wl.scene
