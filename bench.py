@@ -903,6 +903,8 @@ def run_refine(args):
     e0 = np.linalg.norm(T_start[:, :3, 3].cpu().numpy() - hidden, axis=1)
     e1 = np.linalg.norm(T_end[:, :3, 3].cpu().numpy() - hidden, axis=1)
     xi = torch.zeros((M, 6), device=dev, requires_grad=True)
+    sigma.grad = None
+    pout.grad = None
     ll = F.apply(xi, sigma, pout, ctx, slot, T_end, smooth["half_window"])
     ll.sum().backward()
     mean_ms = float(np.mean(ms))

@@ -240,13 +240,17 @@ __device__ __forceinline__ float pixel_ell(const Lik &L, const float *lut, const
 }
 
 
-// Kind-1 terms of pixel i: S_i = sum_j N_ij with N_ij = (2 pi s^2)^(-3/2) exp(-d_ij^2 / (2 s^2))
-// and dS_i = sum_j N_ij (d_ij^2 / s^2 - 3) / s (= d S_i / d s).
+// Kind-1 value and derivatives of pixel i in one pass over its window. With
+// E_i = sum_j exp(-d_ij^2 / (2 s^2)) (accumulated exactly as pixel_ell does, so l equals
+// pixel_ell's value bit for bit), S_i = (2 pi s^2)^(-3/2) E_i and p_i = a + b S_i:
+//   l  = log p_i
+//   gs = d l / d s     = b (2 pi s^2)^(-3/2) sum_j exp(..) (d_ij^2 / s^2 - 3) / (s p_i)
+//   gp = d l / d p_out = (1 / V - S_i / K) / p_i
+//   bp = b / p_i (the weight of pixel i in d LL / d z_j).
 template <class Fetch>
-__device__ __forceinline__ void pixel_terms(const Lik &L, const Cam &c, float4 q, int xi, int yi, Fetch fetch,
-                                            float &Si, float &dSi) {
-    Si = 0.f;
-    dSi = 0.f;
+__device__ __forceinline__ void pixel_ell_grads(const Lik &L, const Cam &c, float4 q, int xi, int yi, Fetch fetch,
+                                                float &l, float &gs, float &gp, float &bp) {
+    float E = 0.f, D = 0.f;
     for (int dy = -L.w; dy <= L.w; ++dy) {
         const int yj = yi + dy;
         if (yj < 0 || yj >= c.H) continue;
@@ -259,19 +263,17 @@ __device__ __forceinline__ void pixel_terms(const Lik &L, const Cam &c, float4 q
             const float rx = ((float)xj + 0.5f - c.cx) * c.inv_fx;
             const float ex = fmaf(-z, rx, q.x), ey = fmaf(-z, ry, q.y), ez = q.z - z;
             const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-            const float N = L.gnorm * __expf(-d2 * L.inv2s2);
-            Si += N;
-            dSi += N * (d2 * L.inv_s2 - 3.f) / L.s;
+            const float e = __expf(-d2 * L.inv2s2);
+            E += e;
+            D = fmaf(e, fmaf(d2, L.inv_s2, -3.f), D);
         }
     }
-}
-
-// d l_i / d s and d l_i / d p_out from the kind-1 terms; also returns b / p_i.
-__device__ __forceinline__ void pixel_noise_grads(const Lik &L, float Si, float dSi, float &gs, float &gp, float &bp) {
-    const float p = fmaf(L.b, Si, L.a);
-    gs = L.b * dSi / p;
-    gp = (L.inv_V - Si * L.inv_K) / p;
-    bp = L.b / p;
+    const float p = fmaf(L.bg, E, L.a);
+    l = __logf(p);
+    const float ip = 1.f / p;
+    gs = L.bg * D / L.s * ip;
+    gp = fmaf(-L.gnorm * E, L.inv_K, L.inv_V) * ip;
+    bp = L.b * ip;
 }
 
 }  // namespace b3d

@@ -25,26 +25,28 @@
 namespace b3d {
 
 constexpr int kGradSmem = kRegionPx * ((int)sizeof(unsigned long long) + 3 * (int)sizeof(float));
+constexpr int kGradThreads = 512;  // threads per hypothesis: a launch of a few hundred hypotheses is one wave
+constexpr int kGradMinBlocks = 2;
 
-template <class PS>
-__global__ void __launch_bounds__(kThreads) k_grad(SceneView S, Lik L, PS P, int64_t n_hyp, float *out_ll,
-                                                   float *out_dpose, float *out_ds, float *out_dp) {
+template <class PS, int NT>
+__global__ void __launch_bounds__(NT, kGradMinBlocks)
+    k_grad(SceneView S, Lik L, PS P, int64_t n_hyp, float *out_ll, float *out_dpose, float *out_ds, float *out_dp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long *zb = reinterpret_cast<unsigned long long *>(smem_raw);
     float *zd = reinterpret_cast<float *>(zb + kRegionPx);  // rendered depth per Z pixel
     int *tj = reinterpret_cast<int *>(zd + kRegionPx);      // original face of the object, or -1
-    float *ip = reinterpret_cast<float *>(tj + kRegionPx);  // b / p_i
-    __shared__ float s_lut[kMaxLut];
+    float *ip = reinterpret_cast<float *>(tj + kRegionPx);  // (b / p_i) (2 pi s^2)^(-3/2) / s^2
     __shared__ float s_pose[12];
+    __shared__ float s_cof[9];  // cofactor matrix of the linear part: maps object normals to camera normals
     __shared__ int s_bb[5];
     __shared__ int s_front;
-    __shared__ float s_red[kThreads / 32];
+    __shared__ float s_red[9][NT / 32];
 
     const Cam &c = S.cam;
     const MeshView &m = S.mesh;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int i = tid; i < L.n_lut; i += nt) s_lut[i] = L.lut[i];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int w = L.w;
+    const float wscale = L.gnorm * L.inv_s2;
 
     for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
         __syncthreads();
@@ -53,6 +55,17 @@ __global__ void __launch_bounds__(kThreads) k_grad(SceneView S, Lik L, PS P, int
             bool front = false;
             s_bb[4] = object_bbox(m, s_pose, c, s_bb, &front) ? 1 : 0;
             s_front = front ? 1 : 0;
+            // columns of the cofactor matrix: m1 x m2, m2 x m0, m0 x m1 (m_k the columns of
+            // the linear part), so that (M a) x (M b) = cof(M) (a x b)
+            const float *R = s_pose;
+            const float m0[3] = {R[0], R[3], R[6]}, m1[3] = {R[1], R[4], R[7]}, m2[3] = {R[2], R[5], R[8]};
+            const float *cols[3][2] = {{m1, m2}, {m2, m0}, {m0, m1}};
+            for (int k = 0; k < 3; ++k) {
+                const float *u = cols[k][0], *v = cols[k][1];
+                s_cof[0 + k] = u[1] * v[2] - u[2] * v[1];
+                s_cof[3 + k] = u[2] * v[0] - u[0] * v[2];
+                s_cof[6 + k] = u[0] * v[1] - u[1] * v[0];
+            }
         }
         __syncthreads();
         const float *pose = s_pose;
@@ -81,9 +94,9 @@ __global__ void __launch_bounds__(kThreads) k_grad(SceneView S, Lik L, PS P, int
                     const int rx0 = max(zx0, bx0), rx1 = min(zx1, bx1), ry0 = max(zy0, by0), ry1 = min(zy1, by1);
                     const bool need = rx0 <= rx1 && ry0 <= ry1;
                     if (need) {
-                        for (int i = tid; i < zw * zh; i += nt) zb[i] = kEmptyKey;
+                        for (int i = tid; i < zw * zh; i += NT) zb[i] = kEmptyKey;
                         __syncthreads();
-                        for (int t = tid; t < n_t; t += nt) {
+                        for (int t = tid; t < n_t; t += NT) {
                             const int4 tr = tris[t];
                             float4 A, B, C;
                             tri_screen(m, tr, pose, c, A, B, C);
@@ -94,8 +107,8 @@ __global__ void __launch_bounds__(kThreads) k_grad(SceneView S, Lik L, PS P, int
                         }
                         __syncthreads();
                     }
-                    for (int i = tid; i < zw * zh; i += nt) {
-                        const int gx = zx0 + i % zw, gy = zy0 + i / zw;
+                    for (int i = tid; i < zw * zh; i += NT) {
+                        const int gy = zy0 + i / zw, gx = zx0 + (i - (i / zw) * zw);
                         const unsigned long long kb = S.bg[(int64_t)gy * c.W + gx];
                         unsigned long long key = kb;
                         int t = -1;
@@ -108,29 +121,29 @@ __global__ void __launch_bounds__(kThreads) k_grad(SceneView S, Lik L, PS P, int
                     }
                     __syncthreads();
                     auto fetch = [&](int xj, int yj) { return zd[(yj - zy0) * zw + (xj - zx0)]; };
-                    // pass A over I; deltas accumulate over the tile T only
-                    for (int k = tid; k < iw * ih; k += nt) {
-                        const int x = ix0 + k % iw, y = iy0 + k / iw;
+                    // pass A over I (one window loop gives l_i and its derivatives); deltas
+                    // accumulate over the tile T only
+                    for (int k = tid; k < iw * ih; k += NT) {
+                        const int y = iy0 + k / iw, x = ix0 + (k - (k / iw) * iw);
                         const int64_t gi = (int64_t)y * c.W + x;
                         const float4 q = S.obs[gi];
                         float bp = 0.f;
                         if (q.w != 0.f) {
-                            float Si, dSi, gs, gp;
-                            pixel_terms(L, c, q, x, y, fetch, Si, dSi);
-                            pixel_noise_grads(L, Si, dSi, gs, gp, bp);
+                            float l, gs, gp;
+                            pixel_ell_grads(L, c, q, x, y, fetch, l, gs, gp, bp);
                             if (x >= tx0 && x <= tx1 && y >= ty0 && y <= ty1) {
-                                acc_l += pixel_ell(L, s_lut, c, q, x, y, fetch) - S.ell_bg[gi];
+                                acc_l += l - S.ell_bg[gi];
                                 acc_s += gs - S.gs_bg[gi];
                                 acc_p += gp - S.gp_bg[gi];
                             }
                         }
-                        ip[k] = bp;
+                        ip[k] = bp * wscale;
                     }
                     __syncthreads();
                     // pass B over the object's rendered pixels in T
                     const int tww = tx1 - tx0 + 1;
-                    for (int k = tid; k < tww * (ty1 - ty0 + 1); k += nt) {
-                        const int x = tx0 + k % tww, y = ty0 + k / tww;
+                    for (int k = tid; k < tww * (ty1 - ty0 + 1); k += NT) {
+                        const int y = ty0 + k / tww, x = tx0 + (k - (k / tww) * tww);
                         const int zi = (y - zy0) * zw + (x - zx0);
                         const int t = tj[zi];
                         if (t < 0) continue;
@@ -149,20 +162,18 @@ __global__ void __launch_bounds__(kThreads) k_grad(SceneView S, Lik L, PS P, int
                                 const float4 qi = S.obs[(int64_t)yi * c.W + xi];
                                 const float ex = qi.x - qx, ey = qi.y - qy, ez = qi.z - qz;
                                 const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                                const float N = L.gnorm * __expf(-d2 * L.inv2s2);
-                                g += bpi * N * fmaf(ex, rx, fmaf(ey, ry, ez)) * L.inv_s2;
+                                g = fmaf(bpi * __expf(-d2 * L.inv2s2), fmaf(ex, rx, fmaf(ey, ry, ez)), g);
                             }
                         }
-                        // triangle normal in the camera frame
+                        // the face's normal: object-frame cross product mapped by the cofactor matrix
                         const int4 f = m.faces[t];
-                        float ax, ay, az, bx, by, bz, cx_, cy_, cz_;
                         const float4 A = m.verts[f.x], B = m.verts[f.y], C = m.verts[f.z];
-                        xform(pose, A.x, A.y, A.z, ax, ay, az);
-                        xform(pose, B.x, B.y, B.z, bx, by, bz);
-                        xform(pose, C.x, C.y, C.z, cx_, cy_, cz_);
-                        const float e1x = bx - ax, e1y = by - ay, e1z = bz - az;
-                        const float e2x = cx_ - ax, e2y = cy_ - ay, e2z = cz_ - az;
-                        const float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+                        const float e1x = B.x - A.x, e1y = B.y - A.y, e1z = B.z - A.z;
+                        const float e2x = C.x - A.x, e2y = C.y - A.y, e2z = C.z - A.z;
+                        const float ox = e1y * e2z - e1z * e2y, oy = e1z * e2x - e1x * e2z, oz = e1x * e2y - e1y * e2x;
+                        const float nx = fmaf(s_cof[0], ox, fmaf(s_cof[1], oy, s_cof[2] * oz));
+                        const float ny = fmaf(s_cof[3], ox, fmaf(s_cof[4], oy, s_cof[5] * oz));
+                        const float nz = fmaf(s_cof[6], ox, fmaf(s_cof[7], oy, s_cof[8] * oz));
                         const float nr = fmaf(nx, rx, fmaf(ny, ry, nz));
                         if (nr == 0.f) continue;
                         const float gn = g / nr;
@@ -177,18 +188,21 @@ __global__ void __launch_bounds__(kThreads) k_grad(SceneView S, Lik L, PS P, int
                 }
             }
         }
-        float vals[9] = {acc_l, acc_s, acc_p, g6[0], g6[1], g6[2], g6[3], g6[4], g6[5]};
+        // one reduction of the nine sums: warp trees, then warps in order
+        const float vals[9] = {acc_l, acc_s, acc_p, g6[0], g6[1], g6[2], g6[3], g6[4], g6[5]};
+#pragma unroll
         for (int k = 0; k < 9; ++k) {
-            const float tot = block_sum(vals[k], s_red);
-            if (tid == 0) vals[k] = tot;
-            __syncthreads();
+            const float v = warp_sum(vals[k]);
+            if (lane == 0) s_red[k][wid] = v;
         }
-        if (tid == 0) {
-            out_ll[h] = (float)(S.sums_bg[0] + (double)vals[0]);
-            if (out_ds) out_ds[h] = (float)(S.sums_bg[1] + (double)vals[1]);
-            if (out_dp) out_dp[h] = (float)(S.sums_bg[2] + (double)vals[2]);
-            if (out_dpose)
-                for (int k = 0; k < 6; ++k) out_dpose[6 * h + k] = vals[3 + k];
+        __syncthreads();
+        if (tid < 9) {
+            float tot = 0.f;
+            for (int k = 0; k < NT / 32; ++k) tot += s_red[tid][k];
+            if (tid == 0) out_ll[h] = (float)(S.sums_bg[0] + (double)tot);
+            else if (tid == 1) { if (out_ds) out_ds[h] = (float)(S.sums_bg[1] + (double)tot); }
+            else if (tid == 2) { if (out_dp) out_dp[h] = (float)(S.sums_bg[2] + (double)tot); }
+            else if (out_dpose) out_dpose[6 * h + (tid - 3)] = tot;
         }
     }
 }
@@ -196,8 +210,8 @@ __global__ void __launch_bounds__(kThreads) k_grad(SceneView S, Lik L, PS P, int
 int launch_grad_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, float *dpose, float *dsigma,
                      float *dpout, int grid, cudaStream_t s) {
     if (n <= 0) return 0;
-    auto kern = k_grad<PoseList>;
-    const int per_sm = kernel_ctas_per_sm(kern, kThreads, kGradSmem);
+    auto kern = k_grad<PoseList, kGradThreads>;
+    const int per_sm = kernel_ctas_per_sm(kern, kGradThreads, kGradSmem);
     int g = grid;
     if (g <= 0) {
         static int sms = 0;
@@ -210,7 +224,7 @@ int launch_grad_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, f
         g = per_sm * sms;
     }
     g = (int)std::min<int64_t>(g, n);
-    kern<<<g, kThreads, kGradSmem, s>>>(sv, L, P, n, ll, dpose, dsigma, dpout);
+    kern<<<g, kGradThreads, kGradSmem, s>>>(sv, L, P, n, ll, dpose, dsigma, dpout);
     return g;
 }
 

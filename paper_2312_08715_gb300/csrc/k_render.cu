@@ -290,9 +290,8 @@ __global__ void __launch_bounds__(256) k_bg_tables(SceneView S, Lik L, float *el
             auto fetch = [&](int xj, int yj) { return key_depth(S.bg[(int64_t)yj * c.W + xj], L.miss_mode, c.far_z); };
             l = pixel_ell(L, s_lut, c, q, x, y, fetch);
             if (gs_bg) {
-                float Si, dSi, bp;
-                pixel_terms(L, c, q, x, y, fetch, Si, dSi);
-                pixel_noise_grads(L, Si, dSi, gs, gp, bp);
+                float l1, bp;
+                pixel_ell_grads(L, c, q, x, y, fetch, l1, gs, gp, bp);
             }
         }
         ell_bg[i] = l;
