@@ -483,7 +483,7 @@ def run_materialised(args):
 
     def step():
         b3d.b3d_render_batch(ctx.h, FIRST_SLOT, n, poses, depth, None, stream)
-        b3d.b3d_score_depth_batch(ctx.h, n, depth, None, lik, ll, stream)
+        b3d.b3d_score_depth_batch(ctx.h, FIRST_SLOT, n, depth, None, lik, ll, stream)
 
     for _ in range(args.warmup):
         step()
@@ -503,6 +503,12 @@ def run_materialised(args):
     r_ms, r_n = b3d.b3d_kernel_time(ctx.h, b3d.B3D_K_RENDER)
     s_ms, s_n = b3d.b3d_kernel_time(ctx.h, b3d.B3D_K_SCORE_DEPTH)
     ctx.sync()
+    # the same hypotheses through the fused kernel: the two forms agree to FP32 accuracy
+    ll_fused = ctx.score(FIRST_SLOT, poses, wl.lik)
+    ctx.sync()
+    dll = (ll.double() - ll_fused.double()).abs()
+    agree = {"max_abs": float(dll.max()), "median_abs": float(dll.median()),
+             "max_rel": float((dll / ll_fused.double().abs().clamp_min(1.0)).max())}
     px = H * W
     peak = _measured_peaks().get("hbm_gbs", 6800.0)
     wr = 4.0 * px * n / (r_ms / r_n / 1e3) / 1e9
@@ -514,6 +520,7 @@ def run_materialised(args):
         "config": config_dict(wl, {"workload": "render-then-score form: first stage of the first object, 145,800 "
                                                "hypotheses, depth images in HBM",
                                    "hyps_per_step": n, "l2": "images (11.2 GB) exceed L2"}),
+        "agreement_with_fused": agree,
         "render": {"ms": r_ms / r_n, "write_gbs": wr, "frac_of_hbm": wr / peak},
         "score_depth": {"ms": s_ms / s_n, "read_gbs": rd, "frac_of_hbm": rd / peak},
         "roofline": {"bound": "hbm", "achieved": 8.0 * px * n / (total_ms / args.steps / 1e3) / 1e9, "peak": peak,

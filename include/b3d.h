@@ -178,9 +178,16 @@ b3d_status b3d_score_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const 
 
 /* Score materialised depth images: depth_dev [n_hyp, H, W] (e.g. from b3d_render_batch)
  * against the scene's observation; triid_dev [n_hyp, H, W] is needed only for
- * miss_mode 1 (pixels with id -1 carry no point), else may be NULL. loglik_dev [n_hyp]. */
-b3d_status b3d_score_depth_batch(b3d_ctx *ctx, int64_t n_hyp, const float *depth_dev, const int32_t *triid_dev,
-                                 const b3d_lik_params *lik, float *loglik_dev, b3d_stream stream);
+ * miss_mode 1 (pixels with id -1 carry no point), else may be NULL. loglik_dev [n_hyp]
+ * receives sum_i l_i. The images may hold any depths. A pixel whose window holds exactly
+ * the depths of a reference image takes the reference's term, computed once per scene and
+ * likelihood (the same value, bit for bit), so the cost follows the region where an image
+ * differs from the reference: the scene without object obj_slot (images of that object
+ * re-posed, as b3d_render_batch writes them, differ only around it), or with every object
+ * when obj_slot is -1. The choice changes the sums only by FP32 summation order. */
+b3d_status b3d_score_depth_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const float *depth_dev,
+                                 const int32_t *triid_dev, const b3d_lik_params *lik, float *loglik_dev,
+                                 b3d_stream stream);
 
 /* Expand one coarse-to-fine stage around centre_pose (host [16]) with grid frame G (host
  * [9], row-major cam_from_grid): poses_dev [n^3 * n_rot, 16] in hypothesis order (see

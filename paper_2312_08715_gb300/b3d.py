@@ -124,7 +124,7 @@ _SIGNATURES = {
     "b3d_set_object_pose_dev": (C.c_int32, [_P, C.c_int32, _P, _P]),
     "b3d_render_batch": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, _P, _P, _P]),
     "b3d_score_batch": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_lik_params), _P, _P]),
-    "b3d_score_depth_batch": (C.c_int32, [_P, C.c_int64, _P, _P, C.POINTER(b3d_lik_params), _P, _P]),
+    "b3d_score_depth_batch": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, _P, C.POINTER(b3d_lik_params), _P, _P]),
     "b3d_score_noise_batch": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_noise_grid), _P, _P, _P]),
     "b3d_render_camera_batch": (C.c_int32, [_P, C.c_int64, _P, _P, _P, _P]),
     "b3d_expand_hypotheses": (C.c_int32, [_P, _P, _P, C.POINTER(b3d_stage), _P, _P]),
@@ -302,8 +302,8 @@ def b3d_score_batch(ctx, obj_slot, n_hyp, poses_dev, lik: b3d_lik_params, loglik
                                               _addr(loglik_dev), _stream(stream)))
 
 
-def b3d_score_depth_batch(ctx, n_hyp, depth_dev, triid_dev, lik: b3d_lik_params, loglik_dev, stream=None):
-    return _check(ctx, load().b3d_score_depth_batch(ctx, n_hyp, _addr(depth_dev), _addr(triid_dev), C.byref(lik),
+def b3d_score_depth_batch(ctx, obj_slot, n_hyp, depth_dev, triid_dev, lik: b3d_lik_params, loglik_dev, stream=None):
+    return _check(ctx, load().b3d_score_depth_batch(ctx, obj_slot, n_hyp, _addr(depth_dev), _addr(triid_dev), C.byref(lik),
                                                     _addr(loglik_dev), _stream(stream)))
 
 
@@ -729,10 +729,12 @@ class Context:
         b3d_score_noise_batch(self.h, slot, n, P, grid, ll, marg, self.stream)
         return ll, marg
 
-    def score_depth(self, depth, lik: dict, tid=None):
+    def score_depth(self, depth, lik: dict, tid=None, slot=-1):
+        """Sum of l_i of each image; slot: the object the images re-pose (-1: none), which
+        only narrows the region compared against the scene."""
         n = depth.shape[0]
         ll = self.torch.empty(n, dtype=self.torch.float32, device=self.device)
-        b3d_score_depth_batch(self.h, n, depth, tid, lik_params(**lik), ll, self.stream)
+        b3d_score_depth_batch(self.h, slot, n, depth, tid, lik_params(**lik), ll, self.stream)
         return ll
 
     def expand(self, centre, grid_frame, stage):

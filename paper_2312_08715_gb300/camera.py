@@ -59,7 +59,7 @@ class CameraTracker:
             poses, depth_buf, ll = self._buf(n)
             b3d.b3d_expand_hypotheses(ctx.h, centre, np.eye(3, dtype=np.float32), b3d.stage_params(st), poses, ctx.stream)
             b3d.b3d_render_camera_batch(ctx.h, n, poses, depth_buf, None, ctx.stream)
-            b3d.b3d_score_depth_batch(ctx.h, n, depth_buf, None, liks[k], ll, ctx.stream)
+            b3d.b3d_score_depth_batch(ctx.h, -1, n, depth_buf, None, liks[k], ll, ctx.stream)
             b3d.b3d_lse_resample(ctx.h, n, ll, m, seed, k, logz, idx, logq, ctx.stream)
             drawn = idx.long()
             best = drawn[t.argmax(ll[drawn])]

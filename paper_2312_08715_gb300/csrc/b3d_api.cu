@@ -54,11 +54,12 @@ thread_local std::string g_create_error;
 // different objects of one scene can be scored in the same launch.
 struct BgCache {
     unsigned long long *bg = nullptr;
+    float *bgd = nullptr;  // [2][npx] background depth under miss modes 0 and 1
     float *ell = nullptr, *gs = nullptr, *gp = nullptr;
     double *sums = nullptr, *part = nullptr;  // sums [3]; per-block partials of the table kernel
     unsigned *counter = nullptr;               // its last-block ticket (zero between launches)
     int64_t cap = 0, gcap = 0;
-    bool dirty = true, lik_valid = false, grad_valid = false;
+    bool dirty = true, lik_valid = false, grad_valid = false, bgd_valid = false;
     LikKey key{};
     // noise-grid tables [kMaxNoise][H W], their sums [kMaxNoise], partials and ticket
     float *nell = nullptr;
@@ -340,9 +341,10 @@ b3d_status ensure_bg(b3d_ctx *ctx, int32_t slot, cudaStream_t s) {
     const int64_t npx = (int64_t)ctx->cam.W * ctx->cam.H;
     b3d_status st;
     if (c.cap < npx) {
-        dfree(ctx, c.bg); dfree(ctx, c.ell); dfree(ctx, c.gs); dfree(ctx, c.gp);
+        dfree(ctx, c.bg); dfree(ctx, c.bgd); dfree(ctx, c.ell); dfree(ctx, c.gs); dfree(ctx, c.gp);
         c.cap = c.gcap = 0;
         if ((st = dalloc(ctx, &c.bg, (size_t)npx, "background z-buffer")) != B3D_OK) return st;
+        if ((st = dalloc(ctx, &c.bgd, (size_t)2 * npx, "background depth")) != B3D_OK) return st;
         if ((st = dalloc(ctx, &c.ell, (size_t)npx, "background likelihood")) != B3D_OK) return st;
         if (!c.sums && (st = dalloc(ctx, &c.sums, 3, "background sums")) != B3D_OK) return st;
         dfree(ctx, c.part);
@@ -366,8 +368,19 @@ b3d_status ensure_bg(b3d_ctx *ctx, int32_t slot, cudaStream_t s) {
         ++ctx->launches;
     }
     c.dirty = false;
-    c.lik_valid = c.grad_valid = c.nvalid = false;
+    c.lik_valid = c.grad_valid = c.nvalid = c.bgd_valid = false;
     return check_launch(ctx, "background render");
+}
+
+// The background's depth under both miss modes (after ensure_bg), for the materialised form.
+b3d_status ensure_bg_depth(b3d_ctx *ctx, int32_t slot, cudaStream_t s) {
+    BgCache &c = bg_cache(ctx, slot);
+    if (c.bgd_valid) return B3D_OK;
+    Timed tm(ctx, B3D_K_SCENE, s);
+    launch_bg_depth((int64_t)ctx->cam.W * ctx->cam.H, ctx->cam.far_z, c.bg, c.bgd, s);
+    ++ctx->launches;
+    c.bgd_valid = true;
+    return check_launch(ctx, "background depth");
 }
 
 SceneView scene_view(b3d_ctx *ctx, int32_t slot) {
@@ -377,6 +390,7 @@ SceneView scene_view(b3d_ctx *ctx, int32_t slot) {
     if ((size_t)(slot + 1) < ctx->bgc.size()) {
         const BgCache &c = ctx->bgc[(size_t)(slot + 1)];
         sv.bg = c.bg;
+        sv.bgd = c.bgd;
         sv.ell_bg = c.ell;
         sv.ll_bg = c.sums;
         sv.gs_bg = c.gs;
@@ -1138,11 +1152,11 @@ b3d_status b3d_render_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = ensure_bg(ctx, obj_slot, s)) != B3D_OK) return st;
+    if (!triid_dev && (st = ensure_bg_depth(ctx, obj_slot, s)) != B3D_OK) return st;
     {
         Timed tm(ctx, B3D_K_RENDER, s);
-        launch_render_list(scene_view(ctx, obj_slot), PoseList{poses_dev}, n_hyp, depth_dev, triid_dev, 0, s);
+        ctx->launches += launch_render_list(scene_view(ctx, obj_slot), PoseList{poses_dev}, n_hyp, depth_dev, triid_dev, 0, s);
     }
-    ++ctx->launches;
     return check_launch(ctx, "render_batch");
 }
 
@@ -1239,11 +1253,16 @@ b3d_status b3d_score_noise_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, 
     return check_launch(ctx, "score_noise_batch");
 }
 
-b3d_status b3d_score_depth_batch(b3d_ctx *ctx, int64_t n_hyp, const float *depth_dev, const int32_t *triid_dev,
-                                 const b3d_lik_params *lik, float *loglik_dev, b3d_stream stream) {
+b3d_status b3d_score_depth_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const float *depth_dev,
+                                 const int32_t *triid_dev, const b3d_lik_params *lik, float *loglik_dev,
+                                 b3d_stream stream) {
     if (!ctx) return B3D_EINVAL;
     ctx->err.clear();
     if (!ctx->has_scene) return fail(ctx, B3D_EINVAL, "no scene: call b3d_set_scene first");
+    if (obj_slot != -1) {
+        b3d_status sst = check_slot(ctx, obj_slot);
+        if (sst != B3D_OK) return sst;
+    }
     Lik L;
     b3d_status st = make_lik(ctx, lik, &L);
     if (st != B3D_OK) return st;
@@ -1251,14 +1270,15 @@ b3d_status b3d_score_depth_batch(b3d_ctx *ctx, int64_t n_hyp, const float *depth
     if (n_hyp == 0) return B3D_OK;
     if (!depth_dev || !loglik_dev) return fail(ctx, B3D_EINVAL, "depth_dev and loglik_dev must be non-NULL");
     if (lik->miss_mode == 1 && !triid_dev) return fail(ctx, B3D_EINVAL, "miss_mode 1 needs triid_dev");
-    if ((int64_t)ctx->cam.W * (2 * lik->half_window + 1) > 2 * kRegionPx)
-        return fail(ctx, B3D_EINVAL, "image too wide for this window in score_depth_batch (W (2w+1) must be <= 8192)");
     DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ensure_bg(ctx, obj_slot, s)) != B3D_OK) return st;
+    if ((st = ensure_bg_depth(ctx, obj_slot, s)) != B3D_OK) return st;
+    if ((st = ensure_bg_lik(ctx, obj_slot, lik, L, false, s)) != B3D_OK) return st;
     {
-        Timed tm(ctx, B3D_K_SCORE_DEPTH, (cudaStream_t)stream);
-        launch_score_depth(scene_view(ctx, -1), L, depth_dev, triid_dev, n_hyp, loglik_dev, 0, (cudaStream_t)stream);
+        Timed tm(ctx, B3D_K_SCORE_DEPTH, s);
+        ctx->launches += launch_score_depth(scene_view(ctx, obj_slot), L, depth_dev, triid_dev, n_hyp, loglik_dev, 0, s);
     }
-    ++ctx->launches;
     return check_launch(ctx, "score_depth_batch");
 }
 

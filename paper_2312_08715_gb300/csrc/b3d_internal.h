@@ -100,6 +100,7 @@ struct SceneView {
     Cam cam;
     const float4 *obs;                 // [H*W] observed points (x, y, z, 1) or (0,0,0,0) if not scored
     const unsigned long long *bg;      // [H*W] (depth bits << 32 | triangle id) of the fixed objects
+    const float *bgd;                  // [2][H*W] their depth, misses at the far plane / -1 (miss modes 0, 1)
     const float *ell_bg;               // [H*W] l_i of the fixed objects alone (0 where not scored)
     const double *ll_bg;               // [1]   sum of ell_bg
     const float *gs_bg;                // [H*W] d l_i / d sigma, fixed objects alone (gradient only)
@@ -180,6 +181,8 @@ inline int kernel_ctas_per_sm(K kernel, int threads, int smem) {
 // ---- launchers (k_render.cu) -------------------------------------------------------------
 void launch_obs_points(const Cam &cam, const float *depth, float4 *obs, cudaStream_t s);
 void launch_bg_clear(unsigned long long *bg, int64_t n, cudaStream_t s);
+// bgd[m * W H + i] = depth of background key i under miss mode m (0: far plane, 1: -1)
+void launch_bg_depth(int64_t n, float far_z, const unsigned long long *bg, float *bgd, cudaStream_t s);
 void launch_bg_raster(const Cam &cam, const MeshView &m, const float *pose16_dev, int tri_base,
                       unsigned long long *bg, cudaStream_t s);
 // Per-pixel background terms and their double-precision sums (sums[0..2]); part holds
@@ -189,9 +192,12 @@ void launch_bg_tables(const SceneView &sv, const Lik &L, float *ell_bg, float *g
                       unsigned *counter, double *sums, cudaStream_t s);
 int launch_score_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, int grid, cudaStream_t s);
 int launch_score_grid(const SceneView &sv, const Lik &L, PoseGrid P, int64_t n, float *ll, int grid, cudaStream_t s);
+// Materialised render; returns the number of kernel launches.
 int launch_render_list(const SceneView &sv, PoseList P, int64_t n, float *depth, int *tid, int grid, cudaStream_t s);
-void launch_score_depth(const SceneView &sv, const Lik &L, const float *depth, const int *tid, int64_t n,
-                        float *ll, int grid, cudaStream_t s);
+// Materialised images (sv: the scene's full background and its terms); returns the number of
+// kernel launches.
+int launch_score_depth(const SceneView &sv, const Lik &L, const float *depth, const int *tid, int64_t n, float *ll,
+                       int grid, cudaStream_t s);
 int launch_grad_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, float *dpose,
                      float *dsigma, float *dpout, int grid, cudaStream_t s);
 

@@ -27,70 +27,6 @@
 
 namespace b3d {
 
-// ------------------------------------------------------------------------------------------
-// render kernel: depth and triangle id of every pixel (64-bit keys)
-// ------------------------------------------------------------------------------------------
-template <class PS>
-__global__ void __launch_bounds__(kThreads) k_render(SceneView S, PS P, int64_t n_hyp, float *out_depth, int *out_tid) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned long long *zb = reinterpret_cast<unsigned long long *>(smem_raw);  // [kRegionPx]
-    __shared__ float s_pose[12];
-    __shared__ int s_bb[4];
-    __shared__ int s_flags;
-    const Cam &c = S.cam;
-    const MeshView &m = S.mesh;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int64_t npx = (int64_t)c.W * c.H;
-    for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
-        __syncthreads();
-        if (tid == 0) {
-            pose12(P, h, s_pose);
-            bool front = false;
-            s_flags = (object_bbox(m, s_pose, c, s_bb, &front) ? 1 : 0) | (front ? 4 : 0);
-        }
-        __syncthreads();
-        const float *pose = s_pose;
-        const bool has_bb = (s_flags & 1) != 0, front = (s_flags & 4) != 0;
-        const int bx0 = s_bb[0], bx1 = s_bb[1], by0 = s_bb[2], by1 = s_bb[3];
-        const int4 *tris = front ? m.tris_surf : m.tris_full;
-        const int n_t = front ? m.n_surf : m.n_full;
-        const int cull = front ? m.closed : 0;
-        const int tw = min(c.W, kRegionPx);
-        const int th = max(1, kRegionPx / tw);
-        for (int ty0 = 0; ty0 < c.H; ty0 += th) {
-            for (int tx0 = 0; tx0 < c.W; tx0 += tw) {
-                const int tx1 = min(tx0 + tw - 1, c.W - 1), ty1 = min(ty0 + th - 1, c.H - 1);
-                const int zw = tx1 - tx0 + 1, zh = ty1 - ty0 + 1;
-                const int rx0 = max(tx0, bx0), rx1 = min(tx1, bx1), ry0 = max(ty0, by0), ry1 = min(ty1, by1);
-                const bool need = has_bb && rx0 <= rx1 && ry0 <= ry1;
-                if (need) {
-                    for (int i = tid; i < zw * zh; i += nt) zb[i] = kEmptyKey;
-                    __syncthreads();
-                    for (int t = tid; t < n_t; t += nt) {
-                        const int4 tr = tris[t];
-                        float4 A, B, C;
-                        tri_screen(m, tr, pose, c, A, B, C);
-                        const unsigned gid = (unsigned)(S.tri_base + tr.w);
-                        raster_tri(A, B, C, cull, rx0, rx1, ry0, ry1, c.far_z, [&](int x, int y, float z) {
-                            atomicMin(&zb[(y - ty0) * zw + (x - tx0)], pack_key(z, gid));
-                        });
-                    }
-                    __syncthreads();
-                }
-                for (int i = tid; i < zw * zh; i += nt) {
-                    const int gx = tx0 + i % zw, gy = ty0 + i / zw;
-                    const int64_t gi = (int64_t)gy * c.W + gx;
-                    unsigned long long key = S.bg[gi];
-                    if (need) key = min(key, zb[i]);
-                    out_depth[h * npx + gi] = key_depth(key, 0, c.far_z);
-                    if (out_tid) out_tid[h * npx + gi] = key == kEmptyKey ? -1 : (int)(unsigned)(key & 0xffffffffu);
-                }
-                __syncthreads();
-            }
-        }
-    }
-}
-
 // Camera hypotheses: every scene object k at H_h P_k, H_h the hypothesised camera_from_world
 // pose and P_k the object's world pose (the scene poses), rendered into the full image
 // (nothing is fixed, so there is no background).
@@ -177,6 +113,14 @@ __global__ void k_obs_points(Cam c, const float *depth, float4 *obs) {
         } else {
             obs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
+    }
+}
+
+__global__ void k_bg_depth(int64_t n, float far_z, const unsigned long long *bg, float *bgd) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = bg[i];
+        bgd[i] = key_depth(k, 0, far_z);
+        bgd[n + i] = key_depth(k, 1, far_z);
     }
 }
 
@@ -339,51 +283,6 @@ __global__ void __launch_bounds__(256) k_bg_tables(SceneView S, Lik L, float *el
 }
 
 // ------------------------------------------------------------------------------------------
-// two-pass scoring of materialised depth images [n, H, W]
-// ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_score_depth(SceneView S, Lik L, const float *depth, const int *tid_in,
-                                                          int64_t n_hyp, float *out_ll) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *zd = reinterpret_cast<float *>(smem_raw);
-    __shared__ float s_lut[kMaxLut];
-    __shared__ float s_red[kThreads / 32];
-    const Cam &c = S.cam;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int i = tid; i < L.n_lut; i += nt) s_lut[i] = L.lut[i];
-    const int w = L.w;
-    const int64_t npx = (int64_t)c.W * c.H;
-    const int rows = max(1, (2 * kRegionPx) / c.W - 2 * w);  // 32 KB of float depths per tile
-    for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
-        const float *img = depth + h * npx;
-        const int *tim = tid_in ? tid_in + h * npx : nullptr;
-        float acc = 0.f;
-        for (int ty0 = 0; ty0 < c.H; ty0 += rows) {
-            const int ty1 = min(ty0 + rows - 1, c.H - 1);
-            const int zy0 = max(ty0 - w, 0), zy1 = min(ty1 + w, c.H - 1);
-            const int nz = (zy1 - zy0 + 1) * c.W;
-            __syncthreads();
-            for (int i = tid; i < nz; i += nt) {
-                const int64_t gi = (int64_t)zy0 * c.W + i;
-                float d = img[gi];
-                if (L.miss_mode == 1 && tim[gi] < 0) d = -1.f;
-                zd[i] = d;
-            }
-            __syncthreads();
-            const int n_t = (ty1 - ty0 + 1) * c.W;
-            for (int k = tid; k < n_t; k += nt) {
-                const int x = k % c.W, y = ty0 + k / c.W;
-                const float4 q = S.obs[(int64_t)y * c.W + x];
-                if (q.w == 0.f) continue;
-                acc += pixel_ell(L, s_lut, c, q, x, y, [&](int xj, int yj) { return zd[(yj - zy0) * c.W + xj]; });
-            }
-        }
-        const float tot = block_sum(acc, s_red);
-        if (tid == 0) out_ll[h] = tot;
-        __syncthreads();
-    }
-}
-
-// ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
 
@@ -464,15 +363,6 @@ int launch_score_grid(const SceneView &sv, const Lik &L, PoseGrid P, int64_t n, 
     return launch_score(sv, L, P, n, ll, grid, s);
 }
 
-int launch_render_list(const SceneView &sv, PoseList P, int64_t n, float *depth, int *tid, int grid, cudaStream_t s) {
-    if (n <= 0) return 0;
-    const int smem = kRegionPx * (int)sizeof(unsigned long long);
-    auto kern = k_render<PoseList>;
-    const int g = persistent_grid(kern, smem, n, grid);
-    kern<<<g, kThreads, smem, s>>>(sv, P, n, depth, tid);
-    return g;
-}
-
 int launch_render_camera(const Cam &cam, const MeshView *meshes, const int *tri_base, const float *world, int n_obj,
                          PoseList P, int64_t n, float *depth, int *tid, cudaStream_t s) {
     if (n <= 0) return 0;
@@ -483,17 +373,13 @@ int launch_render_camera(const Cam &cam, const MeshView *meshes, const int *tri_
     return g;
 }
 
-void launch_score_depth(const SceneView &sv, const Lik &L, const float *depth, const int *tid, int64_t n, float *ll,
-                        int grid, cudaStream_t s) {
-    if (n <= 0) return;
-    const int smem = 2 * kRegionPx * (int)sizeof(float);
-    const int g = persistent_grid(k_score_depth, smem, n, grid);
-    k_score_depth<<<g, kThreads, smem, s>>>(sv, L, depth, tid, n, ll);
-}
-
 void launch_obs_points(const Cam &cam, const float *depth, float4 *obs, cudaStream_t s) {
     const int64_t n = (int64_t)cam.W * cam.H;
     k_obs_points<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(cam, depth, obs);
+}
+
+void launch_bg_depth(int64_t n, float far_z, const unsigned long long *bg, float *bgd, cudaStream_t s) {
+    k_bg_depth<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(n, far_z, bg, bgd);
 }
 
 void launch_bg_clear(unsigned long long *bg, int64_t n, cudaStream_t s) {

@@ -232,13 +232,125 @@ def test_two_pass_matches_fused(orc, single_object):
     ctx = gpu_context(sc, obs)
     d, t = ctx.render(0, poses)
     ll2 = _np(ctx.score_depth(d, wl.lik, t))
+    ll2s = _np(ctx.score_depth(d, wl.lik, t, slot=0))
     ll1 = _np(ctx.score(0, poses, wl.lik))
     lk_b = dict(wl.lik, miss_mode=1)
-    ll3 = _np(ctx.score_depth(d, lk_b, t))
+    ll3 = _np(ctx.score_depth(d, lk_b, t, slot=0))
     ctx.sync()
     _check_ll(ll1, ref, "fused")
     _check_ll(ll2, ref, "two-pass")
+    _check_ll(ll2s, ref, "two-pass against the slot's background")
     _check_ll(ll3, orc.score(sc, 0, poses, lk_b, obs), "two-pass miss_mode 1")
+
+
+def test_two_pass_tabletop_composite(orc, tabletop):
+    """The materialised form on the five-object tabletop: render (background fill, then the
+    object over its screen box) and score (the box where each image differs from the scene,
+    scored against the background terms) == the oracle, in both miss modes, with and without
+    the id output."""
+    wl = tabletop
+    sc = wl.scene
+    obs = observed(orc, wl)
+    poses = jitter_poses(np.random.default_rng(21), wl.hidden, 12, trans=0.03, rot_deg=20)
+    ctx = gpu_context(sc, obs)
+    d, t = ctx.render(wl.slot, poses)
+    d_only, _ = ctx.render(wl.slot, poses, want_tid=False)
+    for lk in (wl.lik, dict(wl.lik, miss_mode=1), dict(kind=1, radius=0.004, p_outlier=0.02, half_window=2)):
+        ref = orc.score(sc, wl.slot, poses, lk, obs)
+        for slot in (-1, wl.slot, 0):
+            ll = _np(ctx.score_depth(d, lk, t, slot=slot))
+            ctx.sync()
+            _check_ll(ll, ref, f"two-pass tabletop {lk}, reference without slot {slot}")
+    ctx.sync()
+    _check_render(orc, sc, wl.slot, poses[:4], _np(d[:4]), _np(t[:4]))
+    _check_depth(orc, sc, wl.slot, poses[:4], _np(d_only[:4]))
+    ctx.close()
+
+
+def _check_depth(orc, scene, slot, poses, depth, max_frac=1e-4):
+    """Depth-only renders (the rectangle rasteriser): within 1e-5 relative of the oracle
+    except at pixels it flags as edge or depth ties, and those at most max_frac of all."""
+    n_bad = n_px = 0
+    for k, P in enumerate(poses):
+        od, _, of = orc.render(scene, slot=slot, slot_pose=P, edge_tol=1e-4, z_tol=1e-5, want_flags=True)
+        bad = np.abs(depth[k] - od) > 1e-5 * od
+        assert not (bad & ((of & 1) == 0)).any(), f"pose {k}: {int((bad & ((of & 1) == 0)).sum())} unflagged depth mismatches"
+        n_bad += int(bad.sum())
+        n_px += bad.size
+    assert n_bad <= max(1, max_frac * n_px), f"{n_bad} of {n_px} pixels differ"
+
+
+def _oracle_image_ll(orc, cam, lk, depth, tid, obs):
+    out = []
+    for k in range(depth.shape[0]):
+        ell, _, _, _ = orc.pixel_loglik(cam, lk, depth[k].astype(np.float64), None if tid is None else tid[k], obs)
+        out.append(ell.sum())
+    return np.array(out)
+
+
+@pytest.mark.parametrize("offset", [0, 1])
+def test_score_depth_of_arbitrary_images(orc, tabletop, offset):
+    """Images that are not renders of the scene: the observation itself, renders with noisy
+    patches, images of one constant depth and of misses only. offset 1 shifts the image
+    buffer by one float (no 16-byte vector access). Smooth likelihood (no FP32 inlier-ball
+    decisions), against the oracle's per-pixel terms summed in FP64."""
+    from paper_2312_08715_gb300 import b3d
+    wl = tabletop
+    sc = wl.scene
+    cam = sc.camera
+    obs = observed(orc, wl)
+    rng = np.random.default_rng(22)
+    poses = jitter_poses(rng, wl.hidden, 4, trans=0.02, rot_deg=10)
+    ctx = gpu_context(sc, obs)
+    d, _ = ctx.render(wl.slot, poses)
+    imgs = [obs.astype(np.float32)]
+    for k in range(4):
+        im = _np(d[k]).copy()
+        y, x = rng.integers(0, cam.height - 8), rng.integers(0, cam.width - 8)
+        im[y:y + 8, x:x + 8] += rng.normal(0, 0.01, size=(8, 8)).astype(np.float32)
+        imgs.append(im)
+    imgs.append(np.full((cam.height, cam.width), 0.9, np.float32))
+    imgs.append(np.full((cam.height, cam.width), cam.far, np.float32))
+    imgs = np.stack(imgs)
+    n, H, W = imgs.shape
+    buf = torch.zeros(n * H * W + offset, dtype=torch.float32, device="cuda")
+    view = buf[offset:].view(n, H, W)
+    view.copy_(torch.as_tensor(imgs))
+    lk = dict(kind=1, radius=0.004, p_outlier=0.02, half_window=2)
+    ll = torch.empty(n, dtype=torch.float32, device="cuda")
+    b3d.b3d_score_depth_batch(ctx.h, -1, n, view, None, b3d.lik_params(**lk), ll, ctx.stream)
+    got = _np(ll).astype(np.float64)
+    ctx.sync()
+    ref = _oracle_image_ll(orc, cam, lk, imgs, None, obs)
+    scale = np.array([np.abs(orc.pixel_loglik(cam, lk, im.astype(np.float64), None, obs)[0]).sum() for im in imgs])
+    assert (np.abs(got - ref) <= 1e-4 * scale).all(), (got - ref, scale)
+    ctx.close()
+
+
+@pytest.mark.parametrize("offset", [0, 1])
+def test_render_fill_paths(orc, single_object, offset):
+    """The background fill with 16-byte vector stores (aligned outputs) and with scalar
+    stores (outputs one element off a 16-byte boundary) write identical images, with ids
+    (triangle rasteriser) and depth only (rectangle rasteriser, checked against the
+    oracle)."""
+    from paper_2312_08715_gb300 import b3d
+    wl = single_object
+    sc = wl.scene
+    ctx = gpu_context(sc, observed(orc, wl))
+    poses = torch.as_tensor(jitter_poses(np.random.default_rng(23), wl.hidden, 8), device="cuda")
+    d0, t0 = ctx.render(0, poses)
+    H, W = sc.camera.height, sc.camera.width
+    db = torch.zeros(8 * H * W + offset, dtype=torch.float32, device="cuda")
+    tb = torch.zeros(8 * H * W + offset, dtype=torch.int32, device="cuda")
+    b3d.b3d_render_batch(ctx.h, 0, 8, poses.reshape(8, 16), db[offset:], tb[offset:], ctx.stream)
+    d1, _ = ctx.render(0, poses, want_tid=False)
+    db2 = torch.zeros(8 * H * W + offset, dtype=torch.float32, device="cuda")
+    b3d.b3d_render_batch(ctx.h, 0, 8, poses.reshape(8, 16), db2[offset:], None, ctx.stream)
+    ctx.sync()
+    assert torch.equal(db[offset:].view(8, H, W), d0) and torch.equal(tb[offset:].view(8, H, W), t0)
+    assert torch.equal(db2[offset:].view(8, H, W), d1)
+    _check_depth(orc, sc, 0, _np(poses), _np(d1))
+    ctx.close()
 
 
 def test_tabletop_first_stage_full_size_sampled(orc, tabletop):
