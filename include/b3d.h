@@ -300,8 +300,8 @@ b3d_status b3d_score_grad(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const f
 b3d_status b3d_render_camera_batch(b3d_ctx *ctx, int64_t n_hyp, const float *poses_dev, float *depth_dev,
                                    int32_t *triid_dev, b3d_stream stream);
 
-/* Hierarchical noise (Alg. 1 lines 11-12: p_out ~ U(0,1), sigma ~ U(0, sigma_max), and
- * "score hypotheses under several noise settings"): a grid of n_radius inlier radii (kind 0)
+/* Hierarchical noise (Alg. 1: p_out ~ U(0,1), sigma ~ U(0, sigma_max), hypotheses scored
+ * under several noise settings): a grid of n_radius inlier radii (kind 0)
  * or Gaussian standard deviations (kind 1) times n_pout outlier probabilities. Setting
  * g = i * n_pout + j is (radius[i], p_outlier[j]); log_weight[g] is the log of its prior mass
  * (quadrature weight; all 0 for equal weights). volume, norm, miss_mode as b3d_lik_params. */

@@ -300,7 +300,7 @@ def smc_parse(scene, n_fixed, centres, G, lk: dict, depth_obs, stages, m, seed, 
 
 
 def score_noise(scene, slot, poses, kind, radii, p_outliers, half_window, depth_obs, log_weight=None, n_threads=0):
-    """Hierarchical noise (Alg. 1 lines 11-12): the log-likelihood of each hypothesis under
+    """Hierarchical noise (Alg. 1): the log-likelihood of each hypothesis under
     every setting (radii[i], p_outliers[j]) at g = i * len(p_outliers) + j, and the marginal
     log sum_g exp(ll_g + log_weight_g), the noise integrated out over the grid with the
     settings' prior masses. Returns ll [n, G], marginal [n], and per setting the flags' scale

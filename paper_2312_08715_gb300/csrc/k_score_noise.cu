@@ -1,5 +1,5 @@
 // k_score_noise.cu - scoring under a grid of noise settings (the hierarchical noise of
-// Alg. 1 lines 11-12): each hypothesis is rendered once (render_tiles of the fused kernel)
+// Alg. 1): each hypothesis is rendered once (render_tiles of the fused kernel)
 // and every scored pixel's window is evaluated under all n_radius x n_pout settings, with
 // the per-setting background terms of the fixed objects subtracted as in the single-setting
 // kernel (the same per-pixel routine builds the background tables, so unchanged pixels
