@@ -539,6 +539,16 @@ def test_errors_and_budget(orc, single_object):
         b3d.b3d_score_batch(ctx.h, 0, -1, P, b3d.lik_params(), out)
     assert e.value.status == b3d.B3D_EINVAL
     b3d.b3d_score_batch(ctx.h, 0, 0, P, b3d.lik_params(), out)  # n = 0 is a no-op
+    H, W = sc.camera.height, sc.camera.width
+    img = torch.zeros((1, H, W), device="cuda")
+    for slot, status in ((1, b3d.B3D_ENOTFOUND), (-2, b3d.B3D_ENOTFOUND)):
+        with pytest.raises(b3d.B3DError) as e:
+            b3d.b3d_score_depth_batch(ctx.h, slot, 1, img, None, b3d.lik_params(), out)
+        assert e.value.status == status
+    with pytest.raises(b3d.B3DError) as e:  # miss mode 1 needs the id images
+        b3d.b3d_score_depth_batch(ctx.h, 0, 1, img, None, b3d.lik_params(miss_mode=1), out)
+    assert e.value.status == b3d.B3D_EINVAL
+    b3d.b3d_score_depth_batch(ctx.h, 0, 0, img, None, b3d.lik_params(), out)  # n = 0 is a no-op
     ctx.sync()
     small = b3d.Context(0, hbm_budget_bytes=64 * 1024)
     with pytest.raises(b3d.B3DError) as e:
