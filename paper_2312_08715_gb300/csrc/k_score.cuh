@@ -195,14 +195,14 @@ constexpr int kCandX = B3D_CAND_X, kCandY = B3D_CAND_Y;
 
 // A rectangle edge a->b staged for the pixel tests: its canonical origin (the
 // lexicographically smaller endpoint, as edge_fn) and direction, with the quad's
-// orientation sign and the canonical swap folded into the direction. Sign flips commute
-// with round-to-nearest, so fmaf(E.z, py - E.y, -(E.w * (px - E.x))) equals
-// s * edge_fn(a, b, p) bit for bit (up to the sign of a zero), and the test is e >= 0.
+// orientation sign folded into the direction. Relative to the canonical direction
+// (from the smaller endpoint to the larger) the swap and the sign cancel:
+// (sw ? -s : s) * (sw ? a - b : b - a) = s * (b - a) exactly, since negation is exact in
+// round-to-nearest. So fmaf(E.z, py - E.y, -(E.w * (px - E.x))) equals s * edge_fn(a, b, p)
+// bit for bit (up to the sign of a zero), and the test is e >= 0.
 __device__ __forceinline__ float4 stage_edge(float ax, float ay, float bx, float by, float s) {
     const bool sw = (bx < ax) || (bx == ax && by < ay);
-    const float x0 = sw ? bx : ax, y0 = sw ? by : ay, x1 = sw ? ax : bx, y1 = sw ? ay : by;
-    const float sg = sw ? -s : s;
-    return make_float4(x0, y0, sg * (x1 - x0), sg * (y1 - y0));
+    return make_float4(sw ? bx : ax, sw ? by : ay, s * (bx - ax), s * (by - ay));
 }
 
 __device__ __forceinline__ bool staged_inside(const float4 &E, float px, float py) {
@@ -416,9 +416,11 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                                     rec[3] = stage_edge(C3.x, C3.y, C0.x, C0.y, sgn);
                                     // 1/z = al px + be py + K over the quad's plane
                                     const float K = fmaf(-al, C0.x, fmaf(-be, C0.y, C0.z));
-                                    // the candidate's row is floor((k + 1/2) / pairs per row), exact in
-                                    // float for the region's sizes (margin 1/(2 width) >> rounding)
-                                    rec[4] = make_float4(al, be, K, 1.0f / (float)bw2);
+                                    // the candidate's row is floor((k + 1/2) / candidates per row), exact
+                                    // in float with an approximate reciprocal for the region's sizes (the
+                                    // quotient is at least 1/(2 bw2) from an integer; the error is below
+                                    // (k + 1/2) 2^-21 / bw2)
+                                    rec[4] = make_float4(al, be, K, __fdividef(1.0f, (float)bw2));
                                     rec[5] = make_float4(__int_as_float(x0), __int_as_float(y0), __int_as_float(bw2),
                                                          __int_as_float((x1 - x0) | ((y1 - y0) << 16)));
                                 }
