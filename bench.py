@@ -54,7 +54,7 @@ UNIT_NAMES = ["hypotheses", "corners", "primitives", "pixel_tests", "fragments",
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b3d", choices=["b3d", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU work of the oracle baseline sample")
@@ -445,7 +445,9 @@ def run_reference(args):
     t0 = time.perf_counter()
     O.score(sub, FIRST_SLOT, probe, wl.lik, obs, flags=False, arrays=arrays)
     per = (time.perf_counter() - t0) / len(probe)
-    n_step = int(max(2 * cores, min(len(poses), 8.0 / max(per, 1e-6))))
+    # about 30 s of CPU work for the whole run, at least 1.5 s per step
+    step_s = max(1.5, 30.0 / (args.warmup + args.steps))
+    n_step = int(max(2 * cores, min(len(poses), step_s / max(per, 1e-6))))
     times = []
     for s in range(args.warmup + args.steps):
         sample = poses[rng.choice(len(poses), n_step, replace=False)]

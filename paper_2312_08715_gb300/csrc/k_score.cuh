@@ -466,7 +466,8 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
 #pragma unroll
                                     for (int d = 0; d < kCandX; ++d) {
                                         const float px = (float)(x + d) + 0.5f;
-                                        if (x + d <= xe && y + e <= ye && staged_inside(E0, px, py) &&
+                                        // rows of single-row candidates never pass the box (row < rows)
+                                        if (x + d <= xe && (kCandY == 1 || y + e <= ye) && staged_inside(E0, px, py) &&
                                             staged_inside(E1, px, py) && staged_inside(E2, px, py) &&
                                             staged_inside(E3, px, py)) {
                                             const float z = __fdividef(1.0f, fmaf(Pl.x, px, fmaf(Pl.y, py, Pl.z)));
