@@ -192,6 +192,7 @@ void launch_bg_tables(const SceneView &sv, const Lik &L, float *ell_bg, float *g
                       unsigned *counter, double *sums, cudaStream_t s);
 int launch_score_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, int grid, cudaStream_t s);
 int launch_score_grid(const SceneView &sv, const Lik &L, PoseGrid P, int64_t n, float *ll, int grid, cudaStream_t s);
+// ---- launchers (k_materialised.cu) -------------------------------------------------------
 // Materialised render; returns the number of kernel launches.
 int launch_render_list(const SceneView &sv, PoseList P, int64_t n, float *depth, int *tid, int grid, cudaStream_t s);
 // Materialised images (sv: the scene's full background and its terms); returns the number of

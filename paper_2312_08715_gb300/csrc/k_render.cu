@@ -1,13 +1,12 @@
-// k_render.cu - rasterisation and windowed-likelihood kernels of libb3d.
+// k_render.cu - scene set-up kernels of libb3d and the camera-hypothesis renderer, plus the
+// launch dispatch of the fused score kernel (whose shapes live in k_score_*.cu).
 //
-// The render kernel draws one pose hypothesis per CTA iteration into a shared-memory
-// z-buffer of packed (depth bits << 32 | triangle id) keys (64-bit atomicMin: the nearest
-// fragment wins, equal depths go to the smaller id) and composites it with the fixed
-// objects' background keys. The score kernel does the same with depth bits alone, then
-// scores every observed pixel whose (2w+1)^2 window can see the object (the windowed Eq. 1
-// likelihood of Sec. III-B). Pixels whose window cannot see the object keep their
-// background term, precomputed once per scene, so a hypothesis costs work in proportion to
-// its screen footprint:
+// Set-up, once per scene (or per fixed object): the observed point cloud; the background
+// z-buffer of the fixed objects, packed (depth bits << 32 | triangle id) keys built with
+// 64-bit atomicMin (the nearest fragment wins, equal depths go to the smaller id); the
+// per-pixel background terms l_i(bg) of the windowed Eq. 1 likelihood (Sec. III-B) and
+// their FP64 sum, which let the score kernels work in proportion to a hypothesis's screen
+// footprint:
 //   LL_h = sum_i l_i(h) = LL_bg + sum_{i in footprint + w} (l_i(h) - l_i(bg)),
 // an exact identity (the terms outside the dilated footprint are equal, bit for bit, since
 // they are computed by the same device function from the same inputs).
