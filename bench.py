@@ -798,13 +798,18 @@ def run_serving(args):
                     hbm_reserved_gb=stats["hbm_reserved"] / 1e9, failed=stats["frames_failed"],
                     clocks=clk.summary()), poses
 
-    sat, poses_sat = serve(0, 0)
+    # Each camera keeps one frame in flight (it submits frame f + 1 when frame f's result is
+    # back): at saturation a frame's latency is the frames ahead of it over the throughput
+    # (Little's law). Two in flight per camera gives the same throughput at twice the latency;
+    # cameras paced at 30 fps (faster than the server) likewise queue two frames each.
+    one, poses_one = serve(0, 0, depth=1)
+    sat, _ = serve(0, 0)
     paced, _ = serve(30.0, 0)
-    solo, poses_solo = serve(0, 1)
-    same = all(np.array_equal(poses_sat[k], poses_solo[k]) for k in poses_sat)
+    solo, poses_solo = serve(0, 1, depth=1)
+    same = all(np.array_equal(poses_one[k], poses_solo[k]) for k in poses_one)
     print(json.dumps({
-        "metric": METRIC, "value": sat["hyp_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.frames - W,
-        "warmup": W, "ms_per_step": 1e3 * sat["wall_s"] / (args.frames - W), "higher_is_better": True,
+        "metric": METRIC, "value": one["hyp_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.frames - W,
+        "warmup": W, "ms_per_step": 1e3 * one["wall_s"] / (args.frames - W), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "workload_kind": "serving",
         "config": {"workload": f"serving: {len(streams)} tracking sessions, 320x240 depth at 30 fps, 1-6 voxel "
                                "objects (2k-8k voxels, 5 mm) + table, per frame and object 5^3 x 50 = 6,250 "
@@ -812,13 +817,14 @@ def run_serving(args):
                    "sessions": len(streams), "tracked_objects": n_items, "hyps_per_object_frame": hyp_item,
                    "frames_per_session": args.frames - W, "score_kernel_tuning": tuning,
                    "batch_linger_us": args.linger_us,
-                   "step": "one frame of every session (value: saturated aggregate throughput)"},
-        "latency_ms": {"p50": sat["p50_ms"], "p99": sat["p99_ms"]},
-        "saturated": sat, "paced_30fps": paced,
+                   "step": "one frame of every session (value: aggregate throughput with one frame in flight "
+                           "per camera)"},
+        "latency_ms": {"p50": one["p50_ms"], "p99": one["p99_ms"], "frames_in_flight_per_session": 1},
+        "one_frame_in_flight": one, "two_frames_in_flight": sat, "paced_30fps": paced,
         "no_cross_session_batching": solo,
-        "speedup_vs_unbatched": sat["hyp_per_s"] / solo["hyp_per_s"],
+        "speedup_vs_unbatched": one["hyp_per_s"] / solo["hyp_per_s"],
         "outputs_equal_to_unbatched": bool(same),
-        "clocks": sat["clocks"],
+        "clocks": one["clocks"],
     }), flush=True)
 
 

@@ -109,8 +109,11 @@ def test_render_large_footprint_and_ragged_image(orc):
         _check_render(orc, sc, 0, poses, _np(d), _np(t), max_frac=5e-4)
         lik = dict(kind=0, radius=0.005, p_outlier=0.01, half_window=2)
         ll = _np(ctx.score(0, poses, lik))
+        ll2 = _np(ctx.score_depth(d, lik, t, slot=0))  # 37 x 29: no 16-byte vector access
         ctx.sync()
-        _check_ll(ll, orc.score(sc, 0, poses, lik, obs), "large footprint")
+        ref = orc.score(sc, 0, poses, lik, obs)
+        _check_ll(ll, ref, "large footprint")
+        _check_ll(ll2, ref, "large footprint, materialised")
 
 
 @pytest.mark.parametrize("nt,hi", [(64, 0), (128, 1), (256, 0)])
@@ -291,9 +294,10 @@ def _oracle_image_ll(orc, cam, lk, depth, tid, obs):
 @pytest.mark.parametrize("offset", [0, 1])
 def test_score_depth_of_arbitrary_images(orc, tabletop, offset):
     """Images that are not renders of the scene: the observation itself, renders with noisy
-    patches, images of one constant depth and of misses only. offset 1 shifts the image
-    buffer by one float (no 16-byte vector access). Smooth likelihood (no FP32 inlier-ball
-    decisions), against the oracle's per-pixel terms summed in FP64."""
+    patches, images of one constant depth and of misses only, then the same with random id
+    images in miss mode 1. offset 1 shifts the buffers by one element (no 16-byte vector
+    access). Smooth likelihood (no FP32 inlier-ball decisions), against the oracle's
+    per-pixel terms summed in FP64."""
     from paper_2312_08715_gb300 import b3d
     wl = tabletop
     sc = wl.scene
@@ -324,6 +328,19 @@ def test_score_depth_of_arbitrary_images(orc, tabletop, offset):
     ref = _oracle_image_ll(orc, cam, lk, imgs, None, obs)
     scale = np.array([np.abs(orc.pixel_loglik(cam, lk, im.astype(np.float64), None, obs)[0]).sum() for im in imgs])
     assert (np.abs(got - ref) <= 1e-4 * scale).all(), (got - ref, scale)
+    # miss mode 1: ids mark a random third of the pixels as carrying no point
+    ids = np.where(rng.random((n, H, W)) < 1 / 3, -1, 0).astype(np.int32)
+    tbuf = torch.zeros(n * H * W + offset, dtype=torch.int32, device="cuda")
+    tview = tbuf[offset:].view(n, H, W)
+    tview.copy_(torch.as_tensor(ids))
+    lk1 = dict(lk, miss_mode=1)
+    b3d.b3d_score_depth_batch(ctx.h, wl.slot, n, view, tview, b3d.lik_params(**lk1), ll, ctx.stream)
+    got1 = _np(ll).astype(np.float64)
+    ctx.sync()
+    ref1 = _oracle_image_ll(orc, cam, lk1, imgs, ids, obs)
+    scale1 = np.array([np.abs(orc.pixel_loglik(cam, lk1, im.astype(np.float64), i, obs)[0]).sum()
+                       for im, i in zip(imgs, ids)])
+    assert (np.abs(got1 - ref1) <= 1e-4 * scale1).all(), (got1 - ref1, scale1)
     ctx.close()
 
 
