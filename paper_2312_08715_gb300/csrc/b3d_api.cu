@@ -878,7 +878,7 @@ b3d_status b3d_load_mesh(b3d_ctx *ctx, const float *verts, int64_t n_v, const in
 
     // 5. voxel rectangles: a closed mesh whose surface triangles pair up into unit squares of
     //    the vertex lattice (distinct coordinates per axis), each square axis-aligned; the
-    //    squares of each plane are merged into rectangles of at most 3 x 3 squares
+    //    squares of each plane are merged into rectangles of at most 4 x 4 squares
     std::vector<uint2> h_quads;
     std::vector<int> h_off;
     std::vector<float> h_coords;
@@ -953,7 +953,7 @@ b3d_status b3d_load_mesh(b3d_ctx *ctx, const float *verts, int64_t n_v, const in
                 // side, so the union renders exactly as the squares do) of at most
                 // kMaxRectExtent squares a side: a long strip seen at an angle has a screen box
                 // many times its area, and the rasteriser tests every pixel of the box
-                constexpr int kMaxRectExtent = 3;
+                constexpr int kMaxRectExtent = 4;
                 std::vector<uint2> rects;
                 for (auto &pl : planes) {
                     const int cls = pl.first.first, p = pl.first.second;
