@@ -326,6 +326,9 @@ template <class PS>
 static int launch_score(const SceneView &sv, const Lik &L, PS P, int64_t n, float *ll, int grid, cudaStream_t s) {
     if (n <= 0) return 0;
     const int c = grid & 255;
+    // work counting is compiled into one launch shape only (kStatsNT x kStatsMinB = 128 x 6,
+    // checked where that shape is instantiated): use it whenever work is counted
+    if (sv.stats) return launch_score_nt<PS, 128, 6>(sv, L, P, n, ll, c, s);
     switch ((grid >> 8) & 15) {
     case 1: return launch_score_nt<PS, 128, 6>(sv, L, P, n, ll, c, s);
     case 2: return launch_score_nt<PS, 64, 10>(sv, L, P, n, ll, c, s);

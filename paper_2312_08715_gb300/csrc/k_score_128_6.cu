@@ -3,6 +3,8 @@
 #include "k_score.cuh"
 
 namespace b3d {
+// the dispatcher sends work-counting launches to this shape
+static_assert(kStatsNT == 128 && kStatsMinB == 6, "work counting is compiled for 128 x 6 only");
 template int launch_score_nt<PoseList, 128, 6>(const SceneView &, const Lik &, PoseList, int64_t, float *, int,
                                                   cudaStream_t);
 template int launch_score_nt<PoseGrid, 128, 6>(const SceneView &, const Lik &, PoseGrid, int64_t, float *, int,
