@@ -209,6 +209,31 @@ def test_every_launch_shape_matches_oracle(orc, single_object):
     ctx.close()
 
 
+def test_work_counters_do_not_depend_on_the_tuned_shape(orc, single_object):
+    """Work counting is compiled into one launch shape; a counting launch uses it whatever
+    shape is tuned, so the counts (and the roofline built on them) never come out empty."""
+    from paper_2312_08715_gb300 import b3d
+    wl = single_object
+    sc = wl.scene
+    obs = observed(orc, wl)
+    poses = orc.expand(wl.hidden, np.eye(3), 5, 0.01, orc.rotation_set(1, 3, 0.1)).astype(np.float32)
+    ctx = gpu_context(sc, obs)
+    counts = []
+    for nt, hi in [(128, 0), (128, 1), (256, 0), (32, 1)]:
+        b3d.b3d_set_tuning(ctx.h, 64, nt, 0, hi)
+        b3d.b3d_set_instrumentation(ctx.h, b3d.B3D_INSTR_WORK)
+        b3d.b3d_work_counters(ctx.h)  # reads and clears
+        ll = _np(ctx.score(0, poses, wl.lik))
+        ctx.sync()
+        counts.append(np.asarray(b3d.b3d_work_counters(ctx.h)))
+        b3d.b3d_set_instrumentation(ctx.h, 0)
+        _check_ll(ll, orc.score(sc, 0, poses, wl.lik, obs), f"counting with {nt}/{hi} tuned")
+    assert counts[0][0] == len(poses) and (counts[0] > 0).all(), counts[0]
+    for c in counts[1:]:
+        assert np.array_equal(c, counts[0]), (c, counts[0])
+    ctx.close()
+
+
 @pytest.mark.parametrize("w,miss_mode", [(2, 0), (1, 1)])
 def test_score_smooth_and_miss_modes(orc, single_object, w, miss_mode):
     wl = single_object
