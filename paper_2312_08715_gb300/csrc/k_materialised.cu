@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(kThreads) k_render_obj(SceneView S, PS P, int6
                     y += dq;
                     if (x >= zw) { x -= zw; ++y; }
                 }
+                __syncthreads();  // the next tile clears the z-buffer this one was read from
             }
         }
     }
