@@ -292,6 +292,19 @@ b3d_status b3d_score_grad(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const f
                           const b3d_lik_params *lik, float *loglik_dev, float *dpose_dev, float *dsigma_dev,
                           float *dpout_dev, b3d_stream stream);
 
+/* Gradient pose refinement under the smooth (kind 1) likelihood, every step on the device:
+ * n_steps Adam steps (learning rate lr, moments beta1, beta2, epsilon eps, as torch.optim.Adam
+ * without weight decay) ascending loglik in the left se(3) perturbation of b3d_score_grad,
+ * each step re-basing the pose (T <- Exp([v, w]^) T, so the perturbation restarts at 0 and
+ * its gradient stays exact): one forward + backward launch and one update launch per step.
+ * poses_dev [n, 16] (row-major 4x4) is updated in place; loglik_dev [n] (may be NULL)
+ * receives the log-likelihood at the poses the last step scored (before its update). The
+ * Adam moments live in context scratch and start at 0 on every call. n_steps >= 1,
+ * lr > 0, 0 <= beta1, beta2 < 1, eps > 0. */
+b3d_status b3d_refine_smooth(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, float *poses_dev,
+                             const b3d_lik_params *lik, int32_t n_steps, float lr, float beta1, float beta2, float eps,
+                             float *loglik_dev, b3d_stream stream);
+
 /* Camera hypotheses (the camera-pose tracking of Sec. IV, Table 1): render n_hyp hypothesised
  * camera poses poses_dev [n_hyp, 16] (row-major camera_from_world) of the scene, every object
  * k at H_h P_k where P_k is its scene pose read as world_from_object. Writes depth_dev

@@ -134,6 +134,8 @@ _SIGNATURES = {
     "b3d_score_multi": (C.c_int32, [_P, C.c_int32, C.POINTER(b3d_score_item), C.POINTER(b3d_lik_params), _P]),
     "b3d_enumerate_multi": (C.c_int32, [_P, C.c_int32, C.POINTER(b3d_c2f_item), C.POINTER(b3d_lik_params), _P]),
     "b3d_score_grad": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_lik_params), _P, _P, _P, _P, _P]),
+    "b3d_refine_smooth": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_lik_params), C.c_int32, C.c_float,
+                                      C.c_float, C.c_float, C.c_float, _P, _P]),
     "b3d_lse_resample_noalloc": (C.c_int32, [C.c_int64, _P, C.c_int32, C.c_uint64, C.c_int32, _P, _P, _P, _P]),
     "b3d_get_tuning": (C.c_int32, [_P, C.POINTER(b3d_tuning)]),
     "b3d_set_tuning": (C.c_int32, [_P, C.POINTER(b3d_tuning)]),
@@ -370,6 +372,12 @@ def b3d_score_grad(ctx, obj_slot, n_hyp, poses_dev, lik: b3d_lik_params, loglik_
     return _check(ctx, load().b3d_score_grad(ctx, obj_slot, n_hyp, _addr(poses_dev), C.byref(lik), _addr(loglik_dev),
                                              _addr(dpose_dev), _addr(dsigma_dev), _addr(dpout_dev),
                                              _stream(stream)))
+
+
+def b3d_refine_smooth(ctx, obj_slot, n_hyp, poses_dev, lik: b3d_lik_params, n_steps, lr, beta1=0.9, beta2=0.999,
+                      eps=1e-8, loglik_dev=None, stream=None):
+    return _check(ctx, load().b3d_refine_smooth(ctx, obj_slot, n_hyp, _addr(poses_dev), C.byref(lik), n_steps, lr,
+                                                beta1, beta2, eps, _addr(loglik_dev), _stream(stream)))
 
 
 def b3d_get_tuning(ctx) -> dict:
@@ -774,6 +782,16 @@ class Context:
         dp = t.empty(n, dtype=t.float32, device=self.device)
         b3d_score_grad(self.h, slot, n, P, lik_params(**lik), ll, dpose, ds, dp, self.stream)
         return ll, dpose, ds, dp
+
+    def refine(self, slot, poses, lik: dict, n_steps, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        """Adam refinement of poses [n, 4, 4] under the smooth likelihood, all on the device;
+        returns the refined poses (a new tensor) and the log-likelihood the last step scored."""
+        t = self.torch
+        P = self._dev(poses, t.float32).reshape(-1, 16).clone()
+        ll = t.empty(P.shape[0], dtype=t.float32, device=self.device)
+        b3d_refine_smooth(self.h, slot, P.shape[0], P, lik_params(**lik), n_steps, lr, beta1, beta2, eps, ll,
+                          self.stream)
+        return P.reshape(-1, 4, 4), ll
 
     def set_object_pose_dev(self, obj, pose_dev):
         b3d_set_object_pose_dev(self.h, obj, pose_dev, self.stream)

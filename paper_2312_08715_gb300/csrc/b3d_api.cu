@@ -104,6 +104,8 @@ struct b3d_ctx {
     // coarse-to-fine and resampling scratch
     float *d_ll = nullptr;
     int64_t ll_cap = 0;
+    float *d_refine = nullptr;  // [n][6 + 6 + 6 + 1]: Adam moments m, v, gradients, scores
+    int64_t refine_cap = 0;
     float2 *d_part = nullptr;
     unsigned *d_counter = nullptr;
     float *d_logz = nullptr;
@@ -1688,6 +1690,52 @@ b3d_status b3d_score_grad(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const f
     }
     ++ctx->launches;
     return check_launch(ctx, "score_grad");
+}
+
+b3d_status b3d_refine_smooth(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, float *poses_dev,
+                             const b3d_lik_params *lik, int32_t n_steps, float lr, float beta1, float beta2, float eps,
+                             float *loglik_dev, b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    b3d_status st = check_slot(ctx, obj_slot);
+    if (st != B3D_OK) return st;
+    Lik L;
+    if ((st = make_lik(ctx, lik, &L)) != B3D_OK) return st;
+    if (lik->kind != 1) return fail(ctx, B3D_EINVAL, "refine_smooth needs the smooth likelihood (kind 1)");
+    if (n_hyp < 0) return fail(ctx, B3D_EINVAL, "n_hyp must be >= 0");
+    if (n_steps < 1) return fail(ctx, B3D_EINVAL, "n_steps must be >= 1");
+    if (!(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f) ||
+        !std::isfinite(lr) || !std::isfinite(eps))
+        return fail(ctx, B3D_EINVAL, "need lr > 0, 0 <= beta1, beta2 < 1, eps > 0 (finite)");
+    if (n_hyp == 0) return B3D_OK;
+    if (!poses_dev) return fail(ctx, B3D_EINVAL, "poses_dev must be non-NULL");
+    if (!aligned16(poses_dev)) return fail(ctx, B3D_EINVAL, "poses_dev must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_hyp > ctx->refine_cap) {
+        dfree(ctx, ctx->d_refine);
+        ctx->refine_cap = 0;
+        if ((st = dalloc(ctx, &ctx->d_refine, (size_t)19 * n_hyp, "refinement state")) != B3D_OK) return st;
+        ctx->refine_cap = n_hyp;
+    }
+    float *m = ctx->d_refine, *v = m + 6 * n_hyp, *dpose = v + 6 * n_hyp, *ll = dpose + 6 * n_hyp;
+    cudaMemsetAsync(m, 0, sizeof(float) * 12 * (size_t)n_hyp, s);
+    if ((st = ensure_bg(ctx, obj_slot, s)) != B3D_OK) return st;
+    if ((st = ensure_bg_lik(ctx, obj_slot, lik, L, true, s)) != B3D_OK) return st;
+    const SceneView sv = scene_view(ctx, obj_slot);
+    double p1 = 1.0, p2 = 1.0;
+    for (int t = 1; t <= n_steps; ++t) {
+        {
+            Timed tm(ctx, B3D_K_GRAD, s);
+            launch_grad_list(sv, L, PoseList{poses_dev}, n_hyp, t == n_steps && loglik_dev ? loglik_dev : ll, dpose,
+                             nullptr, nullptr, 0, s);
+        }
+        p1 *= beta1;
+        p2 *= beta2;
+        launch_adam_se3(n_hyp, dpose, m, v, poses_dev, lr, beta1, beta2, eps, (float)(1.0 - p1), (float)(1.0 - p2), s);
+        ctx->launches += 2;
+    }
+    return check_launch(ctx, "refine_smooth");
 }
 
 b3d_status b3d_get_tuning(b3d_ctx *ctx, b3d_tuning *out) {

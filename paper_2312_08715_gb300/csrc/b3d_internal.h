@@ -199,6 +199,10 @@ int launch_render_list(const SceneView &sv, PoseList P, int64_t n, float *depth,
 // kernel launches.
 int launch_score_depth(const SceneView &sv, const Lik &L, const float *depth, const int *tid, int64_t n, float *ll,
                        int grid, cudaStream_t s);
+// Adam step + se(3) re-basing of n poses [n, 16] from their loglik gradients dpose [n, 6]
+// (k_grad.cu); m, v [n, 6] moments; bc1, bc2 the bias corrections of this step.
+void launch_adam_se3(int64_t n, const float *dpose, float *m, float *v, float *poses, float lr, float b1, float b2,
+                     float eps, float bc1, float bc2, cudaStream_t s);
 int launch_grad_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, float *dpose,
                      float *dsigma, float *dpout, int grid, cudaStream_t s);
 

@@ -114,3 +114,44 @@ def test_adam_refinement_raises_the_likelihood(scene):
     err1 = np.linalg.norm(_np(T)[:, :3, 3] - wl.hidden[:3, 3], axis=1)
     assert np.median(err1) < np.median(err0)
     ctx.close()
+
+
+def test_library_refinement_step_matches_torch_adam(scene):
+    """One step of b3d_refine_smooth (forward + backward kernel, then the fused Adam and se(3)
+    re-basing kernel) against the same step through autograd and torch.optim.Adam."""
+    from paper_2312_08715_gb300 import b3d
+    wl, obs = scene
+    ctx = gpu_context(wl.scene, obs)
+    T0 = torch.as_tensor(jitter_poses(np.random.default_rng(7), wl.hidden, 64, trans=0.006, rot_deg=4), device="cuda")
+    lr = 5e-4
+    F = b3d.make_score_smooth()
+    xi = torch.zeros((64, 6), device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([xi], lr=lr)
+    ll = F.apply(xi, LIK["radius"], LIK["p_outlier"], ctx, wl.slot, T0, LIK["half_window"])
+    (-ll.sum()).backward()
+    opt.step()
+    with torch.no_grad():
+        T_ref = b3d._se3_exp(xi) @ T0
+    T_lib, ll_lib = ctx.refine(wl.slot, T0, LIK, 1, lr)
+    ctx.sync()
+    assert torch.equal(ll_lib, ll.detach())  # the scores of the poses the step started from
+    assert (T_lib - T_ref).abs().max().item() < 2e-6
+    ctx.close()
+
+
+def test_library_refinement_raises_the_likelihood(scene):
+    wl, obs = scene
+    ctx = gpu_context(wl.scene, obs)
+    T = torch.as_tensor(jitter_poses(np.random.default_rng(6), wl.hidden, 64, trans=0.006, rot_deg=4), device="cuda")
+    ll0 = ctx.score(wl.slot, T, LIK)
+    T1, _ = ctx.refine(wl.slot, T, LIK, 30, 5e-4)
+    ll1 = ctx.score(wl.slot, T1, LIK)
+    ctx.sync()
+    assert float((ll1 - ll0).mean()) > 0
+    assert float((ll1 > ll0).float().mean()) > 0.8
+    err0 = np.linalg.norm(_np(T)[:, :3, 3] - wl.hidden[:3, 3], axis=1)
+    err1 = np.linalg.norm(_np(T1)[:, :3, 3] - wl.hidden[:3, 3], axis=1)
+    assert np.median(err1) < np.median(err0)
+    R = _np(T1)[:, :3, :3]
+    assert np.abs(R @ R.transpose(0, 2, 1) - np.eye(3)).max() < 1e-4  # re-basing keeps rotations orthonormal
+    ctx.close()
