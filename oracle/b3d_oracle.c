@@ -76,7 +76,7 @@ static void pixel_ray(const orc_camera *cam, int u, int v, double r[3]) {
     r[2] = 1.0;
 }
 
-/* V of Eq. 1, "the volume of the visible scene". Reading: the camera frustum between the
+/* V of Eq. 1, the volume of the scene the camera sees. Reading: the camera frustum between the
  * near and far planes. A slice at depth z spans (W z / fx) x (H z / fy), so
  * V = (W H / (fx fy)) * (far^3 - near^3) / 3. */
 double orc_frustum_volume(const orc_camera *cam) {
