@@ -84,6 +84,9 @@ struct b3d_ctx {
     bool has_scene = false;
     Cam cam{};
     std::vector<int32_t> obj_mesh;
+    // per-object z-buffers for shared slot backgrounds (see ctx_prepare_shared_bg)
+    std::vector<unsigned long long *> objz;
+    std::vector<char> objz_ok;
     std::vector<int64_t> tri_base;
     float *d_poses = nullptr;
     int pose_cap = 0;
@@ -327,10 +330,13 @@ BgCache &bg_cache(b3d_ctx *ctx, int32_t slot) {
     return ctx->bgc[k];
 }
 
-// Mark the background of every slot whose z-buffer holds object `obj` (-1: all slots).
+// Mark the background of every slot whose z-buffer holds object `obj` (-1: all slots), and
+// the object's own z-buffer of the shared backgrounds.
 void bg_invalidate(b3d_ctx *ctx, int32_t obj) {
     for (size_t k = 0; k < ctx->bgc.size(); ++k)
         if (obj < 0 || (int32_t)k != obj + 1) ctx->bgc[k].dirty = true;
+    for (size_t o = 0; o < ctx->objz_ok.size(); ++o)
+        if (obj < 0 || (int32_t)o == obj) ctx->objz_ok[o] = 0;
 }
 
 void bg_invalidate_lik(b3d_ctx *ctx) {
@@ -1069,6 +1075,9 @@ b3d_status b3d_set_scene(b3d_ctx *ctx, const b3d_intrinsics *intr, int32_t n_obj
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t npx = (int64_t)intr->width * intr->height;
     b3d_status st;
+    for (unsigned long long *z : ctx->objz) dfree(ctx, z);  // shared backgrounds follow the new scene
+    ctx->objz.clear();
+    ctx->objz_ok.clear();
     if (npx > ctx->px_cap) {
         dfree(ctx, ctx->d_obs);
         ctx->px_cap = 0;
@@ -1933,7 +1942,73 @@ float *ctx_scene_poses(b3d_ctx *ctx) { return ctx->d_poses; }
 
 int *ctx_err_flag(b3d_ctx *ctx) { return ctx->d_err; }
 
-void ctx_poses_changed(b3d_ctx *ctx) { bg_invalidate(ctx, -1); }
+b3d_status ctx_prepare_shared_bg(b3d_ctx *ctx, cudaStream_t s) {
+    if (!ctx->has_scene) return fail(ctx, B3D_EINVAL, "no scene");
+    const size_t n_obj = ctx->obj_mesh.size();
+    if (n_obj - 1 > (size_t)kMaxBgSources) return B3D_OK;  // too many objects: per-slot rendering
+    const int64_t npx = (int64_t)ctx->cam.W * ctx->cam.H;
+    DeviceGuard g(ctx->device);
+    for (unsigned long long *z : ctx->objz) dfree(ctx, z);
+    ctx->objz.assign(n_obj, nullptr);
+    ctx->objz_ok.assign(n_obj, 0);
+    for (size_t o = 0; o < n_obj; ++o) {
+        b3d_status st = dalloc(ctx, &ctx->objz[o], (size_t)npx, "object z-buffer");
+        if (st != B3D_OK) {
+            for (unsigned long long *z : ctx->objz) dfree(ctx, z);
+            ctx->objz.clear();
+            ctx->objz_ok.clear();
+            return st;
+        }
+    }
+    (void)s;
+    return B3D_OK;
+}
+
+void ctx_tracked_moved(b3d_ctx *ctx, int32_t n_slots) {
+    if (ctx->objz.empty()) {
+        bg_invalidate(ctx, -1);
+        return;
+    }
+    for (int32_t o = 0; o < n_slots && o < (int32_t)ctx->obj_mesh.size(); ++o) bg_invalidate(ctx, o);
+}
+
+b3d_status ctx_build_slot_bgs(b3d_ctx *ctx, int32_t n_slots, cudaStream_t s) {
+    if (ctx->objz.empty()) return B3D_OK;  // not prepared: ensure_bg renders each slot's background
+    const int32_t n_obj = (int32_t)ctx->obj_mesh.size();
+    const int64_t npx = (int64_t)ctx->cam.W * ctx->cam.H;
+    bool any = false;
+    for (int32_t k = 0; k < n_slots && k < n_obj; ++k) {
+        const size_t i = (size_t)k + 1;
+        if (i < ctx->bgc.size() && ctx->bgc[i].dirty && ctx->bgc[i].cap >= npx) any = true;
+    }
+    if (!any) return B3D_OK;
+    DeviceGuard g(ctx->device);
+    Timed tm(ctx, B3D_K_SCENE, s);
+    for (int32_t o = 0; o < n_obj; ++o) {
+        if (ctx->objz_ok[o]) continue;
+        const MeshRec &m = ctx->meshes[ctx->obj_mesh[o]];
+        launch_bg_clear(ctx->objz[o], npx, s);
+        ++ctx->launches;
+        if (m.n_full > 0) {
+            launch_bg_raster(ctx->cam, view_of(m), ctx->d_poses + 16 * o, (int)ctx->tri_base[o], ctx->objz[o], s);
+            ++ctx->launches;
+        }
+        ctx->objz_ok[o] = 1;
+    }
+    const unsigned long long *src[kMaxBgSources];
+    for (int32_t k = 0; k < n_slots && k < n_obj; ++k) {
+        BgCache &c = bg_cache(ctx, k);
+        if (!c.dirty || c.cap < npx) continue;
+        int n_src = 0;
+        for (int32_t o = 0; o < n_obj; ++o)
+            if (o != k && ctx->meshes[ctx->obj_mesh[o]].n_full > 0) src[n_src++] = ctx->objz[o];
+        launch_bg_min(npx, src, n_src, c.bg, s);
+        ++ctx->launches;
+        c.dirty = false;
+        c.lik_valid = c.grad_valid = c.nvalid = c.bgd_valid = false;
+    }
+    return check_launch(ctx, "shared backgrounds");
+}
 
 b3d_status ctx_prepare_slot(b3d_ctx *ctx, int32_t slot, const b3d_lik_params *lik, const b3d_c2f_schedule *sch,
                             cudaStream_t s) {

@@ -181,6 +181,9 @@ inline int kernel_ctas_per_sm(K kernel, int threads, int smem) {
 // ---- launchers (k_render.cu) -------------------------------------------------------------
 void launch_obs_points(const Cam &cam, const float *depth, float4 *obs, cudaStream_t s);
 void launch_bg_clear(unsigned long long *bg, int64_t n, cudaStream_t s);
+// dst[i] = min over the n_src buffers src[k][i] (n_src <= kMaxBgSources), kEmptyKey if none
+constexpr int kMaxBgSources = 16;
+void launch_bg_min(int64_t n, const unsigned long long *const *src, int n_src, unsigned long long *dst, cudaStream_t s);
 // bgd[m * W H + i] = depth of background key i under miss mode m (0: far plane, 1: -1)
 void launch_bg_depth(int64_t n, float far_z, const unsigned long long *bg, float *bgd, cudaStream_t s);
 void launch_bg_raster(const Cam &cam, const MeshView &m, const float *pose16_dev, int tri_base,
@@ -246,7 +249,14 @@ void ctx_set_budget(b3d_ctx *ctx, uint64_t budget);
 b3d_status ctx_alloc_bytes(b3d_ctx *ctx, size_t bytes, void **out, const char *what);
 float *ctx_scene_poses(b3d_ctx *ctx);  // device [n_obj, 16]
 int *ctx_err_flag(b3d_ctx *ctx);       // device [1]
-void ctx_poses_changed(b3d_ctx *ctx);  // after writing ctx_scene_poses on the device
+// Shared backgrounds of a context whose first n_slots objects are hypothesised in turn (a
+// tracking session): one z-buffer per object (allocated by ctx_prepare_shared_bg, rendered
+// when its pose changed), each slot's background the per-pixel minimum over the other
+// objects' buffers (the same keys as rasterising them into one buffer). ctx_tracked_moved:
+// the poses of objects [0, n_slots) changed on the device (the others kept theirs).
+b3d_status ctx_prepare_shared_bg(b3d_ctx *ctx, cudaStream_t s);
+b3d_status ctx_build_slot_bgs(b3d_ctx *ctx, int32_t n_slots, cudaStream_t s);
+void ctx_tracked_moved(b3d_ctx *ctx, int32_t n_slots);
 // Allocate and fill everything a batched enumeration of `slot` needs (background caches,
 // likelihood tables, rotation sets), so later calls allocate nothing.
 b3d_status ctx_prepare_slot(b3d_ctx *ctx, int32_t slot, const b3d_lik_params *lik, const b3d_c2f_schedule *sch,

@@ -200,6 +200,10 @@ b3d_status issue_batch(b3d_server *S, const std::vector<Frame> &frames, const st
             *msg = std::string("set_observation: ") + b3d_last_error(x->ctx);
             return st;
         }
+        if ((st = ctx_build_slot_bgs(x->ctx, x->n_track, s)) != B3D_OK) {
+            *msg = std::string("backgrounds: ") + b3d_last_error(x->ctx);
+            return st;
+        }
         float *poses = ctx_scene_poses(x->ctx);
         for (int32_t k = 0; k < x->n_track; ++k) {
             b3d_c2f_item it;
@@ -226,7 +230,7 @@ b3d_status issue_batch(b3d_server *S, const std::vector<Frame> &frames, const st
         const Frame &f = frames[i];
         const size_t pb = sizeof(float) * 16 * x->n_track;
         cudaError_t e = cudaMemcpyAsync(ctx_scene_poses(x->ctx), x->d_map, pb, cudaMemcpyDeviceToDevice, s);
-        ctx_poses_changed(x->ctx);
+        ctx_tracked_moved(x->ctx, x->n_track);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(x->h_res + (size_t)f.ring * x->n_track * 16, x->d_map, pb, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
@@ -478,6 +482,9 @@ b3d_status build_session(b3d_server *S, const b3d_session_desc *d, uint64_t cap,
     for (int32_t k = 0; k < d->n_track; ++k)
         if ((st = ctx_prepare_slot(ctx, k, &S->cfg.lik, &S->cfg.schedule, s)) != B3D_OK)
             return bail(st, "object " + std::to_string(k) + ": " + b3d_last_error(ctx));
+    // one z-buffer per object: each frame re-renders the tracked objects once and the fixed
+    // ones never, instead of every other object once per tracked slot
+    if ((st = ctx_prepare_shared_bg(ctx, s)) != B3D_OK) return bail(st, b3d_last_error(ctx));
     if ((st = b3d_sync(ctx, s)) != B3D_OK) return bail(st, b3d_last_error(ctx));
     // everything the session's frames use is allocated now: freeze its budget there
     x->reserved = ctx_used_bytes(ctx);
@@ -826,7 +833,7 @@ b3d_status b3d_session_import(b3d_server *S, int32_t id, const float *poses, con
     if (e == cudaSuccess && particles)
         e = cudaMemcpy(x->d_part, particles, sizeof(float) * nt * M * 16, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && logw) e = cudaMemcpy(x->d_logw, logw, sizeof(float) * nt * M, cudaMemcpyHostToDevice);
-    ctx_poses_changed(x->ctx);
+    ctx_tracked_moved(x->ctx, x->n_track);
     {
         std::lock_guard<std::mutex> lk(S->mu);
         x->next_index = next_frame;

@@ -123,6 +123,18 @@ __global__ void k_bg_depth(int64_t n, float far_z, const unsigned long long *bg,
     }
 }
 
+struct BgSources {
+    const unsigned long long *p[kMaxBgSources];
+};
+
+__global__ void k_bg_min(int64_t n, BgSources src, int n_src, unsigned long long *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long v = kEmptyKey;
+        for (int k = 0; k < n_src; ++k) v = min(v, src.p[k][i]);
+        dst[i] = v;
+    }
+}
+
 __global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long v) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
@@ -382,6 +394,12 @@ void launch_obs_points(const Cam &cam, const float *depth, float4 *obs, cudaStre
 
 void launch_bg_depth(int64_t n, float far_z, const unsigned long long *bg, float *bgd, cudaStream_t s) {
     k_bg_depth<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(n, far_z, bg, bgd);
+}
+
+void launch_bg_min(int64_t n, const unsigned long long *const *src, int n_src, unsigned long long *dst, cudaStream_t s) {
+    BgSources b{};
+    for (int k = 0; k < n_src && k < kMaxBgSources; ++k) b.p[k] = src[k];
+    k_bg_min<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(n, b, std::min(n_src, kMaxBgSources), dst);
 }
 
 void launch_bg_clear(unsigned long long *bg, int64_t n, cudaStream_t s) {
