@@ -97,6 +97,63 @@ __global__ void __launch_bounds__(kThreads) k_render_camera(Cam c, const MeshVie
     }
 }
 
+// Depth only, for images whose whole z-buffer fits in shared memory: the nearest depth of
+// every object at H_h P_k in 32-bit depth bits (the same nearest depth as the 64-bit keys),
+// one pass over each object's triangles per hypothesis (the tiled kernel above sets every
+// triangle up once per screen tile).
+constexpr int kMaxCamObjects = 16;
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_render_camera_depth(Cam c, const MeshView *meshes, const float *world,
+                                                            int n_obj, PoseList P, int64_t n_hyp, float *out_depth) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned *zb = reinterpret_cast<unsigned *>(smem_raw);  // [W H] depth bits
+    __shared__ float s_pose[kMaxCamObjects][12];
+    __shared__ int s_bb[kMaxCamObjects][4];
+    __shared__ int s_flags[kMaxCamObjects];
+    const int tid = threadIdx.x;
+    const int npx = c.W * c.H;
+    for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
+        __syncthreads();
+        for (int k = tid; k < n_obj; k += NT) {
+            // pose of object k in the hypothesised camera, H_h P_k, in the layout of pose12
+            float Hh[12];
+            pose12(P, h, Hh);
+            const float *W = world + 16 * k;
+            for (int r = 0; r < 3; ++r) {
+                for (int col = 0; col < 3; ++col)
+                    s_pose[k][3 * r + col] = fmaf(Hh[3 * r], W[col], fmaf(Hh[3 * r + 1], W[4 + col], Hh[3 * r + 2] * W[8 + col]));
+                s_pose[k][9 + r] = fmaf(Hh[3 * r], W[3], fmaf(Hh[3 * r + 1], W[7], fmaf(Hh[3 * r + 2], W[11], Hh[9 + r])));
+            }
+            bool front = false;
+            s_flags[k] = (object_bbox(meshes[k], s_pose[k], c, s_bb[k], &front) ? 1 : 0) | (front ? 4 : 0);
+        }
+        for (int i = tid; i < npx; i += NT) zb[i] = 0xffffffffu;
+        __syncthreads();
+        for (int k = 0; k < n_obj; ++k) {
+            if (!(s_flags[k] & 1)) continue;
+            const MeshView &m = meshes[k];
+            const bool front = (s_flags[k] & 4) != 0;
+            const int4 *tris = front ? m.tris_surf : m.tris_full;
+            const int n_t = front ? m.n_surf : m.n_full;
+            const int cull = front ? m.closed : 0;
+            const int rx0 = s_bb[k][0], rx1 = s_bb[k][1], ry0 = s_bb[k][2], ry1 = s_bb[k][3];
+            for (int t = tid; t < n_t; t += NT) {
+                float4 A, B, C;
+                tri_screen(m, tris[t], s_pose[k], c, A, B, C);
+                raster_tri(A, B, C, cull, rx0, rx1, ry0, ry1, c.far_z,
+                           [&](int x, int y, float z) { atomicMin(&zb[y * c.W + x], __float_as_uint(z)); });
+            }
+        }
+        __syncthreads();
+        float *dst = out_depth + h * npx;
+        for (int i = tid; i < npx; i += NT) {
+            const unsigned v = zb[i];
+            dst[i] = v == 0xffffffffu ? c.far_z : __uint_as_float(v);
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // scene set-up kernels
 // ------------------------------------------------------------------------------------------
@@ -380,6 +437,23 @@ int launch_score_grid(const SceneView &sv, const Lik &L, PoseGrid P, int64_t n, 
 int launch_render_camera(const Cam &cam, const MeshView *meshes, const int *tri_base, const float *world, int n_obj,
                          PoseList P, int64_t n, float *depth, int *tid, cudaStream_t s) {
     if (n <= 0) return 0;
+    const int64_t npx = (int64_t)cam.W * cam.H;
+    if (!tid && n_obj <= kMaxCamObjects && npx * (int64_t)sizeof(unsigned) <= 200 * 1024) {
+        // depth only and the image's z-buffer fits in shared memory: one pass per hypothesis
+        const int smem = (int)(npx * (int64_t)sizeof(unsigned));
+        if (npx > 16384) {
+            auto kern = k_render_camera_depth<1024>;
+            const int per_sm = kernel_ctas_per_sm(kern, 1024, smem);
+            const int g = (int)std::min<int64_t>((int64_t)per_sm * sm_count(), n);
+            kern<<<g, 1024, smem, s>>>(cam, meshes, world, n_obj, P, n, depth);
+            return g;
+        }
+        auto kern = k_render_camera_depth<256>;
+        const int per_sm = kernel_ctas_per_sm(kern, 256, smem);
+        const int g = (int)std::min<int64_t>((int64_t)per_sm * sm_count(), n);
+        kern<<<g, 256, smem, s>>>(cam, meshes, world, n_obj, P, n, depth);
+        return g;
+    }
     const int smem = kRegionPx * (int)sizeof(unsigned long long);
     auto kern = k_render_camera;
     const int g = persistent_grid(kern, smem, n, 0);

@@ -57,6 +57,24 @@ def test_render_camera_matches_oracle(orc, size):
     ctx.close()
 
 
+@pytest.mark.parametrize("size", [25, 100, 200, 240])
+def test_depth_only_camera_render_equals_keyed_render(size):
+    """Depth-only camera renders (the whole image's z-buffer in shared memory up to 200 KB;
+    256 threads up to 16,384 pixels, 1,024 above; 240x240 is past the limit and tiles) give
+    the nearest depth of the 64-bit-key render, bit for bit."""
+    from paper_2312_08715_gb300 import b3d
+    v = synth.camera_video(1, size, n_frames=2)
+    Hs = _perturb(np.random.default_rng(5), v.cam_from_world[0], 40, 0.02, 5.0)
+    ctx = b3d.Context(0)
+    ids = [ctx.load_mesh(m, closed=c) for m, c in zip(v.scene.meshes, _closed(v.scene))]
+    ctx.set_scene(v.scene.camera, ids, v.scene.poses, np.zeros((size, size), np.float32))
+    d_key, _ = ctx.render_camera(Hs)
+    d_only, _ = ctx.render_camera(Hs, want_tid=False)
+    ctx.sync()
+    assert torch.equal(d_key, d_only)
+    ctx.close()
+
+
 def test_camera_tracking_follows_the_video(orc):
     from paper_2312_08715_gb300.camera import CameraTracker
     v = synth.camera_video(1, 64, n_frames=12)
