@@ -129,6 +129,9 @@ struct LseShared {
     float red[kLseThreads / 32];
     float w[kLseMaxBlocks];
     float pre[kLseMaxBlocks];  // exclusive prefix of w
+    float cp[kLseThreads / 32][kLseMinChunk];         // per warp: inclusive prefix of one chunk,
+    float cl[kLseThreads / 32][kLseMinChunk];         // its scores
+    unsigned cm[kLseThreads / 32][kLseMinChunk / 32];  // and which of its weights are positive
     float M, S;
     bool last;
 };
@@ -193,17 +196,44 @@ __device__ __forceinline__ void lse_body(LseShared &sh, int bid, int nb, const f
         s_w[b] = (p.x > -INFINITY && M > -INFINITY) ? p.y * __expf(p.x - M) : 0.f;
     }
     __syncthreads();
-    if (tid == 0) {  // fixed-order prefix (B <= 1024 values)
-        float acc = 0.f;
-        for (int b = 0; b < B; ++b) { s_pre[b] = acc; acc += s_w[b]; }
-        s_S = acc;
-        *counter = 0u;
-        *logz = (M > -INFINITY) ? M + __logf(acc) : -INFINITY;
-        if (!(M > -INFINITY) && m > 0) atomicOr(err, 4);
+    {
+        // exclusive prefix of the chunk weights in a fixed order: every thread sums a run of
+        // consecutive chunks, the run totals are scanned (warp scans, then the warps in
+        // order), and each thread writes its run's prefixes
+        const int R = (B + kLseThreads - 1) / kLseThreads;
+        const int r0 = min(tid * R, B), r1 = min(r0 + R, B);
+        float run = 0.f;
+        for (int b = r0; b < r1; ++b) run += s_w[b];
+        float inc = run;
+        for (int o = 1; o < 32; o <<= 1) {
+            const float up = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += up;
+        }
+        if (lane == 31) s_red[wid] = inc;
+        __syncthreads();
+        if (tid == 0) {
+            float acc = 0.f;
+            for (int k = 0; k < nw; ++k) {
+                const float v = s_red[k];
+                s_red[k] = acc;
+                acc += v;
+            }
+            s_S = acc;
+            *counter = 0u;
+            *logz = (M > -INFINITY) ? M + __logf(acc) : -INFINITY;
+            if (!(M > -INFINITY) && m > 0) atomicOr(err, 4);
+        }
+        __syncthreads();
+        float acc = s_red[wid] + (inc - run);
+        for (int b = r0; b < r1; ++b) {
+            s_pre[b] = acc;
+            acc += s_w[b];
+        }
     }
     __syncthreads();
     const float S = s_S;
     const float Z = (M > -INFINITY) ? M + __logf(S) : -INFINITY;
+    int cached = -1;  // the chunk whose prefix this warp holds
     for (int k = wid; k < m; k += nw) {
         if (!(M > -INFINITY)) {
             if (lane == 0) { idx[k] = -1; logq[k] = -INFINITY; }
@@ -224,6 +254,63 @@ __device__ __forceinline__ void lse_body(LseShared &sh, int bid, int nb, const f
             while (b > 0 && s_w[b] == 0.f) --b;
         }
         const int64_t e0 = (int64_t)b * chunk, e1 = std::min<int64_t>(n, e0 + chunk);
+        if (chunk <= kLseMinChunk) {
+            // the chunk's inclusive prefix (the same groups of 32 and the same warp scans as
+            // the streaming search below, so the same sums) and its positive weights, kept
+            // per warp: further draws in the chunk only search shared memory
+            float *cp = sh.cp[wid], *cl = sh.cl[wid];
+            unsigned *cm = sh.cm[wid];
+            const int len = (int)(e1 - e0);
+            if (b != cached) {
+                constexpr int G = kLseMinChunk / 32;
+                float lv[G];  // every load of the chunk in flight before the scan
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    const int i = 32 * j + lane;
+                    lv[j] = i < len ? __ldcg(&ll[e0 + i]) : -INFINITY;
+                }
+                float c1 = s_pre[b];
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    const int i = 32 * j + lane;
+                    if (32 * j >= len) break;
+                    const float wv = i < len ? lse_weight(lv[j], M) : 0.f;
+                    float inc = wv;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const float up = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += up;
+                    }
+                    if (i < len) {
+                        cp[i] = c1 + inc;
+                        cl[i] = lv[j];
+                    }
+                    const unsigned pos = __ballot_sync(0xffffffffu, i < len && wv > 0.f);
+                    if (lane == 0) cm[j] = pos;
+                    c1 += __shfl_sync(0xffffffffu, inc, 31);
+                }
+                cached = b;
+                __syncwarp();
+            }
+            if (lane == 0) {
+                // first element with a positive weight whose inclusive prefix exceeds t (the
+                // prefix never decreases); if rounding leaves none, the last positive one
+                int lo = 0, hi = len;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cp[mid] > t) hi = mid; else lo = mid + 1;
+                }
+                int found = -1;
+                for (int i = lo; i < len; ++i)
+                    if ((cm[i >> 5] >> (i & 31)) & 1u) { found = i; break; }
+                if (found < 0)
+                    for (int i = len - 1; i >= 0; --i)
+                        if ((cm[i >> 5] >> (i & 31)) & 1u) { found = i; break; }
+                idx[k] = found >= 0 ? (int)(e0 + found) : -1;
+                logq[k] = found >= 0 ? cl[found] - Z : -INFINITY;
+            }
+            __syncwarp();
+            continue;
+        }
         float c0 = s_pre[b];
         int64_t found = -1, last_pos = -1;
         // 128 elements per pass, four independent loads in flight per lane
