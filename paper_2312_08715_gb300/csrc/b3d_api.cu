@@ -111,6 +111,7 @@ struct b3d_ctx {
     int64_t refine_cap = 0;
     float2 *d_part = nullptr;
     unsigned *d_counter = nullptr;
+    unsigned long long *d_work = nullptr;  // hypothesis counter of the score kernel
     float *d_logz = nullptr;
     int *d_idx = nullptr;
     float *d_logq_tmp = nullptr;
@@ -528,6 +529,7 @@ b3d_status ensure_scratch(b3d_ctx *ctx, int64_t n_ll, int m) {
         cudaMemset(ctx->d_counter, 0, sizeof(unsigned));
         if ((st = dalloc(ctx, &ctx->d_logz, B3D_MAX_STAGES, "log normalisers")) != B3D_OK) return st;
         if ((st = dalloc(ctx, &ctx->d_centre, 3 * 16, "grid centres")) != B3D_OK) return st;
+        if ((st = dalloc(ctx, &ctx->d_work, 1, "score work counter")) != B3D_OK) return st;
     }
     if (m > ctx->idx_cap) {
         dfree(ctx, ctx->d_idx);
@@ -1371,7 +1373,8 @@ b3d_status b3d_enumerate_c2f(b3d_ctx *ctx, int32_t obj_slot, const float *centre
         if ((st = rotation_table(ctx, sch->stage[t], &rot[t], s)) != B3D_OK) return st;
     if ((st = ensure_bg(ctx, obj_slot, s)) != B3D_OK) return st;
     if ((st = ensure_bg_lik(ctx, obj_slot, lik, L, false, s)) != B3D_OK) return st;
-    const SceneView sv = scene_view(ctx, obj_slot);
+    SceneView sv = scene_view(ctx, obj_slot);
+    sv.work = ctx->d_work;  // CTAs take hypotheses from a counter
     {
         Timed tm(ctx, B3D_K_SCENE, s);
         launch_set16(ctx->d_centre, centre_pose, s);
@@ -1816,7 +1819,8 @@ b3d_status b3d_autotune(b3d_ctx *ctx, int32_t obj_slot, const float *centre_pose
                 ctx->cta_threads = nt;
                 ctx->ctas_per_sm = cps;
                 ctx->high_occupancy = hi;
-                const SceneView sv = scene_view(ctx, obj_slot);
+                SceneView sv = scene_view(ctx, obj_slot);
+                sv.work = ctx->d_work;  // as enumerate_c2f launches it
                 launch_score_grid(sv, L, P, n, ctx->d_ll, ctx->score_code(), s);  // warm
                 cudaEventRecord(e0, s);
                 launch_score_grid(sv, L, P, n, ctx->d_ll, ctx->score_code(), s);

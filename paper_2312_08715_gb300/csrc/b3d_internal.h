@@ -111,6 +111,8 @@ struct SceneView {
     int *err;                          // device error flag
     unsigned long long *stats;         // [kNumStats] work counters, or NULL (no counting)
     int tile_w;                        // widest screen tile of the score kernel (pixels)
+    unsigned long long *work;          // hypothesis counter of the score kernel (zeroed by its launcher) or
+                                       // NULL: CTA c takes hypotheses c, c + grid, ...
 };
 
 // Hypothesis poses as 12 floats: R row-major (9) then t (3).

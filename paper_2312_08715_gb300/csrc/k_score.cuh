@@ -605,14 +605,26 @@ __global__ void __launch_bounds__(NT, MINB)
     const int tid = threadIdx.x;
     for (int i = tid; i < L.n_lut; i += blockDim.x) s_lut[i] = L.lut[i];
     unsigned long long cnt[kNumStats] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
-        __syncthreads();
+    __shared__ long long s_next;
+    // With a counter, CTAs take their next hypothesis from it as they finish one (so they all
+    // finish together however uneven the hypotheses' costs); thread 0 asks for it at the start
+    // of the current one and publishes it at the end.
+    int64_t h = blockIdx.x;
+    __syncthreads();
+    while (h < n_hyp) {
+        long long nxt = h + gridDim.x;
         if (tid == 0) {
+            if (S.work) nxt = (long long)gridDim.x + (long long)atomicAdd(S.work, 1ull);
             if (STATS) ++cnt[0];
             pose12(P, h, sh.pose);
         }
         const float tot = score_body<STATS, WT, NT>(S, L, s_lut, sh, s_stage, zb, lat, cnt);
-        if (tid == 0) out_ll[h] = (float)(*S.ll_bg + (double)tot);
+        if (tid == 0) {
+            out_ll[h] = (float)(*S.ll_bg + (double)tot);
+            s_next = nxt;
+        }
+        __syncthreads();  // the next write of s_next comes after score_body's barriers
+        h = s_next;
     }
     if (STATS)
         for (int k = 0; k < kNumStats; ++k)
@@ -701,6 +713,7 @@ int launch_score_nt(const SceneView &sv, const Lik &L, PS P, int64_t n, float *l
     // grid > 0: CTAs per SM requested by the tuning (capped by occupancy); 0: occupancy
     const int ctas = grid > 0 ? std::min(grid, per_sm) : per_sm;
     const int g = (int)std::min<int64_t>((int64_t)ctas * score_sm_count(), std::max<int64_t>(n, 1));
+    if (sv.work) cudaMemsetAsync(sv.work, 0, sizeof(unsigned long long), s);
     kern<<<g, NT, smem, s>>>(sv, L, P, n, ll);
     return g;
 }
