@@ -111,7 +111,8 @@ struct b3d_ctx {
     int64_t refine_cap = 0;
     float2 *d_part = nullptr;
     unsigned *d_counter = nullptr;
-    unsigned long long *d_work = nullptr;  // hypothesis counter of the score kernel
+    unsigned long long *d_work = nullptr;  // ring of kWorkRing hypothesis counters of the persistent kernels
+    unsigned work_slot = 0;
     float *d_logz = nullptr;
     int *d_idx = nullptr;
     float *d_logq_tmp = nullptr;
@@ -416,6 +417,10 @@ SceneView scene_view(b3d_ctx *ctx, int32_t slot) {
     return sv;
 }
 
+// A hypothesis counter for one persistent launch (its launcher zeroes it): a ring, so launches
+// of this context on different streams use different counters unless kWorkRing are in flight.
+unsigned long long *take_work(b3d_ctx *ctx) { return ctx->d_work + (ctx->work_slot++ % kWorkRing); }
+
 // Per-pixel terms of the background of `slot` (after ensure_bg) for these likelihood
 // parameters; with grad, also the sigma / p_out derivative tables.
 b3d_status ensure_bg_lik(b3d_ctx *ctx, int32_t slot, const b3d_lik_params *lp, const Lik &L, bool grad,
@@ -529,7 +534,6 @@ b3d_status ensure_scratch(b3d_ctx *ctx, int64_t n_ll, int m) {
         cudaMemset(ctx->d_counter, 0, sizeof(unsigned));
         if ((st = dalloc(ctx, &ctx->d_logz, B3D_MAX_STAGES, "log normalisers")) != B3D_OK) return st;
         if ((st = dalloc(ctx, &ctx->d_centre, 3 * 16, "grid centres")) != B3D_OK) return st;
-        if ((st = dalloc(ctx, &ctx->d_work, 1, "score work counter")) != B3D_OK) return st;
     }
     if (m > ctx->idx_cap) {
         dfree(ctx, ctx->d_idx);
@@ -704,8 +708,10 @@ b3d_status b3d_create(b3d_ctx **out, int32_t device, uint64_t hbm_budget_bytes) 
     ctx->budget = hbm_budget_bytes;
     DeviceGuard g(device);
     b3d_status st = dalloc(ctx, &ctx->d_err, 1, "error flag");
+    if (st == B3D_OK) st = dalloc(ctx, &ctx->d_work, kWorkRing, "work counters");
     if (st != B3D_OK) {
         g_create_error = ctx->err;
+        if (ctx->d_err) cudaFree(ctx->d_err);
         delete ctx;
         return st;
     }
@@ -1168,7 +1174,9 @@ b3d_status b3d_render_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const
     if (!triid_dev && (st = ensure_bg_depth(ctx, obj_slot, s)) != B3D_OK) return st;
     {
         Timed tm(ctx, B3D_K_RENDER, s);
-        ctx->launches += launch_render_list(scene_view(ctx, obj_slot), PoseList{poses_dev}, n_hyp, depth_dev, triid_dev, 0, s);
+        SceneView sv = scene_view(ctx, obj_slot);
+        sv.work = take_work(ctx);
+        ctx->launches += launch_render_list(sv, PoseList{poses_dev}, n_hyp, depth_dev, triid_dev, 0, s);
     }
     return check_launch(ctx, "render_batch");
 }
@@ -1191,7 +1199,9 @@ b3d_status b3d_score_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const 
     if ((st = ensure_bg_lik(ctx, obj_slot, lik, L, false, s)) != B3D_OK) return st;
     {
         Timed tm(ctx, B3D_K_SCORE, s);
-        launch_score_list(scene_view(ctx, obj_slot), L, PoseList{poses_dev}, n_hyp, loglik_dev, ctx->score_code(), s);
+        SceneView sv = scene_view(ctx, obj_slot);
+        sv.work = take_work(ctx);
+        launch_score_list(sv, L, PoseList{poses_dev}, n_hyp, loglik_dev, ctx->score_code(), s);
     }
     ++ctx->launches;
     return check_launch(ctx, "score_batch");
@@ -1260,7 +1270,9 @@ b3d_status b3d_score_noise_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, 
     const BgCache &c = bg_cache(ctx, obj_slot);
     {
         Timed tm(ctx, B3D_K_SCORE, s);
-        launch_score_noise(scene_view(ctx, obj_slot), N, poses_dev, n_hyp, c.nell, c.nsums, loglik_dev, marginal_dev, s);
+        SceneView sv = scene_view(ctx, obj_slot);
+        sv.work = take_work(ctx);
+        launch_score_noise(sv, N, poses_dev, n_hyp, c.nell, c.nsums, loglik_dev, marginal_dev, s);
     }
     ++ctx->launches;
     return check_launch(ctx, "score_noise_batch");
@@ -1290,7 +1302,9 @@ b3d_status b3d_score_depth_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, 
     if ((st = ensure_bg_lik(ctx, obj_slot, lik, L, false, s)) != B3D_OK) return st;
     {
         Timed tm(ctx, B3D_K_SCORE_DEPTH, s);
-        ctx->launches += launch_score_depth(scene_view(ctx, obj_slot), L, depth_dev, triid_dev, n_hyp, loglik_dev, 0, s);
+        SceneView sv = scene_view(ctx, obj_slot);
+        sv.work = take_work(ctx);
+        ctx->launches += launch_score_depth(sv, L, depth_dev, triid_dev, n_hyp, loglik_dev, 0, s);
     }
     return check_launch(ctx, "score_depth_batch");
 }
@@ -1374,7 +1388,7 @@ b3d_status b3d_enumerate_c2f(b3d_ctx *ctx, int32_t obj_slot, const float *centre
     if ((st = ensure_bg(ctx, obj_slot, s)) != B3D_OK) return st;
     if ((st = ensure_bg_lik(ctx, obj_slot, lik, L, false, s)) != B3D_OK) return st;
     SceneView sv = scene_view(ctx, obj_slot);
-    sv.work = ctx->d_work;  // CTAs take hypotheses from a counter
+    sv.work = take_work(ctx);  // CTAs take hypotheses from a counter
     {
         Timed tm(ctx, B3D_K_SCENE, s);
         launch_set16(ctx->d_centre, centre_pose, s);
@@ -1820,7 +1834,7 @@ b3d_status b3d_autotune(b3d_ctx *ctx, int32_t obj_slot, const float *centre_pose
                 ctx->ctas_per_sm = cps;
                 ctx->high_occupancy = hi;
                 SceneView sv = scene_view(ctx, obj_slot);
-                sv.work = ctx->d_work;  // as enumerate_c2f launches it
+                sv.work = take_work(ctx);  // as enumerate_c2f launches it
                 launch_score_grid(sv, L, P, n, ctx->d_ll, ctx->score_code(), s);  // warm
                 cudaEventRecord(e0, s);
                 launch_score_grid(sv, L, P, n, ctx->d_ll, ctx->score_code(), s);

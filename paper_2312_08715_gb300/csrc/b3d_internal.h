@@ -19,6 +19,7 @@ namespace b3d {
 constexpr int kThreads = B3D_THREADS;  // threads per CTA of the render/score kernels
 constexpr int kScoreMinBlocks = B3D_SCORE_MIN_BLOCKS;  // CTAs per SM the score kernel is built for
 constexpr int kRegionPx = 4096;        // z-buffer pixels per screen tile in shared memory
+constexpr int kWorkRing = 64;          // hypothesis counters per context (one per launch in flight)
 constexpr int kMaxPlanes = 511;        // lattice planes per axis of a quad mesh
 constexpr int kMaxHalfWindow = 7;
 constexpr int kMaxLut = (2 * kMaxHalfWindow + 1) * (2 * kMaxHalfWindow + 1) + 1;
@@ -111,7 +112,7 @@ struct SceneView {
     int *err;                          // device error flag
     unsigned long long *stats;         // [kNumStats] work counters, or NULL (no counting)
     int tile_w;                        // widest screen tile of the score kernel (pixels)
-    unsigned long long *work;          // hypothesis counter of the score kernel (zeroed by its launcher) or
+    unsigned long long *work;          // hypothesis counter of a persistent kernel (zeroed by its launcher) or
                                        // NULL: CTA c takes hypotheses c, c + grid, ...
 };
 

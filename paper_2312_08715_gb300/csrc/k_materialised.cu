@@ -140,9 +140,15 @@ __global__ void __launch_bounds__(NT, MINB) k_render_fused(SceneView S, PoseList
     const Cam &c = S.cam;
     const int tid = threadIdx.x;
     const int64_t npx = (int64_t)c.W * c.H;
-    for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
+    __shared__ long long s_next;
+    int64_t h = blockIdx.x;  // then from the counter S.work when given
+    while (h < n_hyp) {
         __syncthreads();
-        if (tid == 0) pose12(P, h, sh.pose);
+        long long nxt = h + gridDim.x;
+        if (tid == 0) {
+            if (S.work) nxt = (long long)gridDim.x + (long long)atomicAdd(S.work, 1ull);
+            pose12(P, h, sh.pose);
+        }
         float *dst = out_depth + h * npx;
         // the background first; render_tiles' barriers order these stores before the tiles'
         if (V == 4) {
@@ -164,6 +170,9 @@ __global__ void __launch_bounds__(NT, MINB) k_render_fused(SceneView S, PoseList
                                         if (x >= tww) { x -= tww; ++y; }
                                     }
                                 });
+        if (tid == 0) s_next = nxt;
+        __syncthreads();
+        h = s_next;
     }
 }
 
@@ -201,8 +210,12 @@ __global__ void __launch_bounds__(NT, MINB) k_score_fused(SceneView S, Lik L, co
     const int w = WT > 0 ? WT : L.w;
     const int64_t npx = (int64_t)c.W * c.H;
     const float *bgd = S.bgd + (MM ? npx : 0);
-    for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
+    __shared__ long long s_next;
+    int64_t h = blockIdx.x;  // then from the counter S.work when given
+    while (h < n_hyp) {
         __syncthreads();
+        long long nxt = h + gridDim.x;
+        if (tid == 0 && S.work) nxt = (long long)gridDim.x + (long long)atomicAdd(S.work, 1ull);
         const float *img = depth + h * npx;
         const int *tim = MM ? tid_in + h * npx : nullptr;
         // 1. the box of pixels whose depth bits differ from the background's
@@ -316,7 +329,12 @@ __global__ void __launch_bounds__(NT, MINB) k_score_fused(SceneView S, Lik L, co
             }
         }
         const float tot = block_sum(acc, s_red);
-        if (tid == 0) out_ll[h] = (float)(*S.ll_bg + (double)tot);
+        if (tid == 0) {
+            out_ll[h] = (float)(*S.ll_bg + (double)tot);
+            s_next = nxt;
+        }
+        __syncthreads();
+        h = s_next;
     }
 }
 
@@ -354,6 +372,7 @@ int launch_render_list(const SceneView &sv, PoseList P, int64_t n, float *depth,
     const int n_lat = sv.mesh.nc[0] + sv.mesh.nc[1] + sv.mesh.nc[2];
     const int smem = score_region<kMatNT>() * (int)sizeof(unsigned) + n_lat * (int)sizeof(float4);
     auto kern = vec ? k_render_fused<kMatNT, kMatMinB, 4> : k_render_fused<kMatNT, kMatMinB, 1>;
+    if (sv.work) cudaMemsetAsync(sv.work, 0, sizeof(unsigned long long), s);
     kern<<<persistent_grid(kern, kMatNT, smem, n, grid), kMatNT, smem, s>>>(sv, P, n, depth);
     return 1;
 }
@@ -366,6 +385,7 @@ static void launch_score_fused(const SceneView &sv, const Lik &L, const float *d
     const bool vec = npx % 4 == 0 && aligned16p(depth) && (!mm || aligned16p(tid));
     auto kern = vec ? (mm ? k_score_fused<WT, kMatNT, kMatMinB, 4, 1> : k_score_fused<WT, kMatNT, kMatMinB, 4, 0>)
                     : (mm ? k_score_fused<WT, kMatNT, kMatMinB, 1, 1> : k_score_fused<WT, kMatNT, kMatMinB, 1, 0>);
+    if (sv.work) cudaMemsetAsync(sv.work, 0, sizeof(unsigned long long), s);
     kern<<<persistent_grid(kern, kMatNT, 0, n, grid), kMatNT, 0, s>>>(sv, L, depth, tid, n, ll);
 }
 

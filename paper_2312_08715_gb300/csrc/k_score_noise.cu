@@ -138,9 +138,15 @@ __global__ void __launch_bounds__(NT, MINB)
     const Cam &c = S.cam;
     const int64_t npx = (int64_t)c.W * c.H;
     const int G = N.nr * N.np;
-    for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
+    __shared__ long long s_next;
+    int64_t h = blockIdx.x;  // then from the counter S.work, as in the single-setting kernel
+    while (h < n_hyp) {
         __syncthreads();
-        if (tid == 0) pose12(P, h, sh.pose);
+        long long nxt = h + gridDim.x;
+        if (tid == 0) {
+            if (S.work) nxt = (long long)gridDim.x + (long long)atomicAdd(S.work, 1ull);
+            pose12(P, h, sh.pose);
+        }
         float acc[kMaxNoise];
 #pragma unroll
         for (int g = 0; g < kMaxNoise; ++g) acc[g] = 0.f;
@@ -192,7 +198,10 @@ __global__ void __launch_bounds__(NT, MINB)
             for (int g = 0; g < kMaxNoise; ++g)
                 if ((g >> 2) < N.nr && (g & 3) < N.np) sum += exp(s_ll[g] + (double)N.logw[g] - m);
             out_marg[h] = (float)(m + log(sum));
+            s_next = nxt;
         }
+        __syncthreads();
+        h = s_next;
     }
 }
 
@@ -212,6 +221,7 @@ void launch_score_noise(const SceneView &sv, const NoiseLik &N, const float *pos
     auto kern = k_score_noise<NT, MINB>;
     const int per_sm = kernel_ctas_per_sm(kern, NT, smem);
     const int g = (int)std::min<int64_t>((int64_t)per_sm * score_sm_count(), std::max<int64_t>(n_hyp, 1));
+    if (sv.work) cudaMemsetAsync(sv.work, 0, sizeof(unsigned long long), s);
     kern<<<g, NT, smem, s>>>(sv, N, PoseList{poses}, n_hyp, nell, nsums, out_ll, out_marg);
 }
 
