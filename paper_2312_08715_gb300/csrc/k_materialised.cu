@@ -151,9 +151,17 @@ __global__ void __launch_bounds__(NT, MINB) k_render_fused(SceneView S, PoseList
         }
         float *dst = out_depth + h * npx;
         // the background first; render_tiles' barriers order these stores before the tiles'
-        if (V == 4) {
+        if (V == 4) {  // four loads in flight per thread
             const float4 *src = reinterpret_cast<const float4 *>(S.bgd);
-            for (int64_t k = tid; k < npx / 4; k += NT) __stcs(reinterpret_cast<float4 *>(dst) + k, __ldg(src + k));
+            float4 *d4 = reinterpret_cast<float4 *>(dst);
+            const int n4 = (int)(npx / 4);
+            int k = tid;
+            for (; k + 3 * NT < n4; k += 4 * NT) {
+                const float4 a0 = __ldg(src + k), a1 = __ldg(src + k + NT), a2 = __ldg(src + k + 2 * NT),
+                             a3 = __ldg(src + k + 3 * NT);
+                __stcs(d4 + k, a0); __stcs(d4 + k + NT, a1); __stcs(d4 + k + 2 * NT, a2); __stcs(d4 + k + 3 * NT, a3);
+            }
+            for (; k < n4; k += NT) __stcs(d4 + k, __ldg(src + k));
         } else {
             for (int64_t k = tid; k < npx; k += NT) __stcs(dst + k, __ldg(S.bgd + k));
         }
@@ -351,7 +359,13 @@ static int persistent_grid(K kernel, int threads, int smem, int64_t n, int grid)
     return (int)std::min<int64_t>((int64_t)per_sm * score_sm_count(), std::max<int64_t>(n, 1));
 }
 
-constexpr int kMatNT = 128, kMatMinB = 6;  // launch shape of the fused materialised kernels
+// Launch shape of the fused materialised kernels: 128-thread CTAs; register caps from
+// launch-bound sweeps on the 160x120 tabletop stage (145,800 images): the renderer at 8
+// CTAs per SM (64 registers; 3.64 against 3.77 ms at 6), the ball scorer at 10 (48
+// registers, no spills; 2.32 against 2.59 ms at 6, 2.44 at 8, 2.53 at 12, where it spills).
+constexpr int kMatNT = 128, kRenderMinB = 8;
+template <int WT>
+constexpr int score_fused_minb() { return WT == 1 ? 10 : 6; }
 
 int launch_render_list(const SceneView &sv, PoseList P, int64_t n, float *depth, int *tid, int grid, cudaStream_t s) {
     if (n <= 0) return 0;
@@ -371,7 +385,7 @@ int launch_render_list(const SceneView &sv, PoseList P, int64_t n, float *depth,
     const bool vec = npx % 4 == 0 && aligned16p(depth);
     const int n_lat = sv.mesh.nc[0] + sv.mesh.nc[1] + sv.mesh.nc[2];
     const int smem = score_region<kMatNT>() * (int)sizeof(unsigned) + n_lat * (int)sizeof(float4);
-    auto kern = vec ? k_render_fused<kMatNT, kMatMinB, 4> : k_render_fused<kMatNT, kMatMinB, 1>;
+    auto kern = vec ? k_render_fused<kMatNT, kRenderMinB, 4> : k_render_fused<kMatNT, kRenderMinB, 1>;
     if (sv.work) cudaMemsetAsync(sv.work, 0, sizeof(unsigned long long), s);
     kern<<<persistent_grid(kern, kMatNT, smem, n, grid), kMatNT, smem, s>>>(sv, P, n, depth);
     return 1;
@@ -383,8 +397,9 @@ static void launch_score_fused(const SceneView &sv, const Lik &L, const float *d
     const int64_t npx = (int64_t)sv.cam.W * sv.cam.H;
     const bool mm = L.miss_mode == 1;
     const bool vec = npx % 4 == 0 && aligned16p(depth) && (!mm || aligned16p(tid));
-    auto kern = vec ? (mm ? k_score_fused<WT, kMatNT, kMatMinB, 4, 1> : k_score_fused<WT, kMatNT, kMatMinB, 4, 0>)
-                    : (mm ? k_score_fused<WT, kMatNT, kMatMinB, 1, 1> : k_score_fused<WT, kMatNT, kMatMinB, 1, 0>);
+    constexpr int MB = score_fused_minb<WT>();
+    auto kern = vec ? (mm ? k_score_fused<WT, kMatNT, MB, 4, 1> : k_score_fused<WT, kMatNT, MB, 4, 0>)
+                    : (mm ? k_score_fused<WT, kMatNT, MB, 1, 1> : k_score_fused<WT, kMatNT, MB, 1, 0>);
     if (sv.work) cudaMemsetAsync(sv.work, 0, sizeof(unsigned long long), s);
     kern<<<persistent_grid(kern, kMatNT, 0, n, grid), kMatNT, 0, s>>>(sv, L, depth, tid, n, ll);
 }
