@@ -98,7 +98,10 @@ typedef struct {
  * rot_kind 0: Fibonacci-sphere set, R_k the minimal-arc rotation taking +z to
  *   d_k = (sqrt(1-z^2) cos(2 pi k / phi), sqrt(1-z^2) sin(2 pi k / phi), z),
  *   z = 1 - (2k+1)/n_rot, phi the golden ratio;
- * rot_kind 1: perturbation set, R_k = Exp(theta_k d_k), theta_k = rot_max (2 frac((k+1/2)/phi) - 1). */
+ * rot_kind 1: perturbation set, uniform in the ball of rotation vectors of radius rot_max:
+ *   R_0 = I; for k >= 1, R_k = Exp(rot_max cbrt(u0) e), e = (sqrt(1-z^2) cos(2 pi u2),
+ *   sqrt(1-z^2) sin(2 pi u2), z), z = 1 - 2 u1, (u0, u1, u2) = frac(1/2 + k (1/g, 1/g^2, 1/g^3))
+ *   the 3-D R-sequence (g^4 = g + 1), evaluated in exact 64-bit fixed point. */
 typedef struct {
     int32_t n_per_axis;
     float step;

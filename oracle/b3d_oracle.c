@@ -601,13 +601,28 @@ static void rot_axis_angle(const double axis[3], double angle, double *R) {
     R[6] = k[2] * k[0] * C - k[1] * s; R[7] = k[2] * k[1] * C + k[0] * s; R[8] = c + k[2] * k[2] * C;
 }
 
+/* Weyl sequence frac(1/2 + k a) in exact 64-bit fixed point: A = round(2^64 a); the top 53
+ * bits of 2^63 + k A (mod 2^64) give the value as a double in [0, 1). */
+static double weyl_u(uint64_t A, int32_t k) {
+    const uint64_t x = 0x8000000000000000ull + (uint64_t)k * A;
+    return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+}
+
 /* Rotation sets (reading; the paper gives no scheme):
  *   kind 0, Fibonacci sphere: d_k = (sqrt(1-z^2) cos(2 pi k / phi), sqrt(1-z^2) sin(2 pi k / phi), z),
  *           z = 1 - (2k+1)/n, phi the golden ratio; R_k is the minimal-arc rotation taking
  *           +z to d_k (pi about x for the antipode, identity for +z itself).
- *   kind 1, perturbation: R_k = Exp(theta_k d_k) with d_k as above and
- *           theta_k = rot_max (2 frac((k + 1/2) / phi) - 1).
+ *   kind 1, perturbation: a low-discrepancy set uniform in the ball of rotation vectors of
+ *           radius rot_max. R_0 is the identity (the grid centre's own rotation); for k >= 1,
+ *           R_k = Exp(rot_max cbrt(u0) d) with d = (sqrt(1-z^2) cos(2 pi u2),
+ *           sqrt(1-z^2) sin(2 pi u2), z), z = 1 - 2 u1, where (u0, u1, u2) = frac(1/2 + k a)
+ *           is the 3-D R-sequence (Roberts): a = (1/g, 1/g^2, 1/g^3), g the real root above 1
+ *           of x^4 = x + 1. (u -> the ball is volume-preserving: radius cbrt(u0), direction
+ *           uniform on the sphere.)
  * Output R[n, 9] row-major. */
+#define ORC_R3_A1 0xd1b54a32d192ed04ull /* round(2^64 / g) */
+#define ORC_R3_A2 0xabc98388fb8fac03ull /* round(2^64 / g^2) */
+#define ORC_R3_A3 0x8cb92ba72f3d8dd7ull /* round(2^64 / g^3) */
 int orc_rotation_set(int32_t kind, int32_t n, double rot_max, double *R) {
     if (n <= 0 || !R || (kind != 0 && kind != 1)) return ORC_EINVAL;
     const double phi = (1.0 + sqrt(5.0)) / 2.0;
@@ -628,11 +643,12 @@ int orc_rotation_set(int32_t kind, int32_t n, double rot_max, double *R) {
                 rot_axis_angle(ax, atan2(sn, z), Rk);
             }
         } else {
-            double fr = (k + 0.5) / phi;
-            fr -= floor(fr);
-            double theta = rot_max * (2.0 * fr - 1.0);
-            if (theta == 0.0) { double I[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}; memcpy(Rk, I, sizeof I); }
-            else rot_axis_angle(d, theta, Rk);
+            const double u0 = weyl_u(ORC_R3_A1, k), u1 = weyl_u(ORC_R3_A2, k), u2 = weyl_u(ORC_R3_A3, k);
+            const double theta = rot_max * cbrt(u0);
+            const double zz = 1.0 - 2.0 * u1, s = sqrt(fmax(0.0, 1.0 - zz * zz));
+            double e[3] = {s * cos(2.0 * ORC_PI * u2), s * sin(2.0 * ORC_PI * u2), zz};
+            if (k == 0 || theta == 0.0) { double I[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}; memcpy(Rk, I, sizeof I); }
+            else rot_axis_angle(e, theta, Rk);
         }
     }
     return ORC_OK;

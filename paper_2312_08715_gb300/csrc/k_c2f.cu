@@ -54,6 +54,12 @@ __device__ void axis_angle(double kx, double ky, double kz, double ang, float *R
     R[6] = (float)(kz * kx * C - ky * s); R[7] = (float)(kz * ky * C + kx * s); R[8] = (float)(c + kz * kz * C);
 }
 
+// frac(1/2 + k a) with A = round(2^64 a): the top 53 bits of 2^63 + k A (mod 2^64), exact
+__device__ __forceinline__ double weyl_u(unsigned long long A, int k) {
+    const unsigned long long x = 0x8000000000000000ull + (unsigned long long)k * A;
+    return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+}
+
 __global__ void k_rotation_set(int kind, int n, double rot_max, float *out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -74,11 +80,16 @@ __global__ void k_rotation_set(int kind, int n, double rot_max, float *out) {
             axis_angle(-dy, dx, 0.0, atan2(sn, dz), R);
         }
     } else {
-        double fr = (k + 0.5) / phi;
-        fr -= floor(fr);
-        const double theta = rot_max * (2.0 * fr - 1.0);
-        if (theta == 0.0) for (int i = 0; i < 9; ++i) R[i] = I[i];
-        else axis_angle(dx, dy, dz, theta, R);
+        // low-discrepancy set uniform in the ball of rotation vectors of radius rot_max:
+        // member 0 the identity, member k the 3-D R-sequence point frac(1/2 + k (1/g, 1/g^2,
+        // 1/g^3)) (g^4 = g + 1) mapped volume-preservingly onto the ball (radius cbrt(u0),
+        // z = 1 - 2 u1, azimuth 2 pi u2); the sequence in exact 64-bit fixed point
+        const double u0 = weyl_u(0xd1b54a32d192ed04ull, k), u1 = weyl_u(0xabc98388fb8fac03ull, k);
+        const double u2 = weyl_u(0x8cb92ba72f3d8dd7ull, k);
+        const double theta = rot_max * cbrt(u0);
+        const double ez = 1.0 - 2.0 * u1, es = sqrt(fmax(0.0, 1.0 - ez * ez));
+        if (k == 0 || theta == 0.0) for (int i = 0; i < 9; ++i) R[i] = I[i];
+        else axis_angle(es * cos(2.0 * pi * u2), es * sin(2.0 * pi * u2), ez, theta, R);
     }
 }
 

@@ -395,6 +395,22 @@ def test_render_fill_paths(orc, single_object, offset):
     ctx.close()
 
 
+@pytest.mark.parametrize("kind,n_rot,rot_max", [(1, 1, 0.2), (1, 7, 0.05), (1, 200, math.radians(10)),
+                                                (1, 2048, math.radians(1)), (1, 4097, math.radians(2)), (0, 200, 0.0)])
+def test_rotation_sets_match_oracle(orc, single_object, kind, n_rot, rot_max):
+    """The library's rotation sets (computed on the device) against the oracle's, member by
+    member, through the grid expansion of a rotated, offset centre."""
+    wl = single_object
+    ctx = gpu_context(wl.scene, observed(orc, wl))
+    st = synth.StageSpec(3, 0.004, kind, n_rot, rot_max)
+    got = _np(ctx.expand(wl.centre, wl.grid_frame, st))
+    ctx.sync()
+    want = orc.expand(wl.centre, wl.grid_frame, 3, 0.004, orc.rotation_set(kind, n_rot, rot_max))
+    np.testing.assert_allclose(got, want, atol=2e-6)
+    if kind == 1:  # member 0 is the identity: the centre's own rotation is in every set
+        np.testing.assert_allclose(got[13], wl.centre, atol=2e-6)
+
+
 def test_tabletop_first_stage_full_size_sampled(orc, tabletop):
     """Full first-stage grid (9^3 x 200 = 145,800 hypotheses) in one launch, 40 sampled
     hypotheses checked against the oracle one by one; the grid poses against the oracle's."""

@@ -305,20 +305,34 @@ def test_fibonacci_rotations_are_minimal_arcs(orc):
 
 
 def test_perturbation_rotations(orc):
-    n, tmax = 200, math.radians(10)
-    R = orc.rotation_set(1, n, tmax)
-    phi = (1 + 5 ** 0.5) / 2
-    for k in range(n):
-        np.testing.assert_allclose(R[k] @ R[k].T, np.eye(3), atol=1e-12)
-        assert np.linalg.det(R[k]) == pytest.approx(1.0)
-        fr = ((k + 0.5) / phi) % 1.0
-        theta = tmax * (2 * fr - 1)
-        rv = Rotation.from_matrix(R[k]).as_rotvec()
-        assert np.linalg.norm(rv) == pytest.approx(abs(theta), abs=1e-9)
-        z = 1 - (2 * k + 1) / n
-        rho = math.sqrt(1 - z * z)
-        d = np.array([rho * math.cos(2 * math.pi * k / phi), rho * math.sin(2 * math.pi * k / phi), z])
-        np.testing.assert_allclose(rv, theta * d, atol=1e-9)
+    """Kind 1 is a low-discrepancy set uniform in the ball of rotation vectors of radius
+    rot_max, the identity first. Pinned by what such a set must satisfy: rotations within
+    the radius, the moments of the uniform ball (P(|r| <= R/2) = 1/8, E|r| = 3R/4,
+    E[r r^T] = R^2/5 I, E[r] = 0), and a covering radius within twice the radius of the
+    ball's volume per point (the earlier set, whose angle and axis azimuth came from one
+    golden-ratio sequence, left holes of 0.49 R at 2,048 members)."""
+    assert np.array_equal(orc.rotation_set(1, 1, 0.2)[0], np.eye(3))
+    for n, tmax in ((2048, math.radians(1.0)), (200, math.radians(10)), (4096, 0.3)):
+        R = orc.rotation_set(1, n, tmax)
+        assert np.array_equal(R[0], np.eye(3))
+        np.testing.assert_allclose(np.einsum("nij,nkj->nik", R, R), np.broadcast_to(np.eye(3), R.shape), atol=1e-12)
+        np.testing.assert_allclose(np.linalg.det(R), 1.0, atol=1e-12)
+        rv = Rotation.from_matrix(R[1:]).as_rotvec()
+        r = np.linalg.norm(rv, axis=1)
+        assert r.max() <= tmax * (1 + 1e-9) and r.min() > 0
+        tol = 3.0 / math.sqrt(n)  # a few standard errors of a random set; a uniform low-discrepancy set does better
+        assert abs(np.mean(r <= tmax / 2) - 1 / 8) < tol
+        assert abs(r.mean() / tmax - 0.75) < tol
+        assert np.abs(rv.mean(axis=0)).max() / tmax < tol
+        np.testing.assert_allclose(rv.T @ rv / len(rv) / (tmax ** 2 / 5), np.eye(3), atol=2 * tol)
+        # coverage: seeded targets uniform in the ball of 0.9 R
+        rng = np.random.default_rng(n)
+        u = rng.normal(size=(300, 3))
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        targets = Rotation.from_rotvec(u * (0.9 * tmax * rng.random(300)[:, None] ** (1 / 3)))
+        members = Rotation.from_matrix(R)
+        nearest = max(np.linalg.norm((members.inv() * targets[i]).as_rotvec(), axis=1).min() for i in range(300))
+        assert nearest < 2.0 * tmax * (4 * math.pi / (3 * n)) ** (1 / 3), nearest / tmax
 
 
 def test_expand_grid_layout(orc):
