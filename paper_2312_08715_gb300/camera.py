@@ -2,8 +2,8 @@
 poses around the previous estimate. Each stage renders every hypothesised camera's view of
 the whole scene (b3d_render_camera_batch), scores the images (b3d_score_depth_batch),
 normalises and draws (b3d_lse_resample); the best drawn cell centres the next stage, and
-the frame's estimate is the best drawn cell of all stages (a finer grid need not contain the
-coarser grid's best pose: its rotation set has no identity). Argument marshalling and the
+the frame's estimate is the best drawn cell of all stages (each grid contains its centre,
+but a stage's draws need not include it). Argument marshalling and the
 choice of the best drawn cell only; every render, score, normalisation and draw runs in the
 library.
 """
