@@ -191,7 +191,7 @@ class StageSpec:
     step: float
     rot_kind: int   # 0 Fibonacci-sphere set, 1 perturbation set
     n_rot: int
-    rot_max: float  # radians (perturbation half-range)
+    rot_max: float  # radians (radius of the perturbation set's ball of rotation vectors)
 
 
 @dataclasses.dataclass
