@@ -178,8 +178,11 @@ static void pixel_range(double lo, double hi, double tol, int n, int *a, int *b)
     *b = (int)fb;
 }
 
-int orc_render(const orc_camera *cam, const orc_scene *sc, int32_t slot, const double *slot_pose,
-               double edge_tol_px, double z_tol_rel, double *depth, int32_t *triid, uint8_t *flags) {
+/* zmove (optional, with flags): per pixel, the largest |depth change| among the alternatives
+ * that set its flags (0 where none). */
+static int render_core(const orc_camera *cam, const orc_scene *sc, int32_t slot, const double *slot_pose,
+                       double edge_tol_px, double z_tol_rel, double *depth, int32_t *triid, uint8_t *flags,
+                       double *zmove) {
     if (!cam || !sc || !depth || !triid || cam->width <= 0 || cam->height <= 0) return ORC_EINVAL;
     const int W = cam->width, H = cam->height;
     const int64_t P = (int64_t)W * H;
@@ -191,7 +194,10 @@ int orc_render(const orc_camera *cam, const orc_scene *sc, int32_t slot, const d
 
     for (int pass = 0; pass < (flags ? 2 : 1); ++pass) {
         if (pass == 1)
-            for (int64_t i = 0; i < P; ++i) flags[i] = 0;
+            for (int64_t i = 0; i < P; ++i) {
+                flags[i] = 0;
+                if (zmove) zmove[i] = 0.0;
+            }
         for (int o = 0; o < sc->n_obj; ++o) {
             const double *Po = object_pose(sc, o, slot, slot_pose);
             const double *verts = sc->verts + 3 * sc->v_off[o];
@@ -230,6 +236,7 @@ int orc_render(const orc_camera *cam, const orc_scene *sc, int32_t slot, const d
                             if (z <= zb * (1.0 + z_tol_rel)) {
                                 flags[i] |= 1;
                                 if (fabs(z - zb) > z_tol_rel * zb) flags[i] |= 2;
+                                if (zmove) zmove[i] = fmax(zmove[i], fabs(z - zb));
                             }
                         }
                     }
@@ -245,9 +252,13 @@ int orc_render(const orc_camera *cam, const orc_scene *sc, int32_t slot, const d
                     double alt = isinf(second_z[i]) ? cam->far_z : second_z[i];
                     flags[i] |= 1;
                     if (fabs(alt - best_z[i]) > z_tol_rel * best_z[i]) flags[i] |= 2;
+                    if (zmove) zmove[i] = fmax(zmove[i], fabs(alt - best_z[i]));
                 }
                 /* near-equal depths: the id decided by the depth test could swap */
-                if (second_z[i] - best_z[i] <= z_tol_rel * best_z[i]) flags[i] |= 1;
+                if (second_z[i] - best_z[i] <= z_tol_rel * best_z[i]) {
+                    flags[i] |= 1;
+                    if (zmove) zmove[i] = fmax(zmove[i], second_z[i] - best_z[i]);
+                }
             }
         } else {
             depth[i] = cam->far_z;
@@ -255,6 +266,11 @@ int orc_render(const orc_camera *cam, const orc_scene *sc, int32_t slot, const d
     }
     free(best_z); free(second_z); free(best_m);
     return ORC_OK;
+}
+
+int orc_render(const orc_camera *cam, const orc_scene *sc, int32_t slot, const double *slot_pose,
+               double edge_tol_px, double z_tol_rel, double *depth, int32_t *triid, uint8_t *flags) {
+    return render_core(cam, sc, slot, slot_pose, edge_tol_px, z_tol_rel, depth, triid, flags, NULL);
 }
 
 /* Depth with visibility held fixed: pixel i keeps triangle triid[i] (rendered with the
@@ -406,11 +422,21 @@ static double count_flip_bound(const orc_camera *cam, const orc_lik *lk, int n, 
  * Outputs per hypothesis h (each optional except ll):
  *   ll[h]     = sum_i l_i
  *   scale[h]  = sum_i |l_i|                (the tolerance scale)
- *   bound[h]  = largest |change of ll| that FP32-resolution decisions could cause: for
- *               every depth-ambiguous rendered pixel (flag bit 1), one point's jump for
- *               each observed pixel whose window contains it; plus, for kind 0, the change
- *               of l_i when its borderline pairs (|d^2 - r^2| <= border_tol r^2) flip.
- *   n_flag[h] = number of depth-ambiguous rendered pixels; n_border[h] = borderline pairs.
+ *   bound[h]  = largest |change of ll| that FP32-resolution decisions could cause:
+ *               - every depth-ambiguous rendered pixel j (flag bit 1) may move anywhere:
+ *                 one point's jump for each valid observed pixel whose window contains it;
+ *               - a rendered pixel j whose id is a tie but whose depth stays within
+ *                 z_tol_rel (bit 0 without bit 1) may move along its ray to the depth of
+ *                 an alternative: by up to delta_j = m_j |r_j|, m_j the largest depth
+ *                 change among the alternatives that set its flag (0 for coplanar ones);
+ *               - kind 0: the change of l_i when its borderline pairs flip, a pair (i, j)
+ *                 being borderline when |d^2 - r^2| <= border_tol r^2 or, for such a tie
+ *                 pixel j, when |d - r| <= delta_j;
+ *               - kind 1: for each tie pixel j and valid observed i in its window, the
+ *                 change of l_i when S_i moves by the Gaussian's steepest slope
+ *                 (2 pi s^2)^(-3/2) e^(-1/2) / s times delta_j.
+ *   n_flag[h] = number of depth-ambiguous rendered pixels; n_border[h] = pairs within the
+ *               border_tol band.
  */
 int orc_score(const orc_camera *cam, const orc_scene *sc, int32_t slot, int64_t n_hyp, const double *poses,
               const orc_lik *lk, const double *depth_obs, double edge_tol_px, double z_tol_rel, double border_tol,
@@ -430,12 +456,14 @@ int orc_score(const orc_camera *cam, const orc_scene *sc, int32_t slot, int64_t 
         double *depth = malloc(sizeof(double) * P), *ell = malloc(sizeof(double) * P);
         int32_t *tid = malloc(sizeof(int32_t) * P), *cnt = malloc(sizeof(int32_t) * P);
         uint8_t *fl = want_flags ? malloc(P) : NULL;
-        if (!depth || !ell || !tid || !cnt || (want_flags && !fl)) {
+        double *ss = want_flags && lk->kind == 1 ? malloc(sizeof(double) * P) : NULL;
+        double *zmv = want_flags ? malloc(sizeof(double) * P) : NULL;
+        if (!depth || !ell || !tid || !cnt || (want_flags && (!fl || !zmv)) || (want_flags && lk->kind == 1 && !ss)) {
             err = ORC_ENOMEM;
         } else {
-            orc_render(cam, sc, slot, poses + 16 * h, edge_tol_px, z_tol_rel, depth, tid, fl);
+            render_core(cam, sc, slot, poses + 16 * h, edge_tol_px, z_tol_rel, depth, tid, fl, zmv);
             int64_t nb = 0;
-            orc_pixel_loglik(cam, lk, depth, tid, depth_obs, border_tol, ell, cnt, NULL, &nb);
+            orc_pixel_loglik(cam, lk, depth, tid, depth_obs, border_tol, ell, cnt, ss, &nb);
             double s = 0, a = 0, bd = 0;
             int32_t nf = 0;
             for (int64_t i = 0; i < P; ++i) {
@@ -455,7 +483,32 @@ int orc_score(const orc_camera *cam, const orc_scene *sc, int32_t slot, int64_t 
                                 if (!isnan(ell[(int64_t)yi * W + xi])) bd += jump;
                             }
                     }
-                if (lk->kind == 0 && nb > 0) {
+                int n_tie = 0; /* id ties whose depth may move, by at most z_tol (bit 0 only) */
+                for (int64_t j = 0; j < P; ++j)
+                    if ((fl[j] & 3) == 1 && zmv[j] > 0 && !(lk->miss_mode == 1 && tid[j] < 0)) ++n_tie;
+                if (lk->kind == 1 && n_tie > 0) {
+                    double V, K;
+                    lik_constants(cam, lk, &V, &K);
+                    const double s_ = lk->radius, pa = lk->p_outlier / V, pb = (1.0 - lk->p_outlier) / K;
+                    const double slope = pow(2.0 * ORC_PI * s_ * s_, -1.5) * exp(-0.5) / s_;
+                    for (int y = 0; y < H; ++y)
+                        for (int x = 0; x < W; ++x) {
+                            const int64_t j = (int64_t)y * W + x;
+                            if ((fl[j] & 3) != 1 || (lk->miss_mode == 1 && tid[j] < 0)) continue;
+                            double rj[3];
+                            pixel_ray(cam, x, y, rj);
+                            const double dN = slope * zmv[j] * sqrt(dot3(rj, rj));
+                            for (int dy = -w; dy <= w; ++dy)
+                                for (int dx = -w; dx <= w; ++dx) {
+                                    int xi = x + dx, yi = y + dy;
+                                    if (xi < 0 || xi >= W || yi < 0 || yi >= H) continue;
+                                    const int64_t i = (int64_t)yi * W + xi;
+                                    if (isnan(ell[i])) continue;
+                                    bd += log(pa + pb * (ss[i] + dN)) - log(pa + pb * fmax(ss[i] - dN, 0.0));
+                                }
+                        }
+                }
+                if (lk->kind == 0 && (nb > 0 || n_tie > 0)) {
                     /* recount borderline pairs per observed pixel to size their steps */
                     const double r2 = lk->radius * lk->radius;
                     for (int y = 0; y < H; ++y)
@@ -478,7 +531,10 @@ int orc_score(const orc_camera *cam, const orc_scene *sc, int32_t slot, int64_t 
                                         double d = depth_obs[i] * ri[k] - depth[j] * rj[k];
                                         d2 += d * d;
                                     }
-                                    if (fabs(d2 - r2) <= border_tol * r2) ++k_b;
+                                    const int tie = (fl[j] & 3) == 1;
+                                    if (fabs(d2 - r2) <= border_tol * r2 ||
+                                        (tie && fabs(sqrt(d2) - lk->radius) <= zmv[j] * sqrt(dot3(rj, rj))))
+                                        ++k_b;
                                 }
                             if (k_b > 0) bd += count_flip_bound(cam, lk, cnt[i], k_b);
                         }
@@ -490,7 +546,7 @@ int orc_score(const orc_camera *cam, const orc_scene *sc, int32_t slot, int64_t 
             if (n_flag) n_flag[h] = nf;
             if (n_border) n_border[h] = (int32_t)nb;
         }
-        free(depth); free(ell); free(tid); free(cnt); free(fl);
+        free(depth); free(ell); free(tid); free(cnt); free(fl); free(ss); free(zmv);
     }
     return err;
 }
