@@ -930,6 +930,278 @@ int orc_score_grad(const orc_camera *cam, const orc_scene *sc, int32_t slot, int
     return err;
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Bound on the gradient change FP32 visibility decisions can cause (kind 1)              */
+/* ------------------------------------------------------------------------------------ */
+/*
+ * The gradient of orc_score_grad holds visibility fixed, so a rendered pixel j whose
+ * assignment FP32 may decide differently (flagged by orc_render with edge_tol_px and
+ * z_tol_rel) can give the FP32 path another gradient. The alternatives of a flagged pixel
+ * are the ones that set its flag:
+ *   - a triangle other than the winner whose coverage is within edge_tol_px of its boundary
+ *     and whose depth is not behind the winner's by more than z_tol_rel;
+ *   - a covering triangle whose depth is within z_tol_rel of the winner's;
+ *   - when the winner's own coverage is within edge_tol_px: the nearest other covering
+ *     triangle, else the background (a miss).
+ * For each alternative the exact change of (dLL/dxi [6], dLL/ds, dLL/dp_out) when j alone
+ * switches to it (all other pixels held) is formed from the definitions of orc_score_grad:
+ * the observed pixels i in win(j) get S_i' = S_i - N(qt_i - q_j) + N(qt_i - q_j'); the
+ * slot object's rendered pixels k within 2w of j get g_k through the changed 1/p_i; j
+ * itself gets g_j' dz_j'/dxi (dz/dxi from the alternative's plane; 0 when it is not the
+ * slot object's). gbound[h, 0..7] is the sum over flagged pixels of the largest absolute
+ * change, component by component, over their alternatives: a first-order bound (single
+ * switches added, their interaction neglected). n_flag[h] counts the flagged pixels.
+ */
+#define ORC_MAX_ALT 8
+
+typedef struct {
+    int32_t t;     /* global triangle id, -1 for the background */
+    double z;      /* its depth at the pixel */
+    double n[3];   /* its camera-frame plane normal (slot object only) */
+} orc_alt;
+
+static void tri_normal_cam(const orc_scene *sc, int32_t slot, const double *slot_pose, int32_t g, double n[3]) {
+    int o = 0;
+    while (o + 1 < sc->n_obj && g >= sc->f_off[o + 1]) ++o;
+    const double *Po = object_pose(sc, o, slot, slot_pose);
+    const double *verts = sc->verts + 3 * sc->v_off[o];
+    const int32_t *f = sc->faces + 3 * (int64_t)g;
+    double A[3], B[3], C[3], e1[3], e2[3];
+    apply_pose(Po, verts + 3 * (int64_t)f[0], A);
+    apply_pose(Po, verts + 3 * (int64_t)f[1], B);
+    apply_pose(Po, verts + 3 * (int64_t)f[2], C);
+    for (int k = 0; k < 3; ++k) { e1[k] = B[k] - A[k]; e2[k] = C[k] - A[k]; }
+    cross3(e1, e2, n);
+}
+
+static void add_alt(orc_alt *list, uint8_t *cnt, int32_t t, double z, const double n[3]) {
+    for (int k = 0; k < *cnt; ++k)
+        if (list[k].t == t) return;
+    if (*cnt >= ORC_MAX_ALT) return;
+    orc_alt *a = &list[(*cnt)++];
+    a->t = t;
+    a->z = z;
+    for (int k = 0; k < 3; ++k) a->n[k] = n ? n[k] : 0.0;
+}
+
+int orc_score_grad_bound(const orc_camera *cam, const orc_scene *sc, int32_t slot, int64_t n_hyp,
+                         const double *poses, const orc_lik *lk, const double *depth_obs, double edge_tol_px,
+                         double z_tol_rel, double *gbound, int32_t *n_flag, int32_t n_threads) {
+    if (!cam || !sc || !lk || lk->kind != 1 || !depth_obs || !gbound || (n_hyp > 0 && !poses)) return ORC_EINVAL;
+    if (slot < 0 || slot >= sc->n_obj || !(lk->radius > 0) || lk->half_window < 0 || lk->half_window > 4)
+        return ORC_EINVAL;
+    const int W = cam->width, H = cam->height, w = lk->half_window;
+    const int64_t P = (int64_t)W * H;
+    double V, K;
+    lik_constants(cam, lk, &V, &K);
+    const double s = lk->radius, s2 = s * s;
+    const double gnorm = pow(2.0 * ORC_PI * s2, -1.5);
+    const double a = lk->p_outlier / V, b = (1.0 - lk->p_outlier) / K;
+    const int64_t f0 = sc->f_off[slot], f1 = sc->f_off[slot + 1];
+    const double tol = edge_tol_px;
+    int err = ORC_OK;
+#ifdef _OPENMP
+    if (n_threads <= 0) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
+#endif
+    for (int64_t h = 0; h < n_hyp; ++h) {
+        const double *Ph = poses + 16 * h;
+        double *depth = malloc(sizeof(double) * P), *S = malloc(sizeof(double) * P);
+        double *dS = malloc(sizeof(double) * P), *pp = malloc(sizeof(double) * P);
+        double *wm = malloc(sizeof(double) * P), *sec_z = malloc(sizeof(double) * P);
+        double *J = malloc(sizeof(double) * 6 * P);
+        int32_t *tid = malloc(sizeof(int32_t) * P), *sec_t = malloc(sizeof(int32_t) * P);
+        uint8_t *fl = malloc(P), *nalt = malloc(P);
+        orc_alt *alts = malloc(sizeof(orc_alt) * ORC_MAX_ALT * P);
+        if (!depth || !S || !dS || !pp || !wm || !sec_z || !J || !tid || !sec_t || !fl || !nalt || !alts) {
+            err = ORC_ENOMEM;
+            goto done;
+        }
+        orc_render(cam, sc, slot, Ph, edge_tol_px, z_tol_rel, depth, tid, fl);
+        for (int64_t i = 0; i < P; ++i) { nalt[i] = 0; wm[i] = INFINITY; sec_z[i] = INFINITY; sec_t[i] = -1; }
+        /* alternatives of the flagged pixels: one pass over every triangle's pixel box */
+        for (int o = 0; o < sc->n_obj; ++o) {
+            const double *Po = object_pose(sc, o, slot, Ph);
+            const double *verts = sc->verts + 3 * sc->v_off[o];
+            for (int64_t f = sc->f_off[o]; f < sc->f_off[o + 1]; ++f) {
+                tri_cam t;
+                if (!setup_tri(cam, Po, verts, sc->faces + 3 * f, &t)) continue;
+                double umin = fmin(t.su[0], fmin(t.su[1], t.su[2])), umax = fmax(t.su[0], fmax(t.su[1], t.su[2]));
+                double vmin = fmin(t.sv[0], fmin(t.sv[1], t.sv[2])), vmax = fmax(t.sv[0], fmax(t.sv[1], t.sv[2]));
+                int x0, x1, y0, y1;
+                pixel_range(umin, umax, tol, W, &x0, &x1);
+                pixel_range(vmin, vmax, tol, H, &y0, &y1);
+                for (int y = y0; y <= y1; ++y)
+                    for (int x = x0; x <= x1; ++x) {
+                        const int64_t i = (int64_t)y * W + x;
+                        if (!fl[i]) continue;
+                        double r[3];
+                        pixel_ray(cam, x, y, r);
+                        const double m = coverage_margin(&t, x + 0.5, y + 0.5);
+                        const double z = plane_depth(&t, r);
+                        if (!(z <= cam->far_z)) continue;
+                        const int32_t g = (int32_t)f;
+                        if (g == tid[i]) { wm[i] = m; continue; }
+                        const double zb = tid[i] >= 0 ? depth[i] : cam->far_z;
+                        if ((fabs(m) < tol && z <= zb * (1.0 + z_tol_rel)) || (m >= 0 && z - zb <= z_tol_rel * zb))
+                            add_alt(alts + ORC_MAX_ALT * i, nalt + i, g, z, t.n);
+                        if (m >= 0 && (z < sec_z[i] || (z == sec_z[i] && g < sec_t[i]))) { sec_z[i] = z; sec_t[i] = g; }
+                    }
+            }
+        }
+        for (int64_t i = 0; i < P; ++i) {
+            if (!fl[i] || tid[i] < 0 || !(wm[i] < tol)) continue;
+            if (sec_t[i] >= 0) {
+                double n[3];
+                tri_normal_cam(sc, slot, Ph, sec_t[i], n);
+                add_alt(alts + ORC_MAX_ALT * i, nalt + i, sec_t[i], sec_z[i], n);
+            } else {
+                add_alt(alts + ORC_MAX_ALT * i, nalt + i, -1, cam->far_z, NULL);
+            }
+        }
+        /* observed side: S_i, dS_i/ds, p_i; rendered side: dz_k/dxi of the slot's pixels */
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const int64_t i = (int64_t)y * W + x;
+                pp[i] = 0;
+                const double d_obs = depth_obs[i];
+                if (!(d_obs > 0) || !isfinite(d_obs)) continue;
+                double ri[3];
+                pixel_ray(cam, x, y, ri);
+                double Si = 0, dSi = 0;
+                for (int dy = -w; dy <= w; ++dy)
+                    for (int dx = -w; dx <= w; ++dx) {
+                        int xj = x + dx, yj = y + dy;
+                        if (xj < 0 || xj >= W || yj < 0 || yj >= H) continue;
+                        const int64_t j = (int64_t)yj * W + xj;
+                        if (lk->miss_mode == 1 && tid[j] < 0) continue;
+                        double rj[3], d2 = 0;
+                        pixel_ray(cam, xj, yj, rj);
+                        for (int k = 0; k < 3; ++k) { double d = d_obs * ri[k] - depth[j] * rj[k]; d2 += d * d; }
+                        const double N = gnorm * exp(-d2 / (2.0 * s2));
+                        Si += N;
+                        dSi += N * (d2 / (s2 * s) - 3.0 / s);
+                    }
+                S[i] = Si; dS[i] = dSi; pp[i] = a + b * Si;
+            }
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const int64_t k = (int64_t)y * W + x;
+                for (int c = 0; c < 6; ++c) J[6 * k + c] = 0;
+                if (tid[k] < f0 || tid[k] >= f1) continue;
+                double n[3], r[3], q[3], qxn[3];
+                tri_normal_cam(sc, slot, Ph, tid[k], n);
+                pixel_ray(cam, x, y, r);
+                for (int c = 0; c < 3; ++c) q[c] = depth[k] * r[c];
+                cross3(q, n, qxn);
+                const double nr = dot3(n, r);
+                for (int c = 0; c < 3; ++c) { J[6 * k + c] = n[c] / nr; J[6 * k + 3 + c] = qxn[c] / nr; }
+            }
+        double gb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int32_t nf = 0;
+        double Sn[81], dSn[81], pn[81];  /* the window of j: (2w+1)^2 <= 81 for w <= 4 */
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const int64_t j = (int64_t)y * W + x;
+                if (!nalt[j]) continue;
+                ++nf;
+                double rj[3];
+                pixel_ray(cam, x, y, rj);
+                const int old_pt = !(lk->miss_mode == 1 && tid[j] < 0);
+                const double z_old = depth[j];
+                double worst[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                for (int q = 0; q < nalt[j]; ++q) {
+                    const orc_alt *A = alts + ORC_MAX_ALT * j + q;
+                    const int new_pt = !(lk->miss_mode == 1 && A->t < 0);
+                    const double z_new = A->t >= 0 ? A->z : cam->far_z;
+                    double dlt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    /* observed pixels i in win(j): new S_i, dS_i, p_i; sigma and p_out terms */
+                    for (int dy = -w; dy <= w; ++dy)
+                        for (int dx = -w; dx <= w; ++dx) {
+                            const int ii = (dy + w) * (2 * w + 1) + (dx + w);
+                            int xi = x + dx, yi = y + dy;
+                            pn[ii] = 0;
+                            if (xi < 0 || xi >= W || yi < 0 || yi >= H) continue;
+                            const int64_t i = (int64_t)yi * W + xi;
+                            if (pp[i] == 0) continue;
+                            double ri[3], d2o = 0, d2n = 0;
+                            pixel_ray(cam, xi, yi, ri);
+                            for (int c = 0; c < 3; ++c) {
+                                double qt = depth_obs[i] * ri[c];
+                                d2o += (qt - z_old * rj[c]) * (qt - z_old * rj[c]);
+                                d2n += (qt - z_new * rj[c]) * (qt - z_new * rj[c]);
+                            }
+                            const double No = old_pt ? gnorm * exp(-d2o / (2.0 * s2)) : 0.0;
+                            const double Nn = new_pt ? gnorm * exp(-d2n / (2.0 * s2)) : 0.0;
+                            Sn[ii] = S[i] - No + Nn;
+                            dSn[ii] = dS[i] - (old_pt ? No * (d2o / (s2 * s) - 3.0 / s) : 0.0) +
+                                      (new_pt ? Nn * (d2n / (s2 * s) - 3.0 / s) : 0.0);
+                            pn[ii] = a + b * Sn[ii];
+                            dlt[6] += b * dSn[ii] / pn[ii] - b * dS[i] / pp[i];
+                            dlt[7] += (1.0 / V - Sn[ii] / K) / pn[ii] - (1.0 / V - S[i] / K) / pp[i];
+                        }
+                    /* the slot's rendered pixels k within 2w of j: g_k through the changed p_i */
+                    for (int ky = y - 2 * w; ky <= y + 2 * w; ++ky)
+                        for (int kx = x - 2 * w; kx <= x + 2 * w; ++kx) {
+                            if (kx < 0 || kx >= W || ky < 0 || ky >= H) continue;
+                            const int64_t k = (int64_t)ky * W + kx;
+                            const int is_j = k == j;
+                            const int slot_old = tid[k] >= f0 && tid[k] < f1;
+                            const int slot_new = is_j ? (A->t >= f0 && A->t < f1) : slot_old;
+                            if (!slot_old && !slot_new) continue;
+                            double rk[3];
+                            pixel_ray(cam, kx, ky, rk);
+                            double g_old = 0, g_new = 0;
+                            for (int dy = -w; dy <= w; ++dy)
+                                for (int dx = -w; dx <= w; ++dx) {
+                                    int xi = kx + dx, yi = ky + dy;
+                                    if (xi < 0 || xi >= W || yi < 0 || yi >= H) continue;
+                                    const int64_t i = (int64_t)yi * W + xi;
+                                    if (pp[i] == 0) continue;
+                                    const int in_j = abs(xi - x) <= w && abs(yi - y) <= w;
+                                    const double p_new = in_j ? pn[(yi - y + w) * (2 * w + 1) + (xi - x + w)] : pp[i];
+                                    double ri[3];
+                                    pixel_ray(cam, xi, yi, ri);
+                                    for (int v = 0; v < 2; ++v) {
+                                        if (v == 0 && !slot_old) continue;
+                                        if (v == 1 && !slot_new) continue;
+                                        const double zk = (is_j && v == 1) ? z_new : depth[k];
+                                        double diff[3], d2 = 0;
+                                        for (int c = 0; c < 3; ++c) {
+                                            diff[c] = depth_obs[i] * ri[c] - zk * rk[c];
+                                            d2 += diff[c] * diff[c];
+                                        }
+                                        const double t = gnorm * exp(-d2 / (2.0 * s2)) * dot3(diff, rk) / s2;
+                                        if (v == 0) g_old += b * t / pp[i];
+                                        else g_new += b * t / p_new;
+                                    }
+                                }
+                            double Jn[6];
+                            if (is_j && slot_new) {
+                                double qn[3], qxn[3];
+                                for (int c = 0; c < 3; ++c) qn[c] = z_new * rk[c];
+                                cross3(qn, A->n, qxn);
+                                const double nr = dot3(A->n, rk);
+                                for (int c = 0; c < 3; ++c) { Jn[c] = A->n[c] / nr; Jn[3 + c] = qxn[c] / nr; }
+                            } else {
+                                for (int c = 0; c < 6; ++c) Jn[c] = J[6 * k + c];
+                            }
+                            for (int c = 0; c < 6; ++c)
+                                dlt[c] += (slot_new ? g_new * Jn[c] : 0.0) - (slot_old ? g_old * J[6 * k + c] : 0.0);
+                        }
+                    for (int c = 0; c < 8; ++c) worst[c] = fmax(worst[c], fabs(dlt[c]));
+                }
+                for (int c = 0; c < 8; ++c) gb[c] += worst[c];
+            }
+        for (int c = 0; c < 8; ++c) gbound[8 * h + c] = gb[c];
+        if (n_flag) n_flag[h] = nf;
+    done:
+        free(depth); free(S); free(dS); free(pp); free(wm); free(sec_z); free(J);
+        free(tid); free(sec_t); free(fl); free(nalt); free(alts);
+    }
+    return err;
+}
+
 int orc_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

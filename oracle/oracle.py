@@ -244,6 +244,21 @@ def score_grad(scene, slot, poses, lk: dict, depth_obs, n_threads=0, arrays=None
     return dict(ll=ll, dpose=dpose, dsigma=ds, dpout=dp)
 
 
+def score_grad_bound(scene, slot, poses, lk: dict, depth_obs, edge_tol=1e-4, z_tol=1e-5, n_threads=0, arrays=None):
+    """Per hypothesis, the bound [n, 8] on how far FP32 visibility decisions can move
+    (dLL/dxi [6], dLL/dsigma, dLL/dp_out) of score_grad, and the number of flagged pixels."""
+    sa = arrays or SceneArrays(scene)
+    P = _f64(poses).reshape(-1, 16)
+    n = P.shape[0]
+    gb = np.empty((n, 8))
+    nf = np.empty(n, np.int32)
+    rc = lib().orc_score_grad_bound(C.byref(sa.cam), C.byref(sa.st), C.c_int32(slot), C.c_int64(n), _p(P),
+                                    C.byref(lik(**lk)), _p(_f64(depth_obs)), C.c_double(edge_tol), C.c_double(z_tol),
+                                    _p(gb), _p(nf), C.c_int32(n_threads))
+    assert rc == 0, rc
+    return dict(gbound=gb, n_flag=nf)
+
+
 def max_threads() -> int:
     return int(lib().orc_max_threads())
 

@@ -257,3 +257,85 @@ def test_smooth_bound_of_depth_ties(orc):
             n_obs = (min(x + 1, 7) - max(x - 1, 0) + 1) * (min(y + 1, 7) - max(y - 1, 0) + 1)
             want += n_obs * (math.log(a + b * (g + dN)) - math.log(a + b * (g - dN)))
     assert r["bound"][0] == pytest.approx(want, rel=1e-9)
+
+
+# ---------------------------------------------------------------------------------------
+# the gradient bound
+# ---------------------------------------------------------------------------------------
+
+SMOOTH = dict(kind=1, radius=0.005, p_outlier=0.01, half_window=1)
+
+
+def _grad(orc, scene, obs):
+    g = orc.score_grad(scene, 0, scene.poses[0][None], SMOOTH, obs)
+    return np.concatenate([g["dpose"][0], g["dsigma"], g["dpout"]])
+
+
+def _gbound(orc, scene, obs):
+    r = orc.score_grad_bound(scene, 0, scene.poses[0][None], SMOOTH, obs, edge_tol=EDGE_TOL, z_tol=Z_TOL)
+    return r["gbound"][0], int(r["n_flag"][0])
+
+
+def test_gradient_bound_is_zero_without_flags(orc):
+    """Rectangle x in [-0.25, 0.25], y in [-0.25, 0.125] at z = 1 (screen [2, 6] x [2, 5]):
+    every edge half a pixel from the centres, the diagonal (4v - 3u = 2 through the corners)
+    >= 0.1 px from every centre. No pixel is flagged, so nothing can move the gradient."""
+    sc = _scene([_square(-0.25, 0.25, -0.25, 0.125, 1.0)])
+    assert not _render(orc, sc)[2].any()
+    gb, nf = _gbound(orc, sc, np.full((8, 8), 1.002))
+    assert nf == 0 and (gb == 0).all()
+
+
+@pytest.mark.parametrize("shift_px", [0.0, 0.5 * EDGE_TOL])
+def test_gradient_bound_of_one_edge_pixel_is_its_switch(orc, shift_px):
+    """A one-row rectangle x in [-0.1875 + shift/8, 0.25], y in [-0.125, 0] at z = 1 covers
+    row 3, columns 2..5 (column 2 only when shift = 0, on its edge). Pixel (3, 2) is the
+    only flagged pixel, its one alternative the other assignment (background or the
+    rectangle). The two renders differ at that pixel alone (the plane and every other
+    pixel's depth, ray and normal are the same), so the gradient of the FP64 definition
+    (orc_score_grad, pinned by central differences) changes by exactly the switch the bound
+    adds: gbound = |grad(shift = 0) - grad(shift = tol/2)|, component by component, seen
+    from either side. The observation is a wall 2 mm behind the plane."""
+    obs = np.full((8, 8), 1.002)
+    sc = _scene([_square(-0.1875 + shift_px / 8.0, 0.25, -0.125, 0.0, 1.0)])
+    sc_in = _scene([_square(-0.1875, 0.25, -0.125, 0.0, 1.0)])
+    sc_out = _scene([_square(-0.1875 + 0.5 * EDGE_TOL / 8.0, 0.25, -0.125, 0.0, 1.0)])
+    assert (_render(orc, sc_in)[1][3, 2] >= 0) and (_render(orc, sc_out)[1][3, 2] < 0)
+    gb, nf = _gbound(orc, sc, obs)
+    want = np.abs(_grad(orc, sc_in, obs) - _grad(orc, sc_out, obs))
+    assert nf == 1
+    assert want[2] > 0 and want[6] > 0 and want[7] > 0  # (x, y and z-rotation terms vanish face-on)
+    np.testing.assert_allclose(gb, want, rtol=1e-9, atol=1e-12 * want.max())
+
+
+def _roof(right_first):
+    """A crease: plane z = 1 + (x_e - x)/2 for x in [-0.25, x_e] and plane z = 1 for x in
+    [x_e, 0.25], x_e = -0.0625 (on the centres of column 3), y in [-0.125, 0] (row 3). Both
+    planes give depth 1 on the crease, with different normals."""
+    xe = -0.0625
+    zl = 1.0 + 0.5 * (xe + 0.25)
+    left = [[-0.25, -0.125, zl], [xe, -0.125, 1.0], [xe, 0.0, 1.0], [-0.25, 0.0, zl]]
+    right = [[xe, -0.125, 1.0], [0.25, -0.125, 1.0], [0.25, 0.0, 1.0], [xe, 0.0, 1.0]]
+    v = np.array(right + left if right_first else left + right, np.float32)
+    f = np.array([[0, 1, 2], [0, 2, 3], [4, 5, 6], [4, 6, 7]], np.int32)
+    return _scene([synth.Mesh(verts=v, faces=f)])
+
+
+def test_gradient_bound_of_a_crease_pixel_is_its_switch(orc):
+    """On the crease pixel (3, 3) both planes reach depth 1 exactly: an id tie between two
+    triangles of the slot object with different planes, so the pixel's dz/dxi depends on
+    which wins (bit 0; the depth does not move). Listing the right plane's triangles first
+    hands the tie to the other plane (equal depths go to the smaller id) and changes
+    nothing else, so the gradient difference of the two listings is exactly the switch."""
+    obs = np.full((8, 8), 1.002)
+    a, b = _roof(False), _roof(True)
+    ta, tb = _render(orc, a)[1], _render(orc, b)[1]
+    # the first-listed plane wins in each: the left plane in a, the right plane in b
+    assert 0 <= ta[3, 3] < 2 and 0 <= tb[3, 3] < 2
+    fa = _render(orc, a)[2]
+    assert fa[3, 3] == 1 and fa.sum() == 1
+    gb, nf = _gbound(orc, a, obs)
+    want = np.abs(_grad(orc, a, obs) - _grad(orc, b, obs))
+    assert nf == 1
+    np.testing.assert_allclose(gb, want, rtol=1e-9, atol=1e-12 * np.abs(_grad(orc, a, obs)).max())
+    assert want[:6].max() > 0 and want[6:].max() == 0  # the depth stays: sigma and p_out do not move
