@@ -41,3 +41,42 @@ def jitter_poses(rng, pose, n, trans=0.02, rot_deg=10.0):
 def ll_tolerance(ref):
     """|LL_gpu - LL_oracle| <= 1e-4 * sum_i |l_i| + the oracle's ambiguity bound."""
     return 1e-4 * ref["scale"] + ref["bound"]
+
+
+def check_ll(got, ref, what, tight_frac=0.9):
+    """Every hypothesis within 1e-4 * scale + the oracle's FP32-decision bound, and most
+    of them within 1e-4 * scale alone (the bound is not what makes them pass)."""
+    tol = ll_tolerance(ref)
+    err = np.abs(np.asarray(got, np.float64) - ref["ll"])
+    bad = np.nonzero(err > tol)[0]
+    assert bad.size == 0, f"{what}: {bad.size} hypotheses outside tolerance, e.g. {bad[:5]} err {err[bad[:5]]} tol {tol[bad[:5]]}"
+    tight = err <= 1e-4 * ref["scale"]
+    print(f"{what}: n={err.size} max|dLL|={err.max():.3g} median={np.median(err):.3g} "
+          f"tight={tight.mean():.3f} flagged={np.mean(ref['bound'] > 0):.3f}")
+    assert tight.mean() >= tight_frac, f"{what}: only {tight.mean():.2f} of hypotheses within 1e-4 * scale"
+    return err
+
+
+def check_grad(dpose, dsigma, dpout, ref, gbound, what):
+    """Per hypothesis, each gradient (the se(3) pose gradient by its norm, dLL/dsigma,
+    dLL/dp_out) within 1e-3 relative of the FP64 oracle plus the oracle's bound on what FP32
+    visibility decisions can move it (oracle.score_grad_bound: the exact change of switching
+    each flagged pixel to each of its alternatives, summed); and every hypothesis whose bound
+    is zero within 1e-3 alone. Returns the fraction of hypotheses within 1e-3 alone."""
+    rows = np.linalg.norm
+    parts = (("pose", dpose, ref["dpose"], rows(gbound[:, :6], axis=1), lambda a: rows(a, axis=1)),
+             ("sigma", dsigma, ref["dsigma"], gbound[:, 6], np.abs),
+             ("p_out", dpout, ref["dpout"], gbound[:, 7], np.abs))
+    tight_all = np.ones(len(ref["ll"]), bool)
+    for name, g, r, b, norm in parts:
+        err = norm(np.asarray(g, np.float64) - r)
+        scale = norm(r)
+        bad = np.nonzero(err > 1e-3 * scale + b)[0]
+        assert bad.size == 0, f"{what} {name}: hypotheses {bad} rel err {(err / scale)[bad]} bound {(b / scale)[bad]}"
+        tight = err <= 1e-3 * scale
+        loose = np.nonzero(~tight & (b == 0))[0]
+        assert loose.size == 0, f"{what} {name}: unbounded hypotheses {loose} rel err {(err / scale)[loose]}"
+        print(f"{what} {name}: max rel {np.max(err / scale):.2e} median {np.median(err / scale):.2e} "
+              f"within 1e-3 alone {tight.mean():.3f} bounded {np.mean(b > 0):.3f}")
+        tight_all &= tight
+    return float(tight_all.mean())

@@ -30,12 +30,14 @@ def _perturb(rng, H, n, trans, rot_deg):
     return np.stack(out).astype(np.float32)
 
 
-@pytest.mark.parametrize("size", [25, 64])
-def test_render_camera_matches_oracle(orc, size):
+@pytest.mark.parametrize("size,n", [(25, 64), (64, 24)])
+def test_render_camera_matches_oracle(orc, size, n):
+    """Ids identical except at flagged pixels, and at no more than 1e-4 of all pixels (40,000
+    and 98,304 pixels here, so 4 and 9 pixels); depth within 1e-5 relative where ids agree."""
     from paper_2312_08715_gb300 import b3d
     v = synth.camera_video(0, size, n_frames=2)
     rng = np.random.default_rng(3)
-    Hs = _perturb(rng, v.cam_from_world[0], 6, 0.01, 3.0)
+    Hs = _perturb(rng, v.cam_from_world[0], n, 0.01, 3.0)
     ctx = b3d.Context(0)
     ids = [ctx.load_mesh(m, closed=c) for m, c in zip(v.scene.meshes, _closed(v.scene))]
     ctx.set_scene(v.scene.camera, ids, v.scene.poses, np.zeros((size, size), np.float32))
@@ -53,7 +55,8 @@ def test_render_camera_matches_oracle(orc, size):
         assert (np.abs(d[k][agree] - od[agree]) / od[agree]).max() <= 1e-5
         n_mis += int(mis.sum())
         n_px += mis.size
-    assert n_mis <= max(1, 1e-3 * n_px)
+    print(f"camera renders {size}x{size}: {n_mis} of {n_px} ids differ (all at flagged pixels)")
+    assert n_mis <= max(1, 1e-4 * n_px)
     ctx.close()
 
 

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 from paper_2312_08715_gb300 import synth
-from _scenes import gpu_context, jitter_poses, ll_tolerance, observed
+from _scenes import check_grad, check_ll, gpu_context, jitter_poses, ll_tolerance, observed
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -39,18 +39,7 @@ def _check_render(orc, scene, slot, poses, depth, tid, max_frac=1e-4):
     return n_mis
 
 
-def _check_ll(got, ref, what):
-    """Every hypothesis within 1e-4 * scale + the oracle's FP32-decision bound, and most
-    of them within 1e-4 * scale alone (the bound is not what makes them pass)."""
-    tol = ll_tolerance(ref)
-    err = np.abs(got.astype(np.float64) - ref["ll"])
-    bad = np.nonzero(err > tol)[0]
-    assert bad.size == 0, f"{what}: {bad.size} hypotheses outside tolerance, e.g. {bad[:5]} err {err[bad[:5]]} tol {tol[bad[:5]]}"
-    tight = err <= 1e-4 * ref["scale"]
-    print(f"{what}: n={err.size} max|dLL|={err.max():.3g} median={np.median(err):.3g} "
-          f"tight={tight.mean():.3f} flagged={np.mean(ref['bound'] > 0):.3f}")
-    assert tight.mean() >= 0.9, f"{what}: only {tight.mean():.2f} of hypotheses within 1e-4 * scale"
-    return err
+_check_ll = check_ll
 
 
 def _check_argmax(got, ref):
@@ -477,6 +466,44 @@ def test_lse_resample_degenerate(orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("n,n_shards", [(145800, 3), (2049, 2), (7, 3)])
+def test_lse_resample_shards_match_the_unsplit_call(orc, n, n_shards):
+    """A categorical split into contiguous shards, as over ranks (the exchange of a sharded
+    C2F stage): each shard's log normaliser, then each shard's draws by
+    b3d_lse_resample_shard with its share of the probability, one shard after another on
+    this GPU. Combined by maximum, every draw has one owner and the draws are the unsplit
+    call's and the oracle's, except draws whose CDF margin is below 1e-5."""
+    from paper_2312_08715_gb300 import b3d, multigpu
+    ctx = b3d.Context(0)
+    ll = synth.random_ll(np.random.default_rng(n + 1), n)
+    t = torch.as_tensor(ll, device="cuda")
+    m, seed, stage = 100, 77, 2
+    spans = [multigpu.shard_range(n, r, n_shards) for r in range(n_shards)]
+    logz_all = [float(ctx.lse_resample(t[b:e], 0, seed, stage)[0].item()) for b, e in spans]
+    idx = np.full(m, -1, np.int64)
+    logq = np.full(m, -np.inf)
+    owners = np.zeros(m, np.int64)
+    for r, (b, e) in enumerate(spans):
+        Z, before, mass = multigpu.shard_masses(logz_all, r)
+        zl, i, q = ctx.lse_resample_shard(t[b:e], m, seed, stage, before, mass, Z, b)
+        ctx.sync()
+        assert float(_np(zl)[0]) == pytest.approx(logz_all[r], abs=0)
+        i, q = _np(i).astype(np.int64), _np(q).astype(np.float64)
+        owners += i >= 0
+        assert ((i == -1) | ((i >= b) & (i < e))).all()
+        idx, logq = np.maximum(idx, i), np.maximum(logq, q)
+    assert (owners == 1).all()
+    _, gi, gq = ctx.lse_resample(t, m, seed, stage)
+    ctx.sync()
+    oi, oq, om = orc.resample(ll.astype(np.float64), m, seed, stage)
+    solid = om > 1e-5
+    np.testing.assert_array_equal(idx[solid], oi[solid])
+    np.testing.assert_array_equal(idx[solid], _np(gi)[solid])
+    Z, _ = orc.lse(ll.astype(np.float64))
+    np.testing.assert_allclose(logq[solid], oq[solid], atol=1e-4 * max(1.0, abs(Z)))
+    ctx.close()
+
+
 # ---------------------------------------------------------------------------------------
 # coarse-to-fine enumeration
 # ---------------------------------------------------------------------------------------
@@ -556,6 +583,9 @@ def test_enumerate_c2f_tabletop_tracks_hidden_pose(orc, tabletop):
 # ---------------------------------------------------------------------------------------
 
 def test_score_grad_matches_oracle(orc, single_object):
+    """Every hypothesis: within 1e-3 relative of the oracle's gradient plus its bound on what
+    FP32 visibility decisions at flagged pixels can move it; at least 6 of the 8 within 1e-3
+    alone (so the bound cannot be what makes the test pass)."""
     wl = single_object
     sc = wl.scene
     obs = observed(orc, wl)
@@ -567,13 +597,9 @@ def test_score_grad_matches_oracle(orc, single_object):
     ctx.sync()
     sref = orc.score(sc, 0, poses, lik, obs)
     _check_ll(ll, sref, "score_grad forward")
-    for k in range(len(poses)):
-        if sref["bound"][k] > 0:
-            continue  # a flagged pixel may change visibility between FP32 and FP64
-        g, gr = dpose[k], ref["dpose"][k]
-        assert np.linalg.norm(g - gr) <= 1e-3 * np.linalg.norm(gr), (k, g, gr)
-        assert ds[k] == pytest.approx(ref["dsigma"][k], rel=1e-3)
-        assert dp[k] == pytest.approx(ref["dpout"][k], rel=1e-3)
+    gb = orc.score_grad_bound(sc, 0, poses, lik, obs)["gbound"]
+    frac = check_grad(dpose, ds, dp, ref, gb, "single object")
+    assert frac >= 6 / 8, frac
 
 
 # ---------------------------------------------------------------------------------------

@@ -5,7 +5,7 @@ window; and gradient-based pose refinement after enumeration."""
 import numpy as np
 import pytest
 
-from _scenes import gpu_context, jitter_poses, observed
+from _scenes import check_grad, gpu_context, jitter_poses, observed
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -66,23 +66,22 @@ def test_noise_gradients_match_central_differences(scene):
 
 
 def test_pose_gradient_matches_oracle_on_tabletop(orc, scene):
-    """Every hypothesis of this five-object scene has a few flagged pixels (edge or depth
-    ties whose visibility FP32 and FP64 may decide differently, each moving the gradient by
-    that pixel's share), so the bar is on the distribution: half of the hypotheses within
-    1e-3 of the FP64 oracle, all within 2e-2."""
+    """Every hypothesis of this five-object scene, every gradient (pose, sigma, p_out):
+    within 1e-3 relative of the FP64 oracle plus the oracle's bound on what the FP32 path's
+    visibility decisions at flagged pixels (edge or depth ties) can move it; the hypotheses
+    none of whose flagged pixels can move a gradient are held to 1e-3 alone, and at least
+    90% of all hypotheses are within 1e-3 alone."""
     wl, obs = scene
     ctx = gpu_context(wl.scene, obs)
-    poses = jitter_poses(np.random.default_rng(5), wl.hidden, 24, trans=0.005, rot_deg=3)
+    poses = jitter_poses(np.random.default_rng(5), wl.hidden, 48, trans=0.005, rot_deg=3)
     ll, dpose, ds, dp = (_np(x) for x in ctx.score_grad(wl.slot, poses, LIK))
     ctx.sync()
     ref = orc.score_grad(wl.scene, wl.slot, poses, LIK, obs)
     sref = orc.score(wl.scene, wl.slot, poses, LIK, obs)
     assert (np.abs(ll - ref["ll"]) <= 1e-4 * sref["scale"] + sref["bound"]).all()
-    e_pose = np.linalg.norm(dpose - ref["dpose"], axis=1) / np.linalg.norm(ref["dpose"], axis=1)
-    e_s = np.abs(ds - ref["dsigma"]) / np.abs(ref["dsigma"])
-    e_p = np.abs(dp - ref["dpout"]) / np.abs(ref["dpout"])
-    for name, e in (("pose", e_pose), ("sigma", e_s), ("p_out", e_p)):
-        assert np.median(e) <= 1e-3 and e.max() <= 2e-2, (name, np.sort(e))
+    gb = orc.score_grad_bound(wl.scene, wl.slot, poses, LIK, obs)["gbound"]
+    frac = check_grad(dpose, ds, dp, ref, gb, "tabletop")
+    assert frac >= 0.9, frac  # the bound is not what makes the test pass
     ctx.close()
 
 

@@ -304,3 +304,82 @@ def test_device_timeout_shorter_than_a_batch_fails_the_server(streams):
     assert e.value.status == b3d.B3D_EDEVICE
     srv.close()
     torch.cuda.synchronize()
+
+
+_M64 = (1 << 64) - 1
+
+
+def _splitmix64(z):
+    """SplitMix64's output function (Steele, Lea and Flood, 2014), from its definition."""
+    z = (z + 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def test_server_frame_matches_oracle_at_320x240(orc):
+    """The serving workload's image (320x240, fx = fy = 300) and per-frame enumeration (5^3
+    translations of 1 cm x 50 perturbations of up to 5 deg around each tracked object's
+    estimate, the other objects held at theirs, 16 particles) on a session of three
+    2k-8k-voxel objects, where a hypothesis spans several score tiles. Against the FP64 oracle:
+      - each object's scores of the frame's 6,250 hypotheses, through the batched kernel, on
+        48 sampled hypotheses and the GPU's argmax: within 1e-4 of the summed per-pixel terms
+        plus the oracle's FP32-decision bound, most within 1e-4 alone; the GPU argmax is the
+        oracle's best of the sample unless their gap is inside the tolerance;
+      - the whole frame, enumerated by the oracle with the frame's seed (SplitMix64 of session
+        seed, frame and object): the server's estimate is the oracle's best drawn cell and its
+        particles are the oracle's, within 2e-6."""
+    from paper_2312_08715_gb300 import b3d
+    from _scenes import check_ll, gpu_context, ll_tolerance
+    st = synth.tracking_stream(0, n_objects=3, n_frames=1, seed_base=9100)
+    cam = st.scene.camera
+    assert (cam.width, cam.height, cam.fx) == (320, 240, 300.0) and st.n_track == 3
+    depth, _ = orc.render(st.scene_at(0))
+    obs = synth.corrupt_depth(depth, cam.far, st.draws(0))
+    stage = synth.tracking_stage()
+    m = 16
+    sch = b3d.schedule([stage], m, 0, np.eye(3))
+    cfg = b3d.server_config(b3d.lik_params(**LIK), sch, max_batch_items=8, max_inflight=1, queue_depth=2,
+                            device_timeout_ms=60000)
+    srv = b3d.Server(cfg)
+    sid = _open(srv, st)
+    r0 = srv.wait(srv.submit(sid, obs), 60000)
+    assert r0["status"] == 0
+    state = srv.export_session(sid)
+    srv.close()
+    # every hypothesis of the frame through the batched kernel
+    ctx = gpu_context(st.scene, obs)  # the scene at the session's starting estimates
+    owner = b3d.Context(0)
+    R = orc.rotation_set(1, stage.n_rot, stage.rot_max)
+    grids, items, outs = [], [], []
+    for k in range(st.n_track):
+        P = orc.expand(st.truth[0][k], st.grid_frame, stage.n_per_axis, stage.step, R)
+        grids.append(P)
+        Pd = torch.as_tensor(P.astype(np.float32), device="cuda")
+        o = torch.full((len(P),), float("nan"), device="cuda")
+        outs.append((Pd, o))
+        items.append((ctx.h, k, len(P), Pd, o))
+    b3d.b3d_score_multi(owner.h, items, b3d.lik_params(**LIK), owner.stream)
+    owner.sync()
+    rng = np.random.default_rng(77)
+    for k in range(st.n_track):
+        ll = outs[k][1].cpu().numpy()
+        assert np.isfinite(ll).all()
+        top = int(np.argmax(ll))
+        sel = np.unique(np.concatenate([rng.choice(len(ll), 48, replace=False), [top]]))
+        ref = orc.score(st.scene, k, grids[k][sel], LIK, obs)
+        check_ll(ll[sel], ref, f"320x240 object {k}")
+        best = int(np.argmax(ref["ll"]))
+        if sel[best] != top:
+            assert ref["ll"][best] - ref["ll"][sel == top][0] <= 2 * ll_tolerance(ref)[best]
+    # the whole frame on the oracle
+    for k in range(st.n_track):
+        seed = _splitmix64(_splitmix64(_splitmix64(st.seed) ^ 0) ^ k)
+        assert seed == b3d.b3d_frame_seed(st.seed, 0, k)
+        ref = orc.enumerate_c2f(st.scene, k, st.truth[0][k], st.grid_frame, LIK, obs, [stage], m, seed)
+        idx, logw = ref["idx"][0], ref["logw"]
+        order = np.lexsort((idx, -logw))  # highest score, ties to the smaller index
+        np.testing.assert_allclose(r0["poses"][k], grids[k][idx[order[0]]], atol=2e-6)
+        np.testing.assert_allclose(state["particles"][k], ref["particles"], atol=2e-6)
+    ctx.close()
+    owner.close()
