@@ -207,22 +207,43 @@ b3d_status b3d_expand_hypotheses(b3d_ctx *ctx, const float *centre_pose, const f
 b3d_status b3d_lse_resample(b3d_ctx *ctx, int64_t n, const float *loglik_dev, int32_t m, uint64_t seed,
                             int32_t stage, float *logz_dev, int32_t *idx_dev, float *logq_dev, b3d_stream stream);
 
+/* One rank's part of b3d_lse_resample when the scores of one categorical (one C2F stage,
+ * Sec. III-B) are split over ranks in contiguous shards, rank r holding scores
+ * [index_base, index_base + n) of the whole vector. With logz_r the log normaliser of each
+ * rank's shard (this call's logz_dev, or b3d_lse_resample with m = 0), log Z the
+ * log-sum-exp of all logz_r, mass_before = sum over earlier ranks of exp(logz_r - log Z)
+ * and mass = exp(logz_r - log Z) (the last rank passes 1 - mass_before, so that every
+ * uniform has an owner): draw k (the uniform u_k of b3d_lse_resample, same seed, stage and
+ * counter) belongs to this rank when mass_before <= u_k < mass_before + mass, and then
+ * idx_dev[k] = index_base + min{ h : sum_{g<=h} exp(ll_g) > ((u_k - mass_before) / mass)
+ * sum_g exp(ll_g) } over this shard, which in exact arithmetic is the index the unsplit
+ * call draws; logq_dev[k] = ll[idx] - logz_global. Draws of other ranks get idx -1 and logq
+ * -inf, so combining the ranks' outputs by maximum gives every draw. logz_dev [1] receives
+ * this shard's own log normaliser. Errors: B3D_EINVAL for n outside [1, 2^31-1], m < 0,
+ * NULL outputs, masses outside [0, 1] or index_base + n > 2^31. */
+b3d_status b3d_lse_resample_shard(b3d_ctx *ctx, int64_t n, const float *loglik_dev, int32_t m, uint64_t seed,
+                                  int32_t stage, double mass_before, double mass, double logz_global, int64_t index_base,
+                                  float *logz_dev, int32_t *idx_dev, float *logq_dev, b3d_stream stream);
+
 /* Log-sum-exp and resampling for callers that cannot allocate device memory. The paper has
  * no counterpart: this is a library service. It computes exactly what b3d_lse_resample
  * computes (same kernel, same definition of idx/logq/logz), without a context and without
  * allocating: the kernel's scratch (1024 partial sums and a completion counter, 8 KB) is a
  * fixed array inside the library that every GPU loading the library holds until the
- * process exits. Callers that cannot allocate include code running while a CUDA graph is
- * captured (allocation is not capturable), code under another framework's allocator lock
- * or hard memory cap, and embeddings that forbid the library from allocating.
- *   - Works on the calling thread's current device. The first call on a device looks up
- *     the array's device address (once per device); make that first call before any
- *     stream capture begins.
+ * process exits. Callers that cannot allocate include code under another framework's
+ * allocator lock or hard memory cap (an allocation would deadlock or fail), loops that
+ * cannot afford the implicit device synchronisation an allocation may bring, and
+ * embeddings that forbid the library from allocating.
+ *   - Works on the calling thread's current device. The first call on a device (and the
+ *     first after the device's context was reset) looks up the array's device address,
+ *     which may load the library's module there; make that first call before any stream
+ *     capture begins.
  *   - Every call shares the one array and clears its counter on `stream` first; calls
  *     that overlap on the GPU (other streams, other threads) race: serialise them.
  *   - n must be in [1, B3D_NOALLOC_MAX_SCORES] (else B3D_EINVAL), m >= 0, outputs as in
- *     b3d_lse_resample. If every score is -inf, idx is -1 and logz is -inf. Returns
- *     B3D_EINVAL or B3D_ECUDA on error; there is no context, so no b3d_last_error text. */
+ *     b3d_lse_resample. If every score is -inf (m > 0), every idx is -1, every logq -inf
+ *     and logz -inf: that is how this call reports the case (there is no context, so no
+ *     b3d_sync flag and no b3d_last_error text). Returns B3D_EINVAL or B3D_ECUDA on error. */
 #define B3D_NOALLOC_MAX_SCORES 2147483647LL
 b3d_status b3d_lse_resample_noalloc(int64_t n, const float *loglik_dev, int32_t m, uint64_t seed, int32_t stage,
                                     float *logz_dev, int32_t *idx_dev, float *logq_dev, b3d_stream stream);
@@ -307,6 +328,15 @@ b3d_status b3d_score_grad(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const f
 b3d_status b3d_refine_smooth(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, float *poses_dev,
                              const b3d_lik_params *lik, int32_t n_steps, float lr, float beta1, float beta2, float eps,
                              float *loglik_dev, b3d_stream stream);
+
+/* The left se(3) update of the gradient's parameterisation (the convention of
+ * b3d_score_grad): out_dev[i] = Exp([v_i, w_i]^) poses_dev[i] for n twists xi_dev [n, 6]
+ * ordered (v, w) and row-major 4x4 poses [n, 16]; Exp by Rodrigues' formula and the SE(3) V
+ * matrix, in FP32 with series forms below a rotation of 0.1 rad. out_dev may be poses_dev.
+ * The same arithmetic re-bases the poses inside b3d_refine_smooth. n >= 0; B3D_EINVAL for
+ * NULL buffers when n > 0. */
+b3d_status b3d_se3_compose(b3d_ctx *ctx, int64_t n, const float *xi_dev, const float *poses_dev, float *out_dev,
+                           b3d_stream stream);
 
 /* Camera hypotheses (the camera-pose tracking of Sec. IV, Table 1): render n_hyp hypothesised
  * camera poses poses_dev [n_hyp, 16] (row-major camera_from_world) of the scene, every object

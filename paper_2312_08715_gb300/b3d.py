@@ -137,6 +137,9 @@ _SIGNATURES = {
     "b3d_refine_smooth": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_lik_params), C.c_int32, C.c_float,
                                       C.c_float, C.c_float, C.c_float, _P, _P]),
     "b3d_lse_resample_noalloc": (C.c_int32, [C.c_int64, _P, C.c_int32, C.c_uint64, C.c_int32, _P, _P, _P, _P]),
+    "b3d_se3_compose": (C.c_int32, [_P, C.c_int64, _P, _P, _P, _P]),
+    "b3d_lse_resample_shard": (C.c_int32, [_P, C.c_int64, _P, C.c_int32, C.c_uint64, C.c_int32, C.c_double, C.c_double,
+                                           C.c_double, C.c_int64, _P, _P, _P, _P]),
     "b3d_get_tuning": (C.c_int32, [_P, C.POINTER(b3d_tuning)]),
     "b3d_set_tuning": (C.c_int32, [_P, C.POINTER(b3d_tuning)]),
     "b3d_autotune": (C.c_int32, [_P, C.c_int32, _P, _P, C.POINTER(b3d_stage), C.POINTER(b3d_lik_params),
@@ -347,6 +350,13 @@ def b3d_expand_hypotheses(ctx, centre_pose, grid_frame, stage: b3d_stage, poses_
 def b3d_lse_resample(ctx, n, loglik_dev, m, seed, stage, logz_dev, idx_dev, logq_dev, stream=None):
     return _check(ctx, load().b3d_lse_resample(ctx, n, _addr(loglik_dev), m, seed, stage, _addr(logz_dev),
                                                _addr(idx_dev), _addr(logq_dev), _stream(stream)))
+
+
+def b3d_lse_resample_shard(ctx, n, loglik_dev, m, seed, stage, mass_before, mass, logz_global, index_base, logz_dev,
+                           idx_dev, logq_dev, stream=None):
+    return _check(ctx, load().b3d_lse_resample_shard(ctx, n, _addr(loglik_dev), m, seed, stage, float(mass_before),
+                                                     float(mass), float(logz_global), int(index_base), _addr(logz_dev),
+                                                     _addr(idx_dev), _addr(logq_dev), _stream(stream)))
 
 
 def b3d_lse_resample_noalloc(n, loglik_dev, m, seed, stage, logz_dev, idx_dev, logq_dev, stream=None):
@@ -759,6 +769,17 @@ class Context:
         b3d_lse_resample(self.h, ll.numel(), ll, m, seed, stage, logz, idx, logq, self.stream)
         return logz, idx[:m], logq[:m]
 
+    def lse_resample_shard(self, ll, m, seed, stage, mass_before, mass, logz_global, index_base):
+        """This rank's draws of a categorical split over ranks (idx -1 where another rank owns
+        the draw), and its shard's own log normaliser."""
+        t = self.torch
+        logz = t.empty(1, dtype=t.float32, device=self.device)
+        idx = t.empty(max(m, 1), dtype=t.int32, device=self.device)
+        logq = t.empty(max(m, 1), dtype=t.float32, device=self.device)
+        b3d_lse_resample_shard(self.h, ll.numel(), ll, m, seed, stage, mass_before, mass, logz_global, index_base, logz,
+                               idx, logq, self.stream)
+        return logz, idx[:m], logq[:m]
+
     def enumerate_c2f(self, slot, centre, stages, lik: dict, n_particles, seed, grid_frame, out=None,
                       path_density=False):
         t = self.torch
@@ -783,6 +804,16 @@ class Context:
         b3d_score_grad(self.h, slot, n, P, lik_params(**lik), ll, dpose, ds, dp, self.stream)
         return ll, dpose, ds, dp
 
+    def se3_compose(self, xi, poses, out=None):
+        """Exp(xi^) T for twists xi [n, 6] (v, w) and poses [n, 4, 4] (a new tensor, or out)."""
+        t = self.torch
+        x = self._dev(xi, t.float32).reshape(-1, 6)
+        P = self._dev(poses, t.float32).reshape(-1, 16)
+        if out is None:
+            out = t.empty((P.shape[0], 4, 4), dtype=t.float32, device=self.device)
+        b3d_se3_compose(self.h, P.shape[0], x, P, out, self.stream)
+        return out
+
     def refine(self, slot, poses, lik: dict, n_steps, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         """Adam refinement of poses [n, 4, 4] under the smooth likelihood, all on the device;
         returns the refined poses (a new tensor) and the log-likelihood the last step scored."""
@@ -800,24 +831,8 @@ class Context:
         b3d_sync(self.h, self.stream)
 
 
-def _se3_exp(xi):
-    """Exp of twists xi [n, 6] = (v, w) as 4x4 matrices (Rodrigues with the SE(3) V matrix)."""
-    import torch
-    v, w = xi[:, :3], xi[:, 3:]
-    th = torch.linalg.norm(w, dim=1, keepdim=True).clamp_min(1e-12)
-    k = w / th
-    K = torch.zeros(xi.shape[0], 3, 3, dtype=xi.dtype, device=xi.device)
-    K[:, 0, 1], K[:, 0, 2], K[:, 1, 0] = -k[:, 2], k[:, 1], k[:, 2]
-    K[:, 1, 2], K[:, 2, 0], K[:, 2, 1] = -k[:, 0], -k[:, 1], k[:, 0]
-    s, c = torch.sin(th)[..., None], torch.cos(th)[..., None]
-    I = torch.eye(3, dtype=xi.dtype, device=xi.device).expand_as(K)
-    R = I + s * K + (1 - c) * (K @ K)
-    V = I + ((1 - c) / th[..., None]) * K + ((th[..., None] - s) / th[..., None]) * (K @ K)
-    T = torch.zeros(xi.shape[0], 4, 4, dtype=xi.dtype, device=xi.device)
-    T[:, :3, :3] = R
-    T[:, :3, 3] = (V @ v[..., None])[..., 0]
-    T[:, 3, 3] = 1
-    return T
+def b3d_se3_compose(ctx, n, xi_dev, poses_dev, out_dev, stream=None):
+    return _check(ctx, load().b3d_se3_compose(ctx, n, _addr(xi_dev), _addr(poses_dev), _addr(out_dev), _stream(stream)))
 
 
 def make_score_smooth():
@@ -833,7 +848,7 @@ def make_score_smooth():
 
         @staticmethod
         def forward(fctx, xi, sigma, p_out, b3d_ctx, slot, T0, half_window):
-            poses = (_se3_exp(xi.detach()) @ T0).contiguous()
+            poses = b3d_ctx.se3_compose(xi.detach(), T0)
             lik = dict(kind=1, radius=float(sigma), p_outlier=float(p_out), half_window=int(half_window))
             ll, dpose, ds, dp = b3d_ctx.score_grad(slot, poses, lik)
             fctx.save_for_backward(dpose, ds, dp)

@@ -1359,6 +1359,37 @@ b3d_status b3d_lse_resample(b3d_ctx *ctx, int64_t n, const float *loglik_dev, in
     return check_launch(ctx, "lse_resample");
 }
 
+b3d_status b3d_lse_resample_shard(b3d_ctx *ctx, int64_t n, const float *loglik_dev, int32_t m, uint64_t seed,
+                                  int32_t stage, double mass_before, double mass, double logz_global, int64_t index_base,
+                                  float *logz_dev, int32_t *idx_dev, float *logq_dev, b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    if (n < 1 || n > INT32_MAX) return fail(ctx, B3D_EINVAL, "n must be in [1, 2^31-1]");
+    if (m < 0) return fail(ctx, B3D_EINVAL, "m must be >= 0");
+    if (!loglik_dev || !logz_dev) return fail(ctx, B3D_EINVAL, "loglik_dev and logz_dev must be non-NULL");
+    if (m > 0 && (!idx_dev || !logq_dev)) return fail(ctx, B3D_EINVAL, "idx_dev and logq_dev must be non-NULL when m > 0");
+    if (!(mass_before >= 0.0 && mass_before <= 1.0) || !(mass >= 0.0 && mass_before + mass <= 1.0 + 1e-12))
+        return fail(ctx, B3D_EINVAL, "need 0 <= mass_before, 0 <= mass and mass_before + mass <= 1");
+    if (std::isnan(logz_global) || logz_global == INFINITY) return fail(ctx, B3D_EINVAL, "logz_global must be < +inf");
+    if (index_base < 0 || index_base + n > (int64_t)INT32_MAX + 1)
+        return fail(ctx, B3D_EINVAL, "index_base + n must be in [0, 2^31]");
+    DeviceGuard g(ctx->device);
+    b3d_status st = ensure_scratch(ctx, 0, 0);
+    if (st != B3D_OK) return st;
+    LseShard sh;
+    sh.before = mass_before;
+    sh.mass = mass;
+    sh.logz = (float)logz_global;
+    sh.base = (long long)index_base;
+    {
+        Timed tm(ctx, B3D_K_RESAMPLE, (cudaStream_t)stream);
+        launch_lse_shard(loglik_dev, n, m, seed, stage, sh, ctx->d_part, ctx->d_counter, logz_dev, idx_dev, logq_dev,
+                         ctx->d_err, (cudaStream_t)stream);
+    }
+    ++ctx->launches;
+    return check_launch(ctx, "lse_resample_shard");
+}
+
 b3d_status b3d_enumerate_c2f(b3d_ctx *ctx, int32_t obj_slot, const float *centre_pose, const b3d_c2f_schedule *sch,
                              const b3d_lik_params *lik, float *particles_dev, float *logw_dev, float *logq_dev,
                              b3d_stream stream) {
@@ -1762,6 +1793,19 @@ b3d_status b3d_refine_smooth(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, floa
         ctx->launches += 2;
     }
     return check_launch(ctx, "refine_smooth");
+}
+
+b3d_status b3d_se3_compose(b3d_ctx *ctx, int64_t n, const float *xi_dev, const float *poses_dev, float *out_dev,
+                           b3d_stream stream) {
+    if (!ctx) return B3D_EINVAL;
+    ctx->err.clear();
+    if (n < 0) return fail(ctx, B3D_EINVAL, "n must be >= 0");
+    if (n == 0) return B3D_OK;
+    if (!xi_dev || !poses_dev || !out_dev) return fail(ctx, B3D_EINVAL, "xi_dev, poses_dev and out_dev must be non-NULL");
+    DeviceGuard g(ctx->device);
+    launch_se3_compose(n, xi_dev, poses_dev, out_dev, (cudaStream_t)stream);
+    ++ctx->launches;
+    return check_launch(ctx, "se3_compose");
 }
 
 b3d_status b3d_get_tuning(b3d_ctx *ctx, b3d_tuning *out) {

@@ -144,6 +144,15 @@ struct __align__(16) BatchItem {
 };
 static_assert(sizeof(BatchItem) % 16 == 0, "BatchItem must tile float4 copies");
 
+// One rank's share of a categorical whose scores are split over ranks (contiguous shards):
+// the probability mass of the ranks before it, its own mass (the last rank's runs to 1),
+// the global log normaliser and the global index of its first score.
+struct LseShard {
+    double before, mass;
+    float logz;
+    long long base;
+};
+
 // One scene's segment of a batched log-sum-exp + resampling launch.
 struct LseItem {
     const float *ll;
@@ -207,6 +216,7 @@ int launch_score_depth(const SceneView &sv, const Lik &L, const float *depth, co
                        int grid, cudaStream_t s);
 // Adam step + se(3) re-basing of n poses [n, 16] from their loglik gradients dpose [n, 6]
 // (k_grad.cu); m, v [n, 6] moments; bc1, bc2 the bias corrections of this step.
+void launch_se3_compose(int64_t n, const float *xi, const float *in, float *out, cudaStream_t s);
 void launch_adam_se3(int64_t n, const float *dpose, float *m, float *v, float *poses, float lr, float b1, float b2,
                      float eps, float bc1, float bc2, cudaStream_t s);
 int launch_grad_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, float *dpose,
@@ -230,6 +240,8 @@ void launch_expand(PoseGrid P, int64_t n, float *poses, cudaStream_t s);
 int lse_blocks(int64_t n);
 void launch_lse_resample(const float *ll, int64_t n, int m, uint64_t seed, int stage, float2 *part,
                          unsigned *counter, float *logz, int *idx, float *logq, int *err, cudaStream_t s);
+void launch_lse_shard(const float *ll, int64_t n, int m, uint64_t seed, int stage, const LseShard &shard, float2 *part,
+                      unsigned *counter, float *logz, int *idx, float *logq, int *err, cudaStream_t s);
 void launch_c2f_select(const float *ll, const int *idx, int m, PoseGrid P, const float *logz, int last, int path,
                        int stage, uint64_t seed, int n_stages, float *centre_next, float *particles, float *logw,
                        float *logq, cudaStream_t s);

@@ -1,14 +1,13 @@
 // b3d_noalloc.cu - log-sum-exp + categorical resampling without any device allocation.
 //
-// Some callers cannot allocate device memory at the moment they need to resample: code
-// running while a CUDA graph is being captured (cudaMalloc is not a capturable operation),
-// a host thread holding a custom allocator's lock or working under a hard memory cap owned
-// by another framework, or an embedding that forbids the library from touching the
-// allocator at all. For them, b3d_lse_resample_noalloc runs the same kernel as
-// b3d_lse_resample, but its scratch (the per-block partial sums and the completion
-// counter) lives in the fixed-size array below, part of the library's module image:
-// every GPU that loads the library holds it until the process exits, and nothing is
-// allocated or freed per call.
+// Some callers cannot allocate device memory at the moment they need to resample: a host
+// thread holding a custom allocator's lock or working under a hard memory cap owned by
+// another framework, a loop that cannot afford the implicit synchronisation an allocation
+// may bring, or an embedding that forbids the library from touching the allocator at all.
+// For them, b3d_lse_resample_noalloc runs the same kernel as b3d_lse_resample, but its
+// scratch (the per-block partial sums and the completion counter) lives in the fixed-size
+// array below, part of the library's module image: every GPU that loads the library holds
+// it until the process exits, and nothing is allocated or freed per call.
 //
 // Because every call shares this one array, calls that overlap on the GPU (on different
 // streams, or from different threads without ordering) race on it; serialise them.
@@ -30,10 +29,44 @@ static __device__ __align__(256) float2 g_lse_scratch[kNoallocBlocks + 1];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-float2 *g_scratch_addr[kMaxDevices] = {nullptr};
+struct Cached {
+    unsigned long long ctx_id = 0;  // the context the address belongs to (0: none yet)
+    float2 *addr = nullptr;
+};
+Cached g_scratch_addr[kMaxDevices];
 
-// Device address of g_lse_scratch on the current device, looked up once per device. In host
-// code the name g_lse_scratch is only a host-side stand-in, never a device address.
+// The driver's identifier of the calling thread's current context: unique for the life of
+// the process, so a context created after a device reset never matches an old one. 0 when
+// there is no current context or the driver cannot say. Called with g_mu held.
+unsigned long long current_context_id() {
+    using GetCurrent = int (*)(void **);                       // cuCtxGetCurrent(CUcontext *)
+    using GetId = int (*)(void *, unsigned long long *);       // cuCtxGetId(CUcontext, unsigned long long *)
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+    }
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+    return 0;
+}
+
+// Device address of g_lse_scratch in the current device's context. In host code the name
+// g_lse_scratch is only a host-side stand-in, never a device address. The address is looked
+// up once per device and context: a context created after a device reset (where the module,
+// and with it the array, may load elsewhere) gets a fresh lookup.
 b3d_status scratch_for_current_device(float2 **out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -41,16 +74,19 @@ b3d_status scratch_for_current_device(float2 **out) {
         return B3D_ECUDA;
     }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    Cached &c = g_scratch_addr[dev];
+    const unsigned long long id = current_context_id();
+    if (!c.addr || id == 0 || id != c.ctx_id) {
         void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_lse_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_lse_scratch);  // creates the context if needed
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             return B3D_ECUDA;
         }
-        g_scratch_addr[dev] = static_cast<float2 *>(p);
+        c.addr = static_cast<float2 *>(p);
+        c.ctx_id = current_context_id();
     }
-    *out = g_scratch_addr[dev];
+    *out = c.addr;
     return B3D_OK;
 }
 
@@ -74,6 +110,9 @@ extern "C" b3d_status b3d_lse_resample_noalloc(int64_t n, const float *loglik_de
         return B3D_ECUDA;
     }
     unsigned *counter = reinterpret_cast<unsigned *>(tail);
+    // The kernel raises this word when every score is -inf; that case also shows in the
+    // outputs (idx -1, logq -inf, logz -inf), which is how this entry point reports it. The
+    // word stays in the shared scratch and the next call clears it.
     int *err = reinterpret_cast<int *>(tail) + 1;
     b3d::launch_lse_resample(loglik_dev, n, m, seed, stage, scratch, counter, logz_dev, idx_dev, logq_dev, err, s);
     e = cudaGetLastError();

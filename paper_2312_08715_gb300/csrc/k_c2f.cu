@@ -147,10 +147,16 @@ struct LseShared {
     bool last;
 };
 
-// Block bid of nb blocks working on one score vector (see k_lse_resample).
+// Block bid of nb blocks working on one score vector (see k_lse_resample). With a shard
+// (the vector is one rank's contiguous part of a categorical split over ranks), draw k
+// belongs to this rank when its uniform u falls in [before, before + mass), the rank's share
+// of the probability; its index within the vector is then the inverse CDF at
+// (u - before) / mass, which is the global inverse CDF at u in exact arithmetic. Draws of
+// other ranks get idx -1; logq uses the global normaliser; idx is offset by base.
 __device__ __forceinline__ void lse_body(LseShared &sh, int bid, int nb, const float *ll, int64_t n, int chunk, int m,
                                          unsigned long long seed, int stage, float2 *part, unsigned *counter,
-                                         float *logz, int *idx, float *logq, int *err) {
+                                         float *logz, int *idx, float *logq, int *err,
+                                         const LseShard *shard = nullptr) {
     float *s_red = sh.red, *s_w = sh.w, *s_pre = sh.pre;
     float &s_M = sh.M, &s_S = sh.S;
     bool &s_last = sh.last;
@@ -232,7 +238,7 @@ __device__ __forceinline__ void lse_body(LseShared &sh, int bid, int nb, const f
             s_S = acc;
             *counter = 0u;
             *logz = (M > -INFINITY) ? M + __logf(acc) : -INFINITY;
-            if (!(M > -INFINITY) && m > 0) atomicOr(err, 4);
+            if (!(M > -INFINITY) && m > 0 && !shard) atomicOr(err, 4);
         }
         __syncthreads();
         float acc = s_red[wid] + (inc - run);
@@ -243,7 +249,8 @@ __device__ __forceinline__ void lse_body(LseShared &sh, int bid, int nb, const f
     }
     __syncthreads();
     const float S = s_S;
-    const float Z = (M > -INFINITY) ? M + __logf(S) : -INFINITY;
+    const float Z = shard ? shard->logz : ((M > -INFINITY) ? M + __logf(S) : -INFINITY);
+    const long long ibase = shard ? shard->base : 0;
     int cached = -1;  // the chunk whose prefix this warp holds
     for (int k = wid; k < m; k += nw) {
         if (!(M > -INFINITY)) {
@@ -251,7 +258,17 @@ __device__ __forceinline__ void lse_body(LseShared &sh, int bid, int nb, const f
             continue;
         }
         const U64x4 r = philox4x64((unsigned long long)k, (unsigned long long)(unsigned)stage, 0ull, 0ull, seed, 0ull);
-        const float t = uniform24(r.v[0]) * S;
+        float t;
+        if (shard) {
+            const double u = (double)(r.v[0] >> 40) * (1.0 / 16777216.0);  // the same 24-bit uniform, exact
+            if (!(u >= shard->before && u < shard->before + shard->mass)) {
+                if (lane == 0) { idx[k] = -1; logq[k] = -INFINITY; }
+                continue;
+            }
+            t = (float)((u - shard->before) / shard->mass) * S;
+        } else {
+            t = uniform24(r.v[0]) * S;
+        }
         // first chunk whose inclusive prefix exceeds t; if rounding leaves none, the last
         // chunk with weight
         int lo = 0, hi = B - 1;
@@ -316,7 +333,7 @@ __device__ __forceinline__ void lse_body(LseShared &sh, int bid, int nb, const f
                 if (found < 0)
                     for (int i = len - 1; i >= 0; --i)
                         if ((cm[i >> 5] >> (i & 31)) & 1u) { found = i; break; }
-                idx[k] = found >= 0 ? (int)(e0 + found) : -1;
+                idx[k] = found >= 0 ? (int)(ibase + e0 + found) : -1;
                 logq[k] = found >= 0 ? cl[found] - Z : -INFINITY;
             }
             __syncwarp();
@@ -351,7 +368,7 @@ __device__ __forceinline__ void lse_body(LseShared &sh, int bid, int nb, const f
         }
         if (found < 0) found = last_pos;
         if (lane == 0) {
-            idx[k] = (int)found;
+            idx[k] = found >= 0 ? (int)(ibase + found) : -1;
             logq[k] = found >= 0 ? __ldcg(&ll[found]) - Z : -INFINITY;
         }
     }
@@ -363,6 +380,15 @@ __global__ void __launch_bounds__(kLseThreads) k_lse_resample(const float *ll, i
                                                               int *err) {
     __shared__ LseShared sh;
     lse_body(sh, blockIdx.x, gridDim.x, ll, n, chunk, m, seed, stage, part, counter, logz, idx, logq, err);
+}
+
+// One rank's shard of a categorical split over ranks (see lse_body).
+__global__ void __launch_bounds__(kLseThreads) k_lse_shard(const float *ll, int64_t n, int chunk, int m,
+                                                           unsigned long long seed, int stage, LseShard shard,
+                                                           float2 *part, unsigned *counter, float *logz, int *idx,
+                                                           float *logq, int *err) {
+    __shared__ LseShared sh;
+    lse_body(sh, blockIdx.x, gridDim.x, ll, n, chunk, m, seed, stage, part, counter, logz, idx, logq, err, &shard);
 }
 
 // Batched: the blocks of every scene's score vector in one grid; block_begin[i] is the
@@ -393,6 +419,14 @@ void launch_lse_resample(const float *ll, int64_t n, int m, uint64_t seed, int s
     const int chunk = (int)((n + B - 1) / B);
     k_lse_resample<<<B, kLseThreads, 0, s>>>(ll, n, chunk, m, (unsigned long long)seed, stage, part, counter, logz, idx,
                                              logq, err);
+}
+
+void launch_lse_shard(const float *ll, int64_t n, int m, uint64_t seed, int stage, const LseShard &shard, float2 *part,
+                      unsigned *counter, float *logz, int *idx, float *logq, int *err, cudaStream_t s) {
+    const int B = lse_blocks(n);
+    const int chunk = (int)((n + B - 1) / B);
+    k_lse_shard<<<B, kLseThreads, 0, s>>>(ll, n, chunk, m, (unsigned long long)seed, stage, shard, part, counter, logz,
+                                          idx, logq, err);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -207,12 +207,57 @@ __global__ void __launch_bounds__(NT, kGradMinBlocks)
     }
 }
 
+// P <- Exp(xi^) P for one row-major 4x4 pose P (rows 0-2 read and written) and the twist
+// xi = (v, w): Rodrigues for the rotation and the SE(3) V matrix for the translation, with
+// series for sin(th)/th, (1 - cos th)/th^2 and (th - sin th)/th^3 below th = 0.1 (in float
+// the closed forms lose most of their digits to cancellation at the angles a refinement
+// step takes).
+__device__ __forceinline__ void se3_left_compose(const float xi[6], float *P) {
+    const float wx = xi[3], wy = xi[4], wz = xi[5];
+    const float th2 = wx * wx + wy * wy + wz * wz, th = sqrtf(th2);
+    float a, b, c;  // R = I + a W + b W^2, V = I + b W + c W^2 with W = [w]x (unnormalised)
+    if (th < 0.1f) {  // series to th^4: the next terms are below 3e-10
+        const float th4 = th2 * th2;
+        a = 1.f - th2 / 6.f + th4 / 120.f;
+        b = 0.5f - th2 / 24.f + th4 / 720.f;
+        c = 1.f / 6.f - th2 / 120.f + th4 / 5040.f;
+    } else {
+        const float s = sinf(th), co = cosf(th);
+        a = s / th;
+        b = (1.f - co) / th2;
+        c = (th - s) / (th2 * th);
+    }
+    const float W[9] = {0.f, -wz, wy, wz, 0.f, -wx, -wy, wx, 0.f};
+    float W2[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            W2[3 * r + q] = W[3 * r] * W[q] + W[3 * r + 1] * W[3 + q] + W[3 * r + 2] * W[6 + q];
+    float R[9], V[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float id = (k % 4 == 0) ? 1.f : 0.f;
+        R[k] = id + a * W[k] + b * W2[k];
+        V[k] = id + b * W[k] + c * W2[k];
+    }
+    float T[12];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        T[4 * r] = P[4 * r]; T[4 * r + 1] = P[4 * r + 1]; T[4 * r + 2] = P[4 * r + 2]; T[4 * r + 3] = P[4 * r + 3];
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float tv = V[3 * r] * xi[0] + V[3 * r + 1] * xi[1] + V[3 * r + 2] * xi[2];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            P[4 * r + q] = R[3 * r] * T[q] + R[3 * r + 1] * T[4 + q] + R[3 * r + 2] * T[8 + q] + (q == 3 ? tv : 0.f);
+    }
+}
+
 // One Adam step per pose on the ascent direction of loglik (gradient g = -dpose of the loss
 // -loglik; moments m, v [n, 6]; bc1 = 1 - beta1^t, bc2 = 1 - beta2^t), then the re-basing
-// T <- Exp(xi^) T with xi = -lr mhat / (sqrt(vhat) + eps) = (v, w): Rodrigues for the
-// rotation and the SE(3) V matrix for the translation, with series for sin(th)/th,
-// (1 - cos th)/th^2 and (th - sin th)/th^3 below th = 0.1 (in float the closed forms lose
-// most of their digits to cancellation at the angles a refinement step takes).
+// T <- Exp(xi^) T with xi = -lr mhat / (sqrt(vhat) + eps).
 __global__ void k_adam_se3(int64_t n, const float *dpose, float *m, float *v, float *poses, float lr, float b1, float b2,
                            float eps, float bc1, float bc2) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -226,48 +271,33 @@ __global__ void k_adam_se3(int64_t n, const float *dpose, float *m, float *v, fl
             v[6 * i + k] = vk;
             xi[k] = -lr * (mk / bc1) / (sqrtf(vk / bc2) + eps);
         }
-        const float wx = xi[3], wy = xi[4], wz = xi[5];
-        const float th2 = wx * wx + wy * wy + wz * wz, th = sqrtf(th2);
-        float a, b, c;  // R = I + a W + b W^2, V = I + b W + c W^2 with W = [w]x (unnormalised)
-        if (th < 0.1f) {  // series to th^4: the next terms are below 3e-10
-            const float th4 = th2 * th2;
-            a = 1.f - th2 / 6.f + th4 / 120.f;
-            b = 0.5f - th2 / 24.f + th4 / 720.f;
-            c = 1.f / 6.f - th2 / 120.f + th4 / 5040.f;
-        } else {
-            const float s = sinf(th), co = cosf(th);
-            a = s / th;
-            b = (1.f - co) / th2;
-            c = (th - s) / (th2 * th);
-        }
-        const float W[9] = {0.f, -wz, wy, wz, 0.f, -wx, -wy, wx, 0.f};
-        float W2[9];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-                W2[3 * r + q] = W[3 * r] * W[q] + W[3 * r + 1] * W[3 + q] + W[3 * r + 2] * W[6 + q];
-        float R[9], V[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const float id = (k % 4 == 0) ? 1.f : 0.f;
-            R[k] = id + a * W[k] + b * W2[k];
-            V[k] = id + b * W[k] + c * W2[k];
-        }
-        float *P = poses + 16 * i;
-        float T[12];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            T[4 * r] = P[4 * r]; T[4 * r + 1] = P[4 * r + 1]; T[4 * r + 2] = P[4 * r + 2]; T[4 * r + 3] = P[4 * r + 3];
-        }
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            const float tv = V[3 * r] * xi[0] + V[3 * r + 1] * xi[1] + V[3 * r + 2] * xi[2];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                P[4 * r + q] = R[3 * r] * T[q] + R[3 * r + 1] * T[4 + q] + R[3 * r + 2] * T[8 + q] + (q == 3 ? tv : 0.f);
-        }
+        se3_left_compose(xi, poses + 16 * i);
     }
+}
+
+// out_i = Exp(xi_i^) in_i for n poses (out may be in): the left se(3) update of the
+// gradient's parameterisation.
+__global__ void k_se3_compose(int64_t n, const float *xi, const float *in, float *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float x[6], P[16];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) x[k] = xi[6 * i + k];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) P[k] = in[16 * i + k];
+        se3_left_compose(x, P);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) out[16 * i + k] = P[k];
+        out[16 * i + 12] = 0.f;
+        out[16 * i + 13] = 0.f;
+        out[16 * i + 14] = 0.f;
+        out[16 * i + 15] = 1.f;
+    }
+}
+
+void launch_se3_compose(int64_t n, const float *xi, const float *in, float *out, cudaStream_t s) {
+    if (n <= 0) return;
+    const int blocks = (int)std::min<int64_t>((n + 127) / 128, 1024);
+    k_se3_compose<<<blocks, 128, 0, s>>>(n, xi, in, out);
 }
 
 void launch_adam_se3(int64_t n, const float *dpose, float *m, float *v, float *poses, float lr, float b1, float b2,

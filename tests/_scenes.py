@@ -80,3 +80,15 @@ def check_grad(dpose, dsigma, dpout, ref, gbound, what):
               f"within 1e-3 alone {tight.mean():.3f} bounded {np.mean(b > 0):.3f}")
         tight_all &= tight
     return float(tight_all.mean())
+
+
+def se3_exp_fp64(xi):
+    """Exp of twists xi [n, 6] = (v, w) as 4x4 matrices in FP64: the matrix exponential of
+    [[W, v], [0, 0]] with W = [w]x (scipy's expm)."""
+    from scipy.linalg import expm
+    xi = np.asarray(xi, np.float64).reshape(-1, 6)
+    out = np.empty((xi.shape[0], 4, 4))
+    for i, (v0, v1, v2, w0, w1, w2) in enumerate(xi):
+        A = np.array([[0, -w2, w1, v0], [w2, 0, -w0, v1], [-w1, w0, 0, v2], [0, 0, 0, 0]])
+        out[i] = expm(A)
+    return out

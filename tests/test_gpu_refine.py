@@ -5,7 +5,7 @@ window; and gradient-based pose refinement after enumeration."""
 import numpy as np
 import pytest
 
-from _scenes import check_grad, gpu_context, jitter_poses, observed
+from _scenes import check_grad, gpu_context, jitter_poses, observed, se3_exp_fp64
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -103,7 +103,7 @@ def test_adam_refinement_raises_the_likelihood(scene):
         (-ll.sum()).backward()
         opt.step()
         with torch.no_grad():
-            T = (b3d._se3_exp(xi) @ T).contiguous()
+            T = ctx.se3_compose(xi, T)
             xi.zero_()
     ll1 = ctx.score(wl.slot, T, LIK)
     assert float((ll1 - ll0).mean()) > 0
@@ -129,12 +129,11 @@ def test_library_refinement_step_matches_torch_adam(scene):
     ll = F.apply(xi, LIK["radius"], LIK["p_outlier"], ctx, wl.slot, T0, LIK["half_window"])
     (-ll.sum()).backward()
     opt.step()
-    with torch.no_grad():
-        T_ref = b3d._se3_exp(xi) @ T0
+    T_ref = se3_exp_fp64(_np(xi)) @ _np(T0).astype(np.float64)
     T_lib, ll_lib = ctx.refine(wl.slot, T0, LIK, 1, lr)
     ctx.sync()
     assert torch.equal(ll_lib, ll.detach())  # the scores of the poses the step started from
-    assert (T_lib - T_ref).abs().max().item() < 2e-6
+    assert np.abs(_np(T_lib) - T_ref).max() < 2e-6
     ctx.close()
 
 
@@ -153,4 +152,24 @@ def test_library_refinement_raises_the_likelihood(scene):
     assert np.median(err1) < np.median(err0)
     R = _np(T1)[:, :3, :3]
     assert np.abs(R @ R.transpose(0, 2, 1) - np.eye(3)).max() < 1e-4  # re-basing keeps rotations orthonormal
+    ctx.close()
+
+
+def test_se3_compose_matches_the_matrix_exponential(scene):
+    """b3d_se3_compose against the matrix exponential of the 4x4 twist matrix (scipy, FP64),
+    for rotations in the series regime (< 0.1 rad), around it and large, in place and not."""
+    wl, obs = scene
+    ctx = gpu_context(wl.scene, obs)
+    rng = np.random.default_rng(12)
+    n = 300
+    xi = np.concatenate([rng.normal(size=(n, 3)) * 0.01, rng.normal(size=(n, 3))], 1)
+    xi[:, 3:] *= (np.logspace(-7, 0.4, n) / np.linalg.norm(xi[:, 3:], axis=1))[:, None]
+    T0 = jitter_poses(rng, wl.hidden, n, trans=0.05, rot_deg=30)
+    want = se3_exp_fp64(xi) @ T0.astype(np.float64)
+    got = _np(ctx.se3_compose(torch.as_tensor(xi, dtype=torch.float32, device="cuda"), T0))
+    T_in = torch.as_tensor(T0, device="cuda").reshape(n, 16).contiguous()
+    same = ctx.se3_compose(torch.as_tensor(xi, dtype=torch.float32, device="cuda"), T_in, out=T_in.reshape(n, 4, 4))
+    ctx.sync()
+    np.testing.assert_allclose(got, want, rtol=0, atol=2e-6)
+    np.testing.assert_array_equal(_np(same), got)
     ctx.close()

@@ -1,8 +1,10 @@
 """The allocation-free resampling entry point, for callers that cannot allocate device
-memory (e.g. while a CUDA graph is being captured, or under another framework's allocator
-lock): called through the C ABI twice in a row, it must give what the context-based
-b3d_lse_resample gives on the same scores. Collected last so that a stop at the first
-failure has already run every other test; it also passes alone in a fresh process."""
+memory (under another framework's allocator lock or memory cap, or in an embedding that
+forbids the library from allocating): called through the C ABI several times in a row, it
+must give what the context-based b3d_lse_resample gives on the same scores, agree with the
+FP64 oracle's resampling, report an all -inf vector in its outputs, and leave the device's
+free memory unchanged. Collected last so that a stop at the first failure has already run
+every other test; it also passes alone in a fresh process."""
 import numpy as np
 import pytest
 
@@ -12,17 +14,16 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _run_noalloc(ll, m, seed, stage):
-    logz = torch.empty(1, device="cuda")
-    idx = torch.full((m,), -7, dtype=torch.int32, device="cuda")
-    logq = torch.empty(m, device="cuda")
+def _run_noalloc(ll, m, seed, stage, out=None):
+    logz, idx, logq = out or (torch.empty(1, device="cuda"), torch.full((m,), -7, dtype=torch.int32, device="cuda"),
+                              torch.empty(m, device="cuda"))
     s = torch.cuda.current_stream()
     b3d.b3d_lse_resample_noalloc(ll.numel(), ll, m, seed, stage, logz, idx, logq, s)
     s.synchronize()
     return logz.cpu().numpy(), idx.cpu().numpy(), logq.cpu().numpy()
 
 
-def test_noalloc_matches_context_entry_point_twice():
+def test_noalloc_matches_context_entry_point_twice(orc):
     ctx = b3d.Context(0)
     rng = np.random.default_rng(2024)
     cases = [(synth.random_ll(rng, 145800), 100, 11, 0), (synth.random_ll(rng, 3001), 37, 12, 2)]
@@ -34,7 +35,46 @@ def test_noalloc_matches_context_entry_point_twice():
         np.testing.assert_allclose(z, z_ref, rtol=1e-6, atol=1e-5)
         np.testing.assert_array_equal(i, i_ref)
         np.testing.assert_allclose(q, q_ref, rtol=1e-6, atol=1e-4)
+        # the FP64 oracle on the same (FP32) scores: the same draws except where the draw's
+        # CDF margin is below FP32 summation accuracy
+        oi, oq, margin = orc.resample(ll_np.astype(np.float64), m, seed, stage)
+        z64, _ = orc.lse(ll_np.astype(np.float64))
+        assert abs(float(z[0]) - z64) <= 1e-6 * abs(z64) + 1e-4
+        firm = margin >= 1e-5
+        assert firm.mean() > 0.9
+        np.testing.assert_array_equal(i[firm], oi[firm])
+        np.testing.assert_allclose(q[firm], oq[firm], rtol=1e-5, atol=1e-3)
     ctx.close()
+
+
+def test_noalloc_all_minus_inf_reports_in_its_outputs():
+    ll = torch.full((5000,), float("-inf"), device="cuda")
+    z, i, q = _run_noalloc(ll, 9, 1, 0)
+    assert np.isneginf(z).all() and (i == -1).all() and np.isneginf(q).all()
+    # the next call starts clean
+    ll2 = torch.as_tensor(synth.random_ll(np.random.default_rng(3), 5000), device="cuda")
+    z2, i2, _ = _run_noalloc(ll2, 9, 1, 0)
+    assert np.isfinite(z2).all() and (i2 >= 0).all() and (i2 < 5000).all()
+
+
+def test_noalloc_allocates_no_device_memory():
+    """After the first call on the device (which may load the library's module, code and
+    fixed array, into the context), further calls leave the free device memory unchanged."""
+    rng = np.random.default_rng(9)
+    ll = torch.as_tensor(synth.random_ll(rng, 200000), device="cuda")
+    m = 64
+    out = (torch.empty(1, device="cuda"), torch.empty(m, dtype=torch.int32, device="cuda"),
+           torch.empty(m, device="cuda"))
+    first = _run_noalloc(ll, m, 5, 1, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    again = [_run_noalloc(ll, m, 5, 1, out) for _ in range(3)]
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    for a in again:
+        for x, y in zip(a, first):
+            np.testing.assert_array_equal(x, y)
 
 
 def test_noalloc_rejects_bad_sizes():
