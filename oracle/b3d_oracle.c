@@ -115,7 +115,12 @@ static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + 
  * Ambiguity flags (optional, flags != NULL), used to make FP32-vs-FP64 parity well posed:
  *   bit 0: the triangle id at this pixel could change under a perturbation of the edge
  *          tests by edge_tol_px pixels or of depths by z_tol_rel (relative);
- *   bit 1: additionally, the depth at this pixel could change by more than z_tol_rel.
+ *   bit 1: additionally, the depth at this pixel could change by more than z_tol_rel;
+ *   bit 2: the depth is ill-conditioned: moving the winning triangle's plane by the FP32
+ *          resolution of its camera-frame vertices (2 ulps of their largest coordinate,
+ *          2^-22 max|v|) moves the depth along the pixel ray by more than z_tol_rel
+ *          (the ray meets the plane at a grazing angle: dz = 2^-22 max|v| / |n.r|, n the
+ *          unit normal, r the pixel ray with r_z = 1).
  * These are computed by a second pass over the triangles; they do not alter the image.
  */
 typedef struct {
@@ -167,6 +172,34 @@ static double plane_depth(const tri_cam *t, const double r[3]) {
 static const double *object_pose(const orc_scene *sc, int o, int32_t slot, const double *slot_pose) {
     if (o == slot && slot_pose) return slot_pose;
     return sc->poses + 16 * (int64_t)o;
+}
+
+/* Camera-frame vertices of the triangle with global id g. */
+static void tri_vertices_cam(const orc_scene *sc, int32_t slot, const double *slot_pose, int32_t g, double A[3],
+                             double B[3], double C[3]) {
+    int o = 0;
+    while (o + 1 < sc->n_obj && g >= sc->f_off[o + 1]) ++o;
+    const double *Po = object_pose(sc, o, slot, slot_pose);
+    const double *verts = sc->verts + 3 * sc->v_off[o];
+    const int32_t *f = sc->faces + 3 * (int64_t)g;
+    apply_pose(Po, verts + 3 * (int64_t)f[0], A);
+    apply_pose(Po, verts + 3 * (int64_t)f[1], B);
+    apply_pose(Po, verts + 3 * (int64_t)f[2], C);
+}
+
+/* Depth change along the ray r (r_z = 1) of pixel (x, y) when the plane of triangle g moves by
+ * the FP32 resolution of its camera-frame vertices: 2^-22 max|v| / |n.r|, n the unit normal. */
+static double depth_resolution(const orc_camera *cam, const orc_scene *sc, int32_t slot, const double *slot_pose,
+                               int32_t g, int x, int y) {
+    double A[3], B[3], C[3], e1[3], e2[3], n[3], r[3];
+    tri_vertices_cam(sc, slot, slot_pose, g, A, B, C);
+    double vmax = 0;
+    for (int k = 0; k < 3; ++k) vmax = fmax(vmax, fmax(fabs(A[k]), fmax(fabs(B[k]), fabs(C[k]))));
+    for (int k = 0; k < 3; ++k) { e1[k] = B[k] - A[k]; e2[k] = C[k] - A[k]; }
+    cross3(e1, e2, n);
+    pixel_ray(cam, x, y, r);
+    const double nr = fabs(dot3(n, r)) / sqrt(dot3(n, n));
+    return nr > 0 ? ldexp(vmax, -22) / nr : INFINITY;
 }
 
 static void pixel_range(double lo, double hi, double tol, int n, int *a, int *b) {
@@ -247,6 +280,12 @@ static int render_core(const orc_camera *cam, const orc_scene *sc, int32_t slot,
         if (triid[i] >= 0) {
             depth[i] = best_z[i];
             if (flags) {
+                /* the winner's depth itself is fixed only to the FP32 resolution of its plane */
+                const double dz = depth_resolution(cam, sc, slot, slot_pose, triid[i], (int)(i % W), (int)(i / W));
+                if (dz > z_tol_rel * best_z[i]) {
+                    flags[i] |= 4;
+                    if (zmove) zmove[i] = fmax(zmove[i], dz);
+                }
                 /* the winner itself barely covers the pixel: the next candidate takes over */
                 if (best_m[i] < tol) {
                     double alt = isinf(second_z[i]) ? cam->far_z : second_z[i];
@@ -429,6 +468,8 @@ static double count_flip_bound(const orc_camera *cam, const orc_lik *lk, int n, 
  *                 z_tol_rel (bit 0 without bit 1) may move along its ray to the depth of
  *                 an alternative: by up to delta_j = m_j |r_j|, m_j the largest depth
  *                 change among the alternatives that set its flag (0 for coplanar ones);
+ *                 so may a pixel whose depth is ill-conditioned (bit 2), by its depth
+ *                 resolution;
  *               - kind 0: the change of l_i when its borderline pairs flip, a pair (i, j)
  *                 being borderline when |d^2 - r^2| <= border_tol r^2 or, for such a tie
  *                 pixel j, when |d - r| <= delta_j;
@@ -483,9 +524,11 @@ int orc_score(const orc_camera *cam, const orc_scene *sc, int32_t slot, int64_t 
                                 if (!isnan(ell[(int64_t)yi * W + xi])) bd += jump;
                             }
                     }
-                int n_tie = 0; /* id ties whose depth may move, by at most z_tol (bit 0 only) */
+                /* pixels whose depth may move by a bounded amount zmv: id ties within z_tol (bit 0
+                 * without bit 1) and ill-conditioned depths (bit 2) */
+                int n_tie = 0;
                 for (int64_t j = 0; j < P; ++j)
-                    if ((fl[j] & 3) == 1 && zmv[j] > 0 && !(lk->miss_mode == 1 && tid[j] < 0)) ++n_tie;
+                    if (!(fl[j] & 2) && zmv[j] > 0 && !(lk->miss_mode == 1 && tid[j] < 0)) ++n_tie;
                 if (lk->kind == 1 && n_tie > 0) {
                     double V, K;
                     lik_constants(cam, lk, &V, &K);
@@ -494,7 +537,7 @@ int orc_score(const orc_camera *cam, const orc_scene *sc, int32_t slot, int64_t 
                     for (int y = 0; y < H; ++y)
                         for (int x = 0; x < W; ++x) {
                             const int64_t j = (int64_t)y * W + x;
-                            if ((fl[j] & 3) != 1 || (lk->miss_mode == 1 && tid[j] < 0)) continue;
+                            if ((fl[j] & 2) || !(zmv[j] > 0) || (lk->miss_mode == 1 && tid[j] < 0)) continue;
                             double rj[3];
                             pixel_ray(cam, x, y, rj);
                             const double dN = slope * zmv[j] * sqrt(dot3(rj, rj));
@@ -531,7 +574,7 @@ int orc_score(const orc_camera *cam, const orc_scene *sc, int32_t slot, int64_t 
                                         double d = depth_obs[i] * ri[k] - depth[j] * rj[k];
                                         d2 += d * d;
                                     }
-                                    const int tie = (fl[j] & 3) == 1;
+                                    const int tie = !(fl[j] & 2) && zmv[j] > 0;
                                     if (fabs(d2 - r2) <= border_tol * r2 ||
                                         (tie && fabs(sqrt(d2) - lk->radius) <= zmv[j] * sqrt(dot3(rj, rj))))
                                         ++k_b;
@@ -942,7 +985,9 @@ int orc_score_grad(const orc_camera *cam, const orc_scene *sc, int32_t slot, int
  *     and whose depth is not behind the winner's by more than z_tol_rel;
  *   - a covering triangle whose depth is within z_tol_rel of the winner's;
  *   - when the winner's own coverage is within edge_tol_px: the nearest other covering
- *     triangle, else the background (a miss).
+ *     triangle, else the background (a miss);
+ *   - when the winner's depth is ill-conditioned (flag bit 2): the same triangle with its
+ *     depth moved either way by its FP32 resolution.
  * For each alternative the exact change of (dLL/dxi [6], dLL/ds, dLL/dp_out) when j alone
  * switches to it (all other pixels held) is formed from the definitions of orc_score_grad:
  * the observed pixels i in win(j) get S_i' = S_i - N(qt_i - q_j) + N(qt_i - q_j'); the
@@ -974,9 +1019,10 @@ static void tri_normal_cam(const orc_scene *sc, int32_t slot, const double *slot
     cross3(e1, e2, n);
 }
 
-static void add_alt(orc_alt *list, uint8_t *cnt, int32_t t, double z, const double n[3]) {
-    for (int k = 0; k < *cnt; ++k)
-        if (list[k].t == t) return;
+static void add_alt(orc_alt *list, uint8_t *cnt, int32_t t, double z, const double n[3], int same_t_ok) {
+    if (!same_t_ok)
+        for (int k = 0; k < *cnt; ++k)
+            if (list[k].t == t) return;
     if (*cnt >= ORC_MAX_ALT) return;
     orc_alt *a = &list[(*cnt)++];
     a->t = t;
@@ -1009,15 +1055,15 @@ int orc_score_grad_bound(const orc_camera *cam, const orc_scene *sc, int32_t slo
         double *depth = malloc(sizeof(double) * P), *S = malloc(sizeof(double) * P);
         double *dS = malloc(sizeof(double) * P), *pp = malloc(sizeof(double) * P);
         double *wm = malloc(sizeof(double) * P), *sec_z = malloc(sizeof(double) * P);
-        double *J = malloc(sizeof(double) * 6 * P);
+        double *J = malloc(sizeof(double) * 6 * P), *zmv = malloc(sizeof(double) * P);
         int32_t *tid = malloc(sizeof(int32_t) * P), *sec_t = malloc(sizeof(int32_t) * P);
         uint8_t *fl = malloc(P), *nalt = malloc(P);
         orc_alt *alts = malloc(sizeof(orc_alt) * ORC_MAX_ALT * P);
-        if (!depth || !S || !dS || !pp || !wm || !sec_z || !J || !tid || !sec_t || !fl || !nalt || !alts) {
+        if (!depth || !S || !dS || !pp || !wm || !sec_z || !J || !zmv || !tid || !sec_t || !fl || !nalt || !alts) {
             err = ORC_ENOMEM;
             goto done;
         }
-        orc_render(cam, sc, slot, Ph, edge_tol_px, z_tol_rel, depth, tid, fl);
+        render_core(cam, sc, slot, Ph, edge_tol_px, z_tol_rel, depth, tid, fl, zmv);
         for (int64_t i = 0; i < P; ++i) { nalt[i] = 0; wm[i] = INFINITY; sec_z[i] = INFINITY; sec_t[i] = -1; }
         /* alternatives of the flagged pixels: one pass over every triangle's pixel box */
         for (int o = 0; o < sc->n_obj; ++o) {
@@ -1044,19 +1090,27 @@ int orc_score_grad_bound(const orc_camera *cam, const orc_scene *sc, int32_t slo
                         if (g == tid[i]) { wm[i] = m; continue; }
                         const double zb = tid[i] >= 0 ? depth[i] : cam->far_z;
                         if ((fabs(m) < tol && z <= zb * (1.0 + z_tol_rel)) || (m >= 0 && z - zb <= z_tol_rel * zb))
-                            add_alt(alts + ORC_MAX_ALT * i, nalt + i, g, z, t.n);
+                            add_alt(alts + ORC_MAX_ALT * i, nalt + i, g, z, t.n, 0);
                         if (m >= 0 && (z < sec_z[i] || (z == sec_z[i] && g < sec_t[i]))) { sec_z[i] = z; sec_t[i] = g; }
                     }
             }
         }
         for (int64_t i = 0; i < P; ++i) {
+            if (fl[i] & 4) {
+                /* an ill-conditioned depth: the same triangle, its depth moved either way by its
+                 * resolution */
+                double n[3];
+                tri_normal_cam(sc, slot, Ph, tid[i], n);
+                add_alt(alts + ORC_MAX_ALT * i, nalt + i, tid[i], depth[i] + zmv[i], n, 1);
+                add_alt(alts + ORC_MAX_ALT * i, nalt + i, tid[i], depth[i] - zmv[i], n, 1);
+            }
             if (!fl[i] || tid[i] < 0 || !(wm[i] < tol)) continue;
             if (sec_t[i] >= 0) {
                 double n[3];
                 tri_normal_cam(sc, slot, Ph, sec_t[i], n);
-                add_alt(alts + ORC_MAX_ALT * i, nalt + i, sec_t[i], sec_z[i], n);
+                add_alt(alts + ORC_MAX_ALT * i, nalt + i, sec_t[i], sec_z[i], n, 0);
             } else {
-                add_alt(alts + ORC_MAX_ALT * i, nalt + i, -1, cam->far_z, NULL);
+                add_alt(alts + ORC_MAX_ALT * i, nalt + i, -1, cam->far_z, NULL, 0);
             }
         }
         /* observed side: S_i, dS_i/ds, p_i; rendered side: dz_k/dxi of the slot's pixels */
@@ -1196,7 +1250,7 @@ int orc_score_grad_bound(const orc_camera *cam, const orc_scene *sc, int32_t slo
         for (int c = 0; c < 8; ++c) gbound[8 * h + c] = gb[c];
         if (n_flag) n_flag[h] = nf;
     done:
-        free(depth); free(S); free(dS); free(pp); free(wm); free(sec_z); free(J);
+        free(depth); free(S); free(dS); free(pp); free(wm); free(sec_z); free(J); free(zmv);
         free(tid); free(sec_t); free(fl); free(nalt); free(alts);
     }
     return err;

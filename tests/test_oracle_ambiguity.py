@@ -339,3 +339,44 @@ def test_gradient_bound_of_a_crease_pixel_is_its_switch(orc):
     assert nf == 1
     np.testing.assert_allclose(gb, want, rtol=1e-9, atol=1e-12 * np.abs(_grad(orc, a, obs)).max())
     assert want[:6].max() > 0 and want[6:].max() == 0  # the depth stays: sigma and p_out do not move
+
+
+@pytest.mark.parametrize("D,cy,flagged", [(0.012, 4.4, True), (0.096, 3.7, False)])
+def test_ill_conditioned_depth_is_flagged(orc, D, cy, flagged):
+    """A horizontal strip y = D (x in [-1, 1], z in [0.5, 1.5]; largest vertex coordinate
+    V = 1.5) seen by pixel row 4 only: its ray (y/z = (4.5 - cy)/8, 0.0125 or 0.1) meets the
+    strip at z = 0.96, the rows above and below miss it, and no edge or diagonal comes
+    within 0.17 px of a centre. On a plane at distance D from the camera centre,
+    |n . r| z = D, so moving the plane by the FP32 resolution of its vertices, 2^-22 V,
+    moves the depth by the relative amount 2^-22 V / D: 3.0e-5 for D = 1.2 cm (above
+    z_tol = 1e-5: bit 2, the depth is ill-conditioned) and 3.7e-6 for D = 9.6 cm (below)."""
+    cam = synth.Camera(8, 8, 8.0, 8.0, 4.0, cy, 0.01, 2.0)
+    v = np.array([[-1, D, 0.5], [1, D, 0.5], [1, D, 1.5], [-1, D, 1.5]], np.float32)
+    sc = _scene([synth.Mesh(verts=v, faces=np.array([[0, 1, 2], [0, 2, 3]], np.int32))], cam)
+    depth, tid, flags = _render(orc, sc)
+    assert (tid[4] >= 0).all() and (tid[np.arange(8) != 4] < 0).all()
+    np.testing.assert_allclose(depth[4], float(np.float32(D)) / ((4.5 - cy) / 8.0), rtol=1e-12)
+    want = np.zeros((8, 8), np.uint8)
+    want[4] = 4 if flagged else 0
+    assert 2.0 ** -22 * 1.5 / float(np.float32(D)) > Z_TOL if flagged else 2.0 ** -22 * 1.5 / float(np.float32(D)) < Z_TOL
+    np.testing.assert_array_equal(flags, want)
+
+
+def test_bound_of_a_pair_seen_through_an_ill_conditioned_depth(orc):
+    """The strip at D = 1.2 cm of the previous test (depth resolution 2^-22 V / |n.r| along
+    each ray of row 4, about 2.9e-5 m) with an observation 8 um beyond the inlier ball of the
+    rendered point in its own pixel (row 4, column 2): outside the 1e-3 band, inside the
+    depth resolution, so the pair can flip: one count step (n = 0, one pair: l(1) - l(0))."""
+    cam = synth.Camera(8, 8, 8.0, 8.0, 4.0, 4.4, 0.01, 2.0)
+    D = 0.012
+    v = np.array([[-1, D, 0.5], [1, D, 0.5], [1, D, 1.5], [-1, D, 1.5]], np.float32)
+    sc = _scene([synth.Mesh(verts=v, faces=np.array([[0, 1, 2], [0, 2, 3]], np.int32))], cam)
+    depth, _, flags = _render(orc, sc)
+    ray = np.array([(2.5 - 4) / 8, (4.5 - 4.4) / 8, 1.0])
+    obs = np.full((8, 8), -1.0)  # nothing else observed
+    obs[4, 2] = depth[4, 2] + (LIK["radius"] + 8e-6) / np.linalg.norm(ray)
+    r = orc.score(sc, 0, sc.poses[0][None], LIK, obs, edge_tol=EDGE_TOL, z_tol=Z_TOL, border_tol=BORDER)
+    V = orc.frustum_volume(cam)
+    K = 9
+    assert r["n_border"][0] == 0 and r["n_flag"][0] == 0
+    assert r["bound"][0] == pytest.approx(_ell(1, 0.005, 0.01, K, V) - _ell(0, 0.005, 0.01, K, V), rel=1e-12)
