@@ -66,6 +66,34 @@ __device__ __forceinline__ void pose12(const PoseGrid &P, int64_t h, float *o) {
     }
 }
 
+// Element e (0..11) of the 12-float pose of hypothesis h, with the expressions of pose12:
+// lanes 0..11 of a warp form the pose together (the grid index is decoded in 32 bits: a
+// stage has fewer than 2^31 hypotheses and at most 1024 points per axis).
+__device__ __forceinline__ float pose_elem(const PoseList &P, int64_t h, int e) {
+    const float *p = P.p + 16 * h;
+    return e < 9 ? p[4 * (e / 3) + e % 3] : p[4 * (e - 9) + 3];
+}
+
+__device__ __forceinline__ float pose_elem(const PoseGrid &P, int64_t h, int e) {
+    const unsigned n = (unsigned)P.n, n2 = n * n, n3 = n2 * n, hh = (unsigned)h;
+    const unsigned ir = hh / n3;
+    unsigned rem = hh - ir * n3;
+    const unsigned ix = rem / n2;
+    rem -= ix * n2;
+    const unsigned iy = rem / n;
+    const unsigned iz = rem - iy * n;
+    const int c = (P.n & 1) ? (P.n - 1) / 2 : P.n / 2;
+    const float *C = P.centre;
+    if (e < 9) {
+        const int a = e / 3, b = e - 3 * a;
+        const float *Rk = P.rot + 9 * ir;
+        return fmaf(C[4 * a + 0], Rk[b], fmaf(C[4 * a + 1], Rk[3 + b], C[4 * a + 2] * Rk[6 + b]));
+    }
+    const int a = e - 9;
+    const float ox = (float)((int)ix - c) * P.step, oy = (float)((int)iy - c) * P.step, oz = (float)((int)iz - c) * P.step;
+    return C[4 * a + 3] + fmaf(P.G[3 * a + 0], ox, fmaf(P.G[3 * a + 1], oy, P.G[3 * a + 2] * oz));
+}
+
 // Camera-frame point of an object-frame point under a 12-float pose.
 __device__ __forceinline__ void xform(const float *P, float x, float y, float z, float &cx, float &cy, float &cz) {
     cx = fmaf(P[0], x, fmaf(P[1], y, fmaf(P[2], z, P[9])));
@@ -129,41 +157,6 @@ __device__ __forceinline__ void raster_tri(float4 A, float4 B, float4 C, int cul
             if (s * e0 < 0.f || s * e1 < 0.f || s * e2 < 0.f) continue;
             const float den = fmaf(e1, A.z, fmaf(e2, B.z, e0 * C.z));
             const float z = area / den;
-            if (!(z <= far_z)) continue;
-            store(x, y, z);
-        }
-    }
-}
-
-// Rasterise a planar convex quadrilateral C0 C1 C2 C3 (screen corners in order, as in
-// raster_tri): a pixel centre is covered when all four oriented edge functions are >= 0
-// (the union of the triangles C0C1C2 and C0C2C3 or C1C2C3 and C1C3C0 alike); the depth is
-// the reciprocal of the quad plane's affine 1/z at the centre.
-template <class Store>
-__device__ __forceinline__ void raster_quad(float4 C0, float4 C1, float4 C2, float4 C3, int rx0, int rx1, int ry0,
-                                            int ry1, float far_z, Store store, unsigned long long *tests = nullptr) {
-    const float area = edge_fn(C0.x, C0.y, C1.x, C1.y, C2.x, C2.y);
-    if (!(area != 0.f)) return;
-    const float umin = fminf(fminf(C0.x, C1.x), fminf(C2.x, C3.x)), umax = fmaxf(fmaxf(C0.x, C1.x), fmaxf(C2.x, C3.x));
-    const float vmin = fminf(fminf(C0.y, C1.y), fminf(C2.y, C3.y)), vmax = fmaxf(fmaxf(C0.y, C1.y), fmaxf(C2.y, C3.y));
-    const int x0 = (int)ceilf(fmaxf(umin - 0.5f, (float)rx0)), x1 = (int)floorf(fminf(umax - 0.5f, (float)rx1));
-    const int y0 = (int)ceilf(fmaxf(vmin - 0.5f, (float)ry0)), y1 = (int)floorf(fminf(vmax - 0.5f, (float)ry1));
-    if (x0 > x1 || y0 > y1) return;
-    if (tests) *tests += (unsigned long long)((x1 - x0 + 1) * (y1 - y0 + 1));
-    const float s = area > 0.f ? 1.f : -1.f;
-    const float du1 = C1.x - C0.x, dv1 = C1.y - C0.y, du2 = C2.x - C0.x, dv2 = C2.y - C0.y;
-    const float dz1 = C1.z - C0.z, dz2 = C2.z - C0.z;
-    const float al = fmaf(dz1, dv2, -(dz2 * dv1)) / area, be = fmaf(dz2, du1, -(dz1 * du2)) / area;
-    for (int y = y0; y <= y1; ++y) {
-        const float py = (float)y + 0.5f;
-        for (int x = x0; x <= x1; ++x) {
-            const float px = (float)x + 0.5f;
-            if (s * edge_fn(C0.x, C0.y, C1.x, C1.y, px, py) < 0.f) continue;
-            if (s * edge_fn(C1.x, C1.y, C2.x, C2.y, px, py) < 0.f) continue;
-            if (s * edge_fn(C2.x, C2.y, C3.x, C3.y, px, py) < 0.f) continue;
-            if (s * edge_fn(C3.x, C3.y, C0.x, C0.y, px, py) < 0.f) continue;
-            const float iz = fmaf(al, px - C0.x, fmaf(be, py - C0.y, C0.z));
-            const float z = 1.0f / iz;
             if (!(z <= far_z)) continue;
             store(x, y, z);
         }

@@ -25,16 +25,22 @@ def _np(t):
 
 
 def _check_render(orc, scene, slot, poses, depth, tid, max_frac=1e-4):
-    n_mis = n_px = 0
+    """Ids identical except at pixels the oracle flags as edge or depth ties (bit 0), and at
+    no more than max_frac of all pixels; depths within 1e-5 relative where the ids agree,
+    except where the oracle flags the depth as ill-conditioned (bit 2: the ray meets the
+    plane so obliquely that the FP32 resolution of the vertices moves it by more)."""
+    n_mis = n_px = n_cond = 0
     for k, P in enumerate(poses):
         od, ot, of = orc.render(scene, slot=slot, slot_pose=P, edge_tol=1e-4, z_tol=1e-5, want_flags=True)
         mis = ot != tid[k]
         assert not (mis & ((of & 1) == 0)).any(), f"pose {k}: {int((mis & ((of & 1) == 0)).sum())} unflagged id mismatches"
-        agree = ~mis
+        agree = ~mis & ((of & 4) == 0)  # where the ids agree and the depth is well conditioned
         rel = np.abs(depth[k][agree] - od[agree]) / od[agree]
         assert rel.max() <= 1e-5, f"pose {k}: depth rel err {rel.max()}"
+        n_cond += int(((of & 4) != 0).sum())
         n_mis += int(mis.sum())
         n_px += mis.size
+    print(f"render ids: {n_mis} of {n_px} pixels differ (all flagged); {n_cond} ill-conditioned depths")
     assert n_mis <= max(1, max_frac * n_px), f"{n_mis} of {n_px} pixels differ"
     return n_mis
 
@@ -81,7 +87,9 @@ def test_render_tabletop_composite(orc, tabletop):
 
 
 def test_render_large_footprint_and_ragged_image(orc):
-    """An object close to the camera covers several screen tiles; a ragged 37x29 image."""
+    """An object close to the camera covers several screen tiles; a ragged 37x29 image. Ids
+    identical except at flagged pixels, and at no more than 1e-4 of the pixels (16 poses:
+    307,200 and 17,168 pixels, so 30 and 1)."""
     rng = np.random.default_rng(13)
     cells = np.array(np.unravel_index(rng.permutation(512)[:300], (8, 8, 8))).T
     mesh = synth.voxel_mesh(cells, 0.02, origin=(-0.08, -0.08, -0.08))
@@ -92,10 +100,10 @@ def test_render_large_footprint_and_ragged_image(orc):
         sc = synth.Scene(cam, [mesh], pose[None].copy())
         obs = orc.render(sc)[0].astype(np.float32)
         ctx = gpu_context(sc, obs)
-        poses = jitter_poses(rng, pose, 4, trans=0.01, rot_deg=5)
+        poses = jitter_poses(rng, pose, 16, trans=0.01, rot_deg=5)
         d, t = ctx.render(0, poses)
         ctx.sync()
-        _check_render(orc, sc, 0, poses, _np(d), _np(t), max_frac=5e-4)
+        _check_render(orc, sc, 0, poses, _np(d), _np(t), max_frac=1e-4)
         lik = dict(kind=0, radius=0.005, p_outlier=0.01, half_window=2)
         ll = _np(ctx.score(0, poses, lik))
         ll2 = _np(ctx.score_depth(d, lik, t, slot=0))  # 37 x 29: no 16-byte vector access
@@ -286,12 +294,13 @@ def test_two_pass_tabletop_composite(orc, tabletop):
 
 def _check_depth(orc, scene, slot, poses, depth, max_frac=1e-4):
     """Depth-only renders (the rectangle rasteriser): within 1e-5 relative of the oracle
-    except at pixels it flags as edge or depth ties, and those at most max_frac of all."""
+    except at pixels it flags as edge or depth ties (bit 0) or ill-conditioned depths
+    (bit 2), and those at most max_frac of all."""
     n_bad = n_px = 0
     for k, P in enumerate(poses):
         od, _, of = orc.render(scene, slot=slot, slot_pose=P, edge_tol=1e-4, z_tol=1e-5, want_flags=True)
         bad = np.abs(depth[k] - od) > 1e-5 * od
-        assert not (bad & ((of & 1) == 0)).any(), f"pose {k}: {int((bad & ((of & 1) == 0)).sum())} unflagged depth mismatches"
+        assert not (bad & ((of & 5) == 0)).any(), f"pose {k}: {int((bad & ((of & 5) == 0)).sum())} unflagged depth mismatches"
         n_bad += int(bad.sum())
         n_px += bad.size
     assert n_bad <= max(1, max_frac * n_px), f"{n_bad} of {n_px} pixels differ"
