@@ -403,7 +403,7 @@ static int launch_score(const SceneView &sv, const Lik &L, PS P, int64_t n, floa
     case 2: return launch_score_nt<PS, 64, 10>(sv, L, P, n, ll, c, s);
     case 3: return launch_score_nt<PS, 32, 16>(sv, L, P, n, ll, c, s);
     case 4: return launch_score_nt<PS, 256, 4>(sv, L, P, n, ll, c, s);
-    case 5: return launch_score_nt<PS, 128, 7>(sv, L, P, n, ll, c, s);
+    case 5: return launch_score_nt<PS, 128, 8>(sv, L, P, n, ll, c, s);
     case 6: return launch_score_nt<PS, 64, 14>(sv, L, P, n, ll, c, s);
     case 7: return launch_score_nt<PS, 32, 24>(sv, L, P, n, ll, c, s);
     default: return launch_score_nt<PS, 256, 3>(sv, L, P, n, ll, c, s);
@@ -419,7 +419,7 @@ int launch_score_multi(const BatchItem *items, int n_items, const int64_t *item_
     case 2: return launch_score_multi_nt<64, 10>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);
     case 3: return launch_score_multi_nt<32, 16>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);
     case 4: return launch_score_multi_nt<256, 4>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);
-    case 5: return launch_score_multi_nt<128, 7>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);
+    case 5: return launch_score_multi_nt<128, 8>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);
     case 6: return launch_score_multi_nt<64, 14>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);
     case 7: return launch_score_multi_nt<32, 24>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);
     default: return launch_score_multi_nt<256, 3>(items, n_items, item_begin, total, chunk, counter, w, max_lat, c, s);

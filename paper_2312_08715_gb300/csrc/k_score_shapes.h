@@ -27,7 +27,7 @@ B3D_SCORE_SHAPE(128, 6)
 B3D_SCORE_SHAPE(64, 10)
 B3D_SCORE_SHAPE(32, 16)
 B3D_SCORE_SHAPE(256, 4)
-B3D_SCORE_SHAPE(128, 7)
+B3D_SCORE_SHAPE(128, 8)
 B3D_SCORE_SHAPE(64, 14)
 B3D_SCORE_SHAPE(32, 24)
 #undef B3D_SCORE_SHAPE
