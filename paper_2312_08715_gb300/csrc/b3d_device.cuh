@@ -66,34 +66,6 @@ __device__ __forceinline__ void pose12(const PoseGrid &P, int64_t h, float *o) {
     }
 }
 
-// Element e (0..11) of the 12-float pose of hypothesis h, with the expressions of pose12:
-// lanes 0..11 of a warp form the pose together (the grid index is decoded in 32 bits: a
-// stage has fewer than 2^31 hypotheses and at most 1024 points per axis).
-__device__ __forceinline__ float pose_elem(const PoseList &P, int64_t h, int e) {
-    const float *p = P.p + 16 * h;
-    return e < 9 ? p[4 * (e / 3) + e % 3] : p[4 * (e - 9) + 3];
-}
-
-__device__ __forceinline__ float pose_elem(const PoseGrid &P, int64_t h, int e) {
-    const unsigned n = (unsigned)P.n, n2 = n * n, n3 = n2 * n, hh = (unsigned)h;
-    const unsigned ir = hh / n3;
-    unsigned rem = hh - ir * n3;
-    const unsigned ix = rem / n2;
-    rem -= ix * n2;
-    const unsigned iy = rem / n;
-    const unsigned iz = rem - iy * n;
-    const int c = (P.n & 1) ? (P.n - 1) / 2 : P.n / 2;
-    const float *C = P.centre;
-    if (e < 9) {
-        const int a = e / 3, b = e - 3 * a;
-        const float *Rk = P.rot + 9 * ir;
-        return fmaf(C[4 * a + 0], Rk[b], fmaf(C[4 * a + 1], Rk[3 + b], C[4 * a + 2] * Rk[6 + b]));
-    }
-    const int a = e - 9;
-    const float ox = (float)((int)ix - c) * P.step, oy = (float)((int)iy - c) * P.step, oz = (float)((int)iz - c) * P.step;
-    return C[4 * a + 3] + fmaf(P.G[3 * a + 0], ox, fmaf(P.G[3 * a + 1], oy, P.G[3 * a + 2] * oz));
-}
-
 // Camera-frame point of an object-frame point under a 12-float pose.
 __device__ __forceinline__ void xform(const float *P, float x, float y, float z, float &cx, float &cy, float &cz) {
     cx = fmaf(P[0], x, fmaf(P[1], y, fmaf(P[2], z, P[9])));

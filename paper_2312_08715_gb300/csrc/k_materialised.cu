@@ -145,7 +145,10 @@ __global__ void __launch_bounds__(NT, MINB) k_render_fused(SceneView S, PoseList
     while (h < n_hyp) {
         __syncthreads();
         long long nxt = h + gridDim.x;
-        if (tid == 0 && S.work) nxt = (long long)gridDim.x + (long long)atomicAdd(S.work, 1ull);
+        if (tid == 0) {
+            if (S.work) nxt = (long long)gridDim.x + (long long)atomicAdd(S.work, 1ull);
+            pose12(P, h, sh.pose);
+        }
         float *dst = out_depth + h * npx;
         // the background first; render_tiles' barriers order these stores before the tiles'
         if (V == 4) {  // four loads in flight per thread
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(NT, MINB) k_render_fused(SceneView S, PoseList
         } else {
             for (int64_t k = tid; k < npx; k += NT) __stcs(dst + k, __ldg(S.bgd + k));
         }
-        render_tiles<false, NT>(S, 0, 0, P, h, sh, s_stage, zb, lat, nullptr,
+        render_tiles<false, NT>(S, 0, 0, sh, s_stage, zb, lat, nullptr,
                                 [&](const float *zd, int zx0, int zy0, int zw, int qx0, int qx1, int qy0, int qy1) {
                                     const int tww = qx1 - qx0 + 1, n = tww * (qy1 - qy0 + 1);
                                     const int dq = NT / tww, dr = NT - dq * tww;

@@ -39,7 +39,7 @@ inline int score_sm_count() {
 // score kernel
 // ------------------------------------------------------------------------------------------
 // One hypothesis per CTA iteration of a persistent grid:
-//  1. pose (formed by every warp); screen bounding box of the object; whether the near plane can cut it. For a
+//  1. pose; screen bounding box of the object; whether the near plane can cut it. For a
 //     quad (voxel) mesh wholly beyond the near plane: the camera position o in the object
 //     frame and, per face class (axis, outward sign), the contiguous range of quads whose
 //     plane has o on its outer side (the faces turned towards the camera); the rest are
@@ -180,7 +180,7 @@ __device__ __forceinline__ bool staged_inside(const float4 &E, float px, float p
 // Per-CTA shared state of one hypothesis.
 template <int NT>
 struct ScoreShared {
-    float pose[NT / 32][12];  // per warp: the hypothesis's pose (every warp forms it)
+    float pose[12];
     int bb[4];
     int fbb[4];   // bounding box of the tile's fragments
     int flags;    // bit 0: on screen, bit 1: rectangle path, bit 2: whole object beyond near
@@ -189,20 +189,16 @@ struct ScoreShared {
     int own[NT];  // per warp: the lane whose candidate run starts at each position of a window
 };
 
-// Renders hypothesis h of the pose source PS, tile by tile, into the shared-memory
-// z-buffer and composites it with the fixed objects' depths (misses: far, or -1 with
-// miss_mode 1); for each tile with fragments calls
+// Renders the hypothesis whose pose thread 0 has put in sh.pose, tile by tile, into the
+// shared-memory z-buffer and composites it with the fixed objects' depths (misses: far, or
+// -1 with miss_mode 1); for each tile with fragments calls
 // visit(zd, zx0, zy0, zw, qx0, qx1, qy0, qy1): the tile's depths zd (origin zx0, zy0, row
 // pitch zw) and the pixels to score, those whose half-window w reaches a fragment. Returns
 // false when the object is off screen (nothing visited). All threads of the CTA must call it.
-// Set-up needs no barrier before it: every warp forms the pose itself (lanes 0..11, one
-// element each, into the warp's slot of shared memory); warp 0 finds the screen box, warp 1
-// (warp 0 in a one-warp CTA) the face-class ranges, and every warp a share of the lattice
-// table. Nothing reads a warp's pose slot after the block sum that ends a hypothesis.
-template <bool STATS, int NT, class PS, class Visit>
-__device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss_mode, const PS &PSRC, int64_t h,
-                                             ScoreShared<NT> &sh, float4 *s_stage, unsigned *zb, float4 *lat,
-                                             unsigned long long *cnt, Visit &&visit) {
+template <bool STATS, int NT, class Visit>
+__device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss_mode, ScoreShared<NT> &sh,
+                                             float4 *s_stage, unsigned *zb, float4 *lat, unsigned long long *cnt,
+                                             Visit &&visit) {
     constexpr int REG = score_region<NT>();
     float *zd = reinterpret_cast<float *>(zb);  // same memory, as depths
     const Cam &c = S.cam;
@@ -211,12 +207,11 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
     const int n_lat = m.nc[0] + m.nc[1] + m.nc[2];
     const int nc0 = m.nc[0], nc01 = m.nc[0] + m.nc[1];
     auto lat_off = [&](int a) { return a == 0 ? 0 : (a == 1 ? nc0 : nc01); };
-    float *P = sh.pose[wid];
-    if (lane < 12) P[lane] = pose_elem(PSRC, h, lane);
-    __syncwarp();
     if (wid == 0) {
-        // lane k < 8 projects corner k of the object's box (the arithmetic of object_bbox,
-        // reduced with exact min / max over the 8 lanes)
+        // warp 0: lane k < 8 projects corner k of the object's box (the arithmetic of
+        // object_bbox, reduced with exact min / max), lane c < 6 finds face class c's range
+        __syncwarp();
+        const float *P = sh.pose;
         float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
         bool cfront = true;
         const bool has = m.n_full > 0;
@@ -234,7 +229,7 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
         }
         const bool front = has && __all_sync(0xffffffffu, cfront);
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
+        for (int o = 16; o > 0; o >>= 1) {
             umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, o));
             umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
             vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
@@ -251,62 +246,59 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
         }
         int f = has && bb0 <= bb1 && bb2 <= bb3 ? 1 : 0;
         if (front) f |= 4;
-        if (f && front && m.n_quads > 0) f |= 2;
+        if (f && front && m.n_quads > 0) {
+            f |= 2;
+            int cnt = 0, b = 0;
+            if (lane < 6) {
+                const int cls = lane, a = cls >> 1;
+                const float *R = P, *t = P + 9;
+                const float oa = -fmaf(R[a], t[0], fmaf(R[3 + a], t[1], R[6 + a] * t[2]));
+                const float *cd = m.coords + lat_off(a);
+                const int n = m.nc[a];
+                int lo = 0, hi = n;  // first plane with coordinate >= o
+                while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] < oa) lo = mid + 1; else hi = mid; }
+                const int below = lo;
+                hi = n;  // first plane with coordinate > o
+                while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] <= oa) lo = mid + 1; else hi = mid; }
+                const int not_above = lo;
+                const int *off = m.class_off + cls * m.np1;
+                // +axis faces face the camera when their plane is below o; -axis when above
+                b = (cls & 1) ? off[0] : off[not_above];
+                const int e = (cls & 1) ? off[below] : off[n];
+                cnt = e - b;
+            }
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                const int up = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += up;
+            }
+            if (lane < 6) {
+                sh.rng[lane] = b;
+                sh.rng[6 + lane] = incl - cnt;
+            }
+            if (lane == 5) sh.rng[12] = incl;
+        }
         if (lane == 0) {
             sh.bb[0] = bb0; sh.bb[1] = bb1; sh.bb[2] = bb2; sh.bb[3] = bb3;
             sh.flags = f;
         }
     }
-    if (m.n_quads > 0 && wid == (nt > 32 ? 1 : 0)) {
-        // lane c < 6 finds the range of face class c's rectangles turned towards the camera
-        // (used only when the object is wholly beyond the near plane)
-        int cnt_c = 0, b = 0;
-        if (lane < 6) {
-            const int cls = lane, a = cls >> 1;
-            const float *R = P, *t = P + 9;
-            const float oa = -fmaf(R[a], t[0], fmaf(R[3 + a], t[1], R[6 + a] * t[2]));
-            const float *cd = m.coords + lat_off(a);
-            const int n = m.nc[a];
-            int lo = 0, hi = n;  // first plane with coordinate >= o
-            while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] < oa) lo = mid + 1; else hi = mid; }
-            const int below = lo;
-            hi = n;  // first plane with coordinate > o
-            while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] <= oa) lo = mid + 1; else hi = mid; }
-            const int not_above = lo;
-            const int *off = m.class_off + cls * m.np1;
-            // +axis faces face the camera when their plane is below o; -axis when above
-            b = (cls & 1) ? off[0] : off[not_above];
-            const int e = (cls & 1) ? off[below] : off[n];
-            cnt_c = e - b;
-        }
-        int incl = cnt_c;
-#pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-            const int up = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += up;
-        }
-        if (lane < 6) {
-            sh.rng[lane] = b;
-            sh.rng[6 + lane] = incl - cnt_c;
-        }
-        if (lane == 5) sh.rng[12] = incl;
-    }
-    if (m.n_quads > 0) {
-        // camera-frame positions of the lattice planes
-        for (int k = tid; k < n_lat; k += nt) {
-            const int a = k < nc0 ? 0 : (k < nc01 ? 1 : 2);
-            const float v = m.coords[k];
-            lat[k] = make_float4(fmaf(P[a], v, a == 0 ? P[9] : 0.f), fmaf(P[3 + a], v, a == 0 ? P[10] : 0.f),
-                                 fmaf(P[6 + a], v, a == 0 ? P[11] : 0.f), 0.f);
-        }
-        if (STATS) cnt[1] += (unsigned long long)((n_lat - tid + nt - 1) / nt);
-    }
     __syncthreads();
     const int flags = sh.flags;
     if (!(flags & 1)) return false;
-    const float *pose = sh.pose[0];
+    const float *pose = sh.pose;
     const bool quad = (flags & 2) != 0, front = (flags & 4) != 0;
     const int bx0 = sh.bb[0], bx1 = sh.bb[1], by0 = sh.bb[2], by1 = sh.bb[3];
+    if (quad) {
+        for (int k = tid; k < n_lat; k += nt) {
+            const int a = k < nc0 ? 0 : (k < nc01 ? 1 : 2);
+            const float v = m.coords[k];
+            lat[k] = make_float4(fmaf(pose[a], v, a == 0 ? pose[9] : 0.f), fmaf(pose[3 + a], v, a == 0 ? pose[10] : 0.f),
+                                 fmaf(pose[6 + a], v, a == 0 ? pose[11] : 0.f), 0.f);
+        }
+        if (STATS) cnt[1] += (unsigned long long)((n_lat - tid + nt - 1) / nt);
+    }
     const int sx0 = max(bx0 - w, 0), sx1 = min(bx1 + w, c.W - 1);
     const int sy0 = max(by0 - w, 0), sy1 = min(by1 + w, c.H - 1);
     const int sw = sx1 - sx0 + 1;
@@ -509,27 +501,24 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
             const int qx0 = max(sh.fbb[0] - w, tx0), qx1 = min(sh.fbb[1] + w, tx1);
             const int qy0 = max(sh.fbb[2] - w, ty0), qy1 = min(sh.fbb[3] + w, ty1);
             visit(static_cast<const float *>(zd), zx0, zy0, zw, qx0, qx1, qy0, qy1);
-            // the next tile clears the z-buffer; after the last one the next write to it comes
-            // after the block sum's barrier and the next set-up's
-            if (tx0 + tw <= sx1 || ty0 + th <= sy1) __syncthreads();
+            __syncthreads();
         }
     }
     return true;
 }
 
-// Scores hypothesis h of the pose source: returns this thread's part of the sum of
-// l_i - l_i(bg) over the pixels whose window can see the object (every part is 0 when it is
-// off screen); block_sum gives the total. All threads of the CTA must call it.
-template <bool STATS, int WT, int NT, class PS>
-__device__ __forceinline__ float score_acc(const SceneView &S, const Lik &L, const PS &PSRC, int64_t h,
-                                           const float *s_lut, ScoreShared<NT> &sh, float4 *s_stage, unsigned *zb,
-                                           float4 *lat, unsigned long long *cnt) {
+// Scores the hypothesis whose pose thread 0 has put in sh.pose: returns, in thread 0, the
+// sum of l_i - l_i(bg) over the pixels whose window can see the object (0 when it is off
+// screen). All threads of the CTA must call it.
+template <bool STATS, int WT, int NT>
+__device__ __forceinline__ float score_body(const SceneView &S, const Lik &L, const float *s_lut, ScoreShared<NT> &sh,
+                                            float4 *s_stage, unsigned *zb, float4 *lat, unsigned long long *cnt) {
     const Cam &c = S.cam;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int w = WT > 0 ? WT : L.w;
     float acc = 0.f;
-    render_tiles<STATS, NT>(
-        S, w, L.miss_mode, PSRC, h, sh, s_stage, zb, lat, cnt,
+    const bool drawn = render_tiles<STATS, NT>(
+        S, w, L.miss_mode, sh, s_stage, zb, lat, cnt,
         [&](const float *zd, int zx0, int zy0, int zw, int qx0, int qx1, int qy0, int qy1) {
             const int tww = qx1 - qx0 + 1, thh = qy1 - qy0 + 1;
             if (WT > 0) {
@@ -567,15 +556,8 @@ __device__ __forceinline__ float score_acc(const SceneView &S, const Lik &L, con
                 }
             }
         });
-    return acc;
-}
-
-// The pose source of a batched launch's item: a list or a coarse-to-fine grid.
-struct ItemPoses {
-    const BatchItem *it;
-};
-__device__ __forceinline__ float pose_elem(const ItemPoses &P, int64_t h, int e) {
-    return P.it->pose_kind == 0 ? pose_elem(P.it->list, h, e) : pose_elem(P.it->grid, h, e);
+    if (!drawn) return 0.f;
+    return block_sum(acc, sh.red);
 }
 
 template <class PS, bool STATS, int WT, int NT, int MINB>
@@ -591,25 +573,26 @@ __global__ void __launch_bounds__(NT, MINB)
     const int tid = threadIdx.x;
     for (int i = tid; i < L.n_lut; i += blockDim.x) s_lut[i] = L.lut[i];
     unsigned long long cnt[kNumStats] = {0, 0, 0, 0, 0, 0, 0, 0};
-    __shared__ long long s_next[2];
+    __shared__ long long s_next;
     // With a counter, CTAs take their next hypothesis from it as they finish one (so they all
     // finish together however uneven the hypotheses' costs); thread 0 asks for it at the start
-    // of the current one and publishes it before the block sum's barrier, in the slot of this
-    // iteration's parity: a warp reads it after that barrier, while the next write to the slot
-    // comes two iterations later, after the next set-up's barrier.
+    // of the current one and publishes it at the end.
     int64_t h = blockIdx.x;
     __syncthreads();
-    for (int it = 0; h < n_hyp; ++it) {
+    while (h < n_hyp) {
         long long nxt = h + gridDim.x;
         if (tid == 0) {
             if (S.work) nxt = (long long)gridDim.x + (long long)atomicAdd(S.work, 1ull);
             if (STATS) ++cnt[0];
+            pose12(P, h, sh.pose);
         }
-        const float acc = score_acc<STATS, WT, NT>(S, L, P, h, s_lut, sh, s_stage, zb, lat, cnt);
-        if (tid == 0) s_next[it & 1] = nxt;
-        const float tot = block_sum(acc, sh.red);
-        if (tid == 0) out_ll[h] = (float)(*S.ll_bg + (double)tot);
-        h = s_next[it & 1];
+        const float tot = score_body<STATS, WT, NT>(S, L, s_lut, sh, s_stage, zb, lat, cnt);
+        if (tid == 0) {
+            out_ll[h] = (float)(*S.ll_bg + (double)tot);
+            s_next = nxt;
+        }
+        __syncthreads();  // the next write of s_next comes after score_body's barriers
+        h = s_next;
     }
     if (STATS)
         for (int k = 0; k < kNumStats; ++k)
@@ -659,9 +642,12 @@ __global__ void __launch_bounds__(NT, MINB)
             }
             const int64_t ib = item_begin[it], ie = min(item_begin[it + 1], e);
             for (; g < ie; ++g) {
-                const float acc = score_acc<false, WT, NT>(s_item.S, s_item.L, ItemPoses{&s_item}, g - ib,
-                                                           s_item.L.lut, sh, s_stage, zb, lat, nullptr);
-                const float tot = block_sum(acc, sh.red);
+                __syncthreads();
+                if (tid == 0) {
+                    if (s_item.pose_kind == 0) pose12(s_item.list, g - ib, sh.pose);
+                    else pose12(s_item.grid, g - ib, sh.pose);
+                }
+                const float tot = score_body<false, WT, NT>(s_item.S, s_item.L, s_item.L.lut, sh, s_stage, zb, lat, nullptr);
                 if (tid == 0) s_item.out_ll[g - ib] = (float)(*s_item.S.ll_bg + (double)tot);
             }
         }

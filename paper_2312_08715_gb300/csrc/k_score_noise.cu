@@ -143,13 +143,16 @@ __global__ void __launch_bounds__(NT, MINB)
     while (h < n_hyp) {
         __syncthreads();
         long long nxt = h + gridDim.x;
-        if (tid == 0 && S.work) nxt = (long long)gridDim.x + (long long)atomicAdd(S.work, 1ull);
+        if (tid == 0) {
+            if (S.work) nxt = (long long)gridDim.x + (long long)atomicAdd(S.work, 1ull);
+            pose12(P, h, sh.pose);
+        }
         float acc[kMaxNoise];
 #pragma unroll
         for (int g = 0; g < kMaxNoise; ++g) acc[g] = 0.f;
         const int nt = blockDim.x;
         render_tiles<false, NT>(
-            S, N.w, N.miss_mode, P, h, sh, s_stage, zb, lat, nullptr,
+            S, N.w, N.miss_mode, sh, s_stage, zb, lat, nullptr,
             [&](const float *zd, int zx0, int zy0, int zw, int qx0, int qx1, int qy0, int qy1) {
                 const int tww = qx1 - qx0 + 1, thh = qy1 - qy0 + 1;
                 const int n_tile = tww * thh;
