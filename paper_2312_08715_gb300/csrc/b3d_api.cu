@@ -56,6 +56,8 @@ struct BgCache {
     unsigned long long *bg = nullptr;
     float *bgd = nullptr;  // [2][npx] background depth under miss modes 0 and 1
     float *ell = nullptr, *gs = nullptr, *gp = nullptr;
+    float2 *qe = nullptr;     // score kernels' packed (observed depth, ell) per pixel
+    unsigned *bgz = nullptr;  // and background depth bits, both written with ell
     double *sums = nullptr, *part = nullptr;  // sums [3]; per-block partials of the table kernel
     unsigned *counter = nullptr;               // its last-block ticket (zero between launches)
     int64_t cap = 0, gcap = 0;
@@ -352,10 +354,13 @@ b3d_status ensure_bg(b3d_ctx *ctx, int32_t slot, cudaStream_t s) {
     b3d_status st;
     if (c.cap < npx) {
         dfree(ctx, c.bg); dfree(ctx, c.bgd); dfree(ctx, c.ell); dfree(ctx, c.gs); dfree(ctx, c.gp);
+        dfree(ctx, c.qe); dfree(ctx, c.bgz);
         c.cap = c.gcap = 0;
         if ((st = dalloc(ctx, &c.bg, (size_t)npx, "background z-buffer")) != B3D_OK) return st;
         if ((st = dalloc(ctx, &c.bgd, (size_t)2 * npx, "background depth")) != B3D_OK) return st;
         if ((st = dalloc(ctx, &c.ell, (size_t)npx, "background likelihood")) != B3D_OK) return st;
+        if ((st = dalloc(ctx, &c.qe, (size_t)npx, "packed observation and background terms")) != B3D_OK) return st;
+        if ((st = dalloc(ctx, &c.bgz, (size_t)npx, "background depth bits")) != B3D_OK) return st;
         if (!c.sums && (st = dalloc(ctx, &c.sums, 3, "background sums")) != B3D_OK) return st;
         dfree(ctx, c.part);
         if ((st = dalloc(ctx, &c.part, (size_t)3 * bg_table_blocks(npx), "background partial sums")) != B3D_OK) return st;
@@ -402,6 +407,8 @@ SceneView scene_view(b3d_ctx *ctx, int32_t slot) {
         sv.bg = c.bg;
         sv.bgd = c.bgd;
         sv.ell_bg = c.ell;
+        sv.qe = c.lik_valid ? c.qe : nullptr;
+        sv.bgz = c.lik_valid ? c.bgz : nullptr;
         sv.ll_bg = c.sums;
         sv.gs_bg = c.gs;
         sv.gp_bg = c.gp;
@@ -440,7 +447,8 @@ b3d_status ensure_bg_lik(b3d_ctx *ctx, int32_t slot, const b3d_lik_params *lp, c
     if (c.lik_valid && c.key == k && (!grad || c.grad_valid)) return B3D_OK;
     SceneView sv = scene_view(ctx, slot);
     Timed tm(ctx, B3D_K_SCENE, s);
-    launch_bg_tables(sv, L, c.ell, grad ? c.gs : nullptr, grad ? c.gp : nullptr, c.part, c.counter, c.sums, s);
+    launch_bg_tables(sv, L, c.ell, grad ? c.gs : nullptr, grad ? c.gp : nullptr, c.qe, c.bgz, c.part, c.counter,
+                     c.sums, s);
     ++ctx->launches;
     c.key = k;
     c.lik_valid = true;
@@ -1095,8 +1103,8 @@ b3d_status b3d_set_scene(b3d_ctx *ctx, const b3d_intrinsics *intr, int32_t n_obj
     // drop the background caches of slots the new scene does not have
     while (ctx->bgc.size() > (size_t)n_obj + 1) {
         BgCache &c = ctx->bgc.back();
-        dfree(ctx, c.bg); dfree(ctx, c.ell); dfree(ctx, c.gs); dfree(ctx, c.gp); dfree(ctx, c.sums);
-        dfree(ctx, c.part); dfree(ctx, c.counter);
+        dfree(ctx, c.bg); dfree(ctx, c.bgd); dfree(ctx, c.ell); dfree(ctx, c.gs); dfree(ctx, c.gp); dfree(ctx, c.sums);
+        dfree(ctx, c.qe); dfree(ctx, c.bgz); dfree(ctx, c.part); dfree(ctx, c.counter);
         dfree(ctx, c.nell); dfree(ctx, c.nsums); dfree(ctx, c.npart); dfree(ctx, c.ncounter);
         ctx->bgc.pop_back();
     }

@@ -47,12 +47,23 @@ __device__ __forceinline__ void pose12(const PoseList &P, int64_t h, float *o) {
 __device__ __forceinline__ void pose12(const PoseGrid &P, int64_t h, float *o) {
     const int n = P.n;
     const int64_t n2 = (int64_t)n * n, n3 = n2 * n;
-    const int ir = (int)(h / n3);
-    int64_t rem = h - (int64_t)ir * n3;
-    const int ix = (int)(rem / n2);
-    rem -= (int64_t)ix * n2;
-    const int iy = (int)(rem / n);
-    const int iz = (int)(rem - (int64_t)iy * n);
+    int ir, ix, iy, iz;
+    if (h <= INT32_MAX && n3 <= INT32_MAX) {  // the same quotients in 32-bit arithmetic
+        const unsigned hh = (unsigned)h, m2 = (unsigned)n2, m3 = (unsigned)n3, m1 = (unsigned)n;
+        const unsigned qr = hh / m3;
+        unsigned r = hh - qr * m3;
+        const unsigned qx = r / m2;
+        r -= qx * m2;
+        const unsigned qy = r / m1;
+        ir = (int)qr; ix = (int)qx; iy = (int)qy; iz = (int)(r - qy * m1);
+    } else {
+        ir = (int)(h / n3);
+        int64_t rem = h - (int64_t)ir * n3;
+        ix = (int)(rem / n2);
+        rem -= (int64_t)ix * n2;
+        iy = (int)(rem / n);
+        iz = (int)(rem - (int64_t)iy * n);
+    }
     const int c = (n & 1) ? (n - 1) / 2 : n / 2;
     const float ox = (float)(ix - c) * P.step, oy = (float)(iy - c) * P.step, oz = (float)(iz - c) * P.step;
     const float *C = P.centre;

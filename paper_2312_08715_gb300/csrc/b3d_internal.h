@@ -103,6 +103,11 @@ struct SceneView {
     const unsigned long long *bg;      // [H*W] (depth bits << 32 | triangle id) of the fixed objects
     const float *bgd;                  // [2][H*W] their depth, misses at the far plane / -1 (miss modes 0, 1)
     const float *ell_bg;               // [H*W] l_i of the fixed objects alone (0 where not scored)
+    // The fused score kernels' per-pixel inputs, packed (12 B a pixel instead of 28, so a
+    // hypothesis's screen box stays in L1 across the CTAs of an SM); NULL until the
+    // likelihood tables of this background are built:
+    const float2 *qe;                  // [H*W] (observed depth or 0 where no point, ell_bg)
+    const unsigned *bgz;               // [H*W] depth bits of the fixed objects (bg >> 32)
     const double *ll_bg;               // [1]   sum of ell_bg
     const float *gs_bg;                // [H*W] d l_i / d sigma, fixed objects alone (gradient only)
     const float *gp_bg;                // [H*W] d l_i / d p_out, fixed objects alone (gradient only)
@@ -203,8 +208,8 @@ void launch_bg_raster(const Cam &cam, const MeshView &m, const float *pose16_dev
 // Per-pixel background terms and their double-precision sums (sums[0..2]); part holds
 // 3 x bg_table_blocks(W H) doubles, counter one zeroed word (left zeroed).
 int bg_table_blocks(int64_t n);
-void launch_bg_tables(const SceneView &sv, const Lik &L, float *ell_bg, float *gs_bg, float *gp_bg, double *part,
-                      unsigned *counter, double *sums, cudaStream_t s);
+void launch_bg_tables(const SceneView &sv, const Lik &L, float *ell_bg, float *gs_bg, float *gp_bg, float2 *qe,
+                      unsigned *bgz, double *part, unsigned *counter, double *sums, cudaStream_t s);
 int launch_score_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, int grid, cudaStream_t s);
 int launch_score_grid(const SceneView &sv, const Lik &L, PoseGrid P, int64_t n, float *ll, int grid, cudaStream_t s);
 // ---- launchers (k_materialised.cu) -------------------------------------------------------

@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(NT, MINB) k_render_fused(SceneView S, PoseList
     const int tid = threadIdx.x;
     const int64_t npx = (int64_t)c.W * c.H;
     __shared__ long long s_next;
+    lattice_coords(S.mesh, lat);  // ordered before use by the loop's first barrier
     int64_t h = blockIdx.x;  // then from the counter S.work when given
     while (h < n_hyp) {
         __syncthreads();

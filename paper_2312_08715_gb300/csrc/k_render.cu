@@ -285,7 +285,8 @@ __global__ void k_bg_raster_px(Cam c, MeshView m, const float *pose16, int tri_b
 // order: each block reduces its pixels into part[3 block ..], and the block that finishes
 // last (a ticket on *counter, which it resets) adds the block partials in block order.
 __global__ void __launch_bounds__(256) k_bg_tables(SceneView S, Lik L, float *ell_bg, float *gs_bg, float *gp_bg,
-                                                   double *part, unsigned *counter, double *out) {
+                                                   float2 *qe, unsigned *bgz, double *part, unsigned *counter,
+                                                   double *out) {
     __shared__ float s_lut[kMaxLut];
     __shared__ double s_red[3][256 / 32];
     __shared__ bool s_last;
@@ -307,6 +308,10 @@ __global__ void __launch_bounds__(256) k_bg_tables(SceneView S, Lik L, float *el
             }
         }
         ell_bg[i] = l;
+        // the score kernels' packed inputs: observed depth (0 where no point) with this term,
+        // and the background's depth bits
+        qe[i] = make_float2(q.w != 0.f ? q.z : 0.f, l);
+        bgz[i] = (unsigned)(S.bg[i] >> 32);
         acc[0] += (double)l;
         if (gs_bg) {
             gs_bg[i] = gs;
@@ -496,10 +501,10 @@ void launch_bg_raster(const Cam &cam, const MeshView &m, const float *pose16_dev
 
 int bg_table_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096)); }
 
-void launch_bg_tables(const SceneView &sv, const Lik &L, float *ell_bg, float *gs_bg, float *gp_bg, double *part,
-                      unsigned *counter, double *sums, cudaStream_t s) {
+void launch_bg_tables(const SceneView &sv, const Lik &L, float *ell_bg, float *gs_bg, float *gp_bg, float2 *qe,
+                      unsigned *bgz, double *part, unsigned *counter, double *sums, cudaStream_t s) {
     const int64_t n = (int64_t)sv.cam.W * sv.cam.H;
-    k_bg_tables<<<bg_table_blocks(n), 256, 0, s>>>(sv, L, ell_bg, gs_bg, gp_bg, part, counter, sums);
+    k_bg_tables<<<bg_table_blocks(n), 256, 0, s>>>(sv, L, ell_bg, gs_bg, gp_bg, qe, bgz, part, counter, sums);
 }
 
 }  // namespace b3d

@@ -96,6 +96,7 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
     }
     float acc = 0.f;
     const bool ball_skips_empty = L.r2 < 0.25f;
+    const float rxc = rx[W];  // the column's own ray
     for (int y = ya; y <= yb; ++y) {
 #pragma unroll
         for (int r = 0; r + 1 < D; ++r) {
@@ -106,8 +107,10 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
         load_row(y + W, win[D - 1]);
         ry[D - 1] = ((float)(y + W) + 0.5f - c.cy) * c.inv_fy;
         const int64_t gi = (int64_t)y * c.W + x;
-        const float4 q = S.obs[gi];
-        if (q.w == 0.f) continue;
+        const float2 qe = S.qe[gi];  // observed depth (0: no point) and the background's term
+        if (qe.x == 0.f) continue;
+        // the observed point, formed from its depth as the observation kernel forms it
+        const float4 q = make_float4(__fmul_rn(qe.x, rxc), __fmul_rn(qe.x, ry[W]), qe.x, 1.f);
         int n = 0;
         float Ssum = 0.f;
         if (L.kind == 0 && ball_skips_empty) {
@@ -136,7 +139,7 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
             }
         }
         const float l = L.kind == 0 ? lut[n] : __logf(fmaf(L.bg, Ssum, L.a));
-        acc += l - S.ell_bg[gi];
+        acc += l - qe.y;
         if (n_px) {
             ++*n_px;
             *n_pairs += (unsigned long long)((min(y + W, c.H - 1) - max(y - W, 0) + 1) *
@@ -150,7 +153,16 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
 // for one more resident CTA per SM than 4096 while still holding a tabletop footprint in one tile)
 template <int NT>
 constexpr int score_region() { return NT <= 64 ? 2048 : (NT == 128 ? 3072 : kRegionPx); }
+// pixels per thread whose background depths the composite loads together
+#ifndef B3D_COMPOSITE_BATCH
+#define B3D_COMPOSITE_BATCH 4
+#endif
+constexpr int kCompBatch = B3D_COMPOSITE_BATCH;
 constexpr int kStageStride = 6;  // float4 per staged rectangle: four edges, plane, pixel box
+// Layout of a warp's 32 staged records: component k of lane l's record at [k * 32 + l], so
+// the lanes' stores and the owners' loads touch consecutive 16-byte words (rather than
+// words 96 bytes apart, which shared four banks between lanes l and l + 4).
+__device__ __forceinline__ int stage_slot(int l, int k) { return k * 32 + l; }
 // Pixels a candidate of the cooperative rasteriser covers (a block of kCandX x kCandY): the
 // owner lookup, record loads and index arithmetic are shared by the block's pixel tests.
 #ifndef B3D_CAND_X
@@ -175,6 +187,15 @@ __device__ __forceinline__ float4 stage_edge(float ax, float ay, float bx, float
 
 __device__ __forceinline__ bool staged_inside(const float4 &E, float px, float py) {
     return fmaf(E.z, py - E.y, -(E.w * (px - E.x))) >= 0.f;
+}
+
+// The mesh's lattice plane coordinates into the .w of the CTA's lattice table, once per
+// mesh (before the barrier that precedes the first render_tiles): each hypothesis's lattice
+// pass then reads them from shared memory rather than from a global load that misses L1.
+__device__ __forceinline__ void lattice_coords(const MeshView &m, float4 *lat) {
+    if (m.n_quads <= 0) return;
+    const int n = m.nc[0] + m.nc[1] + m.nc[2];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) lat[k].w = m.coords[k];
 }
 
 // Per-CTA shared state of one hypothesis.
@@ -293,9 +314,9 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
     if (quad) {
         for (int k = tid; k < n_lat; k += nt) {
             const int a = k < nc0 ? 0 : (k < nc01 ? 1 : 2);
-            const float v = m.coords[k];
+            const float v = lat[k].w;  // the plane's coordinate (lattice_coords)
             lat[k] = make_float4(fmaf(pose[a], v, a == 0 ? pose[9] : 0.f), fmaf(pose[3 + a], v, a == 0 ? pose[10] : 0.f),
-                                 fmaf(pose[6 + a], v, a == 0 ? pose[11] : 0.f), 0.f);
+                                 fmaf(pose[6 + a], v, a == 0 ? pose[11] : 0.f), v);
         }
         if (STATS) cnt[1] += (unsigned long long)((n_lat - tid + nt - 1) / nt);
     }
@@ -377,19 +398,18 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                                     const float al = fmaf(dz1, dv2, -(dz2 * dv1)) * inv;
                                     const float be = fmaf(dz2, du1, -(dz1 * du2)) * inv;
                                     const float sgn = area > 0.f ? 1.f : -1.f;
-                                    float4 *rec = stg + lane * kStageStride;
-                                    rec[0] = stage_edge(C0.x, C0.y, C1.x, C1.y, sgn);
-                                    rec[1] = stage_edge(C1.x, C1.y, C2.x, C2.y, sgn);
-                                    rec[2] = stage_edge(C2.x, C2.y, C3.x, C3.y, sgn);
-                                    rec[3] = stage_edge(C3.x, C3.y, C0.x, C0.y, sgn);
+                                    stg[stage_slot(lane, 0)] = stage_edge(C0.x, C0.y, C1.x, C1.y, sgn);
+                                    stg[stage_slot(lane, 1)] = stage_edge(C1.x, C1.y, C2.x, C2.y, sgn);
+                                    stg[stage_slot(lane, 2)] = stage_edge(C2.x, C2.y, C3.x, C3.y, sgn);
+                                    stg[stage_slot(lane, 3)] = stage_edge(C3.x, C3.y, C0.x, C0.y, sgn);
                                     // 1/z = al px + be py + K over the quad's plane
                                     const float K = fmaf(-al, C0.x, fmaf(-be, C0.y, C0.z));
                                     // the candidate's row is floor((k + 1/2) / candidates per row), exact
                                     // in float with an approximate reciprocal for the region's sizes (the
                                     // quotient is at least 1/(2 bw2) from an integer; the error is below
                                     // (k + 1/2) 2^-21 / bw2)
-                                    rec[4] = make_float4(al, be, K, __fdividef(1.0f, (float)bw2));
-                                    rec[5] = make_float4(__int_as_float(x0), __int_as_float(y0), __int_as_float(bw2),
+                                    stg[stage_slot(lane, 4)] = make_float4(al, be, K, __fdividef(1.0f, (float)bw2));
+                                    stg[stage_slot(lane, 5)] = make_float4(__int_as_float(x0), __int_as_float(y0), __int_as_float(bw2),
                                                          __int_as_float((x1 - x0) | ((y1 - y0) << 16)));
                                 }
                             }
@@ -419,9 +439,9 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                             const int kk = j - __shfl_sync(0xffffffffu, excl, lo);
                             __syncwarp();
                             if (j < n_cand) {
-                                const float4 *rec = stg + lo * kStageStride;
-                                const float4 Pl = rec[4], Bx = rec[5];
-                                const float4 E0 = rec[0], E1 = rec[1], E2 = rec[2], E3 = rec[3];
+                                const float4 Pl = stg[stage_slot(lo, 4)], Bx = stg[stage_slot(lo, 5)];
+                                const float4 E0 = stg[stage_slot(lo, 0)], E1 = stg[stage_slot(lo, 1)];
+                                const float4 E2 = stg[stage_slot(lo, 2)], E3 = stg[stage_slot(lo, 3)];
                                 const int bw2 = __float_as_int(Bx.z), ends = __float_as_int(Bx.w);
                                 const int bx = __float_as_int(Bx.x), by = __float_as_int(Bx.y);
                                 const int xe = bx + (ends & 0xffff), ye = by + (ends >> 16);  // box extent < 2^16
@@ -484,15 +504,32 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                 const int cw = cx1 - cx0 + 1, n_c = cw * (cy1 - cy0 + 1);
                 const int dq = nt / cw, dr = nt - dq * cw;
                 int y = tid / cw, x = tid - y * cw;
-                for (int i = tid; i < n_c; i += nt) {
-                    const int gx = cx0 + x, gy = cy0 + y;
-                    const int zi = (gy - zy0) * zw + (gx - zx0);
-                    const unsigned bgb = (unsigned)(S.bg[(int64_t)gy * c.W + gx] >> 32);
-                    const unsigned v = min(zb[zi], bgb);
-                    zd[zi] = v == 0xffffffffu ? (miss_mode ? -1.f : c.far_z) : __uint_as_float(v);
-                    x += dr;
-                    y += dq;
-                    if (x >= cw) { x -= cw; ++y; }
+                // kCompBatch pixels per thread at a time: their background loads are issued
+                // together, so their latencies overlap
+                for (int i = tid; i < n_c; i += kCompBatch * nt) {
+                    int zi[kCompBatch];
+                    unsigned bgb[kCompBatch];
+#pragma unroll
+                    for (int u = 0; u < kCompBatch; ++u) {
+                        zi[u] = -1;
+                        bgb[u] = 0u;
+                        if (i + u * nt < n_c) {
+                            const int gx = cx0 + x, gy = cy0 + y;
+                            zi[u] = (gy - zy0) * zw + (gx - zx0);
+                            const int64_t gi = (int64_t)gy * c.W + gx;
+                            bgb[u] = S.bgz ? S.bgz[gi] : (unsigned)(S.bg[gi] >> 32);
+                        }
+                        x += dr;
+                        y += dq;
+                        if (x >= cw) { x -= cw; ++y; }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kCompBatch; ++u) {
+                        if (zi[u] >= 0) {
+                            const unsigned v = min(zb[zi[u]], bgb[u]);
+                            zd[zi[u]] = v == 0xffffffffu ? (miss_mode ? -1.f : c.far_z) : __uint_as_float(v);
+                        }
+                    }
                 }
                 if (STATS) cnt[5] += (unsigned long long)((n_c - tid + nt - 1) / nt);
             }
@@ -572,6 +609,7 @@ __global__ void __launch_bounds__(NT, MINB)
     __shared__ float4 s_stage[NT * kStageStride];  // per lane: a rectangle's corners, plane, pixel box
     const int tid = threadIdx.x;
     for (int i = tid; i < L.n_lut; i += blockDim.x) s_lut[i] = L.lut[i];
+    lattice_coords(S.mesh, lat);
     unsigned long long cnt[kNumStats] = {0, 0, 0, 0, 0, 0, 0, 0};
     __shared__ long long s_next;
     // With a counter, CTAs take their next hypothesis from it as they finish one (so they all
@@ -639,6 +677,7 @@ __global__ void __launch_bounds__(NT, MINB)
                 for (int k = tid; k < (int)(sizeof(BatchItem) / sizeof(float4)); k += blockDim.x) dst[k] = src[k];
                 cur = it;
                 __syncthreads();
+                lattice_coords(s_item.S.mesh, lat);  // ordered before use by render_tiles' first barrier
             }
             const int64_t ib = item_begin[it], ie = min(item_begin[it + 1], e);
             for (; g < ie; ++g) {

@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(NT, MINB)
     const int64_t npx = (int64_t)c.W * c.H;
     const int G = N.nr * N.np;
     __shared__ long long s_next;
+    lattice_coords(S.mesh, lat);  // ordered before use by the loop's first barrier
     int64_t h = blockIdx.x;  // then from the counter S.work, as in the single-setting kernel
     while (h < n_hyp) {
         __syncthreads();
