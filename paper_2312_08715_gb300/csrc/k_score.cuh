@@ -108,7 +108,6 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
         ry[D - 1] = ((float)(y + W) + 0.5f - c.cy) * c.inv_fy;
         const int64_t gi = (int64_t)y * c.W + x;
         const float2 qe = S.qe[gi];  // observed depth (0: no point) and the background's term
-        if (qe.x == 0.f) continue;
         // the observed point, formed from its depth as the observation kernel forms it
         const float4 q = make_float4(__fmul_rn(qe.x, rxc), __fmul_rn(qe.x, ry[W]), qe.x, 1.f);
         int n = 0;
@@ -139,6 +138,9 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
             }
         }
         const float l = L.kind == 0 ? lut[n] : __logf(fmaf(L.bg, Ssum, L.a));
+        // a pixel without a point is skipped only now: a branch around the window loop costs
+        // more than the loop (the lanes' pixels diverge)
+        if (qe.x == 0.f) continue;
         acc += l - qe.y;
         if (n_px) {
             ++*n_px;
@@ -274,13 +276,15 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                 const int cls = lane, a = cls >> 1;
                 const float *R = P, *t = P + 9;
                 const float oa = -fmaf(R[a], t[0], fmaf(R[3 + a], t[1], R[6 + a] * t[2]));
-                const float *cd = m.coords + lat_off(a);
+                // the plane coordinates from the lattice table's .w (shared memory, set once
+                // per mesh and rewritten unchanged by each lattice pass, after a barrier)
+                const float4 *cd = lat + lat_off(a);
                 const int n = m.nc[a];
                 int lo = 0, hi = n;  // first plane with coordinate >= o
-                while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] < oa) lo = mid + 1; else hi = mid; }
+                while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid].w < oa) lo = mid + 1; else hi = mid; }
                 const int below = lo;
                 hi = n;  // first plane with coordinate > o
-                while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid] <= oa) lo = mid + 1; else hi = mid; }
+                while (lo < hi) { const int mid = (lo + hi) >> 1; if (cd[mid].w <= oa) lo = mid + 1; else hi = mid; }
                 const int not_above = lo;
                 const int *off = m.class_off + cls * m.np1;
                 // +axis faces face the camera when their plane is below o; -axis when above
@@ -338,7 +342,8 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
             if (tid == 0) { sh.fbb[0] = INT32_MAX; sh.fbb[1] = -1; sh.fbb[2] = INT32_MAX; sh.fbb[3] = -1; }
             __syncthreads();
             if (need) {
-                int fx0 = INT32_MAX, fx1 = -1, fy0 = INT32_MAX, fy1 = -1;  // this lane's fragments
+                // box of this lane's fragments (triangles) or candidate boxes (rectangles)
+                int fx0 = INT32_MAX, fx1 = -1, fy0 = INT32_MAX, fy1 = -1;
                 auto store = [&](int x, int y, float z) {
                     if (STATS) ++cnt[4];
                     atomicMin(&zb[(y - zy0) * zw + (x - zx0)], __float_as_uint(z));
@@ -348,6 +353,28 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                     // Each warp takes 32 rectangles at a time: every lane projects one and
                     // stages its screen corners, plane and pixel box; then the warp shares out
                     // the pixel-centre candidates of all 32 among its lanes.
+                    // Candidate block (x, y) of a rectangle with edges E0-E3, plane Pl and pixel
+                    // box ending at (xe, ye):
+                    auto raster_block = [&](const float4 &E0, const float4 &E1, const float4 &E2, const float4 &E3,
+                                            const float4 &Pl, int x, int y, int xe, int ye) {
+#pragma unroll
+                        for (int e = 0; e < kCandY; ++e) {
+                            const float py = (float)(y + e) + 0.5f;
+#pragma unroll
+                            for (int d = 0; d < kCandX; ++d) {
+                                const float px = (float)(x + d) + 0.5f;
+                                // every test evaluated and one predicated store: branches on the
+                                // tests cost more than the tests (the lanes' pixels diverge)
+                                const bool in = (x + d <= xe) & (kCandY == 1 || y + e <= ye) & staged_inside(E0, px, py) &
+                                                staged_inside(E1, px, py) & staged_inside(E2, px, py) & staged_inside(E3, px, py);
+                                const float z = __fdividef(1.0f, fmaf(Pl.x, px, fmaf(Pl.y, py, Pl.z)));
+                                if (in & (z <= c.far_z)) {
+                                    if (STATS) ++cnt[4];
+                                    atomicMin(&zb[(y + e - zy0) * zw + (x + d - zx0)], __float_as_uint(z));
+                                }
+                            }
+                        }
+                    };
                     const int total = sh.rng[12];
                     float4 *stg = s_stage + (wid * 32) * kStageStride;
                     for (int base = wid * 32; base < total; base += nt) {
@@ -391,6 +418,9 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                                     // candidates are blocks of kCandX x kCandY pixels
                                     const int bw2 = (x1 - x0 + kCandX) / kCandX;
                                     cand = bw2 * ((y1 - y0 + kCandY) / kCandY);
+                                    // the fragment box as the union of the candidate boxes (a pixel in
+                                    // it without a fragment in its window scores 0 exactly)
+                                    fx0 = min(fx0, x0); fx1 = max(fx1, x1); fy0 = min(fy0, y0); fy1 = max(fy1, y1);
                                     if (STATS) cnt[3] += (unsigned long long)((x1 - x0 + 1) * (y1 - y0 + 1));
                                     const float inv = __fdividef(1.0f, area);
                                     const float du1 = C1.x - C0.x, dv1 = C1.y - C0.y, du2 = C2.x - C0.x, dv2 = C2.y - C0.y;
@@ -398,17 +428,22 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                                     const float al = fmaf(dz1, dv2, -(dz2 * dv1)) * inv;
                                     const float be = fmaf(dz2, du1, -(dz1 * du2)) * inv;
                                     const float sgn = area > 0.f ? 1.f : -1.f;
-                                    stg[stage_slot(lane, 0)] = stage_edge(C0.x, C0.y, C1.x, C1.y, sgn);
-                                    stg[stage_slot(lane, 1)] = stage_edge(C1.x, C1.y, C2.x, C2.y, sgn);
-                                    stg[stage_slot(lane, 2)] = stage_edge(C2.x, C2.y, C3.x, C3.y, sgn);
-                                    stg[stage_slot(lane, 3)] = stage_edge(C3.x, C3.y, C0.x, C0.y, sgn);
+                                    const float4 E0 = stage_edge(C0.x, C0.y, C1.x, C1.y, sgn);
+                                    const float4 E1 = stage_edge(C1.x, C1.y, C2.x, C2.y, sgn);
+                                    const float4 E2 = stage_edge(C2.x, C2.y, C3.x, C3.y, sgn);
+                                    const float4 E3 = stage_edge(C3.x, C3.y, C0.x, C0.y, sgn);
                                     // 1/z = al px + be py + K over the quad's plane
                                     const float K = fmaf(-al, C0.x, fmaf(-be, C0.y, C0.z));
                                     // the candidate's row is floor((k + 1/2) / candidates per row), exact
                                     // in float with an approximate reciprocal for the region's sizes (the
                                     // quotient is at least 1/(2 bw2) from an integer; the error is below
                                     // (k + 1/2) 2^-21 / bw2)
-                                    stg[stage_slot(lane, 4)] = make_float4(al, be, K, __fdividef(1.0f, (float)bw2));
+                                    const float4 Pl = make_float4(al, be, K, __fdividef(1.0f, (float)bw2));
+                                    stg[stage_slot(lane, 0)] = E0;
+                                    stg[stage_slot(lane, 1)] = E1;
+                                    stg[stage_slot(lane, 2)] = E2;
+                                    stg[stage_slot(lane, 3)] = E3;
+                                    stg[stage_slot(lane, 4)] = Pl;
                                     stg[stage_slot(lane, 5)] = make_float4(__int_as_float(x0), __int_as_float(y0), __int_as_float(bw2),
                                                          __int_as_float((x1 - x0) | ((y1 - y0) << 16)));
                                 }
@@ -446,23 +481,7 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                                 const int bx = __float_as_int(Bx.x), by = __float_as_int(Bx.y);
                                 const int xe = bx + (ends & 0xffff), ye = by + (ends >> 16);  // box extent < 2^16
                                 const int row = (int)(((float)kk + 0.5f) * Pl.w);
-                                const int x = bx + kCandX * (kk - row * bw2);
-                                const int y = by + kCandY * row;
-#pragma unroll
-                                for (int e = 0; e < kCandY; ++e) {
-                                    const float py = (float)(y + e) + 0.5f;
-#pragma unroll
-                                    for (int d = 0; d < kCandX; ++d) {
-                                        const float px = (float)(x + d) + 0.5f;
-                                        // rows of single-row candidates never pass the box (row < rows)
-                                        if (x + d <= xe && (kCandY == 1 || y + e <= ye) && staged_inside(E0, px, py) &&
-                                            staged_inside(E1, px, py) && staged_inside(E2, px, py) &&
-                                            staged_inside(E3, px, py)) {
-                                            const float z = __fdividef(1.0f, fmaf(Pl.x, px, fmaf(Pl.y, py, Pl.z)));
-                                            if (z <= c.far_z) store(x + d, y + e, z);
-                                        }
-                                    }
-                                }
+                                raster_block(E0, E1, E2, E3, Pl, bx + kCandX * (kk - row * bw2), by + kCandY * row, xe, ye);
                             }
                         }
                         __syncwarp();
