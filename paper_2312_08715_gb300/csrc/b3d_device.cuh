@@ -223,6 +223,18 @@ __device__ __forceinline__ float pixel_ell(const Lik &L, const float *lut, const
 //   gs = d l / d s     = b (2 pi s^2)^(-3/2) sum_j exp(..) (d_ij^2 / s^2 - 3) / (s p_i)
 //   gp = d l / d p_out = (1 / V - S_i / K) / p_i
 //   bp = b / p_i (the weight of pixel i in d LL / d z_j).
+// The per-pixel results of pixel_ell_grads from its window sums E and D (also used by the
+// gradient kernel's unrolled window loop, so both give the same bits).
+__device__ __forceinline__ void grads_from_sums(const Lik &L, float E, float D, float &l, float &gs, float &gp,
+                                                float &bp) {
+    const float p = fmaf(L.bg, E, L.a);
+    l = __logf(p);
+    const float ip = 1.f / p;
+    gs = L.bg * D / L.s * ip;
+    gp = fmaf(-L.gnorm * E, L.inv_K, L.inv_V) * ip;
+    bp = L.b * ip;
+}
+
 template <class Fetch>
 __device__ __forceinline__ void pixel_ell_grads(const Lik &L, const Cam &c, float4 q, int xi, int yi, Fetch fetch,
                                                 float &l, float &gs, float &gp, float &bp) {
@@ -244,12 +256,7 @@ __device__ __forceinline__ void pixel_ell_grads(const Lik &L, const Cam &c, floa
             D = fmaf(e, fmaf(d2, L.inv_s2, -3.f), D);
         }
     }
-    const float p = fmaf(L.bg, E, L.a);
-    l = __logf(p);
-    const float ip = 1.f / p;
-    gs = L.bg * D / L.s * ip;
-    gp = fmaf(-L.gnorm * E, L.inv_K, L.inv_V) * ip;
-    bp = L.b * ip;
+    grads_from_sums(L, E, D, l, gs, gp, bp);
 }
 
 }  // namespace b3d

@@ -1,7 +1,9 @@
 // k_grad.cu - forward + backward of the smooth (Gaussian-window) likelihood.
 //
-// One CTA iteration per hypothesis recomputes the forward (render into a shared-memory
-// z-buffer, composite with the fixed objects) and then, with visibility held fixed:
+// One CTA iteration per hypothesis recomputes the forward with the score kernel's tile
+// renderer in its tagged mode (64-bit (depth, tag) keys: the rectangle's face class, or the
+// triangle's id, of the nearest surface at each pixel; composite with the fixed objects) and
+// then, with visibility held fixed, per tile:
 //   pass A, observed pixels i near the object: S_i, dS_i/ds, p_i = a + b S_i, giving the
 //           deltas of l_i, dl_i/ds, dl_i/dp_out against the background tables and
 //           b / p_i (kept in shared memory);
@@ -9,10 +11,10 @@
 //           = sum_{i : j in win(i)} (b / p_i) N_ij (qt_i - q_j).r_j / s^2,
 //           times dz_j/dxi = [n / (n.r_j), (q_j x n) / (n.r_j)] (left perturbation of the
 //           pose in the camera frame; the point slides along its pixel ray on the plane of
-//           its triangle, normal n), accumulated over j.
-// The forward uses the same triangle sets as the renderer (surface set with back faces
-// skipped when the whole object lies beyond the near plane, every triangle otherwise).
-// Nothing per pixel is stored in global memory.
+//           its face, normal n), accumulated over j.
+// The renderer uses the score kernel's primitive sets (rectangles of a voxel mesh, with the
+// face classes turned away from the camera skipped; triangles otherwise), so the forward is
+// the score kernel's. Nothing per pixel is stored in global memory.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -21,43 +23,46 @@
 
 #include "b3d_device.cuh"
 #include "b3d_internal.h"
+#include "k_score.cuh"
 
 namespace b3d {
 
-constexpr int kGradSmem = kRegionPx * ((int)sizeof(unsigned long long) + 3 * (int)sizeof(float));
-constexpr int kGradThreads = 512;  // threads per hypothesis: a launch of a few hundred hypotheses is one wave
+constexpr int kGradThreads = 256;  // threads per hypothesis: a launch of a few hundred hypotheses is one wave
 constexpr int kGradMinBlocks = 2;
+// dynamic shared memory: 64-bit keys (after the composite: pass A's weights and observed
+// depths), depths and tags of a kRegionPx tile, then the lattice planes
+constexpr int kGradSmemFixed = kRegionPx * ((int)sizeof(unsigned long long) + 2 * (int)sizeof(float));
 
-template <class PS, int NT>
+template <class PS, int NT, int WT>
 __global__ void __launch_bounds__(NT, kGradMinBlocks)
     k_grad(SceneView S, Lik L, PS P, int64_t n_hyp, float *out_ll, float *out_dpose, float *out_ds, float *out_dp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned long long *zb = reinterpret_cast<unsigned long long *>(smem_raw);
-    float *zd = reinterpret_cast<float *>(zb + kRegionPx);  // rendered depth per Z pixel
-    int *tj = reinterpret_cast<int *>(zd + kRegionPx);      // original face of the object, or -1
-    float *ip = reinterpret_cast<float *>(tj + kRegionPx);  // (b / p_i) (2 pi s^2)^(-3/2) / s^2
-    __shared__ float s_pose[12];
+    unsigned *zb = reinterpret_cast<unsigned *>(smem_raw);               // [kRegionPx] 64-bit keys
+    // the keys' memory once the composite has read them: per pixel of I,
+    // ((b / p_i) (2 pi s^2)^(-3/2) / s^2, observed depth)
+    float2 *ipq = reinterpret_cast<float2 *>(smem_raw);
+    float *zd = reinterpret_cast<float *>(smem_raw + kRegionPx * 8);     // depth per zone pixel
+    int *tg = reinterpret_cast<int *>(zd + kRegionPx);                   // face class / triangle id, or -1
+    float4 *lat = reinterpret_cast<float4 *>(tg + kRegionPx);            // lattice planes
+    __shared__ ScoreShared<NT> sh;
+    __shared__ float4 s_stage[NT * kStageStride];
     __shared__ float s_cof[9];  // cofactor matrix of the linear part: maps object normals to camera normals
-    __shared__ int s_bb[5];
-    __shared__ int s_front;
     __shared__ float s_red[9][NT / 32];
 
     const Cam &c = S.cam;
     const MeshView &m = S.mesh;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int w = L.w;
+    const int w = WT > 0 ? WT : L.w;
     const float wscale = L.gnorm * L.inv_s2;
+    lattice_coords(m, lat);  // ordered before use by the loop's first barrier
 
     for (int64_t h = blockIdx.x; h < n_hyp; h += gridDim.x) {
         __syncthreads();
         if (tid == 0) {
-            pose12(P, h, s_pose);
-            bool front = false;
-            s_bb[4] = object_bbox(m, s_pose, c, s_bb, &front) ? 1 : 0;
-            s_front = front ? 1 : 0;
+            pose12(P, h, sh.pose);
             // columns of the cofactor matrix: m1 x m2, m2 x m0, m0 x m1 (m_k the columns of
             // the linear part), so that (M a) x (M b) = cof(M) (a x b)
-            const float *R = s_pose;
+            const float *R = sh.pose;
             const float m0[3] = {R[0], R[3], R[6]}, m1[3] = {R[1], R[4], R[7]}, m2[3] = {R[2], R[5], R[8]};
             const float *cols[3][2] = {{m1, m2}, {m2, m0}, {m0, m1}};
             for (int k = 0; k < 3; ++k) {
@@ -67,113 +72,125 @@ __global__ void __launch_bounds__(NT, kGradMinBlocks)
                 s_cof[6 + k] = u[0] * v[1] - u[1] * v[0];
             }
         }
-        __syncthreads();
-        const float *pose = s_pose;
-        const bool has_bb = s_bb[4] != 0, front = s_front != 0;
-        const int bx0 = s_bb[0], bx1 = s_bb[1], by0 = s_bb[2], by1 = s_bb[3];
-        const int4 *tris = front ? m.tris_surf : m.tris_full;
-        const int n_t = front ? m.n_surf : m.n_full;
-        const int cull = front ? m.closed : 0;
         float acc_l = 0.f, acc_s = 0.f, acc_p = 0.f, g6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (has_bb) {
-            const int sx0 = max(bx0 - w, 0), sx1 = min(bx1 + w, c.W - 1);
-            const int sy0 = max(by0 - w, 0), sy1 = min(by1 + w, c.H - 1);
-            const int sw = sx1 - sx0 + 1;
-            const int tw = min(sw, 48);
-            const int th = max(1, kRegionPx / (tw + 4 * w) - 4 * w);
-            for (int ty0 = sy0; ty0 <= sy1; ty0 += th) {
-                for (int tx0 = sx0; tx0 <= sx1; tx0 += tw) {
-                    const int tx1 = min(tx0 + tw - 1, sx1), ty1 = min(ty0 + th - 1, sy1);
-                    // Z: depths needed by pass A over I = T + w, i.e. T + 2w
-                    const int zx0 = max(tx0 - 2 * w, 0), zx1 = min(tx1 + 2 * w, c.W - 1);
-                    const int zy0 = max(ty0 - 2 * w, 0), zy1 = min(ty1 + 2 * w, c.H - 1);
-                    const int zw = zx1 - zx0 + 1, zh = zy1 - zy0 + 1;
-                    const int ix0 = max(tx0 - w, 0), ix1 = min(tx1 + w, c.W - 1);
-                    const int iy0 = max(ty0 - w, 0), iy1 = min(ty1 + w, c.H - 1);
-                    const int iw = ix1 - ix0 + 1, ih = iy1 - iy0 + 1;
-                    const int rx0 = max(zx0, bx0), rx1 = min(zx1, bx1), ry0 = max(zy0, by0), ry1 = min(zy1, by1);
-                    const bool need = rx0 <= rx1 && ry0 <= ry1;
-                    if (need) {
-                        for (int i = tid; i < zw * zh; i += NT) zb[i] = kEmptyKey;
-                        __syncthreads();
-                        for (int t = tid; t < n_t; t += NT) {
-                            const int4 tr = tris[t];
-                            float4 A, B, C;
-                            tri_screen(m, tr, pose, c, A, B, C);
-                            const unsigned gid = (unsigned)(S.tri_base + tr.w);
-                            raster_tri(A, B, C, cull, rx0, rx1, ry0, ry1, c.far_z, [&](int x, int y, float z) {
-                                atomicMin(&zb[(y - zy0) * zw + (x - zx0)], pack_key(z, gid));
-                            });
-                        }
-                        __syncthreads();
-                    }
-                    for (int i = tid; i < zw * zh; i += NT) {
-                        const int gy = zy0 + i / zw, gx = zx0 + (i - (i / zw) * zw);
-                        const unsigned long long kb = S.bg[(int64_t)gy * c.W + gx];
-                        unsigned long long key = kb;
-                        int t = -1;
-                        if (need && zb[i] < kb) {
-                            key = zb[i];
-                            t = (int)(unsigned)(key & 0xffffffffu) - S.tri_base;
-                        }
-                        zd[i] = key_depth(key, L.miss_mode, c.far_z);
-                        tj[i] = t;
-                    }
-                    __syncthreads();
-                    auto fetch = [&](int xj, int yj) { return zd[(yj - zy0) * zw + (xj - zx0)]; };
-                    // pass A over I (one window loop gives l_i and its derivatives); deltas
-                    // accumulate over the tile T only
-                    for (int k = tid; k < iw * ih; k += NT) {
-                        const int y = iy0 + k / iw, x = ix0 + (k - (k / iw) * iw);
+        // zone = tile + 2w: pass A over I = T + w reads the depths of T + 2w
+        render_tiles<false, NT, true>(
+            S, 2 * w, L.miss_mode, sh, s_stage, zb, lat, nullptr,
+            [&](const float *zdt, int zx0, int zy0, int zw, int, int, int, int, int tx0, int tx1, int ty0, int ty1) {
+                const bool quad = (sh.flags & 2) != 0;
+                // I: pixels whose window reaches a fragment, and that pass B of this tile reads
+                const int ix0 = max(max(sh.fbb[0], tx0) - w, 0), ix1 = min(min(sh.fbb[1], tx1) + w, c.W - 1);
+                const int iy0 = max(max(sh.fbb[2], ty0) - w, 0), iy1 = min(min(sh.fbb[3], ty1) + w, c.H - 1);
+                const int iw = ix1 - ix0 + 1, n_i = iw * (iy1 - iy0 + 1);
+                // pass A: one pixel per thread and step; the window's terms in pixel_ell_grads' order
+                {
+                    const int dq = NT / iw, dr = NT - dq * iw;
+                    int yy = tid / iw, xx = tid - yy * iw;
+                    for (int k = tid; k < n_i; k += NT) {
+                        const int x = ix0 + xx, y = iy0 + yy;
                         const int64_t gi = (int64_t)y * c.W + x;
                         const float4 q = S.obs[gi];
                         float bp = 0.f;
                         if (q.w != 0.f) {
                             float l, gs, gp;
-                            pixel_ell_grads(L, c, q, x, y, fetch, l, gs, gp, bp);
+                            if (WT > 0) {
+                                float E = 0.f, D = 0.f;
+#pragma unroll
+                                for (int dy = -WT; dy <= WT; ++dy) {
+                                    const int yj = y + dy;
+                                    const bool rowok = yj >= 0 && yj < c.H;
+                                    const float ry = ((float)yj + 0.5f - c.cy) * c.inv_fy;
+#pragma unroll
+                                    for (int dx = -WT; dx <= WT; ++dx) {
+                                        const int xj = x + dx;
+                                        const bool ok = rowok && xj >= 0 && xj < c.W;
+                                        const float z = ok ? zdt[(yj - zy0) * zw + (xj - zx0)] : -1.f;
+                                        const float rx = ((float)xj + 0.5f - c.cx) * c.inv_fx;
+                                        const float ex = fmaf(-z, rx, q.x), ey = fmaf(-z, ry, q.y), ez = q.z - z;
+                                        const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                                        const float e = __expf(-d2 * L.inv2s2);
+                                        if (z >= 0.f) {  // predicated: a missing point adds nothing
+                                            E += e;
+                                            D = fmaf(e, fmaf(d2, L.inv_s2, -3.f), D);
+                                        }
+                                    }
+                                }
+                                grads_from_sums(L, E, D, l, gs, gp, bp);
+                            } else {  // runtime half window: pixel_ell_grads' own loop
+                                pixel_ell_grads(L, c, q, x, y, [&](int xj, int yj) { return zdt[(yj - zy0) * zw + (xj - zx0)]; },
+                                                l, gs, gp, bp);
+                            }
                             if (x >= tx0 && x <= tx1 && y >= ty0 && y <= ty1) {
                                 acc_l += l - S.ell_bg[gi];
                                 acc_s += gs - S.gs_bg[gi];
                                 acc_p += gp - S.gp_bg[gi];
                             }
                         }
-                        ip[k] = bp * wscale;
+                        ipq[k] = make_float2(bp * wscale, q.z);
+                        xx += dr;
+                        yy += dq;
+                        if (xx >= iw) { xx -= iw; ++yy; }
                     }
-                    __syncthreads();
-                    // pass B over the object's rendered pixels in T
-                    const int tww = tx1 - tx0 + 1;
-                    for (int k = tid; k < tww * (ty1 - ty0 + 1); k += NT) {
-                        const int y = ty0 + k / tww, x = tx0 + (k - (k / tww) * tww);
+                }
+                __syncthreads();
+                // pass B over the object's rendered pixels in T (within the fragment box)
+                {
+                    const int jx0 = max(sh.fbb[0], tx0), jx1 = min(sh.fbb[1], tx1);
+                    const int jy0 = max(sh.fbb[2], ty0), jy1 = min(sh.fbb[3], ty1);
+                    const int jw = jx1 - jx0 + 1, n_j = jx1 >= jx0 && jy1 >= jy0 ? jw * (jy1 - jy0 + 1) : 0;
+                    const int dq = NT / max(jw, 1), dr = NT - dq * max(jw, 1);
+                    int yy = tid / max(jw, 1), xx = tid - yy * max(jw, 1);
+                    for (int k = tid; k < n_j; k += NT) {
+                        const int x = jx0 + xx, y = jy0 + yy;
+                        xx += dr;
+                        yy += dq;
+                        if (xx >= jw) { xx -= jw; ++yy; }
                         const int zi = (y - zy0) * zw + (x - zx0);
-                        const int t = tj[zi];
+                        const int t = tg[zi];
                         if (t < 0) continue;
-                        const float z = zd[zi];
+                        const float z = zdt[zi];
                         const float rx = ((float)x + 0.5f - c.cx) * c.inv_fx, ry = ((float)y + 0.5f - c.cy) * c.inv_fy;
                         const float qx = z * rx, qy = z * ry, qz = z;
                         float g = 0.f;
-                        for (int dy = -w; dy <= w; ++dy) {
-                            const int yi = y + dy;
-                            if (yi < 0 || yi >= c.H) continue;
-                            for (int dx = -w; dx <= w; ++dx) {
-                                const int xi = x + dx;
-                                if (xi < 0 || xi >= c.W) continue;
-                                const float bpi = ip[(yi - iy0) * iw + (xi - ix0)];
-                                if (bpi == 0.f) continue;
-                                const float4 qi = S.obs[(int64_t)yi * c.W + xi];
-                                const float ex = qi.x - qx, ey = qi.y - qy, ez = qi.z - qz;
-                                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                                g = fmaf(bpi * __expf(-d2 * L.inv2s2), fmaf(ex, rx, fmaf(ey, ry, ez)), g);
-                            }
+                        auto term = [&](int xi, int yi) {
+                            // pixels outside I carry no weight (b / p_i = 0 adds nothing)
+                            const bool ok = xi >= ix0 && xi <= ix1 && yi >= iy0 && yi <= iy1;
+                            const float2 bq = ok ? ipq[(yi - iy0) * iw + (xi - ix0)] : make_float2(0.f, 0.f);
+                            const float bpi = bq.x;
+                            // the observed point from its depth, as the observation kernel forms it
+                            const float rxi = ((float)xi + 0.5f - c.cx) * c.inv_fx, ryi = ((float)yi + 0.5f - c.cy) * c.inv_fy;
+                            const float ex = __fmul_rn(bq.y, rxi) - qx, ey = __fmul_rn(bq.y, ryi) - qy, ez = bq.y - qz;
+                            const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                            g = fmaf(bpi * __expf(-d2 * L.inv2s2), fmaf(ex, rx, fmaf(ey, ry, ez)), g);
+                        };
+                        if (WT > 0) {
+#pragma unroll
+                            for (int dy = -WT; dy <= WT; ++dy)
+#pragma unroll
+                                for (int dx = -WT; dx <= WT; ++dx) term(x + dx, y + dy);
+                        } else {
+                            for (int dy = -w; dy <= w; ++dy)
+                                for (int dx = -w; dx <= w; ++dx) term(x + dx, y + dy);
                         }
-                        // the face's normal: object-frame cross product mapped by the cofactor matrix
-                        const int4 f = m.faces[t];
-                        const float4 A = m.verts[f.x], B = m.verts[f.y], C = m.verts[f.z];
-                        const float e1x = B.x - A.x, e1y = B.y - A.y, e1z = B.z - A.z;
-                        const float e2x = C.x - A.x, e2y = C.y - A.y, e2z = C.z - A.z;
-                        const float ox = e1y * e2z - e1z * e2y, oy = e1z * e2x - e1x * e2z, oz = e1x * e2y - e1y * e2x;
-                        const float nx = fmaf(s_cof[0], ox, fmaf(s_cof[1], oy, s_cof[2] * oz));
-                        const float ny = fmaf(s_cof[3], ox, fmaf(s_cof[4], oy, s_cof[5] * oz));
-                        const float nz = fmaf(s_cof[6], ox, fmaf(s_cof[7], oy, s_cof[8] * oz));
+                        // the face's normal in the camera frame: a rectangle's face class gives its
+                        // axis (the cofactor matrix's column; the sign cancels in n / (n.r)); a
+                        // triangle's object-frame cross product is mapped by the cofactor matrix
+                        float nx, ny, nz;
+                        if (quad) {
+                            const int a = t >> 1;
+                            nx = s_cof[a];
+                            ny = s_cof[3 + a];
+                            nz = s_cof[6 + a];
+                        } else {
+                            const int4 f = m.faces[t - S.tri_base];
+                            const float4 A = m.verts[f.x], B = m.verts[f.y], C = m.verts[f.z];
+                            const float e1x = B.x - A.x, e1y = B.y - A.y, e1z = B.z - A.z;
+                            const float e2x = C.x - A.x, e2y = C.y - A.y, e2z = C.z - A.z;
+                            const float ox = e1y * e2z - e1z * e2y, oy = e1z * e2x - e1x * e2z, oz = e1x * e2y - e1y * e2x;
+                            nx = fmaf(s_cof[0], ox, fmaf(s_cof[1], oy, s_cof[2] * oz));
+                            ny = fmaf(s_cof[3], ox, fmaf(s_cof[4], oy, s_cof[5] * oz));
+                            nz = fmaf(s_cof[6], ox, fmaf(s_cof[7], oy, s_cof[8] * oz));
+                        }
                         const float nr = fmaf(nx, rx, fmaf(ny, ry, nz));
                         if (nr == 0.f) continue;
                         const float gn = g / nr;
@@ -184,10 +201,9 @@ __global__ void __launch_bounds__(NT, kGradMinBlocks)
                         g6[4] += gn * (qz * nx - qx * nz);
                         g6[5] += gn * (qx * ny - qy * nx);
                     }
-                    __syncthreads();
                 }
-            }
-        }
+            },
+            zd, tg);
         // one reduction of the nine sums: warp trees, then warps in order
         const float vals[9] = {acc_l, acc_s, acc_p, g6[0], g6[1], g6[2], g6[3], g6[4], g6[5]};
 #pragma unroll
@@ -310,21 +326,19 @@ void launch_adam_se3(int64_t n, const float *dpose, float *m, float *v, float *p
 int launch_grad_list(const SceneView &sv, const Lik &L, PoseList P, int64_t n, float *ll, float *dpose, float *dsigma,
                      float *dpout, int grid, cudaStream_t s) {
     if (n <= 0) return 0;
-    auto kern = k_grad<PoseList, kGradThreads>;
-    const int per_sm = kernel_ctas_per_sm(kern, kGradThreads, kGradSmem);
+    auto kern = L.w == 2 ? k_grad<PoseList, kGradThreads, 2>
+                         : (L.w == 1 ? k_grad<PoseList, kGradThreads, 1> : k_grad<PoseList, kGradThreads, 0>);
+    const int n_lat = sv.mesh.nc[0] + sv.mesh.nc[1] + sv.mesh.nc[2];
+    const int smem = kGradSmemFixed + n_lat * (int)sizeof(float4);
+    const int per_sm = kernel_ctas_per_sm(kern, kGradThreads, smem);
     int g = grid;
-    if (g <= 0) {
-        static int sms = 0;
-        if (!sms) {
-            int dev = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            sms = std::max(1, sms);
-        }
-        g = per_sm * sms;
-    }
+    if (g <= 0) g = per_sm * score_sm_count();
     g = (int)std::min<int64_t>(g, n);
-    kern<<<g, kGradThreads, kGradSmem, s>>>(sv, L, P, n, ll, dpose, dsigma, dpout);
+    // tiles as wide as the region allows (the score kernel's tuned width is not this kernel's)
+    SceneView v = sv;
+    v.tile_w = kRegionPx;
+    v.work = nullptr;
+    kern<<<g, kGradThreads, smem, s>>>(v, L, P, n, ll, dpose, dsigma, dpout);
     return g;
 }
 

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(NT, MINB) k_render_fused(SceneView S, PoseList
             for (int64_t k = tid; k < npx; k += NT) __stcs(dst + k, __ldg(S.bgd + k));
         }
         render_tiles<false, NT>(S, 0, 0, sh, s_stage, zb, lat, nullptr,
-                                [&](const float *zd, int zx0, int zy0, int zw, int qx0, int qx1, int qy0, int qy1) {
+                                [&](const float *zd, int zx0, int zy0, int zw, int qx0, int qx1, int qy0, int qy1, int, int, int, int) {
                                     const int tww = qx1 - qx0 + 1, n = tww * (qy1 - qy0 + 1);
                                     const int dq = NT / tww, dr = NT - dq * tww;
                                     int y = tid / tww, x = tid - y * tww;

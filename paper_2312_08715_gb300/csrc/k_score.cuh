@@ -215,15 +215,20 @@ struct ScoreShared {
 // Renders the hypothesis whose pose thread 0 has put in sh.pose, tile by tile, into the
 // shared-memory z-buffer and composites it with the fixed objects' depths (misses: far, or
 // -1 with miss_mode 1); for each tile with fragments calls
-// visit(zd, zx0, zy0, zw, qx0, qx1, qy0, qy1): the tile's depths zd (origin zx0, zy0, row
-// pitch zw) and the pixels to score, those whose half-window w reaches a fragment. Returns
-// false when the object is off screen (nothing visited). All threads of the CTA must call it.
-template <bool STATS, int NT, class Visit>
+// visit(zd, zx0, zy0, zw, qx0, qx1, qy0, qy1, tx0, tx1, ty0, ty1): the tile's depths zd
+// (origin zx0, zy0, row pitch zw; the tile [tx0, tx1] x [ty0, ty1] plus w around it) and the
+// pixels to score, those whose half-window w reaches a fragment. Returns false when the
+// object is off screen (nothing visited). All threads of the CTA must call it.
+// TAGS: the z-buffer holds 64-bit keys (depth bits, tag) in zb's memory (kRegionPx of them),
+// the tag being the rectangle's face class or the triangle's global id; the composite writes
+// the depths to zdt and the winning tags to tagt (-1 where the fixed objects are nearer).
+template <bool STATS, int NT, bool TAGS = false, class Visit>
 __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss_mode, ScoreShared<NT> &sh,
                                              float4 *s_stage, unsigned *zb, float4 *lat, unsigned long long *cnt,
-                                             Visit &&visit) {
-    constexpr int REG = score_region<NT>();
-    float *zd = reinterpret_cast<float *>(zb);  // same memory, as depths
+                                             Visit &&visit, float *zdt = nullptr, int *tagt = nullptr) {
+    constexpr int REG = TAGS ? kRegionPx : score_region<NT>();
+    float *zd = TAGS ? zdt : reinterpret_cast<float *>(zb);  // 32-bit keys: the same memory, as depths
+    unsigned long long *zb64 = reinterpret_cast<unsigned long long *>(zb);
     const Cam &c = S.cam;
     const MeshView &m = S.mesh;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
@@ -338,7 +343,10 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
             const int zw = zx1 - zx0 + 1, zh = zy1 - zy0 + 1, nz = zw * zh;
             const int rx0 = max(zx0, bx0), rx1 = min(zx1, bx1), ry0 = max(zy0, by0), ry1 = min(zy1, by1);
             const bool need = rx0 <= rx1 && ry0 <= ry1;
-            for (int i = tid; i < nz; i += nt) zb[i] = 0xffffffffu;
+            for (int i = tid; i < nz; i += nt) {
+                if constexpr (TAGS) zb64[i] = kEmptyKey;
+                else zb[i] = 0xffffffffu;
+            }
             if (tid == 0) { sh.fbb[0] = INT32_MAX; sh.fbb[1] = -1; sh.fbb[2] = INT32_MAX; sh.fbb[3] = -1; }
             __syncthreads();
             if (need) {
@@ -356,7 +364,7 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                     // Candidate block (x, y) of a rectangle with edges E0-E3, plane Pl and pixel
                     // box ending at (xe, ye):
                     auto raster_block = [&](const float4 &E0, const float4 &E1, const float4 &E2, const float4 &E3,
-                                            const float4 &Pl, int x, int y, int xe, int ye) {
+                                            const float4 &Pl, int x, int y, int xe, int ye, bool valid, unsigned tag) {
 #pragma unroll
                         for (int e = 0; e < kCandY; ++e) {
                             const float py = (float)(y + e) + 0.5f;
@@ -365,12 +373,14 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                                 const float px = (float)(x + d) + 0.5f;
                                 // every test evaluated and one predicated store: branches on the
                                 // tests cost more than the tests (the lanes' pixels diverge)
-                                const bool in = (x + d <= xe) & (kCandY == 1 || y + e <= ye) & staged_inside(E0, px, py) &
+                                const bool in = valid & (x + d <= xe) & (kCandY == 1 || y + e <= ye) & staged_inside(E0, px, py) &
                                                 staged_inside(E1, px, py) & staged_inside(E2, px, py) & staged_inside(E3, px, py);
                                 const float z = __fdividef(1.0f, fmaf(Pl.x, px, fmaf(Pl.y, py, Pl.z)));
                                 if (in & (z <= c.far_z)) {
                                     if (STATS) ++cnt[4];
-                                    atomicMin(&zb[(y + e - zy0) * zw + (x + d - zx0)], __float_as_uint(z));
+                                    const int zi = (y + e - zy0) * zw + (x + d - zx0);
+                                    if constexpr (TAGS) atomicMin(&zb64[zi], ((unsigned long long)__float_as_uint(z) << 32) | tag);
+                                    else atomicMin(&zb[zi], __float_as_uint(z));
                                 }
                             }
                         }
@@ -444,8 +454,10 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                                     stg[stage_slot(lane, 2)] = E2;
                                     stg[stage_slot(lane, 3)] = E3;
                                     stg[stage_slot(lane, 4)] = Pl;
+                                    // box extents below 2^16 and 2^13; TAGS: the class in the top bits
+                                    const int ends = (x1 - x0) | ((y1 - y0) << 16) | (TAGS ? cls << 29 : 0);
                                     stg[stage_slot(lane, 5)] = make_float4(__int_as_float(x0), __int_as_float(y0), __int_as_float(bw2),
-                                                         __int_as_float((x1 - x0) | ((y1 - y0) << 16)));
+                                                         __int_as_float(ends));
                                 }
                             }
                         }
@@ -473,15 +485,16 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                             const int j = r0 + lane;
                             const int kk = j - __shfl_sync(0xffffffffu, excl, lo);
                             __syncwarp();
-                            if (j < n_cand) {
+                            {  // lanes past the last candidate run the tests with their stores masked
                                 const float4 Pl = stg[stage_slot(lo, 4)], Bx = stg[stage_slot(lo, 5)];
                                 const float4 E0 = stg[stage_slot(lo, 0)], E1 = stg[stage_slot(lo, 1)];
                                 const float4 E2 = stg[stage_slot(lo, 2)], E3 = stg[stage_slot(lo, 3)];
                                 const int bw2 = __float_as_int(Bx.z), ends = __float_as_int(Bx.w);
                                 const int bx = __float_as_int(Bx.x), by = __float_as_int(Bx.y);
-                                const int xe = bx + (ends & 0xffff), ye = by + (ends >> 16);  // box extent < 2^16
+                                const int xe = bx + (ends & 0xffff), ye = by + (TAGS ? (ends >> 16) & 0x1fff : ends >> 16);
                                 const int row = (int)(((float)kk + 0.5f) * Pl.w);
-                                raster_block(E0, E1, E2, E3, Pl, bx + kCandX * (kk - row * bw2), by + kCandY * row, xe, ye);
+                                raster_block(E0, E1, E2, E3, Pl, bx + kCandX * (kk - row * bw2), by + kCandY * row, xe, ye,
+                                             j < n_cand, (unsigned)ends >> 29);
                             }
                         }
                         __syncwarp();
@@ -494,7 +507,15 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                         float4 A, B, C;
                         tri_screen(m, tris[t], pose, c, A, B, C);
                         if (STATS) { cnt[1] += 3; ++cnt[2]; }
-                        raster_tri(A, B, C, cull, rx0, rx1, ry0, ry1, c.far_z, store, STATS ? &cnt[3] : nullptr);
+                        if constexpr (TAGS) {
+                            const unsigned long long gid = (unsigned)(S.tri_base + tris[t].w);
+                            raster_tri(A, B, C, cull, rx0, rx1, ry0, ry1, c.far_z, [&](int x, int y, float z) {
+                                atomicMin(&zb64[(y - zy0) * zw + (x - zx0)], ((unsigned long long)__float_as_uint(z) << 32) | gid);
+                                fx0 = min(fx0, x); fx1 = max(fx1, x); fy0 = min(fy0, y); fy1 = max(fy1, y);
+                            });
+                        } else {
+                            raster_tri(A, B, C, cull, rx0, rx1, ry0, ry1, c.far_z, store, STATS ? &cnt[3] : nullptr);
+                        }
                     }
                 }
                 // the tile's fragment box: pixels outside it +- w keep their background terms
@@ -527,6 +548,32 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
                 // together, so their latencies overlap
                 for (int i = tid; i < n_c; i += kCompBatch * nt) {
                     int zi[kCompBatch];
+                    if constexpr (TAGS) {
+                        unsigned long long bgk[kCompBatch];
+#pragma unroll
+                        for (int u = 0; u < kCompBatch; ++u) {
+                            zi[u] = -1;
+                            bgk[u] = 0ull;
+                            if (i + u * nt < n_c) {
+                                const int gx = cx0 + x, gy = cy0 + y;
+                                zi[u] = (gy - zy0) * zw + (gx - zx0);
+                                bgk[u] = S.bg[(int64_t)gy * c.W + gx];
+                            }
+                            x += dr;
+                            y += dq;
+                            if (x >= cw) { x -= cw; ++y; }
+                        }
+#pragma unroll
+                        for (int u = 0; u < kCompBatch; ++u) {
+                            if (zi[u] >= 0) {
+                                const unsigned long long key = zb64[zi[u]];
+                                const bool obj = key < bgk[u];
+                                zd[zi[u]] = key_depth(obj ? key : bgk[u], miss_mode, c.far_z);
+                                tagt[zi[u]] = obj ? (int)(unsigned)key : -1;
+                            }
+                        }
+                        continue;
+                    }
                     unsigned bgb[kCompBatch];
 #pragma unroll
                     for (int u = 0; u < kCompBatch; ++u) {
@@ -556,7 +603,7 @@ __device__ __forceinline__ bool render_tiles(const SceneView &S, int w, int miss
             // score the tile's pixels within the fragment box + w
             const int qx0 = max(sh.fbb[0] - w, tx0), qx1 = min(sh.fbb[1] + w, tx1);
             const int qy0 = max(sh.fbb[2] - w, ty0), qy1 = min(sh.fbb[3] + w, ty1);
-            visit(static_cast<const float *>(zd), zx0, zy0, zw, qx0, qx1, qy0, qy1);
+            visit(static_cast<const float *>(zd), zx0, zy0, zw, qx0, qx1, qy0, qy1, tx0, tx1, ty0, ty1);
             __syncthreads();
         }
     }
@@ -575,7 +622,7 @@ __device__ __forceinline__ float score_body(const SceneView &S, const Lik &L, co
     float acc = 0.f;
     const bool drawn = render_tiles<STATS, NT>(
         S, w, L.miss_mode, sh, s_stage, zb, lat, cnt,
-        [&](const float *zd, int zx0, int zy0, int zw, int qx0, int qx1, int qy0, int qy1) {
+        [&](const float *zd, int zx0, int zy0, int zw, int qx0, int qx1, int qy0, int qy1, int, int, int, int) {
             const int tww = qx1 - qx0 + 1, thh = qy1 - qy0 + 1;
             if (WT > 0) {
                 // thread -> (column, run of rows)

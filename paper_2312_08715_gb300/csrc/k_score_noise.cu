@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(NT, MINB)
         const int nt = blockDim.x;
         render_tiles<false, NT>(
             S, N.w, N.miss_mode, sh, s_stage, zb, lat, nullptr,
-            [&](const float *zd, int zx0, int zy0, int zw, int qx0, int qx1, int qy0, int qy1) {
+            [&](const float *zd, int zx0, int zy0, int zw, int qx0, int qx1, int qy0, int qy1, int, int, int, int) {
                 const int tww = qx1 - qx0 + 1, thh = qy1 - qy0 + 1;
                 const int n_tile = tww * thh;
                 const int dq = nt / tww, dr = nt - dq * tww;
