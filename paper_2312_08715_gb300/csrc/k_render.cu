@@ -368,7 +368,17 @@ int kernel_ctas_per_sm_impl(const void *kernel, int threads, int smem) {
     std::lock_guard<std::mutex> lock(mu);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // Dynamic plus static shared memory above 48 KB needs the opt-in. The opt-in is a
+    // per-kernel maximum that only ever rises here: every size a launch uses is queried
+    // first, so it stays covered whatever other sizes are queried later.
+    static std::map<std::pair<const void *, int>, int> opt_in;
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, kernel);
+    int &cur = opt_in[std::make_pair(kernel, dev)];
+    if (smem + (int)fa.sharedSizeBytes > 48 * 1024 && smem > cur) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cur = smem;
+    }
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
     per_sm = per_sm > 0 ? per_sm : 1;
