@@ -96,6 +96,7 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
     }
     float acc = 0.f;
     const bool ball_skips_empty = L.r2 < 0.25f;
+    const float r2b = __int_as_float(__float_as_int(L.r2) + 1) * 0x1p100f;  // (next float above r2) 2^100
     const float rxc = rx[W];  // the column's own ray
     for (int y = ya; y <= yb; ++y) {
 #pragma unroll
@@ -115,15 +116,21 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
         if (L.kind == 0 && ball_skips_empty) {
             // an empty slot holds z = -1, a point at least 1 m from q (q.z > 0): it can only
             // fail the inlier test, so the count needs no separate z >= 0 test
+            // the count on the FMA pipe rather than the (half-rate) ALU pipe: (r2+ - d2) 2^100,
+            // saturated to [0, 1], is 1 exactly when d2 <= r2 (r2+ the next float above r2, and
+            // any nonzero difference times 2^100 is above 1) and 0 otherwise; the same n as the
+            // comparison pixel_ell makes
+            float nf = 0.f;
 #pragma unroll
             for (int r = 0; r < D; ++r) {
 #pragma unroll
                 for (int d = 0; d < D; ++d) {
                     const float z = win[r][d];
                     const float ex = fmaf(-z, rx[d], q.x), ey = fmaf(-z, ry[r], q.y), ez = q.z - z;
-                    n += fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= L.r2 ? 1 : 0;
+                    nf += __saturatef(fmaf(-fmaf(ex, ex, fmaf(ey, ey, ez * ez)), 0x1p100f, r2b));
                 }
             }
+            n = (int)nf;
         } else {
 #pragma unroll
             for (int r = 0; r < D; ++r) {
