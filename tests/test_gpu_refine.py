@@ -42,8 +42,8 @@ def test_autograd_function_returns_the_kernel_gradient(scene):
     assert torch.equal(xi.grad, w[:, None] * dpose)
     assert float(sigma.grad) == pytest.approx(float((w * ds).sum()), rel=1e-6)
     assert float(pout.grad) == pytest.approx(float((w * dp).sum()), rel=1e-6)
-    # the forward agrees with the plain smooth score: another kernel (triangles and a 64-bit
-    # z-buffer rather than merged rectangles), so rendered depths may differ in the last bits
+    # the forward agrees with the plain smooth score: the same rectangles and per-pixel terms,
+    # summed over the pixels in another order (64-bit tagged keys, another thread mapping)
     np.testing.assert_allclose(_np(ll_k), _np(ctx.score(wl.slot, T0, LIK)), rtol=1e-5)
     ctx.close()
 
