@@ -159,9 +159,11 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
 }
 
 // z-buffer pixels per tile for a CTA of NT threads (measured: 3072 for 128 threads leaves room
-// for one more resident CTA per SM than 4096 while still holding a tabletop footprint in one tile)
+// for one more resident CTA per SM than 4096 while still holding a tabletop footprint in one
+// tile; 8192 for 256 threads, 3 CTAs per SM, holds most of a 320x240 footprint in one or two
+// tiles: the serving images' hypotheses re-stage their rectangles for fewer tiles)
 template <int NT>
-constexpr int score_region() { return NT <= 64 ? 2048 : (NT == 128 ? 3072 : kRegionPx); }
+constexpr int score_region() { return NT <= 64 ? 2048 : (NT == 128 ? 3072 : 8192); }
 // pixels per thread whose background depths the composite loads together
 #ifndef B3D_COMPOSITE_BATCH
 #define B3D_COMPOSITE_BATCH 4
