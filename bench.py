@@ -627,7 +627,21 @@ def run_batched(args):
         stream.wait_stream(side)
         return g
 
-    # hypotheses per work-queue grab, picked by timing the captured graph
+    # launch shape for the mix, picked by timing the captured graph: the single-scene
+    # autotuner's pick on the largest scene against 128- and 256-thread CTAs with 64- and
+    # 128-pixel tiles (the largest scene's pick need not suit the smaller ones)
+    shapes = [tuning] + [dict(tuning, tile_w=tw, cta_threads=nt, ctas_per_sm=0, high_occupancy=0)
+                         for nt in (128, 256) for tw in (64, 128)]
+    best = None
+    for t in shapes:
+        tuning = t
+        g = capture(4)
+        time_graph(g, 2)
+        ms = min(time_graph(g, 3))
+        if best is None or ms < best[1]:
+            best = (t, ms)
+    tuning = best[0]
+    # hypotheses per work-queue grab, picked the same way
     best = None
     for chunk in (1, 2, 4, 8, 16, 32):
         g = capture(chunk)
@@ -673,6 +687,7 @@ def run_batched(args):
                                "80x60-320x240, 1,000-50,000 hypotheses per stage), 2 stages, 32 particles, one "
                                "CUDA graph of batched launches per step",
                    "hyps_per_step": hyps_step, "score_kernel_tuning": tuning, "batch_chunk": chunk,
+                   "tuning_candidates": shapes,
                    "l2": "flushed between timed steps (256 MiB write)"},
         "loop_baseline": {"value": hyps_step / (loop_mean / 1e3), "ms_per_step": loop_mean,
                           "note": "b3d_enumerate_c2f looped over the 64 scenes (eager launches)"},
