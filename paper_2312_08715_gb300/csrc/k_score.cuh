@@ -67,6 +67,31 @@ __device__ __forceinline__ float4 sum3(const float4 &X, const float4 &Y, const f
     return make_float4((X.x + Y.x) + Z.x, (X.y + Y.y) + Z.y, (X.z + Y.z) + Z.z, 0.f);
 }
 
+// Packed pairs of FP32 values for the f32x2 arithmetic of sm_100 and later: each lane of a
+// pair is rounded as the scalar operation rounds it, so the results are the scalar ones.
+typedef unsigned long long f32x2_t;
+__device__ __forceinline__ f32x2_t pk2(float a, float b) {
+    f32x2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2_t v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f32x2_t fma2(f32x2_t a, f32x2_t b, f32x2_t c) {
+    f32x2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2_t sub2(f32x2_t a, f32x2_t b) {
+    f32x2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2_t mul2(f32x2_t a, f32x2_t b) {
+    f32x2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Sum of l_i - l_i(bg) over pixel column x, rows [ya, yb], with the (2W+1)^2 window of
 // rendered depths slid down the column in registers. Window slots outside the image (and
 // pixels without a point) hold -1 and contribute nothing; the terms are formed in the same
@@ -98,6 +123,8 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
     const bool ball_skips_empty = L.r2 < 0.25f;
     const float r2b = __int_as_float(__float_as_int(L.r2) + 1) * 0x1p100f;  // (next float above r2) 2^100
     const float rxc = rx[W];  // the column's own ray
+    // negated column rays packed for the f32x2 window terms (half window 1)
+    const f32x2_t nrx01 = pk2(-rx[0], -rx[1]), nrx22 = pk2(-rx[D - 1], -rx[D - 1]);
     for (int y = ya; y <= yb; ++y) {
 #pragma unroll
         for (int r = 0; r + 1 < D; ++r) {
@@ -121,13 +148,33 @@ __device__ __forceinline__ float score_column(const SceneView &S, const Lik &L, 
             // any nonzero difference times 2^100 is above 1) and 0 otherwise; the same n as the
             // comparison pixel_ell makes
             float nf = 0.f;
+            if constexpr (W == 1) {
+                // eight of the nine window elements as four packed pairs (columns 0-1 of each
+                // row, and column 2 of rows 0-1), the last one scalar: per element the same
+                // arithmetic as the scalar loop below; the 0/1 terms add up exactly in any order
+                const f32x2_t qx2 = pk2(q.x, q.x), qy2 = pk2(q.y, q.y), qz2 = pk2(q.z, q.z);
+                auto pair = [&](f32x2_t z2, f32x2_t nrx, f32x2_t nry) {
+                    const f32x2_t ex = fma2(z2, nrx, qx2), ey = fma2(z2, nry, qy2), ez = sub2(qz2, z2);
+                    float d2a, d2b;
+                    upk2(fma2(ex, ex, fma2(ey, ey, mul2(ez, ez))), d2a, d2b);
+                    nf += __saturatef(fmaf(-d2a, 0x1p100f, r2b));
+                    nf += __saturatef(fmaf(-d2b, 0x1p100f, r2b));
+                };
 #pragma unroll
-            for (int r = 0; r < D; ++r) {
+                for (int r = 0; r < D; ++r) pair(pk2(win[r][0], win[r][1]), nrx01, pk2(-ry[r], -ry[r]));
+                pair(pk2(win[0][2], win[1][2]), nrx22, pk2(-ry[0], -ry[1]));
+                const float z = win[2][2];
+                const float exs = fmaf(-z, rx[2], q.x), eys = fmaf(-z, ry[2], q.y), ezs = q.z - z;
+                nf += __saturatef(fmaf(-fmaf(exs, exs, fmaf(eys, eys, ezs * ezs)), 0x1p100f, r2b));
+            } else {
 #pragma unroll
-                for (int d = 0; d < D; ++d) {
-                    const float z = win[r][d];
-                    const float ex = fmaf(-z, rx[d], q.x), ey = fmaf(-z, ry[r], q.y), ez = q.z - z;
-                    nf += __saturatef(fmaf(-fmaf(ex, ex, fmaf(ey, ey, ez * ez)), 0x1p100f, r2b));
+                for (int r = 0; r < D; ++r) {
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        const float z = win[r][d];
+                        const float ex = fmaf(-z, rx[d], q.x), ey = fmaf(-z, ry[r], q.y), ez = q.z - z;
+                        nf += __saturatef(fmaf(-fmaf(ex, ex, fmaf(ey, ey, ez * ez)), 0x1p100f, r2b));
+                    }
                 }
             }
             n = (int)nf;
