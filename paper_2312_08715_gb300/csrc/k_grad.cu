@@ -95,24 +95,49 @@ __global__ void __launch_bounds__(NT, kGradMinBlocks)
                             float l, gs, gp;
                             if (WT > 0) {
                                 float E = 0.f, D = 0.f;
+                                // the window's columns in packed f32x2 pairs (each lane rounded as
+                                // the scalar loop rounds it), the exponentials and the running sums
+                                // per element in the scalar loop's order
+                                const f32x2_t qx2 = pk2(q.x, q.x), qy2 = pk2(q.y, q.y), qz2 = pk2(q.z, q.z);
+                                const f32x2_t nis2 = pk2(-L.inv2s2, -L.inv2s2), is2 = pk2(L.inv_s2, L.inv_s2);
+                                const f32x2_t m3 = pk2(-3.f, -3.f);
+                                float nrx[2 * WT + 1];
+#pragma unroll
+                                for (int dx = -WT; dx <= WT; ++dx) nrx[dx + WT] = -(((float)(x + dx) + 0.5f - c.cx) * c.inv_fx);
+                                auto acc1 = [&](float z, float e, float t) {
+                                    if (z >= 0.f) {  // predicated: a missing point adds nothing
+                                        E += e;
+                                        D = fmaf(e, t, D);
+                                    }
+                                };
 #pragma unroll
                                 for (int dy = -WT; dy <= WT; ++dy) {
                                     const int yj = y + dy;
                                     const bool rowok = yj >= 0 && yj < c.H;
-                                    const float ry = ((float)yj + 0.5f - c.cy) * c.inv_fy;
+                                    const float nry = -(((float)yj + 0.5f - c.cy) * c.inv_fy);
+                                    float zr[2 * WT + 1];
 #pragma unroll
                                     for (int dx = -WT; dx <= WT; ++dx) {
                                         const int xj = x + dx;
-                                        const bool ok = rowok && xj >= 0 && xj < c.W;
-                                        const float z = ok ? zdt[(yj - zy0) * zw + (xj - zx0)] : -1.f;
-                                        const float rx = ((float)xj + 0.5f - c.cx) * c.inv_fx;
-                                        const float ex = fmaf(-z, rx, q.x), ey = fmaf(-z, ry, q.y), ez = q.z - z;
+                                        zr[dx + WT] = (rowok && xj >= 0 && xj < c.W) ? zdt[(yj - zy0) * zw + (xj - zx0)] : -1.f;
+                                    }
+#pragma unroll
+                                    for (int k = 0; k + 1 < 2 * WT + 1; k += 2) {
+                                        const f32x2_t z2 = pk2(zr[k], zr[k + 1]);
+                                        const f32x2_t ex = fma2(z2, pk2(nrx[k], nrx[k + 1]), qx2), ey = fma2(z2, pk2(nry, nry), qy2);
+                                        const f32x2_t ez = sub2(qz2, z2);
+                                        const f32x2_t d2 = fma2(ex, ex, fma2(ey, ey, mul2(ez, ez)));
+                                        float ga, gb, ta, tb;
+                                        upk2(mul2(d2, nis2), ga, gb);
+                                        upk2(fma2(d2, is2, m3), ta, tb);
+                                        acc1(zr[k], __expf(ga), ta);
+                                        acc1(zr[k + 1], __expf(gb), tb);
+                                    }
+                                    {
+                                        const float z = zr[2 * WT];
+                                        const float ex = fmaf(z, nrx[2 * WT], q.x), ey = fmaf(z, nry, q.y), ez = q.z - z;
                                         const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                                        const float e = __expf(-d2 * L.inv2s2);
-                                        if (z >= 0.f) {  // predicated: a missing point adds nothing
-                                            E += e;
-                                            D = fmaf(e, fmaf(d2, L.inv_s2, -3.f), D);
-                                        }
+                                        acc1(z, __expf(-d2 * L.inv2s2), fmaf(d2, L.inv_s2, -3.f));
                                     }
                                 }
                                 grads_from_sums(L, E, D, l, gs, gp, bp);
