@@ -627,29 +627,13 @@ def run_batched(args):
         stream.wait_stream(side)
         return g
 
-    # launch shape for the mix, picked by timing the captured graph: the single-scene
-    # autotuner's pick on the largest scene against 128- and 256-thread CTAs with 64- and
-    # 128-pixel tiles (the largest scene's pick need not suit the smaller ones)
-    shapes = [tuning] + [dict(tuning, tile_w=tw, cta_threads=nt, ctas_per_sm=0, high_occupancy=0)
-                         for nt in (128, 256) for tw in (64, 128)]
-    best = None
-    for t in shapes:
-        tuning = t
-        g = capture(4)
-        time_graph(g, 2)
-        ms = min(time_graph(g, 3))
-        if best is None or ms < best[1]:
-            best = (t, ms)
-    tuning = best[0]
-    # hypotheses per work-queue grab, picked the same way
-    best = None
-    for chunk in (1, 2, 4, 8, 16, 32):
-        g = capture(chunk)
-        time_graph(g, 2)
-        ms = min(time_graph(g, 3))
-        if best is None or ms < best[1]:
-            best = (chunk, ms, g)
-    chunk, _, graph = best
+    # launch shape and batch chunk for the mix, picked by the library's batched autotuner
+    # (timed on these items; the largest scene's single-stage pick need not suit the others)
+    largest_pick = tuning
+    b3d.b3d_set_tuning(owner.h, **tuning)
+    tuning = b3d.b3d_autotune_multi(owner.h, items, lik, owner.stream)
+    chunk = tuning["batch_chunk"]
+    graph = capture(chunk)
     graph = capture(chunk)
     time_graph(graph, args.warmup)
     with ClockSampler() as clk:
@@ -687,7 +671,7 @@ def run_batched(args):
                                "80x60-320x240, 1,000-50,000 hypotheses per stage), 2 stages, 32 particles, one "
                                "CUDA graph of batched launches per step",
                    "hyps_per_step": hyps_step, "score_kernel_tuning": tuning, "batch_chunk": chunk,
-                   "tuning_candidates": shapes,
+                   "largest_scene_single_stage_pick": largest_pick,
                    "l2": "flushed between timed steps (256 MiB write)"},
         "loop_baseline": {"value": hyps_step / (loop_mean / 1e3), "ms_per_step": loop_mean,
                           "note": "b3d_enumerate_c2f looped over the 64 scenes (eager launches)"},

@@ -399,6 +399,17 @@ b3d_status b3d_set_tuning(b3d_ctx *ctx, const b3d_tuning *tuning);
 b3d_status b3d_autotune(b3d_ctx *ctx, int32_t obj_slot, const float *centre_pose, const float *grid_frame,
                         const b3d_stage *stage, const b3d_lik_params *lik, b3d_tuning *best, b3d_stream stream);
 
+/* Autotuner for the batched form: times b3d_enumerate_multi on these items (owner, items and
+ * lik as there) for the owner's current launch shape and for 128- or 256-thread CTAs with 64-
+ * or 128-pixel tiles, then the fastest shape with 1 to 32 hypotheses per work-queue grab;
+ * keeps the fastest tuning in the owner and returns it in *best (may be NULL). The items'
+ * outputs hold the last timed run's results. Synchronises the stream (not for use while
+ * capturing a graph). No counterpart in the paper: the launch shape is a property of this
+ * implementation, and a mix of scenes of uneven size may want another shape than any one
+ * scene (b3d_autotune times a single stage of one object). */
+b3d_status b3d_autotune_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_item *items, const b3d_lik_params *lik,
+                              b3d_tuning *best, b3d_stream stream);
+
 /* Instrumentation (off by default; used by the benchmark).
  * flags bit 0 (B3D_INSTR_TIMING): bracket every kernel launch of the library with CUDA
  *   events recorded on the launching stream; b3d_kernel_time() reports the device time.

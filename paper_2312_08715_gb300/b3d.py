@@ -133,6 +133,8 @@ _SIGNATURES = {
                                       _P, _P, _P, _P]),
     "b3d_score_multi": (C.c_int32, [_P, C.c_int32, C.POINTER(b3d_score_item), C.POINTER(b3d_lik_params), _P]),
     "b3d_enumerate_multi": (C.c_int32, [_P, C.c_int32, C.POINTER(b3d_c2f_item), C.POINTER(b3d_lik_params), _P]),
+    "b3d_autotune_multi": (C.c_int32, [_P, C.c_int32, C.POINTER(b3d_c2f_item), C.POINTER(b3d_lik_params),
+                                       C.POINTER(b3d_tuning), _P]),
     "b3d_score_grad": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_lik_params), _P, _P, _P, _P, _P]),
     "b3d_refine_smooth": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.POINTER(b3d_lik_params), C.c_int32, C.c_float,
                                       C.c_float, C.c_float, C.c_float, _P, _P]),
@@ -439,6 +441,15 @@ def b3d_enumerate_multi(owner, items, lik: b3d_lik_params, stream=None):
     """items: sequence of b3d_c2f_item (see c2f_item)."""
     arr = (b3d_c2f_item * len(items))(*items)
     return _check(owner, load().b3d_enumerate_multi(owner, len(items), arr, C.byref(lik), _stream(stream)))
+
+
+def b3d_autotune_multi(owner, items, lik: b3d_lik_params, stream=None) -> dict:
+    """items: sequence of b3d_c2f_item; returns the tuning kept in the owner."""
+    arr = (b3d_c2f_item * len(items))(*items)
+    t = b3d_tuning()
+    _check(owner, load().b3d_autotune_multi(owner, len(items), arr, C.byref(lik), C.byref(t), _stream(stream)))
+    return dict(tile_w=t.tile_w, cta_threads=t.cta_threads, ctas_per_sm=t.ctas_per_sm, high_occupancy=t.high_occupancy,
+                batch_chunk=t.batch_chunk)
 
 
 def b3d_set_instrumentation(ctx, flags):

@@ -1912,6 +1912,67 @@ b3d_status b3d_autotune(b3d_ctx *ctx, int32_t obj_slot, const float *centre_pose
     return check_launch(ctx, "autotune");
 }
 
+b3d_status b3d_autotune_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_item *items, const b3d_lik_params *lik,
+                              b3d_tuning *best, b3d_stream stream) {
+    if (!owner) return B3D_EINVAL;
+    owner->err.clear();
+    if (n_items < 1 || !items || !lik) return fail(owner, B3D_EINVAL, "need n_items >= 1, items and lik");
+    DeviceGuard g(owner->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const b3d_tuning saved{owner->tile_w, owner->cta_threads, owner->ctas_per_sm, owner->high_occupancy, owner->batch_chunk};
+    auto apply = [&](const b3d_tuning &t) {
+        owner->tile_w = t.tile_w; owner->cta_threads = t.cta_threads; owner->ctas_per_sm = t.ctas_per_sm;
+        owner->high_occupancy = t.high_occupancy; owner->batch_chunk = t.batch_chunk;
+    };
+    // one untimed pass with the current tuning: sizes the scratch and builds every item's tables
+    b3d_status st = b3d_enumerate_multi(owner, n_items, items, lik, stream);
+    if (st != B3D_OK) return st;
+    cudaEvent_t e0 = take_event(owner), e1 = take_event(owner);
+    auto timed = [&](const b3d_tuning &t, float *ms) -> b3d_status {
+        apply(t);
+        b3d_status r = b3d_enumerate_multi(owner, n_items, items, lik, stream);  // warm
+        if (r == B3D_OK) {
+            cudaEventRecord(e0, s);
+            r = b3d_enumerate_multi(owner, n_items, items, lik, stream);
+            cudaEventRecord(e1, s);
+        }
+        if (r != B3D_OK) return r;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) return cuda_fail(owner, e, "autotune_multi");
+        cudaEventElapsedTime(ms, e0, e1);
+        return B3D_OK;
+    };
+    // launch shapes: the current one and 128- or 256-thread CTAs with 64- or 128-pixel tiles
+    std::vector<b3d_tuning> shapes{saved};
+    for (int nt : {128, 256})
+        for (int tw : {64, 128}) shapes.push_back(b3d_tuning{tw, nt, 0, 0, saved.batch_chunk});
+    b3d_tuning win = saved;
+    float win_ms = INFINITY;
+    for (const b3d_tuning &t : shapes) {
+        float ms = 0.f;
+        if ((st = timed(t, &ms)) != B3D_OK) break;
+        if (ms < win_ms) { win_ms = ms; win = t; }
+    }
+    // then hypotheses per work-queue grab
+    for (int chunk : {1, 2, 4, 8, 16, 32}) {
+        if (st != B3D_OK) break;
+        b3d_tuning t = win;
+        t.batch_chunk = chunk;
+        float ms = 0.f;
+        if ((st = timed(t, &ms)) != B3D_OK) break;
+        if (ms < win_ms) { win_ms = ms; win = t; }
+    }
+    owner->event_pool.push_back(e0);
+    owner->event_pool.push_back(e1);
+    if (st != B3D_OK) {
+        apply(saved);
+        return st;
+    }
+    apply(win);
+    if (best) *best = win;
+    return B3D_OK;
+}
+
 b3d_status b3d_set_instrumentation(b3d_ctx *ctx, int32_t flags) {
     if (!ctx) return B3D_EINVAL;
     ctx->err.clear();

@@ -175,3 +175,44 @@ def test_largest_batched_scene_matches_oracle(orc):
         assert ref["ll"][best] - ref["ll"][sel == top][0] <= 2 * ll_tolerance(ref)[best]
     for c in (cb, cs, owner):
         c.close()
+
+
+def test_autotune_multi_keeps_a_candidate_shape_and_bit_identical_results(orc):
+    """The batched autotuner times b3d_enumerate_multi on the items themselves and keeps one
+    of its candidate shapes (the owner's, or 128/256-thread CTAs with 64/128-pixel tiles) and
+    batch chunks (1-32); the batched results under the kept tuning equal the single-scene
+    calls under the same tuning, bit for bit."""
+    from paper_2312_08715_gb300 import b3d
+    scenes = _scenes(orc)
+    M = [16, 8, 32, 5]
+    ctxs, items, outs, centres = [], [], [], []
+    for k, ((wl, obs, slot), m) in enumerate(zip(scenes, M)):
+        ctx = gpu_context(wl.scene, obs)
+        centre = wl.hidden.astype(np.float64).copy()
+        centre[:3, 3] += [0.01, -0.008, 0.012]
+        o = (torch.empty((m, 4, 4), device="cuda"), torch.empty(m, device="cuda"), torch.empty(m, device="cuda"))
+        outs.append(o)
+        items.append(b3d.c2f_item(ctx.h, slot, centre.astype(np.float32), b3d.schedule(_stages(), m, 200 + k, wl.grid_frame),
+                                  *o))
+        ctxs.append(ctx)
+        centres.append(centre.astype(np.float32))
+    owner = b3d.Context(0)
+    b3d.b3d_set_tuning(owner.h, 96, 64, 0, 0, 4)
+    lik = b3d.lik_params(**scenes[0][0].lik)
+    t = b3d.b3d_autotune_multi(owner.h, items, lik, owner.stream)
+    owner.sync()
+    shapes = [(96, 64)] + [(tw, nt) for nt in (128, 256) for tw in (64, 128)]
+    assert (t["tile_w"], t["cta_threads"]) in shapes, t
+    assert t["batch_chunk"] in (1, 2, 4, 8, 16, 32), t
+    assert b3d.b3d_get_tuning(owner.h) == t
+    b3d.b3d_enumerate_multi(owner.h, items, lik, owner.stream)
+    owner.sync()
+    for k, ((wl, obs, slot), m) in enumerate(zip(scenes, M)):
+        b3d.b3d_set_tuning(ctxs[k].h, **t)
+        single = [_np(x).copy() for x in ctxs[k].enumerate_c2f(slot, centres[k], _stages(), wl.lik, m, 200 + k,
+                                                               wl.grid_frame)]
+        ctxs[k].sync()
+        for got, want in zip(outs[k], single):
+            np.testing.assert_array_equal(_np(got), want)
+    for c in ctxs + [owner]:
+        c.close()

@@ -173,3 +173,26 @@ def test_se3_compose_matches_the_matrix_exponential(scene):
     np.testing.assert_allclose(got, want, rtol=0, atol=2e-6)
     np.testing.assert_array_equal(_np(same), got)
     ctx.close()
+
+
+def test_gradient_calls_alternating_meshes_of_different_lattice_sizes(scene):
+    """The gradient kernel's shared memory grows with the mesh's lattice planes: calls on the
+    object with the most planes, then the one with the fewest, then the first again all run
+    (the kernel's shared-memory limit is raised to every size launched, never lowered) and
+    repeat their results bit for bit."""
+    wl, obs = scene
+    ctx = gpu_context(wl.scene, obs)
+    slots = list(range(2, len(wl.scene.meshes)))
+    planes = {s: sum(len(np.unique(wl.scene.meshes[s].verts[:, a])) for a in range(3)) for s in slots}
+    big, small = max(slots, key=planes.get), min(slots, key=planes.get)
+    assert planes[big] > planes[small]
+    rng = np.random.default_rng(8)
+    T = {s: torch.as_tensor(jitter_poses(rng, wl.scene.poses[s], 64, trans=0.004, rot_deg=3), device="cuda")
+         for s in (big, small)}
+    first = [_np(t) for t in ctx.score_grad(big, T[big], LIK)]
+    ctx.score_grad(small, T[small], LIK)
+    again = [_np(t) for t in ctx.score_grad(big, T[big], LIK)]
+    ctx.sync()
+    for a, b in zip(first, again):
+        assert np.array_equal(a, b)
+    ctx.close()
