@@ -16,30 +16,36 @@ namespace b3d {
 // probabilities) of observed point q at pixel (xi, yi), the window's rendered depths given
 // by fetch (negative: no point). The window is visited in pixel_ell's order and each pair's
 // squared distance is formed by pixel_ell's expression; lut holds kNoiseLut entries per g.
-template <class Fetch>
-__device__ __forceinline__ void noise_pixel(const NoiseLik &N, const float *lut, const Cam &c, float4 q, int xi, int yi,
-                                            Fetch fetch, float *l) {
+// WT: the half window compiled in (1, 2; 0: runtime N.w). Every window element is
+// evaluated and its terms predicated (a branch on a missing point costs more than the
+// element: the lanes' pixels diverge); a predicated-off element adds nothing, so the sums
+// are those of the element-skipping loop.
+template <int WT, class Fetch>
+__device__ __forceinline__ void noise_pixel_w(const NoiseLik &N, const float *lut, const Cam &c, float4 q, int xi, int yi,
+                                              Fetch fetch, float *l) {
+    const int w = WT > 0 ? WT : N.w;
     int n[kMaxNoiseR];
     float S[kMaxNoiseR];
 #pragma unroll
     for (int i = 0; i < kMaxNoiseR; ++i) { n[i] = 0; S[i] = 0.f; }
-    for (int dy = -N.w; dy <= N.w; ++dy) {
+#pragma unroll
+    for (int dy = -w; dy <= w; ++dy) {
         const int yj = yi + dy;
-        if (yj < 0 || yj >= c.H) continue;
+        const bool rowok = yj >= 0 && yj < c.H;
         const float ry = ((float)yj + 0.5f - c.cy) * c.inv_fy;
-        for (int dx = -N.w; dx <= N.w; ++dx) {
+#pragma unroll
+        for (int dx = -w; dx <= w; ++dx) {
             const int xj = xi + dx;
-            if (xj < 0 || xj >= c.W) continue;
-            const float z = fetch(xj, yj);
-            if (z < 0.f) continue;
+            const float z = (rowok && xj >= 0 && xj < c.W) ? fetch(xj, yj) : -1.f;
+            const bool valid = z >= 0.f;
             const float rx = ((float)xj + 0.5f - c.cx) * c.inv_fx;
             const float ex = fmaf(-z, rx, q.x), ey = fmaf(-z, ry, q.y), ez = q.z - z;
             const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
 #pragma unroll
             for (int i = 0; i < kMaxNoiseR; ++i) {
                 if (i >= N.nr) break;
-                if (N.kind == 0) n[i] += d2 <= N.r2[i] ? 1 : 0;
-                else S[i] += __expf(-d2 * N.inv2s2[i]);
+                if (N.kind == 0) n[i] += (valid & (d2 <= N.r2[i])) ? 1 : 0;
+                else if (valid) S[i] += __expf(-d2 * N.inv2s2[i]);
             }
         }
     }
@@ -52,6 +58,18 @@ __device__ __forceinline__ void noise_pixel(const NoiseLik &N, const float *lut,
             if (i < N.nr && j < N.np)
                 l[g] = N.kind == 0 ? lut[g * kNoiseLut + n[i]] : __logf(fmaf(N.bg[g], S[i], N.a[j]));
         }
+}
+
+// l_g for every setting g = 4 i + j (internal layout; i < nr radii, j < np outlier
+// probabilities) of observed point q at pixel (xi, yi), the window's rendered depths given
+// by fetch (negative: no point). The window is visited in pixel_ell's order and each pair's
+// squared distance is formed by pixel_ell's expression; lut holds kNoiseLut entries per g.
+template <class Fetch>
+__device__ __forceinline__ void noise_pixel(const NoiseLik &N, const float *lut, const Cam &c, float4 q, int xi, int yi,
+                                            Fetch fetch, float *l) {
+    if (N.w == 1) noise_pixel_w<1>(N, lut, c, q, xi, yi, fetch, l);
+    else if (N.w == 2) noise_pixel_w<2>(N, lut, c, q, xi, yi, fetch, l);
+    else noise_pixel_w<0>(N, lut, c, q, xi, yi, fetch, l);
 }
 
 __device__ __forceinline__ void load_noise_lut(const NoiseLik &N, float *s_lut) {
