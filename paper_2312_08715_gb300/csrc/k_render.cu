@@ -284,6 +284,33 @@ __global__ void k_bg_raster_px(Cam c, MeshView m, const float *pose16, int tri_b
 // Also sums l_i (and the derivative terms) over the image in double precision, in a fixed
 // order: each block reduces its pixels into part[3 block ..], and the block that finishes
 // last (a ticket on *counter, which it resets) adds the block partials in block order.
+// pixel_ell with the half window W compiled in and each window element's terms predicated
+// instead of skipped (a skipped element adds nothing, so n and S, and the value, are
+// pixel_ell's bit for bit).
+template <int W, class Fetch>
+__device__ __forceinline__ float pixel_ell_w(const Lik &L, const float *lut, const Cam &c, float4 q, int xi, int yi,
+                                             Fetch fetch) {
+    int n = 0;
+    float S = 0.f;
+#pragma unroll
+    for (int dy = -W; dy <= W; ++dy) {
+        const int yj = yi + dy;
+        const bool rowok = yj >= 0 && yj < c.H;
+        const float ry = ((float)yj + 0.5f - c.cy) * c.inv_fy;
+#pragma unroll
+        for (int dx = -W; dx <= W; ++dx) {
+            const int xj = xi + dx;
+            const float z = (rowok && xj >= 0 && xj < c.W) ? fetch(xj, yj) : -1.f;
+            const float rx = ((float)xj + 0.5f - c.cx) * c.inv_fx;
+            const float ex = fmaf(-z, rx, q.x), ey = fmaf(-z, ry, q.y), ez = q.z - z;
+            const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            if (L.kind == 0) n += (z >= 0.f && d2 <= L.r2) ? 1 : 0;
+            else if (z >= 0.f) S += __expf(-d2 * L.inv2s2);
+        }
+    }
+    return L.kind == 0 ? lut[n] : __logf(fmaf(L.bg, S, L.a));
+}
+
 __global__ void __launch_bounds__(256) k_bg_tables(SceneView S, Lik L, float *ell_bg, float *gs_bg, float *gp_bg,
                                                    float2 *qe, unsigned *bgz, double *part, unsigned *counter,
                                                    double *out) {
@@ -297,11 +324,12 @@ __global__ void __launch_bounds__(256) k_bg_tables(SceneView S, Lik L, float *el
     double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float4 q = S.obs[i];
-        const int x = (int)(i % c.W), y = (int)(i / c.W);
+        const int y = (int)i / c.W, x = (int)i - y * c.W;  // an image has at most 2^26 pixels
         float l = 0.f, gs = 0.f, gp = 0.f;
         if (q.w != 0.f) {
             auto fetch = [&](int xj, int yj) { return key_depth(S.bg[(int64_t)yj * c.W + xj], L.miss_mode, c.far_z); };
-            l = pixel_ell(L, s_lut, c, q, x, y, fetch);
+            l = L.w == 1 ? pixel_ell_w<1>(L, s_lut, c, q, x, y, fetch)
+                         : (L.w == 2 ? pixel_ell_w<2>(L, s_lut, c, q, x, y, fetch) : pixel_ell(L, s_lut, c, q, x, y, fetch));
             if (gs_bg) {
                 float l1, bp;
                 pixel_ell_grads(L, c, q, x, y, fetch, l1, gs, gp, bp);
