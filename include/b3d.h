@@ -309,7 +309,8 @@ b3d_status b3d_enumerate_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_it
 /* Forward and backward of the smooth (kind 1) likelihood for n_hyp poses: loglik_dev [n],
  * dpose_dev [n, 6] = d loglik / d xi at xi = 0 for the left perturbation
  * T(xi) = Exp([v, w]^) T in the camera frame, ordered (v, w), with visibility held fixed
- * and each rendered point sliding along its pixel ray on its triangle's plane;
+ * and each rendered point sliding along its pixel ray on the plane of its face (the voxel
+ * rectangle, or the triangle of a mesh without rectangles, the forward renders);
  * dsigma_dev [n] and dpout_dev [n] = d loglik / d s and d loglik / d p_outlier. Any of the
  * gradient outputs may be NULL. The forward is recomputed; nothing per pixel is stored. */
 b3d_status b3d_score_grad(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const float *poses_dev,
