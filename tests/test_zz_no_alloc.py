@@ -2,9 +2,10 @@
 memory (under another framework's allocator lock or memory cap, or in an embedding that
 forbids the library from allocating): called through the C ABI several times in a row, it
 must give what the context-based b3d_lse_resample gives on the same scores, agree with the
-FP64 oracle's resampling, report an all -inf vector in its outputs, and leave the device's
-free memory unchanged. Collected last so that a stop at the first failure has already run
-every other test; it also passes alone in a fresh process."""
+FP64 oracle's resampling, report an all -inf vector in its outputs, leave the device's free
+memory unchanged, and replay from a captured CUDA graph. Collected last so that a stop at
+the first failure has already run every other test; it also passes alone in a fresh
+process."""
 import numpy as np
 import pytest
 
@@ -75,6 +76,38 @@ def test_noalloc_allocates_no_device_memory():
     for a in again:
         for x, y in zip(a, first):
             np.testing.assert_array_equal(x, y)
+
+
+def test_noalloc_replays_from_a_cuda_graph():
+    """The entry point's work is one memset of the shared counter and one kernel launch on
+    the caller's stream, so a call captured into a CUDA graph replays: each replay resets the
+    counter itself and reads whatever scores the input buffer holds at that moment."""
+    rng = np.random.default_rng(31)
+    m, seed, stage = 48, 17, 1
+    first_np, second_np = synth.random_ll(rng, 60000), synth.random_ll(rng, 60000)
+    ll = torch.as_tensor(first_np, device="cuda")
+    eager_first = _run_noalloc(ll, m, seed, stage)
+    eager_second = _run_noalloc(torch.as_tensor(second_np, device="cuda"), m, seed, stage)
+    out = (torch.empty(1, device="cuda"), torch.full((m,), -7, dtype=torch.int32, device="cuda"),
+           torch.empty(m, device="cuda"))
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):  # warm-up call on a side stream, as before any capture
+        b3d.b3d_lse_resample_noalloc(ll.numel(), ll, m, seed, stage, *out, side)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b3d.b3d_lse_resample_noalloc(ll.numel(), ll, m, seed, stage, *out, torch.cuda.current_stream())
+    for src, want in ((None, eager_first), (None, eager_first), (second_np, eager_second)):
+        if src is not None:
+            ll.copy_(torch.as_tensor(src, device="cuda"))
+        out[1].fill_(-7)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        for got, ref in zip((t.cpu().numpy() for t in out), want):
+            np.testing.assert_array_equal(got, ref)
 
 
 def test_noalloc_rejects_bad_sizes():
