@@ -35,9 +35,9 @@ struct Cached {
 };
 Cached g_scratch_addr[kMaxDevices];
 
-// The driver's identifier of the calling thread's current context: unique for the life of
+// The CUDA driver's identifier of the calling thread's current context: unique for the life of
 // the process, so a context created after a device reset never matches an old one. 0 when
-// there is no current context or the driver cannot say. Called with g_mu held.
+// there is no current context or the CUDA driver cannot say. Called with g_mu held.
 unsigned long long current_context_id() {
     using GetCurrent = int (*)(void **);                       // cuCtxGetCurrent(CUcontext *)
     using GetId = int (*)(void *, unsigned long long *);       // cuCtxGetId(CUcontext, unsigned long long *)
