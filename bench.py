@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b3d", choices=["b3d", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU work of the oracle baseline sample")
+    ap.add_argument("--ref-seconds", type=float, default=30.0,
+                    help="--impl reference: CPU work of the whole timed oracle run (warm-up included)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mat-hyps", type=int, default=0,
@@ -457,8 +459,8 @@ def run_reference(args):
     t0 = time.perf_counter()
     O.score(sub, FIRST_SLOT, probe, wl.lik, obs, flags=False, arrays=arrays)
     per = (time.perf_counter() - t0) / len(probe)
-    # about 30 s of CPU work for the whole run, at least 1.5 s per step
-    step_s = max(1.5, 30.0 / (args.warmup + args.steps))
+    # about --ref-seconds (30 s) of CPU work for the whole run, at least 1/20 of it per step
+    step_s = max(args.ref_seconds / 20.0, args.ref_seconds / (args.warmup + args.steps))
     n_step = int(max(2 * cores, min(len(poses), step_s / max(per, 1e-6))))
     times = []
     for s in range(args.warmup + args.steps):
