@@ -5,6 +5,7 @@ import ctypes as C
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -115,3 +116,20 @@ def test_oracle_and_product_share_no_code():
     assert "paper_2312_08715_gb300" not in otxt_py.replace("paper_2312_08715_gb300.synth", "")
     otxt = open(os.path.join(ROOT, "oracle", "b3d_oracle.c")).read()
     assert "b3d.h" not in otxt and "b3d_internal" not in otxt
+
+
+
+def test_binding_refuses_to_load_without_the_library(tmp_path):
+    """No CPU fallback: with the compiled library absent (and no build asked for), loading the
+    binding raises instead of handing out anything that computes on the host."""
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_2312_08715_gb300 import b3d\n"
+        "b3d._build.LIB = %r\n"
+        "try:\n"
+        "    b3d.load(build_if_missing=False)\n"
+        "except ImportError as e:\n"
+        "    print('refused' if 'not built' in str(e) else e)\n"
+    ) % (ROOT, str(tmp_path / "missing" / "libb3d.so"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "refused", r.stdout + r.stderr
