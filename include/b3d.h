@@ -179,8 +179,8 @@ b3d_status b3d_render_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const
 b3d_status b3d_score_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, const float *poses_dev,
                            const b3d_lik_params *lik, float *loglik_dev, b3d_stream stream);
 
-/* Score materialised depth images: depth_dev [n_hyp, H, W] (e.g. from b3d_render_batch)
- * against the scene's observation; triid_dev [n_hyp, H, W] is needed only for
+/* Score materialised depth images under the Eq. 1 likelihood: depth_dev [n_hyp, H, W] (e.g.
+ * from b3d_render_batch) against the scene's observation; triid_dev [n_hyp, H, W] is needed only for
  * miss_mode 1 (pixels with id -1 carry no point), else may be NULL. loglik_dev [n_hyp]
  * receives sum_i l_i. The images may hold any depths. A pixel whose window holds exactly
  * the depths of a reference image takes the reference's term, computed once per scene and
@@ -192,9 +192,9 @@ b3d_status b3d_score_depth_batch(b3d_ctx *ctx, int32_t obj_slot, int64_t n_hyp, 
                                  const int32_t *triid_dev, const b3d_lik_params *lik, float *loglik_dev,
                                  b3d_stream stream);
 
-/* Expand one coarse-to-fine stage around centre_pose (host [16]) with grid frame G (host
- * [9], row-major cam_from_grid): poses_dev [n^3 * n_rot, 16] in hypothesis order (see
- * b3d_stage). */
+/* Expand one coarse-to-fine stage (the partition of the pose region into cells, Sec. III-B)
+ * around centre_pose (host [16]) with grid frame G (host [9], row-major cam_from_grid):
+ * poses_dev [n^3 * n_rot, 16] in hypothesis order (see b3d_stage). */
 b3d_status b3d_expand_hypotheses(b3d_ctx *ctx, const float *centre_pose, const float *grid_frame,
                                  const b3d_stage *stage, float *poses_dev, b3d_stream stream);
 
@@ -306,7 +306,8 @@ typedef struct {
 b3d_status b3d_enumerate_multi(b3d_ctx *owner, int32_t n_items, const b3d_c2f_item *items, const b3d_lik_params *lik,
                                b3d_stream stream);
 
-/* Forward and backward of the smooth (kind 1) likelihood for n_hyp poses: loglik_dev [n],
+/* Forward and backward of the smooth (kind 1) likelihood, Eq. 1 with its Gaussian mixture
+ * components (sigma and p_outlier the noise parameters of Alg. 1), for n_hyp poses: loglik_dev [n],
  * dpose_dev [n, 6] = d loglik / d xi at xi = 0 for the left perturbation
  * T(xi) = Exp([v, w]^) T in the camera frame, ordered (v, w), with visibility held fixed
  * and each rendered point sliding along its pixel ray on the plane of its face (the voxel
